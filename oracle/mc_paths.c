@@ -1,0 +1,253 @@
+/*
+ * Plain FP64 Euler-Maruyama Feynman-Kac paths for one knot (a11).
+ * TEST INFRASTRUCTURE ONLY: part of the oracle; never linked into the library.
+ *
+ * The elliptic Feynman-Kac representation (Appendix, Eq. 53 and 56, and
+ * Eq. 25-30 of the paper) with sigma = I:
+ *     dX = b(X) dt + dW,   dY = c(X) Y dt,   dZ = f(X) Y dt,
+ *     X_0 = x_i, Y_0 = 1, Z_0 = 0,
+ * stopped at the first exit tau from the subdomain O_m n Omega (Eq. 26).
+ *
+ * Discretisation (plain Euler-Maruyama, step h, left-point weights):
+ *     X_{k+1} = X_k + b(X_k) h + sqrt(h) xi_k
+ *     Y_{k+1} = Y_k (1 + c(X_k) h)
+ *     Z_{k+1} = Z_k + f(X_k) Y_k h
+ * The path exits at the first step whose end point is outside the open disk
+ * or outside the open domain.  The exit point is where the segment
+ * X_k -> X_{k+1} first meets the circle or dOmega (smaller segment parameter;
+ * a tie goes to dOmega).  The weights are the ones after the exit step.
+ *
+ * Normals: Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo32, knot) and
+ * counter (step, path, 0, 0).  The four 32-bit words (a, b, c, d) give two
+ * 53-bit uniforms u1 = ((a << 21) ^ (b >> 11) + 0.5) 2^-53 and likewise u2
+ * from (c, d); Box-Muller gives xi = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+ *
+ * Output per path: side (0 interface, 1 domain boundary, 2 step cap),
+ * boundary edge, exit point, exit angle about the centre, Y_tau, Z_tau,
+ * number of steps, and optionally the pathwise derivatives of Y_tau and
+ * Z_tau with respect to the RBF weights of c (for the adjoint check).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef struct {
+    int dom_kind;            /* 0 square (x0,y0,x1,y1), 1 disk (cx,cy,R) */
+    double dom[4];
+    int b_kind;              /* 0 zero, 1 (sin x, cos y) */
+    int c_kind;              /* 0 zero, 1 -(1+x^2+y^2), 2 rbf */
+    int f_kind;              /* 0 zero, 1 one, 2 manufactured sin(pi x)cos(pi y) */
+    int n_rbf;
+    const double *rbf_x, *rbf_y, *rbf_w;
+    double rbf_sigma;
+} oracle_problem;
+
+typedef struct {
+    double cx, cy, r;        /* the subdomain's circle */
+    double x0, y0;           /* the knot */
+    uint32_t knot;
+    uint64_t seed;
+    double h;
+    int n_paths;
+    int max_steps;
+} oracle_walk;
+
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        if (round < 9) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* exported for the generator tests */
+void oracle_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    philox4x32_10(ctr, key, out);
+}
+
+static double uniform53(uint32_t a, uint32_t b)
+{
+    uint64_t m = ((uint64_t)a << 21) ^ (uint64_t)(b >> 11);
+    return ((double)m + 0.5) * 1.1102230246251565e-16;   /* 2^-53 */
+}
+
+void oracle_normals(uint64_t seed, uint32_t knot, uint32_t step, uint32_t path, double *xi)
+{
+    uint32_t ctr[4] = {step, path, 0u, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), knot};
+    uint32_t w[4];
+    philox4x32_10(ctr, key, w);
+    double u1 = uniform53(w[0], w[1]);
+    double u2 = uniform53(w[2], w[3]);
+    double rr = sqrt(-2.0 * log(u1));
+    double ang = 2.0 * M_PI * u2;
+    xi[0] = rr * cos(ang);
+    xi[1] = rr * sin(ang);
+}
+
+static void drift(const oracle_problem *p, double x, double y, double *bx, double *by)
+{
+    if (p->b_kind == 1) { *bx = sin(x); *by = cos(y); }
+    else { *bx = 0.0; *by = 0.0; }
+}
+
+static double rbf_sum(const oracle_problem *p, double x, double y)
+{
+    double s = 0.0;
+    double two_s2 = 2.0 * p->rbf_sigma * p->rbf_sigma;
+    for (int q = 0; q < p->n_rbf; ++q) {
+        double dx = x - p->rbf_x[q], dy = y - p->rbf_y[q];
+        s += p->rbf_w[q] * exp(-(dx * dx + dy * dy) / two_s2);
+    }
+    return s;
+}
+
+static double killing(const oracle_problem *p, double x, double y)
+{
+    if (p->c_kind == 1) return -(1.0 + x * x + y * y);
+    if (p->c_kind == 2) { double s = rbf_sum(p, x, y); return s < 0.0 ? s : 0.0; }
+    return 0.0;
+}
+
+static double source(const oracle_problem *p, double x, double y)
+{
+    if (p->f_kind == 1) return 1.0;
+    if (p->f_kind == 2) {
+        double pi = M_PI;
+        double u = sin(pi * x) * cos(pi * y);
+        double ux = pi * cos(pi * x) * cos(pi * y);
+        double uy = -pi * sin(pi * x) * sin(pi * y);
+        double bx, by;
+        drift(p, x, y, &bx, &by);
+        return -(-pi * pi * u + bx * ux + by * uy + killing(p, x, y) * u);
+    }
+    return 0.0;
+}
+
+static int inside_domain(const oracle_problem *p, double x, double y)
+{
+    if (p->dom_kind == 0)
+        return x > p->dom[0] && x < p->dom[2] && y > p->dom[1] && y < p->dom[3];
+    double dx = x - p->dom[0], dy = y - p->dom[1];
+    return dx * dx + dy * dy < p->dom[2] * p->dom[2];
+}
+
+/* Smallest t in (0, 1] where P + t D leaves the disk |z - o| < rad, P inside. */
+static double circle_exit_t(double px, double py, double dx, double dy,
+                            double ox, double oy, double rad)
+{
+    double qx = px - ox, qy = py - oy;
+    double a = dx * dx + dy * dy;
+    double b = qx * dx + qy * dy;
+    double c = qx * qx + qy * qy - rad * rad;      /* < 0 inside */
+    double disc = b * b - a * c;
+    if (disc < 0.0) disc = 0.0;
+    double sq = sqrt(disc);
+    if (b >= 0.0) return -c / (b + sq);
+    return (sq - b) / a;
+}
+
+int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
+                     int8_t *side, int8_t *edge, double *ex, double *ey, double *etheta,
+                     double *Ytau, double *Ztau, int32_t *steps,
+                     double *dY, double *dZ)
+{
+    const double sh = sqrt(w->h);
+    const double r2 = w->r * w->r;
+    int capped = 0;
+    double S[256], dZacc[256];      /* running sums for the RBF-weight derivatives */
+    int nr = (dY != NULL) ? p->n_rbf : 0;
+    if (nr > 256) return -1;
+    for (int path = 0; path < w->n_paths; ++path) {
+        double x = w->x0, y = w->y0, Y = 1.0, Z = 0.0;
+        for (int q = 0; q < nr; ++q) { S[q] = 0.0; dZacc[q] = 0.0; }
+        int k = 0;
+        int done = 0;
+        while (!done) {
+            if (k >= w->max_steps) {
+                side[path] = 2; edge[path] = -1; ex[path] = x; ey[path] = y;
+                etheta[path] = 0.0; Ytau[path] = Y; Ztau[path] = Z; steps[path] = k;
+                ++capped;
+                break;
+            }
+            double xi[2];
+            oracle_normals(w->seed, w->knot, (uint32_t)k, (uint32_t)path, xi);
+            double bx, by;
+            drift(p, x, y, &bx, &by);
+            double cv = killing(p, x, y);
+            double fv = source(p, x, y);
+            double nx = x + bx * w->h + sh * xi[0];
+            double ny = y + by * w->h + sh * xi[1];
+            double Yn = Y * (1.0 + cv * w->h);
+            double Zn = Z + fv * Y * w->h;
+            if (nr) {
+                /* d/dw_q of Y_{k+1} = Y_k (1 + c_k h):  S_q accumulates psi_q h / (1 + c_k h),
+                 * and dZ_{k+1} = dZ_k + f_k h dY_k with dY_k = Y_k S_q (before the update). */
+                double two_s2 = 2.0 * p->rbf_sigma * p->rbf_sigma;
+                double sum = rbf_sum(p, x, y);
+                double active = (p->c_kind == 2 && sum < 0.0) ? 1.0 : 0.0;
+                for (int q = 0; q < nr; ++q) {
+                    double ddx = x - p->rbf_x[q], ddy = y - p->rbf_y[q];
+                    double psi = exp(-(ddx * ddx + ddy * ddy) / two_s2);
+                    dZacc[q] += fv * w->h * Y * S[q];
+                    S[q] += active * psi * w->h / (1.0 + cv * w->h);
+                }
+            }
+            ++k;
+            double ddx = nx - w->cx, ddy = ny - w->cy;
+            int out_c = !(ddx * ddx + ddy * ddy < r2);
+            int out_d = !inside_domain(p, nx, ny);
+            if (!out_c && !out_d) { x = nx; y = ny; Y = Yn; Z = Zn; continue; }
+            double dx = nx - x, dy = ny - y;
+            double tc = 2.0, td = 2.0;
+            int ed = -1;
+            if (out_c) tc = circle_exit_t(x, y, dx, dy, w->cx, w->cy, w->r);
+            if (out_d) {
+                if (p->dom_kind == 0) {
+                    double t;
+                    if (nx <= p->dom[0]) { t = (p->dom[0] - x) / dx; if (t < td) { td = t; ed = 3; } }
+                    if (nx >= p->dom[2]) { t = (p->dom[2] - x) / dx; if (t < td) { td = t; ed = 1; } }
+                    if (ny <= p->dom[1]) { t = (p->dom[1] - y) / dy; if (t < td) { td = t; ed = 0; } }
+                    if (ny >= p->dom[3]) { t = (p->dom[3] - y) / dy; if (t < td) { td = t; ed = 2; } }
+                } else {
+                    td = circle_exit_t(x, y, dx, dy, p->dom[0], p->dom[1], p->dom[2]);
+                    ed = 0;
+                }
+            }
+            if (td <= tc) {
+                side[path] = 1; edge[path] = (int8_t)ed;
+                ex[path] = x + td * dx; ey[path] = y + td * dy;
+                etheta[path] = 0.0;
+            } else {
+                side[path] = 0; edge[path] = -1;
+                ex[path] = x + tc * dx; ey[path] = y + tc * dy;
+                double th = atan2(ey[path] - w->cy, ex[path] - w->cx);
+                if (th < 0.0) th += 2.0 * M_PI;
+                etheta[path] = th;
+            }
+            Ytau[path] = Yn; Ztau[path] = Zn; steps[path] = k;
+            for (int q = 0; q < nr; ++q) {
+                dY[(size_t)path * nr + q] = Yn * S[q];
+                dZ[(size_t)path * nr + q] = dZacc[q];
+            }
+            done = 1;
+        }
+        if (nr && side[path] == 2) {
+            for (int q = 0; q < nr; ++q) {
+                dY[(size_t)path * nr + q] = 0.0;
+                dZ[(size_t)path * nr + q] = 0.0;
+            }
+        }
+    }
+    return capped;
+}

@@ -1,0 +1,184 @@
+"""Pins of the oracle's Monte Carlo rows (a11-a12), Krylov solve (a13) and adjoint (a14).
+
+* The Philox4x32-10 generator against an independent library implementation
+  (Triton's, run by its CPU interpreter in a child process).
+* Normal draws: moments and (uniform) marginals.
+* Brownian exit from a disk (generator Laplacian/2): E[tau] = (R^2 - rho^2)/2
+  and the harmonic measure of a band-limited datum = the Poisson kernel,
+  within 4 standard errors plus the Euler-Maruyama exit bias bound.
+* g = 1, f = c = 0: every perimeter row satisfies 1 + sum_j C_ij = r_i up to
+  the IMQ interpolation error of the constant.
+* The direct solve's residual; GMRES against the direct solve.
+* The adjoint gradient against central finite differences (common random numbers).
+"""
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import adjoint, cover, imq, krylov, mc, problem, system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_philox_against_library_implementation():
+    pytest.importorskip("triton")
+    cases = [((0, 0, 0, 0), (0, 0)), ((7, 3, 0, 0), (0, 12)), ((123456, 42, 0, 0), (99, 31337)),
+             ((0xffffffff, 0xffffffff, 0, 0), (0xffffffff, 0xffffffff))]
+    prog = textwrap.dedent("""
+        import os, sys, json
+        os.environ["TRITON_INTERPRET"] = "1"
+        import torch, triton, triton.language as tl
+        @triton.jit
+        def k(out, seed, c0, c1):
+            z = c1 * 0
+            a, b, c, d = tl.philox(seed, c0, c1, z, z, n_rounds=10)
+            tl.store(out + 0, a); tl.store(out + 1, b); tl.store(out + 2, c); tl.store(out + 3, d)
+        def s32(v):
+            return v - (1 << 32) if v >= (1 << 31) else v
+        res = []
+        for (ctr, key) in json.loads(sys.argv[1]):
+            out = torch.zeros(4, dtype=torch.int32)
+            seed = (key[1] << 32) | key[0]
+            k[(1,)](out, seed, s32(ctr[0]), s32(ctr[1]))
+            res.append([v & 0xffffffff for v in out.tolist()])
+        print(json.dumps(res))
+    """)
+    import json
+    try:
+        outp = subprocess.run([sys.executable, "-c", prog, json.dumps(cases)], capture_output=True,
+                              text=True, timeout=600, env={**os.environ, "TRITON_INTERPRET": "1"})
+    except subprocess.TimeoutExpired:
+        pytest.skip("library Philox did not finish")
+    if outp.returncode != 0:
+        pytest.skip("library Philox unavailable: " + outp.stderr[-300:])
+    ref = json.loads(outp.stdout.strip().splitlines()[-1])
+    for (ctr, key), want in zip(cases, ref):
+        assert mc.philox(ctr, key) == want
+
+
+def test_philox_avalanche_and_uniformity():
+    base = mc.philox((5, 9, 0, 0), (0, 1))
+    flips = []
+    for bit in range(32):
+        o = mc.philox((5 ^ (1 << bit), 9, 0, 0), (0, 1))
+        flips.append(sum(bin(a ^ b).count("1") for a, b in zip(base, o)))
+    assert 40 < np.mean(flips) < 88            # ~64 of 128 bits change
+    xs = np.array([mc.normals(0, 3, s, p) for s in range(200) for p in range(100)])
+    assert abs(xs.mean()) < 0.02
+    assert abs(xs.var() - 1.0) < 0.02
+    assert abs(np.mean(xs[:, 0] * xs[:, 1])) < 0.02
+
+
+def _disk_cover(R=0.3, n=16, ops=None):
+    cfg = workloads.floating_only_disk(R, n, 16, 16)
+    if ops:
+        cfg["op"] = ops
+    cov = cover.build_cover(cfg["domain"], cfg["cover"])
+    cover.build_knots(cov)
+    return cfg, cov
+
+
+def test_mean_exit_time_from_disk():
+    cfg, cov = _disk_cover()
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "one", "g": "zero"}, cov.domain)
+    R = cov.r[0]
+    for rho in (0.0, 0.5, 0.8):
+        h = 1e-5
+        x0 = cov.cx[0] + R * rho
+        rec = mc.walk(op, cov.cx[0], cov.cy[0], R, x0, cov.cy[0], 7, 0, h, 4000)
+        est, se = rec.Z.mean(), rec.Z.std(ddof=1) / math.sqrt(rec.Z.size)
+        exact = 0.5 * (R * R - (R * rho) ** 2)
+        # Euler-Maruyama overshoots the exit by O(sqrt h) in space: bias <= 2 R sqrt(h)
+        assert abs(est - exact) < 4 * se + 2 * R * math.sqrt(h)
+        assert np.all(rec.side == 0)
+
+
+def test_harmonic_measure_is_poisson_kernel():
+    from oracle import spectral
+    cfg, cov = _disk_cover()
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "zero", "g": "zero"}, cov.domain)
+    R, n = cov.r[0], 16
+    rho, phi = 0.45, 1.1
+    x0, y0 = cov.cx[0] + R * rho * math.cos(phi), cov.cy[0] + R * rho * math.sin(phi)
+    h = 1e-5
+    rec = mc.walk(op, cov.cx[0], cov.cy[0], R, x0, y0, 11, 0, h, 6000)
+    tk = 2 * math.pi * np.arange(n) / n
+    H = spectral.fourier_cardinal(rec.etheta, tk, n)
+    est = -H.mean(0)
+    se = H.std(0, ddof=1) / math.sqrt(H.shape[0])
+    want = np.array([spectral.poisson_kernel_row(n, rho, phi, t) for t in tk])
+    assert np.all(np.abs(est - want) < 4 * se + 4 * math.sqrt(h))
+
+
+def test_constant_data_rows():
+    cfg = workloads.tiny(paths=200)
+    cfg["op"] = {"b": "zero", "c": "zero", "f": "zero", "g": "one"}
+    cov = cover.full_cover(cfg)
+    rows = [i for i in range(cov.N) if cov.row_sub[i] >= 0 and not cov.floating[cov.row_sub[i]]][:12]
+    S = system.assemble(cfg, cov, rows=rows)
+    for i in rows:
+        row = S.mc_rows[i]
+        m = cov.row_sub[i]
+        # worst interpolation error of the constant 1 over the sampled exit angles
+        t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, 1.5, row.Kinv).sum(1) - 1).max()
+        lhs = 1.0 + row.vals.sum()
+        assert abs(lhs - row.b) <= err1 + 1e-12, (i, m, lhs, row.b)
+
+
+def test_direct_and_gmres_solves():
+    cfg = workloads.tiny(paths=100)
+    S = system.assemble(cfg)
+    C = S.csr()
+    u = krylov.solve(C, S.b)
+    assert np.linalg.norm(C @ u - S.b) <= 1e-13 * np.linalg.norm(S.b)
+    ug, it, rel = krylov.gmres(C, S.b, restart=30, rtol=1e-13)
+    assert rel <= 1e-13
+    assert np.abs(ug - u).max() < 1e-11
+
+
+def _J(cfg, u_obs, cov):
+    S = system.assemble(cfg, cov, with_grad=True)
+    u = krylov.solve(S.csr(), S.b)
+    return float(np.sum((u - u_obs) ** 2)), S, u
+
+
+def _fd(param, idx, eps, u_obs, cov):
+    cp = workloads.grad(paths=60)
+    cm = workloads.grad(paths=60)
+    for c, sgn in ((cp, 1.0), (cm, -1.0)):
+        if param == "w":
+            c["op"]["rbf"]["w"] = c["op"]["rbf"]["w"].copy()
+            c["op"]["rbf"]["w"][idx] += sgn * eps
+        else:
+            c["op"]["g_coef"] = c["op"]["g_coef"].copy()
+            c["op"]["g_coef"][idx] += sgn * eps
+    return (_J(cp, u_obs, cov)[0] - _J(cm, u_obs, cov)[0]) / (2 * eps)
+
+
+def test_adjoint_against_central_differences():
+    """Central differences with common random numbers.
+
+    With step 1e-4 the truncation error is O(eps^2) and the check is tight
+    (1e-6 relative).  With step 1e-6 the quotient is limited by the rounding
+    of J itself (about kappa(A) u |J| ~ 4e-12 from the disk solves, divided
+    by eps), so it is checked at 2e-5 relative.
+    """
+    cfg = workloads.grad(paths=60)
+    cov = cover.full_cover(cfg)
+    rng = np.random.default_rng(9)
+    u_obs = np.exp(cov.kx) * np.sin(cov.ky) + 0.01 * rng.standard_normal(cov.N)
+    J0, S, u = _J(cfg, u_obs, cov)
+    gw, ga, _lam = adjoint.gradient(cfg, S, u, 2.0 * (u - u_obs))
+    for param, idx, g in (("w", 0, gw), ("w", 17, gw), ("w", 40, gw), ("a", 0, ga), ("a", 5, ga),
+                          ("a", 20, ga)):
+        fd4 = _fd(param, idx, 1e-4, u_obs, cov)
+        assert abs(fd4 - g[idx]) <= 1e-6 * max(1e-2, abs(fd4)), (param, idx, fd4, g[idx])
+        fd6 = _fd(param, idx, 1e-6, u_obs, cov)
+        assert abs(fd6 - g[idx]) <= 2e-5 * max(1e-2, abs(fd6)), (param, idx, fd6, g[idx])
