@@ -1,0 +1,283 @@
+/*
+ * pdd.h -- C ABI of the GB300 (sm_103a) library for the explicit interfacial
+ * system of "An explicit substructuring method for overlapping domain
+ * decomposition based on stochastic calculus" (Moron-Vidal, Bernal, Suzuki).
+ *
+ * The library assembles the sparse, nonsymmetric system C u = r of Eq. 28-30
+ * over a cover of overlapping circles (Sec. 2.1), solves it in FP64 and
+ * differentiates a misfit of u.  Every step runs in CUDA kernels on the
+ * current device; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point:
+ *   - Handles (pdd_cover, pdd_system) own their device memory and are freed
+ *     by the matching destroy call.  Structs passed in are read during the
+ *     call only (host pointers inside them are copied).
+ *   - "dev" pointers are device pointers owned by the caller; "host"
+ *     pointers are host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     queued on it; calls that return counts or statuses synchronise it.
+ *   - Every call returns a pdd_status; PDD_OK is 0.  pdd_last_error()
+ *     returns a thread-local message for the last failure.
+ *   - Sizes are counts of elements unless stated.
+ */
+#ifndef PDD_H
+#define PDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PDD_OK = 0,
+    PDD_EINVAL = 1,            /* bad argument or degenerate discretisation        */
+    PDD_ECOVER_GAP = 2,        /* Eq. 5 violated: a point of Omega is uncovered     */
+    PDD_ECIRCLE_OUTSIDE = 3,   /* Eq. 5 violated: an explicit circle misses Omega   */
+    PDD_EKNOT_UNCOVERED = 4,   /* Sec. 2.1: a knot lies inside no other subdomain  */
+    PDD_ENOCONV = 5,           /* iterative refinement or GMRES did not converge   */
+    PDD_EPATH_CAP = 6,         /* a Monte Carlo path reached its step cap          */
+    PDD_ENOMEM = 7,            /* device allocation failed                          */
+    PDD_ECUDA = 8,             /* CUDA runtime error                                */
+    PDD_EDUPLICATE_KNOT = 9    /* two knots closer than 1e-12                       */
+} pdd_status;
+
+/* ---------------------------------------------------------------------------
+ * Problem statement, Eq. 1-3:  L u + c u + f = 0 in Omega, u = g on dOmega,
+ * with L = (1/2) Laplacian + b . grad  (sigma = I in Eq. 3).
+ * ------------------------------------------------------------------------- */
+
+enum { PDD_DOMAIN_SQUARE = 0,   /* p = {x0, y0, x1, y1}: (x0,x1) x (y0,y1)        */
+       PDD_DOMAIN_DISK = 1 };   /* p = {cx, cy, R, unused}                         */
+
+typedef struct {
+    int kind;
+    double p[4];
+} pdd_domain;
+
+enum { PDD_B_ZERO = 0, PDD_B_SINX_COSY = 1 };                 /* b = (sin x, cos y)  */
+enum { PDD_C_ZERO = 0, PDD_C_QUADRATIC = 1,                    /* c = -(1+x^2+y^2)    */
+       PDD_C_RBF = 2 };              /* c = min(0, sum_p w_p exp(-|x-x_p|^2/(2 s^2))) */
+enum { PDD_F_ZERO = 0, PDD_F_ONE = 1,
+       PDD_F_MANUFACTURED = 2 };     /* f = -(L u* + c u*), u* = sin(pi x) cos(pi y)  */
+enum { PDD_G_EXP_SIN = 0,            /* g = e^x sin y                                 */
+       PDD_G_SIN_COS = 1,            /* g = sin(pi x) cos(pi y)                       */
+       PDD_G_BOUNDARY_FOURIER = 2,   /* g(s) = sum_k a_k cos(2 pi k s/P) + b_k sin(.)  */
+       PDD_G_ONE = 3, PDD_G_ZERO = 4 };
+
+typedef struct {
+    int b_kind, c_kind, f_kind, g_kind;
+    int n_rbf;                        /* PDD_C_RBF: number of Gaussians            */
+    const double *rbf_x, *rbf_y;      /* host, n_rbf centres                        */
+    const double *rbf_w;              /* host, n_rbf weights                        */
+    double rbf_sigma;                 /* Gaussian width                             */
+    int n_gcoef;                      /* PDD_G_BOUNDARY_FOURIER: K_c + K_s          */
+    const double *g_coef;             /* host: a_0..a_{Kc-1}, b_1..b_{Ks}; Kc = ceil(n/2),
+                                         s = arclength counter-clockwise from (x0,y0),
+                                         P = perimeter of the square               */
+} pdd_operator;
+
+/* ---------------------------------------------------------------------------
+ * Cover (Eq. 4-7) and its discretisation (Eq. 8-12).
+ * ------------------------------------------------------------------------- */
+
+enum { PDD_COVER_SQUARE_LATTICE = 0,  /* centres (x_o + i s, y_o + j s)             */
+       PDD_COVER_HEX_LATTICE = 1,     /* rows y_o + k s sqrt(3)/2, x_o + i s (+ s/2 on odd k) */
+       PDD_COVER_EXPLICIT = 2 };      /* centres, radii and grids given per circle  */
+
+typedef struct {
+    int kind;
+    int nx, ny;                       /* lattice index box, i < nx, j (or k) < ny   */
+    double x_origin, y_origin, spacing, radius;
+    int n_knots, n_r, n_theta;        /* uniform discretisation (lattices)          */
+    int n_explicit;                   /* PDD_COVER_EXPLICIT: number of circles       */
+    const double *cx, *cy, *r;        /* host, n_explicit                           */
+    const int *n_knots_per, *n_r_per, *n_theta_per;   /* host, n_explicit           */
+} pdd_cover_spec;
+
+typedef struct pdd_cover pdd_cover;
+typedef struct pdd_system pdd_system;
+
+/*
+ * pdd_build_cover -- Eq. 4-12 and Sec. 3.2 on the device.
+ *   Lattice circles that miss Omega are dropped (Eq. 5, right); explicit
+ *   circles that miss Omega give PDD_ECIRCLE_OUTSIDE.  Circles are floating
+ *   when the closed disk lies in open Omega (Eq. 7).  Knots: theta_j = 2 pi j/n
+ *   on full circles; on arcs the same candidates strictly inside Omega and
+ *   at least 0.25 * 2 pi/n from every junction, plus one knot per junction
+ *   (Dirichlet rows).  Knots are numbered circle by circle, each circle's
+ *   knots by local angle from the midpoint of its largest outside arc.
+ *   Each interior knot's row goes to the circle maximising r_m - |x_i - c_m|
+ *   (Sec. 3.2, footnote 3), ties within 1e-12 r to the lowest index.
+ *   Requires n_knots and n_theta even, n_r >= 1.  Checks Eq. 5 on a sample
+ *   grid of pitch min(r)/4 (PDD_ECOVER_GAP).  Synchronises `stream`.
+ */
+pdd_status pdd_build_cover(const pdd_domain *domain, const pdd_cover_spec *spec,
+                           pdd_cover **out, void *stream);
+
+/* Counts: circles M, floating circles, knots N, nonzeros of C. */
+pdd_status pdd_cover_info(const pdd_cover *cov, int *M, int *M_floating, int *N, int64_t *nnz);
+
+/*
+ * pdd_cover_arrays -- device pointers (owned by the cover, valid until
+ * pdd_destroy_cover) to the cover and its discretisation:
+ *   cx, cy, r [M] (double); floating [M] (uint8); knot_ptr [M+1] (int32, the
+ *   stencil Xi_m is the knot range [knot_ptr[m], knot_ptr[m+1]));
+ *   kx, ky, ku [N] (double; ku = local unwrapped angle); kowner [N] (int32);
+ *   kdir [N] (uint8, 1 = knot on dOmega); row_sub [N] (int32, subdomain of
+ *   each row, -1 for Dirichlet rows); rowptr [N+1], col [nnz] (int32 CSR
+ *   pattern of Eq. 29, columns sorted).  Any output pointer may be NULL.
+ */
+pdd_status pdd_cover_arrays(const pdd_cover *cov, const double **cx, const double **cy,
+                            const double **r, const uint8_t **floating, const int **knot_ptr,
+                            const double **kx, const double **ky, const double **ku,
+                            const int **kowner, const uint8_t **kdir, const int **row_sub,
+                            const int **rowptr, const int **col);
+
+void pdd_destroy_cover(pdd_cover *cov);
+
+/* ---------------------------------------------------------------------------
+ * Assembly of C and r (Eq. 28-35, 40-41).
+ * ------------------------------------------------------------------------- */
+
+enum { PDD_PREC_FP64 = 0,       /* disk LU, solves and paths all in FP64             */
+       PDD_PREC_MIXED = 1 };    /* FP32 disk LU + FP64 refinement; FP32 path
+                                   positions, FP64 weights and score sums           */
+
+enum { PDD_FLOATING_PSEUDOSPECTRAL = 0,   /* Sec. 3.3 (default)                      */
+       PDD_FLOATING_MONTE_CARLO = 1 };    /* integrate floating rows by paths too     */
+
+typedef struct {
+    int precision;            /* PDD_PREC_*                                          */
+    int floating_method;      /* PDD_FLOATING_*                                      */
+    int paths;                /* Monte Carlo paths per knot (> 0)                    */
+    double h;                 /* Euler-Maruyama time step (> 0)                      */
+    uint64_t seed;            /* Philox key word 0 (low 32 bits used)                */
+    double imq_c2;            /* IMQ shape c^2 of Eq. 19 (1.5 in the paper)          */
+    int max_refine;           /* refinement sweeps cap (mixed form), e.g. 12         */
+    double refine_tol;        /* stop when |dx|_inf <= tol |x|_inf per column        */
+} pdd_assembly_opts;
+
+typedef struct {
+    int floating_disks;       /* disks solved                                        */
+    int floating_rows;        /* rows assembled by the pseudospectral path           */
+    int mc_rows;              /* rows assembled by Monte Carlo                       */
+    int64_t path_steps;       /* Euler-Maruyama steps taken                          */
+    int64_t capped_paths;     /* paths that hit the step cap                          */
+    int max_refine_sweeps;    /* most refinement sweeps any disk needed              */
+    int unconverged_disks;    /* disks whose refinement missed refine_tol            */
+    double ms_cover_rows;     /* device time per stage (CUDA events), milliseconds   */
+    double ms_disks;
+    double ms_paths;
+    double ms_finalize;
+} pdd_assembly_stats;
+
+/*
+ * pdd_assemble_G -- C (CSR, pattern of the cover) and r on the device.
+ *   Dirichlet rows: C_ii = 1, r_i = g(x_i).  Floating rows (Eq. 33, 35): per
+ *   disk one Chebyshev(r) x Fourier(theta) collocation matrix, factored once
+ *   (partial-pivoting LU), solved for 1 + #Xi right-hand sides and
+ *   evaluated at the disk's knots.  Perimeter rows (Eq. 29-30): Euler-Maruyama
+ *   paths of dX = b dt + dW, dY = c Y dt, dZ = f Y dt from the knot, stopped
+ *   at the exit from the disk n Omega; IMQ cardinals (Eq. 22) on the arc.
+ *   Philox4x32-10 normals: key (seed, knot), counter (step, path, 0, 0).
+ *   Synchronises `stream`.  PDD_EPATH_CAP when a path exceeds 50 r^2/h steps.
+ */
+pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op,
+                          const pdd_assembly_opts *opts, pdd_system **out, void *stream);
+
+/*
+ * pdd_system_csr -- device pointers owned by the system: val [nnz] (C in the
+ * cover's CSR pattern), b [N] (r), se [nnz] (standard error of Monte Carlo
+ * entries, 0 elsewhere), se_b [N].  Any output pointer may be NULL.
+ */
+pdd_status pdd_system_csr(const pdd_system *sys, const double **val, const double **b,
+                          const double **se, const double **se_b);
+
+/*
+ * pdd_system_mc -- the raw Monte Carlo estimates (device, owned by the
+ * system): for the k-th Monte Carlo row (row id rows[k]), moments
+ * [mom_ptr[k], mom_ptr[k+1]) hold E[1_Gamma Y_tau phi_l(u_tau)] (IMQ basis) or
+ * E[1_Gamma Y_tau H_j] (Fourier cardinals), and bmean[k] = E[1_dOmega g Y + Z].
+ */
+pdd_status pdd_system_mc(const pdd_system *sys, int *n_rows, const int **rows,
+                         const int **mom_ptr, const double **moments, const double **bmean);
+
+pdd_status pdd_system_stats(const pdd_system *sys, pdd_assembly_stats *stats);
+
+void pdd_destroy_system(pdd_system *sys);
+
+/* ---------------------------------------------------------------------------
+ * Global solve (a13): restarted GMRES(m) in FP64 (Sec. 4, Eq. 45 without the
+ * preconditioner) on a CSR sparse matrix-vector product.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    int restart;              /* Krylov subspace size m (1..256)                    */
+    int max_iters;            /* total inner iterations cap                          */
+    double rtol;              /* stop at |r - C u|_2 <= rtol |r|_2                   */
+    int transpose;            /* 1: solve C^T u = r instead                          */
+} pdd_solve_opts;
+
+typedef struct {
+    int iters;
+    double rel_residual;      /* true residual after the last restart              */
+    int converged;
+} pdd_solve_info;
+
+/* Solve the system's C u = r; u_dev [N] caller-owned device memory. */
+pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *u_dev,
+                     pdd_solve_info *info, void *stream);
+
+/*
+ * pdd_solve_csr -- the same solver on any square CSR matrix in device memory
+ * (rowptr [n+1], col [nnz] int32 sorted per row; val [nnz], b [n], u [n]
+ * double).  u is overwritten (the initial guess is 0).  Workspace is
+ * allocated for the call and freed before return.
+ */
+pdd_status pdd_solve_csr(int n, const int *rowptr_dev, const int *col_dev, const double *val_dev,
+                         const double *b_dev, double *u_dev, const pdd_solve_opts *opts,
+                         pdd_solve_info *info, void *stream);
+
+/* y = C x (or C^T x when transpose != 0) for a CSR matrix in device memory. */
+pdd_status pdd_spmv_csr(int n, const int *rowptr_dev, const int *col_dev, const double *val_dev,
+                        const double *x_dev, double *y_dev, int transpose, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint gradient (a14; not in the paper).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * pdd_grad -- dJ/dw (RBF weights of c, n_rbf values) and dJ/da (boundary
+ * Fourier coefficients of g, n_gcoef values) of a misfit J(u), given u and
+ * dJ/du.  lambda solves C^T lambda = dJ/du; floating disks contribute
+ * -z^T diag(psi_q 1{c<0}) V with A^T z = sum_i lambda_i E_i (transposed
+ * disk solves, factors recomputed per disk) and V the disk solution for the
+ * interface data of u; perimeter rows replay their Philox paths (common
+ * random numbers) and accumulate the pathwise derivative of Y_tau and Z_tau.
+ * The operator and options must be those the system was assembled with.
+ * grad_dev [n_rbf + n_gcoef] caller-owned device memory (weights first).
+ * lambda_dev [N] may be NULL.  Synchronises `stream`.
+ */
+pdd_status pdd_grad(const pdd_cover *cov, const pdd_operator *op, const pdd_assembly_opts *opts,
+                    const pdd_system *sys, const double *u_dev, const double *dJdu_dev,
+                    double *grad_dev, double *lambda_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics.
+ * ------------------------------------------------------------------------- */
+
+const char *pdd_last_error(void);
+
+/* Number of kernels this process has launched through the library. */
+int64_t pdd_launch_count(void);
+
+/* Library version string. */
+const char *pdd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDD_H */

@@ -18,7 +18,8 @@ Readings where the paper is silent (also listed in the design notes):
     strictly inside Omega and at least gap * 2 pi / n (gap = 0.25) away from
     every junction angle, plus one knot at each junction;
   * local order: increasing angle measured from the midpoint of the largest
-    arc of the circle that lies outside Omega (0 for a full circle);
+    arc of the circle that lies outside Omega (0 for a full circle; among
+    arcs whose lengths agree to 1e-9 the first in angle order);
   * knots are numbered circle by circle in cover order, then in local order;
   * a knot is inside circle m when r_m - |x - c_m| > 1e-12 r_owner; the best
     score wins and scores within 1e-12 r_owner of the best tie to the lowest m.
@@ -242,7 +243,7 @@ def circle_interface(dom: Domain, cx: float, cy: float, r: float):
             mx = cx + r * math.cos(mid)
             my = cy + r * math.sin(mid)
             outside = not bool(dom.inside_open(mx, my))
-            if outside and (a1 - a0) > best:
+            if outside and (a1 - a0) > best + 1e-9:     # first of equal arcs wins
                 best = a1 - a0
                 theta_s = mid if mid < TWO_PI else mid - TWO_PI
     return ang, pts, theta_s

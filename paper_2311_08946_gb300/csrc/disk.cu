@@ -1,0 +1,888 @@
+// a6-a9: floating rows by Chebyshev(r) x Fourier(theta) collocation on each
+// disk (Sec. 3.3, Eq. 31-35, 40-41), batched over disks.
+//
+//   a6  k_disk_operator: rows of the collocation matrix A of L + c (row-
+//       equilibrated), the right-hand sides [A_IB H, -f] and per-node FP64
+//       coefficients for the matrix-free residual.
+//   a7  k_lu: right-looking blocked LU with partial pivoting, one CTA per
+//       disk, panel in shared memory.  The paper factors by QR (Eq. 41);
+//       LU solves the same systems.
+//   a8  k_lu_solve (+ k_residual): multi-RHS forward/back substitution; in
+//       the mixed form the factors are FP32 and FP64 iterative refinement
+//       with a matrix-free FP64 residual recovers the FP64 solution.
+//   a9  k_disk_eval: tensor interpolation (barycentric Chebyshev in r over all
+//       2 n_r + 2 points, the Fourier cardinal in theta) at the disk's knots,
+//       scattered into the CSR values of C and into r.
+//
+// Grid: N_c = 2 n_r + 1 Chebyshev points x_k = cos(k pi / N_c); unknowns at
+// radius x_k (k = 1..n_r) and angle t_j = 2 pi j / n_theta, index
+// p = (k-1) n_theta + j; a point at x_{N_c - k} < 0 is radius x_k at angle
+// t_j + pi.  With sigma = I the operator in polar coordinates is
+// (1/2)(u_rr + u_r/r + u_tt/r^2) + b_x(cos t u_r - sin t u_t/r)
+//   + b_y(sin t u_r + cos t u_t/r) + c u, and d/dr carries 1/R.
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace pdd {
+
+struct Shape {
+    int nr, nt, nk, nc, n, nrhs;
+    double *x, *D, *D2, *F1, *F2, *Hg;   // device tables
+};
+
+struct DiskDesc {
+    double cx, cy, R;
+    int m, knot_base, row_begin, row_end;
+};
+
+// ---------------------------------------------------------------------------
+// shape tables: Chebyshev points and differentiation matrix (closed form),
+// Fourier differentiation vectors (closed forms), boundary data of each knot
+// ---------------------------------------------------------------------------
+__device__ double fourier_cardinal_cf(double x, int n) {
+    // H(x) = sin(n x / 2) cot(x / 2) / n  (Eq. 18 summed), x reduced to (-pi, pi]
+    x = remainder(x, PDD_TWO_PI);
+    if (x == 0.0) return 1.0;
+    double s = sin(0.5 * n * x), c = cos(0.5 * x), d = sin(0.5 * x);
+    return s * c / (d * n);
+}
+
+__global__ void k_shape_tables(int nr, int nt, int nk, double *x, double *D, double *F1, double *F2,
+                               double *Hg) {
+    const int nc = 2 * nr + 1, np = nc + 1;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) x[k] = sin(PDD_PI * (nc - 2.0 * k) / (2.0 * nc));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+        int i = idx / np, j = idx % np;
+        if (i == j) continue;
+        double ci = (i == 0 || i == nc) ? 2.0 : 1.0, cj = (j == 0 || j == nc) ? 2.0 : 1.0;
+        double sg = ((i + j) & 1) ? -1.0 : 1.0;
+        D[idx] = ci / cj * sg / (x[i] - x[j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {   // negative-sum diagonal
+        double s = 0.0;
+        for (int j = 0; j < np; ++j)
+            if (j != i) s += D[i * np + j];
+        D[i * np + i] = -s;
+    }
+    const double h = PDD_TWO_PI / nt;
+    for (int d = threadIdx.x; d < nt; d += blockDim.x) {
+        if (d == 0) {
+            F1[0] = 0.0;
+            F2[0] = -PDD_PI * PDD_PI / (3.0 * h * h) - 1.0 / 6.0;
+        } else {
+            double sg = (d & 1) ? -1.0 : 1.0;
+            double s = sin(0.5 * d * h), c = cos(0.5 * d * h);
+            F1[d] = 0.5 * sg * c / s;
+            F2[d] = -0.5 * sg / (s * s);
+        }
+    }
+    for (int idx = threadIdx.x; idx < nt * nk; idx += blockDim.x) {
+        int j = idx / nk, col = idx % nk;
+        double t = PDD_TWO_PI * j / nt, tk = PDD_TWO_PI * col / nk;
+        Hg[idx] = fourier_cardinal_cf(t - tk, nk);
+    }
+}
+
+__global__ void k_matmul_sq(const double *A, double *C, int np) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np * np) return;
+    int i = idx / np, j = idx % np;
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) s += A[i * np + k] * A[k * np + j];
+    C[idx] = s;
+}
+
+// ---------------------------------------------------------------------------
+// a6: operator rows
+// ---------------------------------------------------------------------------
+struct NodeCoef {
+    double alpha, beta, gamma, delta, c, s;
+};
+
+__device__ __forceinline__ double a_entry(const Shape &S, int k, int j, int q, double al, double be,
+                                          double ga, double de, double cv, int p) {
+    const int l = q / S.nt + 1, jp = q - (l - 1) * S.nt, half = S.nt >> 1, np = S.nc + 1;
+    double v = 0.0;
+    if (jp == j) v += al * S.D2[k * np + l] + be * S.D[k * np + l];
+    if (jp == (j + half) % S.nt) v += al * S.D2[k * np + S.nc - l] + be * S.D[k * np + S.nc - l];
+    if (l == k) {
+        int d = (j - jp + S.nt) % S.nt;
+        v += ga * S.F2[d] + de * S.F1[d];
+    }
+    if (q == p) v += cv;
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_disk_operator(Problem P, Shape S, const DiskDesc *disks,
+                                                       T *A, long strideA, double *RHS, long strideR,
+                                                       NodeCoef *coef, long strideC) {
+    const int disk = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + warp;
+    if (p >= S.n) return;
+    const DiskDesc dd = disks[disk];
+    const int k = p / S.nt + 1, j = p % S.nt, np = S.nc + 1, half = S.nt >> 1;
+    const double rho = S.x[k];
+    double st, ct;
+    sincos(PDD_TWO_PI * j / S.nt, &st, &ct);
+    const double X = dd.cx + dd.R * rho * ct, Y = dd.cy + dd.R * rho * st;
+    double bx, by;
+    drift(P, X, Y, bx, by);
+    const double cv = killing(P, X, Y);
+    const double fv = source(P, X, Y);
+    const double R2 = dd.R * dd.R;
+    const double al = 0.5 / R2;
+    const double be = 0.5 / (R2 * rho) + (bx * ct + by * st) / dd.R;
+    const double ga = 0.5 / (R2 * rho * rho);
+    const double de = (-bx * st + by * ct) / (dd.R * rho);
+    double amax = 0.0;
+    for (int q = lane; q < S.n; q += 32) amax = fmax(amax, fabs(a_entry(S, k, j, q, al, be, ga, de, cv, p)));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const double sc = amax > 0.0 ? 1.0 / amax : 1.0;
+    T *Arow = A + disk * strideA + (long)p * S.n;
+    for (int q = lane; q < S.n; q += 32) Arow[q] = (T)(sc * a_entry(S, k, j, q, al, be, ga, de, cv, p));
+    const double w0 = al * S.D2[k * np + 0] + be * S.D[k * np + 0];
+    const double wN = al * S.D2[k * np + S.nc] + be * S.D[k * np + S.nc];
+    double *Rrow = RHS + disk * strideR + (long)p * S.nrhs;
+    for (int col = lane; col < S.nk; col += 32)
+        Rrow[col] = sc * (w0 * S.Hg[j * S.nk + col] + wN * S.Hg[((j + half) % S.nt) * S.nk + col]);
+    if (lane == 0) {
+        Rrow[S.nk] = -sc * fv;
+        coef[disk * strideC + p] = NodeCoef{al, be, ga, de, cv, sc};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7: batched LU with partial pivoting (row-major, in place), one CTA per disk
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *permAll, int *infoAll) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Pn = reinterpret_cast<T *>(smem_raw);               // panel rows x NB
+    T *Ut = Pn + (size_t)n * NB;                           // NB x 64 tile of U12
+    __shared__ int piv[NB];
+    __shared__ double rv[8];
+    __shared__ int ri[8];
+    const int disk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T *A = Aall + disk * strideA;
+    int *perm = permAll + (long)disk * n;
+    for (int i = tid; i < n; i += 256) perm[i] = i;
+    int info = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int kb = min(NB, n - k0), rows = n - k0;
+        for (int idx = tid; idx < rows * kb; idx += 256) {
+            int r = idx / kb, c = idx - r * kb;
+            Pn[r * NB + c] = A[(long)(k0 + r) * n + k0 + c];
+        }
+        __syncthreads();
+        for (int c = 0; c < kb; ++c) {
+            double best = -1.0;
+            int bi = c;
+            for (int r = c + tid; r < rows; r += 256) {
+                double v = fabs((double)Pn[r * NB + c]);
+                if (v > best) { best = v; bi = r; }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double b = rv[0];
+                int i0 = ri[0];
+                for (int w = 1; w < 8; ++w)
+                    if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+                piv[c] = i0;
+                if (i0 != c) {
+                    int t = perm[k0 + c];
+                    perm[k0 + c] = perm[k0 + i0];
+                    perm[k0 + i0] = t;
+                }
+            }
+            __syncthreads();
+            const int p = piv[c];
+            if (p != c)
+                for (int cc = tid; cc < kb; cc += 256) {
+                    T t = Pn[c * NB + cc];
+                    Pn[c * NB + cc] = Pn[p * NB + cc];
+                    Pn[p * NB + cc] = t;
+                }
+            __syncthreads();
+            const T d = Pn[c * NB + c];
+            if (d == (T)0 && info == 0) info = k0 + c + 1;
+            for (int r = c + 1 + tid; r < rows; r += 256) {
+                T l = (d != (T)0) ? Pn[r * NB + c] / d : (T)0;
+                Pn[r * NB + c] = l;
+                for (int cc = c + 1; cc < kb; ++cc) Pn[r * NB + cc] -= l * Pn[c * NB + cc];
+            }
+            __syncthreads();
+        }
+        // write the panel back
+        for (int idx = tid; idx < rows * kb; idx += 256) {
+            int r = idx / kb, c = idx - r * kb;
+            A[(long)(k0 + r) * n + k0 + c] = Pn[r * NB + c];
+        }
+        // the panel's row interchanges, applied to the columns outside it
+        for (int c = 0; c < kb; ++c) {
+            const int p = piv[c];
+            if (p != c) {
+                T *ra = A + (long)(k0 + c) * n, *rb = A + (long)(k0 + p) * n;
+                for (int j = tid; j < n - kb; j += 256) {
+                    int col = j < k0 ? j : j + kb;
+                    T t = ra[col];
+                    ra[col] = rb[col];
+                    rb[col] = t;
+                }
+            }
+            __syncthreads();
+        }
+        const int c0 = k0 + kb, nrem = n - c0;
+        if (nrem <= 0) break;
+        // U12 = L11^-1 A12 (unit lower triangular solve, one column per thread)
+        for (int j = c0 + tid; j < n; j += 256) {
+            T u[NB];
+#pragma unroll
+            for (int rr = 0; rr < NB; ++rr) {
+                if (rr < kb) {
+                    T v = A[(long)(k0 + rr) * n + j];
+                    for (int t = 0; t < rr; ++t) v -= Pn[rr * NB + t] * u[t];
+                    u[rr] = v;
+                    A[(long)(k0 + rr) * n + j] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 per thread
+        const int tiles = (nrem + 63) / 64;
+        const int ty = tid >> 4, tx = tid & 15;
+        for (int tj = 0; tj < tiles; ++tj) {
+            const int cbase = c0 + tj * 64;
+            for (int idx = tid; idx < kb * 64; idx += 256) {
+                int t = idx >> 6, jj = idx & 63;
+                int col = cbase + jj;
+                Ut[t * 64 + jj] = col < n ? A[(long)(k0 + t) * n + col] : (T)0;
+            }
+            __syncthreads();
+            for (int ti = 0; ti < tiles; ++ti) {
+                const int rbase = ti * 64;          // index into the panel rows beyond kb
+                T acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+                for (int t = 0; t < kb; ++t) {
+                    T lv[4], uv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        int pr = kb + rbase + ty * 4 + a;
+                        lv[a] = pr < rows ? Pn[pr * NB + t] : (T)0;
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) uv[b] = Ut[t * 64 + tx * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    int row = c0 + rbase + ty * 4 + a;
+                    if (row >= n) continue;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        int col = cbase + tx * 4 + b;
+                        if (col < n) A[(long)row * n + col] -= acc[a][b];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) infoAll[disk] = info;
+}
+
+// ---------------------------------------------------------------------------
+// a8: multi-RHS solve with the LU factors: W = U^-1 L^-1 P R, then X = W
+// (plain form) or X += W with a per-disk convergence test (refinement).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_solve(const T *LUall, int n, long strideA, const int *permAll,
+                                                  const double *Rall, int nrhs, long strideR,
+                                                  T *Wall, double *Xall, int accumulate, int *conv,
+                                                  int *sweeps, double tol) {
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    if (conv && conv[disk]) return;
+    const T *LU = LUall + disk * strideA;
+    const int *perm = permAll + (long)disk * n;
+    const double *R = Rall + disk * strideR;
+    T *W = Wall + disk * strideR;
+    double *X = Xall + disk * strideR;
+    constexpr int TB = 16;
+    // forward: L W = P R (unit lower)
+    for (int i0 = 0; i0 < n; i0 += TB) {
+        const int tb = min(TB, n - i0);
+        for (int o = tid; o < tb * nrhs; o += 256) {
+            int ii = o / nrhs, col = o - ii * nrhs, i = i0 + ii;
+            const T *Li = LU + (long)i * n;
+            T acc = (T)R[(long)perm[i] * nrhs + col];
+            for (int q = 0; q < i0; ++q) acc -= Li[q] * W[(long)q * nrhs + col];
+            W[(long)i * nrhs + col] = acc;
+        }
+        __syncthreads();
+        for (int col = tid; col < nrhs; col += 256) {
+            for (int ii = 1; ii < tb; ++ii) {
+                const T *Li = LU + (long)(i0 + ii) * n;
+                T acc = W[(long)(i0 + ii) * nrhs + col];
+                for (int t = 0; t < ii; ++t) acc -= Li[i0 + t] * W[(long)(i0 + t) * nrhs + col];
+                W[(long)(i0 + ii) * nrhs + col] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    // backward: U W = W (upper, non-unit)
+    for (int iend = n; iend > 0; iend -= TB) {
+        const int i0 = max(0, iend - TB), tb = iend - i0;
+        for (int o = tid; o < tb * nrhs; o += 256) {
+            int ii = o / nrhs, col = o - ii * nrhs, i = i0 + ii;
+            const T *Ui = LU + (long)i * n;
+            T acc = W[(long)i * nrhs + col];
+            for (int q = iend; q < n; ++q) acc -= Ui[q] * W[(long)q * nrhs + col];
+            W[(long)i * nrhs + col] = acc;
+        }
+        __syncthreads();
+        for (int col = tid; col < nrhs; col += 256) {
+            for (int ii = tb - 1; ii >= 0; --ii) {
+                const int i = i0 + ii;
+                const T *Ui = LU + (long)i * n;
+                T acc = W[(long)i * nrhs + col];
+                for (int t = ii + 1; t < tb; ++t) acc -= Ui[i0 + t] * W[(long)(i0 + t) * nrhs + col];
+                W[(long)i * nrhs + col] = acc / Ui[i];
+            }
+        }
+        __syncthreads();
+    }
+    // X = W or X += W; refinement test max|W| <= tol max|X|
+    double dmax = 0.0, xmax = 0.0;
+    for (long o = tid; o < (long)n * nrhs; o += 256) {
+        double w = (double)W[o];
+        double xv = accumulate ? X[o] + w : w;
+        X[o] = xv;
+        dmax = fmax(dmax, fabs(w));
+        xmax = fmax(xmax, fabs(xv));
+    }
+    if (!conv) return;
+    __shared__ double sd[8], sx[8];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if ((tid & 31) == 0) { sd[tid >> 5] = dmax; sx[tid >> 5] = xmax; }
+    __syncthreads();
+    if (tid == 0) {
+        double d = 0.0, x = 0.0;
+        for (int w = 0; w < 8; ++w) { d = fmax(d, sd[w]); x = fmax(x, sx[w]); }
+        sweeps[disk] += 1;
+        if (d <= tol * x) conv[disk] = 1;
+    }
+}
+
+// R = RHS - A X in FP64 without forming A (equilibrated rows)
+__global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefAll, long strideC,
+                                                  const double *RHSall, const double *Xall,
+                                                  double *Rall, long strideR, const int *conv) {
+    const int disk = blockIdx.y;
+    if (conv[disk]) return;
+    extern __shared__ double wsm[];                 // per row: nc-1 radial + nt angular weights
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int p = blockIdx.x * 8 + ty;
+    const int nw = (S.nc - 1) + S.nt, np = S.nc + 1, half = S.nt >> 1;
+    double *w = wsm + ty * nw;
+    const double *X = Xall + disk * strideR;
+    if (p < S.n) {
+        const NodeCoef cf = coefAll[disk * strideC + p];
+        const int k = p / S.nt + 1;
+        for (int l = tx; l < S.nc - 1; l += 32)      // l+1 = 1..nc-1
+            w[l] = cf.alpha * S.D2[k * np + l + 1] + cf.beta * S.D[k * np + l + 1];
+        for (int d = tx; d < S.nt; d += 32) w[S.nc - 1 + d] = cf.gamma * S.F2[d] + cf.delta * S.F1[d];
+    }
+    __syncwarp();
+    if (p >= S.n) return;
+    const NodeCoef cf = coefAll[disk * strideC + p];
+    const int k = p / S.nt + 1, j = p % S.nt;
+    const int jm = (j + half) % S.nt;
+    for (int col = tx; col < S.nrhs; col += 32) {
+        double acc = cf.c * X[(long)p * S.nrhs + col];
+        for (int l = 1; l <= S.nr; ++l) {
+            acc += w[l - 1] * X[(long)((l - 1) * S.nt + j) * S.nrhs + col];
+            acc += w[S.nc - l - 1] * X[(long)((l - 1) * S.nt + jm) * S.nrhs + col];
+        }
+        const double *wa = w + S.nc - 1;
+        const long rb = (long)(k - 1) * S.nt;
+        for (int jp = 0; jp < S.nt; ++jp) {
+            int d = j - jp;
+            d += (d < 0) ? S.nt : 0;
+            acc += wa[d] * X[(rb + jp) * S.nrhs + col];
+        }
+        Rall[disk * strideR + (long)p * S.nrhs + col] =
+            RHSall[disk * strideR + (long)p * S.nrhs + col] - cf.s * acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a9: evaluate at the disk's knots and scatter into C and r
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_disk_eval(Shape S, const DiskDesc *disks, const int *sub_rows,
+                                                   const double *kx, const double *ky,
+                                                   const int *rowptr, const double *Xall,
+                                                   long strideR, int group, int per, double *val,
+                                                   double *b) {
+    extern __shared__ double esm[];                 // per rows x (n + nt) evaluation weights
+    __shared__ double lr[8][130];                   // radial barycentric weights, l = 0..nc
+    __shared__ double sa[8][130];                   // angular cardinals at the grid angles
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    const DiskDesc dd = disks[disk];
+    const double *X = Xall + disk * strideR;
+    const int nE = S.n + S.nt, half = S.nt >> 1;
+    const int gid = tid / group, gl = tid % group;
+    const bool in_group = gid < per;
+    for (int r0 = dd.row_begin; r0 < dd.row_end; r0 += per) {
+        const int row = r0 + gid;
+        const bool active = in_group && row < dd.row_end;
+        double *E = esm + gid * nE;
+        double rho = 0.0;
+        if (active) {
+            const int i = sub_rows[row];
+            const double dx = kx[i] - dd.cx, dy = ky[i] - dd.cy;
+            rho = sqrt(dx * dx + dy * dy) / dd.R;
+            const double phi = atan2(dy, dx);
+            for (int l = gl; l <= S.nc; l += group) {
+                const double wl = ((l & 1) ? -1.0 : 1.0) * ((l == 0 || l == S.nc) ? 0.5 : 1.0);
+                const double d = rho - S.x[l];
+                lr[gid][l] = (d == 0.0) ? 0.0 : wl / d;
+            }
+            for (int a = gl; a < S.nt; a += group)
+                sa[gid][a] = fourier_cardinal_cf(phi - PDD_TWO_PI * a / S.nt, S.nt);
+        }
+        __syncthreads();
+        if (active && gl == 0) {                    // normalise (barycentric formula, 2nd kind)
+            int hit = -1;
+            double den = 0.0;
+            for (int l = 0; l <= S.nc; ++l) {
+                if (rho == S.x[l]) hit = l;
+                den += lr[gid][l];
+            }
+            for (int l = 0; l <= S.nc; ++l)
+                lr[gid][l] = (hit >= 0) ? (l == hit ? 1.0 : 0.0) : lr[gid][l] / den;
+        }
+        __syncthreads();
+        if (active) {
+            // E[k][a] = l_{k+1} S_a + l_{nc-1-k} S_{a+half};  E_B[a] = l_0 S_a + l_nc S_{a+half}
+            for (int q = gl; q < nE; q += group) {
+                if (q < S.n) {
+                    const int kk = q / S.nt, a = q - kk * S.nt;
+                    E[q] = lr[gid][kk + 1] * sa[gid][a] + lr[gid][S.nc - 1 - kk] * sa[gid][(a + half) % S.nt];
+                } else {
+                    const int a = q - S.n;
+                    E[q] = lr[gid][0] * sa[gid][a] + lr[gid][S.nc] * sa[gid][(a + half) % S.nt];
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const int i = sub_rows[row];
+            for (int col = gl; col < S.nrhs; col += group) {
+                double acc = 0.0;
+                for (int q = 0; q < S.n; ++q) acc += E[q] * X[(long)q * S.nrhs + col];
+                if (col < S.nk) {
+                    // boundary ring: G_j = -H_j on the circle
+                    for (int a = 0; a < S.nt; ++a) acc -= E[S.n + a] * S.Hg[a * S.nk + col];
+                    const int off = (i < dd.knot_base) ? 1 : 0;
+                    val[rowptr[i] + off + col] = acc;
+                } else {
+                    b[i] = acc;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct ShapeTables {
+    DevBuf<double> x, D, D2, F1, F2, Hg;
+    Shape S{};
+    void build(int nr, int nt, int nk, cudaStream_t st) {
+        const int nc = 2 * nr + 1, np = nc + 1;
+        x.alloc(np);
+        D.alloc((size_t)np * np);
+        D2.alloc((size_t)np * np);
+        F1.alloc(nt);
+        F2.alloc(nt);
+        Hg.alloc((size_t)nt * nk);
+        PDD_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * np * np, st));
+        PDD_LAUNCH(k_shape_tables, 1, 256, 0, st, nr, nt, nk, x.p, D.p, F1.p, F2.p, Hg.p);
+        PDD_LAUNCH(k_matmul_sq, cdiv((long)np * np, 256), 256, 0, st, D.p, D2.p, np);
+        S = Shape{nr, nt, nk, nc, nr * nt, nk + 1, x.p, D.p, D2.p, F1.p, F2.p, Hg.p};
+    }
+};
+
+static int lu_nb(int n, size_t elem) {
+    // panel n x NB plus an NB x 64 tile must fit in ~200 KB of shared memory
+    int nb = 32;
+    while (nb > 4 && ((size_t)n * nb + (size_t)nb * 64) * elem > 200 * 1024) nb >>= 1;
+    return nb;
+}
+
+template <typename T>
+static void launch_lu(T *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st) {
+    const int nb = lu_nb(n, sizeof(T));
+    const size_t smem = ((size_t)n * nb + (size_t)nb * 64) * sizeof(T);
+    switch (nb) {
+#define PDD_LU_CASE(NBV)                                                                      \
+    case NBV:                                                                                  \
+        PDD_CUDA(cudaFuncSetAttribute(k_lu<T, NBV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem));                                            \
+        PDD_LAUNCH((k_lu<T, NBV>), nd, 256, smem, st, A, n, strideA, perm, info);              \
+        break;
+        PDD_LU_CASE(32)
+        PDD_LU_CASE(16)
+        PDD_LU_CASE(8)
+        PDD_LU_CASE(4)
+#undef PDD_LU_CASE
+        default: fail(PDD_EINVAL, "disk grid too large for the panel kernel");
+    }
+}
+
+template <typename T>
+static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
+                           pdd_system &sys, const ShapeTables &tab, const std::vector<DiskDesc> &disks,
+                           cudaStream_t st) {
+    const Shape S = tab.S;
+    const bool mixed = sizeof(T) == 4;
+    const size_t perA = (size_t)S.n * S.n * sizeof(T);
+    const size_t perR = (size_t)S.n * S.nrhs * sizeof(double);
+    const size_t perDisk = perA + perR * (mixed ? 3 : 1) + (size_t)S.n * S.nrhs * sizeof(T) +
+                           (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + 64;
+    size_t freeb = 0, totb = 0;
+    PDD_CUDA(cudaMemGetInfo(&freeb, &totb));
+    size_t budget = std::min<size_t>((size_t)(0.6 * freeb), (size_t)64 << 30);
+    int wave = (int)std::max<size_t>(1, budget / perDisk);
+    wave = std::min<int>(wave, (int)disks.size());
+    if ((size_t)wave * perDisk > freeb) fail(PDD_ENOMEM, "not enough device memory for one disk");
+    DevBuf<T> A, W;
+    DevBuf<double> RHS, X, Rr;
+    DevBuf<NodeCoef> coef;
+    DevBuf<int> perm, info, conv, sweeps;
+    DevBuf<DiskDesc> dd;
+    A.alloc((size_t)wave * S.n * S.n);
+    W.alloc((size_t)wave * S.n * S.nrhs);
+    RHS.alloc((size_t)wave * S.n * S.nrhs);
+    X.alloc((size_t)wave * S.n * S.nrhs);
+    if (mixed) Rr.alloc((size_t)wave * S.n * S.nrhs);
+    coef.alloc((size_t)wave * S.n);
+    perm.alloc((size_t)wave * S.n);
+    info.alloc(wave);
+    conv.alloc(wave);
+    sweeps.alloc(wave);
+    dd.alloc(wave);
+    const long sA = (long)S.n * S.n, sR = (long)S.n * S.nrhs, sC = S.n;
+    DiskStats ds;
+    for (size_t w0 = 0; w0 < disks.size(); w0 += wave) {
+        const int nd = (int)std::min<size_t>(wave, disks.size() - w0);
+        PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
+        dim3 g_op(cdiv(S.n, 8), nd);
+        PDD_LAUNCH(k_disk_operator<T>, g_op, 256, 0, st, P, S, dd.p, A.p, sA, RHS.p, sR, coef.p, sC);
+        launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
+        if (!mixed) {
+            PDD_LAUNCH(k_lu_solve<T>, nd, 256, 0, st, A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0,
+                       (int *)nullptr, (int *)nullptr, 0.0);
+        } else {
+            PDD_CUDA(cudaMemsetAsync(conv.p, 0, nd * sizeof(int), st));
+            PDD_CUDA(cudaMemsetAsync(sweeps.p, 0, nd * sizeof(int), st));
+            PDD_CUDA(cudaMemsetAsync(X.p, 0, (size_t)nd * sR * sizeof(double), st));
+            const int maxs = std::max(1, o.max_refine);
+            const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-14;
+            const size_t rsm = (size_t)8 * ((S.nc - 1) + S.nt) * sizeof(double);
+            dim3 g_res(cdiv(S.n, 8), nd);
+            for (int s = 0; s < maxs; ++s) {
+                const double *rhs_now = (s == 0) ? RHS.p : Rr.p;
+                PDD_LAUNCH(k_lu_solve<T>, nd, 256, 0, st, A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p,
+                           1, conv.p, sweeps.p, tol);
+                if (s + 1 < maxs)
+                    PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p);
+            }
+            std::vector<int> hc(nd), hs(nd);
+            PDD_CUDA(cudaMemcpyAsync(hc.data(), conv.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PDD_CUDA(cudaMemcpyAsync(hs.data(), sweeps.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PDD_CUDA(cudaStreamSynchronize(st));
+            for (int d = 0; d < nd; ++d) {
+                ds.max_sweeps = std::max(ds.max_sweeps, hs[d]);
+                ds.unconverged += hc[d] ? 0 : 1;
+            }
+        }
+        const int group = (S.nrhs <= 32) ? 32 : ((S.nrhs <= 64) ? 64 : 128);
+        const size_t rowb = (size_t)(S.n + S.nt) * sizeof(double);
+        const int per = (int)std::min<size_t>(256 / group, (180 * 1024) / rowb);
+        if (per < 1 || S.nc + 1 > 130 || S.nt > 130) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
+        const size_t esm = per * rowb;
+        PDD_CUDA(cudaFuncSetAttribute(k_disk_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+        PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p,
+                   cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.b.p);
+        std::vector<int> hinfo(nd);
+        PDD_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        for (int d = 0; d < nd; ++d)
+            if (hinfo[d]) fail(PDD_ENOCONV, "singular collocation matrix");
+        ds.disks += nd;
+        for (int d = 0; d < nd; ++d) ds.rows += disks[w0 + d].row_end - disks[w0 + d].row_begin;
+    }
+    return ds;
+}
+
+DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
+                         pdd_system &sys, cudaStream_t st) {
+    std::map<std::tuple<int, int, int>, std::vector<DiskDesc>> groups;
+    std::vector<double> hcx(cov.M), hcy(cov.M), hr(cov.M);
+    PDD_CUDA(cudaMemcpyAsync(hcx.data(), cov.cx.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaMemcpyAsync(hcy.data(), cov.cy.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaMemcpyAsync(hr.data(), cov.r.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaStreamSynchronize(st));
+    for (int m = 0; m < cov.M; ++m) {
+        if (!cov.h_floating[m]) continue;
+        int a = cov.h_sub_ptr[m], b = cov.h_sub_ptr[m + 1];
+        if (b <= a) continue;
+        if (cov.h_knot_ptr[m + 1] - cov.h_knot_ptr[m] != cov.h_nk[m]) fail(PDD_EINVAL, "floating circle lost knots");
+        groups[{cov.h_nr[m], cov.h_nt[m], cov.h_nk[m]}].push_back(
+            DiskDesc{hcx[m], hcy[m], hr[m], m, cov.h_knot_ptr[m], a, b});
+    }
+    DiskStats all;
+    for (auto &kv : groups) {
+        ShapeTables tab;
+        tab.build(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), st);
+        DiskStats d = (o.precision == PDD_PREC_MIXED)
+                          ? run_group<float>(cov, P, o, sys, tab, kv.second, st)
+                          : run_group<double>(cov, P, o, sys, tab, kv.second, st);
+        all.disks += d.disks;
+        all.rows += d.rows;
+        all.max_sweeps = std::max(all.max_sweeps, d.max_sweeps);
+        all.unconverged += d.unconverged;
+    }
+    return all;
+}
+
+}  // namespace pdd
+
+// ---------------------------------------------------------------------------
+// a14 (floating rows): with V the disk solution for the interface data of u
+// (V = B - sum_j u_j G_j) and A^T z = sum_i lambda_i E_i, the weights of c
+// get -sum_p z_p V_p 1{c<0} psi_q(x_p).  FP64 throughout; factors recomputed.
+// ---------------------------------------------------------------------------
+namespace pdd {
+
+__global__ void __launch_bounds__(256) k_adjoint_vecs(Shape S, const DiskDesc *disks, const int *sub_rows,
+                                                      const double *kx, const double *ky, const double *Xall,
+                                                      long strideR, const double *u, const double *lambda,
+                                                      double *Vall, double *Eall) {
+    __shared__ double lr[130], sa[130];
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    const DiskDesc dd = disks[disk];
+    const double *X = Xall + disk * strideR;
+    double *V = Vall + (long)disk * S.n, *E = Eall + (long)disk * S.n;
+    const int half = S.nt >> 1;
+    for (int p = tid; p < S.n; p += 256) {
+        double v = X[(long)p * S.nrhs + S.nk];
+        for (int c = 0; c < S.nk; ++c) v -= u[dd.knot_base + c] * X[(long)p * S.nrhs + c];
+        V[p] = v;
+        E[p] = 0.0;
+    }
+    for (int row = dd.row_begin; row < dd.row_end; ++row) {
+        const int i = sub_rows[row];
+        const double dx = kx[i] - dd.cx, dy = ky[i] - dd.cy;
+        const double rho = sqrt(dx * dx + dy * dy) / dd.R, phi = atan2(dy, dx);
+        __syncthreads();
+        for (int l = tid; l <= S.nc; l += 256) {
+            const double wl = ((l & 1) ? -1.0 : 1.0) * ((l == 0 || l == S.nc) ? 0.5 : 1.0);
+            const double d = rho - S.x[l];
+            lr[l] = (d == 0.0) ? 0.0 : wl / d;
+        }
+        for (int a = tid; a < S.nt; a += 256) sa[a] = fourier_cardinal_cf(phi - PDD_TWO_PI * a / S.nt, S.nt);
+        __syncthreads();
+        if (tid == 0) {
+            int hit = -1;
+            double den = 0.0;
+            for (int l = 0; l <= S.nc; ++l) {
+                if (rho == S.x[l]) hit = l;
+                den += lr[l];
+            }
+            for (int l = 0; l <= S.nc; ++l) lr[l] = (hit >= 0) ? (l == hit ? 1.0 : 0.0) : lr[l] / den;
+        }
+        __syncthreads();
+        const double li = lambda[i];
+        for (int q = tid; q < S.n; q += 256) {
+            const int kk = q / S.nt, a = q - kk * S.nt;
+            E[q] += li * (lr[kk + 1] * sa[a] + lr[S.nc - 1 - kk] * sa[(a + half) % S.nt]);
+        }
+    }
+}
+
+// z = S A_s^-T e with P A_s = L U (A_s the equilibrated matrix, S its row scales)
+__global__ void __launch_bounds__(256) k_lu_solve_T(const double *LUall, int n, long strideA, const int *permAll,
+                                                    const NodeCoef *coefAll, long strideC, const double *Eall,
+                                                    double *Wall, double *Zall) {
+    __shared__ double red[8];
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    const double *LU = LUall + disk * strideA;
+    const int *perm = permAll + (long)disk * n;
+    const double *e = Eall + (long)disk * n;
+    double *w = Wall + (long)disk * n, *z = Zall + (long)disk * n;
+    // U^T y = e (lower, non-unit): y_i = (e_i - sum_{k<i} U_ki y_k) / U_ii
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = tid; k < i; k += 256) s += LU[(long)k * n + i] * w[k];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += red[q];
+            w[i] = (e[i] - t) / LU[(long)i * n + i];
+        }
+        __syncthreads();
+    }
+    // L^T v = y (upper, unit): v_i = y_i - sum_{k>i} L_ki v_k
+    for (int i = n - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + tid; k < n; k += 256) s += LU[(long)k * n + i] * w[k];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += red[q];
+            w[i] -= t;
+        }
+        __syncthreads();
+    }
+    // P z' = v  ->  z'[perm[i]] = v[i];  z = S z'
+    for (int i = tid; i < n; i += 256) {
+        const int r = perm[i];
+        z[r] = coefAll[disk * strideC + r].s * w[i];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adjoint_contract(Problem P, Shape S, const DiskDesc *disks,
+                                                          const double *Vall, const double *Zall,
+                                                          double *partial) {
+    extern __shared__ double csm[];             // per node: x, y, z V 1{c<0}
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    const DiskDesc dd = disks[disk];
+    double *nx = csm, *ny = csm + S.n, *tv = csm + 2 * S.n;
+    for (int p = tid; p < S.n; p += 256) {
+        const int k = p / S.nt + 1, j = p % S.nt;
+        double st, ct;
+        sincos(PDD_TWO_PI * j / S.nt, &st, &ct);
+        const double X = dd.cx + dd.R * S.x[k] * ct, Y = dd.cy + dd.R * S.x[k] * st;
+        nx[p] = X;
+        ny[p] = Y;
+        const double act = (P.c_kind == PDD_C_RBF && rbf_sum(P, X, Y) < 0.0) ? 1.0 : 0.0;
+        tv[p] = Zall[(long)disk * S.n + p] * Vall[(long)disk * S.n + p] * act;
+    }
+    __syncthreads();
+    const double inv = 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma);
+    for (int q = tid; q < P.n_rbf; q += 256) {
+        double s = 0.0;
+        for (int p = 0; p < S.n; ++p) {
+            const double dx = nx[p] - P.rbf_x[q], dy = ny[p] - P.rbf_y[q];
+            s += tv[p] * exp(-(dx * dx + dy * dy) * inv);
+        }
+        partial[(long)disk * P.n_rbf + q] = -s;
+    }
+}
+
+void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const double *lambda,
+                DevBuf<double> &partial, int &n_part, cudaStream_t st) {
+    n_part = 0;
+    if (P.c_kind != PDD_C_RBF || P.n_rbf == 0) return;
+    std::map<std::tuple<int, int, int>, std::vector<DiskDesc>> groups;
+    std::vector<double> hcx(cov.M), hcy(cov.M), hr(cov.M);
+    PDD_CUDA(cudaMemcpyAsync(hcx.data(), cov.cx.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaMemcpyAsync(hcy.data(), cov.cy.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaMemcpyAsync(hr.data(), cov.r.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaStreamSynchronize(st));
+    int total = 0;
+    for (int m = 0; m < cov.M; ++m) {
+        if (!cov.h_floating[m]) continue;
+        int a = cov.h_sub_ptr[m], b = cov.h_sub_ptr[m + 1];
+        if (b <= a) continue;
+        groups[{cov.h_nr[m], cov.h_nt[m], cov.h_nk[m]}].push_back(
+            DiskDesc{hcx[m], hcy[m], hr[m], m, cov.h_knot_ptr[m], a, b});
+        ++total;
+    }
+    if (!total) return;
+    partial.alloc((size_t)total * P.n_rbf);
+    int done = 0;
+    for (auto &kv : groups) {
+        ShapeTables tab;
+        tab.build(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), st);
+        const Shape S = tab.S;
+        const auto &disks = kv.second;
+        const size_t perDisk = (size_t)S.n * S.n * 8 + (size_t)S.n * S.nrhs * 8 * 3 + (size_t)S.n * 8 * 4 +
+                               (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * 4 + 64;
+        size_t freeb = 0, totb = 0;
+        PDD_CUDA(cudaMemGetInfo(&freeb, &totb));
+        int wave = (int)std::max<size_t>(1, std::min<size_t>((size_t)(0.5 * freeb), (size_t)32 << 30) / perDisk);
+        wave = std::min<int>(wave, (int)disks.size());
+        DevBuf<double> A, W, RHS, X, Vb, Eb, Zb, Wt;
+        DevBuf<NodeCoef> coef;
+        DevBuf<int> perm, info;
+        DevBuf<DiskDesc> dd;
+        A.alloc((size_t)wave * S.n * S.n);
+        W.alloc((size_t)wave * S.n * S.nrhs);
+        RHS.alloc((size_t)wave * S.n * S.nrhs);
+        X.alloc((size_t)wave * S.n * S.nrhs);
+        Vb.alloc((size_t)wave * S.n);
+        Eb.alloc((size_t)wave * S.n);
+        Zb.alloc((size_t)wave * S.n);
+        Wt.alloc((size_t)wave * S.n);
+        coef.alloc((size_t)wave * S.n);
+        perm.alloc((size_t)wave * S.n);
+        info.alloc(wave);
+        dd.alloc(wave);
+        const long sA = (long)S.n * S.n, sR = (long)S.n * S.nrhs, sC = S.n;
+        for (size_t w0 = 0; w0 < disks.size(); w0 += wave) {
+            const int nd = (int)std::min<size_t>(wave, disks.size() - w0);
+            PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
+            dim3 g_op(cdiv(S.n, 8), nd);
+            PDD_LAUNCH(k_disk_operator<double>, g_op, 256, 0, st, P, S, dd.p, A.p, sA, RHS.p, sR, coef.p, sC);
+            launch_lu<double>(A.p, S.n, sA, perm.p, info.p, nd, st);
+            PDD_LAUNCH(k_lu_solve<double>, nd, 256, 0, st, A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0,
+                       (int *)nullptr, (int *)nullptr, 0.0);
+            PDD_LAUNCH(k_adjoint_vecs, nd, 256, 0, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p, X.p, sR, u,
+                       lambda, Vb.p, Eb.p);
+            PDD_LAUNCH(k_lu_solve_T, nd, 256, 0, st, A.p, S.n, sA, perm.p, coef.p, sC, Eb.p, Wt.p, Zb.p);
+            const size_t csm = (size_t)3 * S.n * sizeof(double);
+            PDD_CUDA(cudaFuncSetAttribute(k_adjoint_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+            PDD_LAUNCH(k_adjoint_contract, nd, 256, csm, st, P, S, dd.p, Vb.p, Zb.p,
+                       partial.p + (size_t)(done + w0) * P.n_rbf);
+        }
+        PDD_CUDA(cudaStreamSynchronize(st));
+        done += (int)disks.size();
+    }
+    n_part = total;
+}
+
+}  // namespace pdd

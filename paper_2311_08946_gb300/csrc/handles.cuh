@@ -1,0 +1,110 @@
+// Handle layouts (opaque behind include/pdd.h) and the stage drivers the
+// C ABI calls.  Device arrays are structure-of-arrays in HBM.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct pdd_cover {
+    pdd_domain domain;
+    int M = 0, M_floating = 0, N = 0;
+    int64_t nnz = 0;
+    int max_nk = 0, max_stencil = 0;
+    double max_r = 0.0, min_r = 0.0;
+    // circles
+    pdd::DevBuf<double> cx, cy, r, theta_s;
+    pdd::DevBuf<uint8_t> floating;
+    pdd::DevBuf<int> nk, nr, nt;
+    pdd::DevBuf<int> knot_ptr;             // [M+1]
+    // knots
+    pdd::DevBuf<double> kx, ky, ku;
+    pdd::DevBuf<int> kowner, row_sub;
+    pdd::DevBuf<uint8_t> kdir;
+    // rows grouped by subdomain: rows of circle m are sub_rows[sub_ptr[m] .. sub_ptr[m+1])
+    pdd::DevBuf<int> sub_ptr, sub_rows;
+    // CSR pattern
+    pdd::DevBuf<int> rowptr, col;
+    // spatial hash of circles (uniform grid of pitch max_r)
+    int gx = 0, gy = 0;
+    double gx0 = 0, gy0 = 0, gh = 1;
+    pdd::DevBuf<int> cell_ptr, cell_items;
+    // host copies of small per-circle data
+    std::vector<int> h_knot_ptr, h_sub_ptr, h_nk, h_nr, h_nt;
+    std::vector<uint8_t> h_floating;
+};
+
+struct pdd_system {
+    int N = 0;
+    int64_t nnz = 0;
+    const pdd_cover *cov = nullptr;
+    pdd::DevBuf<double> val, b, se, se_b;
+    // Monte Carlo raw estimates
+    int n_mc = 0;
+    pdd::DevBuf<int> mc_rows, mom_ptr;
+    pdd::DevBuf<double> moments, bmean;
+    pdd_assembly_stats stats{};
+    int precision = 0;
+};
+
+namespace pdd {
+
+// device problem description (uploads the operator's host arrays)
+struct ProblemHolder {
+    Problem P{};
+    DevBuf<double> rbf_x, rbf_y, rbf_w, g_coef;
+    void set(const pdd_domain &dom, const pdd_operator &op, cudaStream_t st);
+};
+
+// stage drivers (each file implements its own)
+void build_cover_impl(const pdd_domain &dom, const pdd_cover_spec &spec, pdd_cover &cov,
+                      cudaStream_t st);
+void assemble_dirichlet(const pdd_cover &cov, const Problem &P, pdd_system &sys, cudaStream_t st);
+
+struct DiskStats {
+    int disks = 0, rows = 0, max_sweeps = 0, unconverged = 0;
+};
+DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
+                         pdd_system &sys, cudaStream_t st);
+
+struct McStats {
+    int rows = 0;
+    int64_t steps = 0, capped = 0;
+    float ms_paths = 0, ms_finalize = 0;
+};
+McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
+                    pdd_system &sys, cudaStream_t st);
+
+struct SolveResult {
+    int iters = 0;
+    double rel = 0;
+    int converged = 0;
+};
+SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b,
+                      double *u, const pdd_solve_opts &o, cudaStream_t st);
+void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const double *x,
+              double *y, cudaStream_t st);
+// explicit transpose of a CSR pattern + values (rows of the result sorted)
+void csr_transpose(int n, int64_t nnz, const int *rowptr, const int *col, const double *val,
+                   DevBuf<int> &rowptr_t, DevBuf<int> &col_t, DevBuf<double> &val_t,
+                   cudaStream_t st);
+
+// adjoint pieces: per-disk (floating rows) and per-row (Monte Carlo) partial
+// gradients, summed in a fixed order by grad_impl
+void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const double *lambda,
+                DevBuf<double> &partial, int &n_part, cudaStream_t st);
+void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o, const pdd_system &sys,
+             const double *u, const double *lambda, DevBuf<double> &partial, int &n_part,
+             cudaStream_t st);
+// K^-1 of every perimeter stencil (offsets per circle, -1 when none)
+void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, DevBuf<long> &koff_m,
+                        cudaStream_t st);
+
+void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
+               const pdd_system &sys, const double *u, const double *dJdu, double *grad,
+               double *lambda, cudaStream_t st);
+
+// device-wide exclusive scan of int32 counts (in place into out, returns the total)
+int64_t exclusive_scan(const int *in, int *out, int n, cudaStream_t st);
+
+}  // namespace pdd

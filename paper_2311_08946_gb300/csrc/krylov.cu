@@ -1,0 +1,289 @@
+// a13: the global solve C u = r (Eq. 28) in FP64 by restarted GMRES(m)
+// (Sec. 4; Eq. 45 without the RAS preconditioner) on a CSR sparse
+// matrix-vector product.
+//
+// Layout: the Krylov basis V is (m+1) x n row-major (each basis vector
+// contiguous); dot products are block partial sums reduced in a fixed order
+// (deterministic).  Orthogonalisation is classical Gram-Schmidt applied
+// twice (CGS2).  The Hessenberg matrix, Givens rotations and the residual
+// estimate live on the device; after convergence every kernel of the cycle
+// sees the stop flag and returns at once, so the host synchronises only once
+// per restart cycle to read the true residual.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace pdd {
+
+static constexpr int kRowsPerBlock = 32;    // 8 lanes per row, 256 threads
+static constexpr int kDotBlock = 256;
+
+struct GState {
+    int stop, iters, k_used, pad;
+    double bnorm, res;
+};
+
+// y = C x, 8 lanes per row
+__global__ void __launch_bounds__(256) k_spmv(int n, const int *rowptr, const int *col, const double *val,
+                                              const double *x, double *y, const GState *gs) {
+    if (gs && gs->stop) return;
+    const int row = blockIdx.x * kRowsPerBlock + (threadIdx.x >> 3), l = threadIdx.x & 7;
+    double s = 0.0;
+    if (row < n)
+        for (int k = rowptr[row] + l; k < rowptr[row + 1]; k += 8) s += val[k] * x[col[k]];
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (row < n && l == 0) y[row] = s;
+}
+
+// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1
+__global__ void __launch_bounds__(kDotBlock) k_dots(int n, int nv, const double *V, const double *w,
+                                                    double *partial, const GState *gs) {
+    if (gs && gs->stop) return;
+    __shared__ double red[kDotBlock / 32];
+    const int G = gridDim.x;
+    const int per = (n + G - 1) / G, a = blockIdx.x * per, b = min(n, a + per);
+    for (int t = 0; t < nv; ++t) {
+        double s = 0.0;
+        const double *v = V + (long)t * n;
+        for (int r = a + threadIdx.x; r < b; r += blockDim.x) s += v[r] * w[r];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int q = 0; q < kDotBlock / 32; ++q) tot += red[q];
+            partial[t * G + blockIdx.x] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// h[t] = sum_blk partial[t][blk]; w -= sum_t V[t] h[t]; column j of H gets h (+= when add)
+__global__ void __launch_bounds__(kDotBlock) k_orth(int n, int nv, const double *V, double *w,
+                                                    const double *partial, int G, double *Hcol, int add,
+                                                    const GState *gs) {
+    if (gs && gs->stop) return;
+    __shared__ double h[257];
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < G; ++q) s += partial[t * G + q];
+        h[t] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t < nv; t += blockDim.x) Hcol[t] = add ? Hcol[t] + h[t] : h[t];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        double s = w[r];
+        for (int t = 0; t < nv; ++t) s -= V[(long)t * n + r] * h[t];
+        w[r] = s;
+    }
+}
+
+// v = w / |w|, with |w| from the partials; Hsub = |w|
+__global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w, double *v,
+                                                         const double *partial, int G, double *Hsub,
+                                                         const GState *gs) {
+    if (gs && gs->stop) return;
+    __shared__ double nrm;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < G; ++q) s += partial[q];
+        nrm = sqrt(s);
+        if (blockIdx.x == 0 && Hsub) *Hsub = nrm;
+    }
+    __syncthreads();
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) v[r] = w[r] * inv;
+}
+
+// apply the previous rotations to column j, make a new one, update g and the stop flag
+__global__ void k_givens(double *H, int ldh, double *cs, double *sn, double *g, int j, double rtol,
+                         int max_iters, GState *gs) {
+    if (gs->stop) return;
+    double *hc = H + (long)j * ldh;                  // column j stored contiguously (ldh = m+1)
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+        hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+        hc[i] = t;
+    }
+    const double a = hc[j], b = hc[j + 1];
+    const double den = hypot(a, b);
+    const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    hc[j] = den;
+    hc[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    gs->iters += 1;
+    gs->k_used = j + 1;
+    gs->res = fabs(g[j + 1]);
+    if (gs->res <= rtol * gs->bnorm || gs->iters >= max_iters || b == 0.0) gs->stop = 1;
+}
+
+// y = H^-1 g (upper triangular k x k), single thread; then stop is cleared for the next cycle
+__global__ void k_upper_solve(const double *H, int ldh, const double *g, double *y, GState *gs) {
+    const int k = gs->k_used;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[(long)c * ldh + i] * y[c];
+        y[i] = s / H[(long)i * ldh + i];
+    }
+}
+
+__global__ void k_xupdate(int n, const double *V, const double *y, const GState *gs, double *x) {
+    const int k = gs->k_used;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        double s = x[r];
+        for (int t = 0; t < k; ++t) s += V[(long)t * n + r] * y[t];
+        x[r] = s;
+    }
+}
+
+// r = b - C x (Cx precomputed in r)
+__global__ void k_residual_vec(int n, const double *b, double *r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = b[i] - r[i];
+}
+
+__global__ void k_cycle_start(GState *gs, const double *partial, int G, double *g, int m, double rtol,
+                              int max_iters, int first) {
+    double s = 0.0;
+    for (int q = 0; q < G; ++q) s += partial[q];
+    const double beta = sqrt(s);
+    if (first) gs->bnorm = beta;                      // x0 = 0, so r0 = b
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    gs->res = beta;
+    gs->k_used = 0;
+    gs->stop = (beta <= rtol * gs->bnorm || gs->iters >= max_iters || beta == 0.0) ? 1 : 0;
+}
+
+void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const double *x, double *y,
+              cudaStream_t st) {
+    PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, x, y, (const GState *)nullptr);
+}
+
+SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
+                      const pdd_solve_opts &o, cudaStream_t st) {
+    const int m = std::max(1, std::min(256, o.restart));
+    const int G = std::max(1, std::min(1024, cdiv(n, 512)));
+    DevBuf<double> V, w, partial, H, cs, sn, g, y;
+    DevBuf<GState> gs;
+    V.alloc((size_t)(m + 1) * n);
+    w.alloc(n);
+    partial.alloc((size_t)(m + 1) * G);
+    H.alloc((size_t)(m + 1) * m);
+    cs.alloc(m);
+    sn.alloc(m);
+    g.alloc(m + 1);
+    y.alloc(m);
+    gs.alloc(1);
+    PDD_CUDA(cudaMemsetAsync(gs.p, 0, sizeof(GState), st));
+    PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
+    PDD_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * (m + 1) * m, st));
+    const int vb = std::min(cdiv(n, 256), 2048);
+    SolveResult res;
+    const int max_iters = std::max(1, o.max_iters);
+    for (int cycle = 0;; ++cycle) {
+        // r = b - C u  (u = 0 on the first cycle)
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
+        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
+        PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, partial.p, G, (double *)nullptr, gs.p);
+        for (int j = 0; j < m; ++j) {
+            double *vj = V.p + (long)j * n;
+            double *Hc = H.p + (long)j * (m + 1);
+            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
+            for (int pass = 0; pass < 2; ++pass) {
+                PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, gs.p);
+                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, G, Hc, pass, gs.p);
+            }
+            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, gs.p);
+            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, partial.p, G,
+                       Hc + j + 1, gs.p);
+            PDD_LAUNCH(k_givens, 1, 1, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
+        }
+        PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H.p, m + 1, g.p, y.p, gs.p);
+        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V.p, y.p, gs.p, u);
+        // true residual
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
+        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
+        std::vector<double> hp(G);
+        GState hg{};
+        PDD_CUDA(cudaMemcpyAsync(hp.data(), partial.p, G * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaMemcpyAsync(&hg, gs.p, sizeof(GState), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        double rs = 0.0;
+        for (int q = 0; q < G; ++q) rs += hp[q];
+        const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
+        res.iters = hg.iters;
+        res.rel = rel;
+        if (hg.bnorm == 0.0 || rel <= o.rtol) {
+            res.converged = 1;
+            break;
+        }
+        if (hg.iters >= max_iters) break;
+    }
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// explicit transpose (counting sort by column, rows then sorted: deterministic)
+// ---------------------------------------------------------------------------
+__global__ void k_col_count(int64_t nnz, const int *col, int *cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[k]], 1);
+}
+
+__global__ void k_t_fill(int n, const int *rowptr, const int *col, const double *val, const int *ptr_t,
+                         int *cursor, int *col_t, double *val_t) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        int c = col[k];
+        int p = ptr_t[c] + atomicAdd(&cursor[c], 1);
+        col_t[p] = i;
+        val_t[p] = val[k];
+    }
+}
+
+__global__ void k_t_sort(int n, const int *ptr_t, int *col_t, double *val_t) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int k = ptr_t[r] + 1; k < ptr_t[r + 1]; ++k) {
+        int c = col_t[k];
+        double v = val_t[k];
+        int q = k - 1;
+        while (q >= ptr_t[r] && col_t[q] > c) {
+            col_t[q + 1] = col_t[q];
+            val_t[q + 1] = val_t[q];
+            --q;
+        }
+        col_t[q + 1] = c;
+        val_t[q + 1] = v;
+    }
+}
+
+void csr_transpose(int n, int64_t nnz, const int *rowptr, const int *col, const double *val, DevBuf<int> &rowptr_t,
+                   DevBuf<int> &col_t, DevBuf<double> &val_t, cudaStream_t st) {
+    DevBuf<int> cnt, cursor;
+    cnt.alloc(n + 1);
+    cursor.alloc(n + 1);
+    rowptr_t.alloc(n + 1);
+    col_t.alloc(std::max<int64_t>(nnz, 1));
+    val_t.alloc(std::max<int64_t>(nnz, 1));
+    PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (n + 1), st));
+    PDD_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (n + 1), st));
+    PDD_LAUNCH(k_col_count, 1024, 256, 0, st, nnz, col, cnt.p);
+    exclusive_scan(cnt.p, rowptr_t.p, n, st);
+    PDD_LAUNCH(k_t_fill, cdiv(n, 256), 256, 0, st, n, rowptr, col, val, rowptr_t.p, cursor.p, col_t.p, val_t.p);
+    PDD_LAUNCH(k_t_sort, cdiv(n, 256), 256, 0, st, n, rowptr_t.p, col_t.p, val_t.p);
+}
+
+}  // namespace pdd

@@ -1,0 +1,784 @@
+// a10-a12: Monte Carlo rows (Eq. 25-30 with the representation of Eq. 53,
+// 56 and sigma = I), IMQ cardinals on perimeter arcs (Eq. 19-22).
+//
+//   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c^2)^-1/2 per perimeter stencil,
+//       Cholesky factor and K^-1 in FP64 (one CTA per circle).
+//   a11 k_paths: Euler-Maruyama paths of dX = b dt + dW, dY = c Y dt,
+//       dZ = f Y dt from the knot, stopped at the first step whose end point
+//       leaves the open disk or the open domain.  One CTA per row; each thread
+//       runs paths p = tid, tid + blockDim, ... (a lane takes its next path as
+//       soon as one exits).  Exit point: the first crossing of the segment
+//       with the circle or dOmega (ties to dOmega).  Normals: Philox4x32-10,
+//       key (seed, knot), counter (step, path, 0, 0).  FP64 form: every
+//       quantity in FP64.  Mixed form: position, drift and normals in FP32,
+//       weights Y, Z and all scores in FP64.  Per-path exit records (side,
+//       angle or arclength, Y, Z) go to a device scratch buffer.
+//   a12 k_mc_finalize: one CTA of 32 warps per row; warp b owns batch b
+//       (paths p = b mod 32) and its lanes own basis functions.  The row's
+//       moments M_l = E[1_Gamma Y phi_l(u)], C_ij = -sum_l (K^-1)_lj M_l (IMQ)
+//       or -M_j (Fourier cardinals), r_i = E[1_dOmega g Y + Z]; standard errors
+//       by batch means over the 32 batches.
+#include <algorithm>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace pdd {
+
+static constexpr int kBatches = 32;
+static constexpr int kMaxStencil = 96;
+
+// ---------------------------------------------------------------------------
+// a10
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const int *knot_ptr,
+                                                     const double *ku, const long *kinv_off,
+                                                     double c2, double *kinv, int *bad) {
+    extern __shared__ double sm[];                    // K (n x n), then L in place
+    const int m = circles[blockIdx.x];
+    const int a = knot_ptr[m], n = knot_ptr[m + 1] - a;
+    double *K = sm;
+    double *Z = sm + n * n;                           // n x n work for the inverse
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        int l = idx / n, k = idx % n;
+        double d = ku[a + l] - ku[a + k];
+        K[idx] = 1.0 / sqrt(d * d + c2);
+    }
+    __syncthreads();
+    // right-looking Cholesky, lower triangle
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            double v = K[j * n + j];
+            if (!(v > 0.0)) atomicAdd(bad, 1);
+            K[j * n + j] = sqrt(fmax(v, 1e-300));
+        }
+        __syncthreads();
+        const double d = K[j * n + j];
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) K[i * n + j] /= d;
+        __syncthreads();
+        for (int idx = tid; idx < (n - j - 1) * (n - j - 1); idx += blockDim.x) {
+            int i = j + 1 + idx / (n - j - 1), k = j + 1 + idx % (n - j - 1);
+            if (k <= i) K[i * n + k] -= K[i * n + j] * K[k * n + j];
+        }
+        __syncthreads();
+    }
+    // K^-1 = L^-T L^-1: column c of the identity per thread
+    for (int c = tid; c < n; c += blockDim.x) {
+        for (int i = 0; i < n; ++i) {                 // L y = e_c
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= K[i * n + k] * Z[k * n + c];
+            Z[i * n + c] = v / K[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {            // L^T x = y
+            double v = Z[i * n + c];
+            for (int k = i + 1; k < n; ++k) v -= K[k * n + i] * Z[k * n + c];
+            Z[i * n + c] = v / K[i * n + i];
+        }
+    }
+    __syncthreads();
+    double *out = kinv + kinv_off[blockIdx.x];
+    for (int idx = tid; idx < n * n; idx += blockDim.x) out[idx] = Z[idx];
+}
+
+// ---------------------------------------------------------------------------
+// a11
+// ---------------------------------------------------------------------------
+struct PathArgs {
+    const int *rows, *row_sub;
+    const double *kx, *ky, *ccx, *ccy, *cr, *theta_s;
+    int paths;
+    double h;
+    uint64_t seed;
+    int8_t *side;
+    double *su, *Y, *Z;
+    unsigned long long *steps;
+    int *capped;
+};
+
+__device__ __forceinline__ double circle_exit_t(double px, double py, double dx, double dy, double ox,
+                                                double oy, double rad) {
+    const double qx = px - ox, qy = py - oy;
+    const double a = dx * dx + dy * dy;
+    const double b = qx * dx + qy * dy;
+    const double c = qx * qx + qy * qy - rad * rad;
+    double disc = b * b - a * c;
+    if (disc < 0.0) disc = 0.0;
+    const double sq = sqrt(disc);
+    return (b >= 0.0) ? -c / (b + sq) : (sq - b) / a;
+}
+
+template <typename R>
+struct Num;
+template <>
+struct Num<double> {
+    __device__ static void normals(uint64_t s, uint32_t k, uint32_t st, uint32_t p, double &a, double &b) {
+        normals64(s, k, st, p, a, b);
+    }
+    __device__ static void drift(const Problem &P, double x, double y, double &bx, double &by) {
+        pdd::drift(P, x, y, bx, by);
+    }
+    __device__ static double sq(double v) { return sqrt(v); }
+};
+template <>
+struct Num<float> {
+    __device__ static void normals(uint64_t s, uint32_t k, uint32_t st, uint32_t p, float &a, float &b) {
+        normals32(s, k, st, p, a, b);
+    }
+    __device__ static void drift(const Problem &P, float x, float y, float &bx, float &by) {
+        if (P.b_kind == PDD_B_SINX_COSY) {
+            bx = sinf(x);
+            by = cosf(y);
+        } else {
+            bx = 0.f;
+            by = 0.f;
+        }
+    }
+    __device__ static float sq(float v) { return sqrtf(v); }
+};
+
+__device__ __forceinline__ float killing32(const Problem &P, float x, float y) {
+    if (P.c_kind == PDD_C_QUADRATIC) return -(1.0f + x * x + y * y);
+    if (P.c_kind == PDD_C_RBF) {
+        float s = 0.f;
+        const float inv = (float)(1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma));
+        for (int q = 0; q < P.n_rbf; ++q) {
+            float dx = x - (float)P.rbf_x[q], dy = y - (float)P.rbf_y[q];
+            s += (float)P.rbf_w[q] * expf(-(dx * dx + dy * dy) * inv);
+        }
+        return s < 0.f ? s : 0.f;
+    }
+    return 0.f;
+}
+
+__device__ __forceinline__ float source32(const Problem &P, float x, float y) {
+    if (P.f_kind == PDD_F_ONE) return 1.0f;
+    if (P.f_kind == PDD_F_MANUFACTURED) {
+        float spx, cpx, spy, cpy;
+        sincospif(x, &spx, &cpx);
+        sincospif(y, &spy, &cpy);
+        const float pi = 3.14159265358979f;
+        float u = spx * cpy, ux = pi * cpx * cpy, uy = -pi * spx * spy;
+        float bx, by;
+        Num<float>::drift(P, x, y, bx, by);
+        return -(-pi * pi * u + bx * ux + by * uy + killing32(P, x, y) * u);
+    }
+    return 0.f;
+}
+
+template <typename R, bool KILL, bool SRC>
+__global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
+    const int slot = blockIdx.x;
+    const int i = A.rows[slot], m = A.row_sub[i];
+    const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m], ts = A.theta_s[m];
+    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
+    const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
+    const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
+    unsigned long long my_steps = 0;
+    int my_capped = 0;
+    for (int p = threadIdx.x; p < A.paths; p += blockDim.x) {
+        R x = (R)A.kx[i], y = (R)A.ky[i];
+        double Yv = 1.0, Zv = 0.0;
+        int k = 0;
+        const long rec = (long)slot * A.paths + p;
+        for (;;) {
+            if (k >= max_steps) {
+                A.side[rec] = 2;
+                A.su[rec] = 0.0;
+                A.Y[rec] = 0.0;
+                A.Z[rec] = 0.0;
+                ++my_capped;
+                break;
+            }
+            R xi0, xi1;
+            Num<R>::normals(A.seed, (uint32_t)i, (uint32_t)k, (uint32_t)p, xi0, xi1);
+            R bx, by;
+            Num<R>::drift(P, x, y, bx, by);
+            double Yn = Yv, Zn = Zv;
+            if (KILL) {
+                double cv = (sizeof(R) == 8) ? killing(P, (double)x, (double)y) : (double)killing32(P, (float)x, (float)y);
+                Yn = Yv * (1.0 + cv * A.h);
+            }
+            if (SRC) {
+                double fv = (sizeof(R) == 8) ? source(P, (double)x, (double)y) : (double)source32(P, (float)x, (float)y);
+                Zn = Zv + fv * Yv * A.h;
+            }
+            const R nx = x + bx * h + sh * xi0;
+            const R ny = y + by * h + sh * xi1;
+            ++k;
+            const R ddx = nx - rcx, ddy = ny - rcy;
+            const bool out_c = !(ddx * ddx + ddy * ddy < r2);
+            const bool out_d = !inside_domain(P, (double)nx, (double)ny);
+            if (!out_c && !out_d) {
+                x = nx;
+                y = ny;
+                Yv = Yn;
+                Zv = Zn;
+                continue;
+            }
+            // exit point on the segment (in FP64 from the FP64 or FP32 end points)
+            const double xd = (double)x, yd = (double)y;
+            const double dx = (double)nx - xd, dy = (double)ny - yd;
+            double tc = 2.0, td = 2.0;
+            int ed = -1;
+            if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
+            if (out_d) {
+                if (P.dom_kind == 0) {
+                    double t;
+                    if ((double)nx <= P.dom[0]) { t = (P.dom[0] - xd) / dx; if (t < td) { td = t; ed = 3; } }
+                    if ((double)nx >= P.dom[2]) { t = (P.dom[2] - xd) / dx; if (t < td) { td = t; ed = 1; } }
+                    if ((double)ny <= P.dom[1]) { t = (P.dom[1] - yd) / dy; if (t < td) { td = t; ed = 0; } }
+                    if ((double)ny >= P.dom[3]) { t = (P.dom[3] - yd) / dy; if (t < td) { td = t; ed = 2; } }
+                } else {
+                    td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
+                    ed = 0;
+                }
+            }
+            if (td <= tc) {
+                const double ex = xd + td * dx, ey = yd + td * dy;
+                A.side[rec] = 1;
+                A.su[rec] = boundary_s(P, ex, ey, ed);
+            } else {
+                const double ex = xd + tc * dx, ey = yd + tc * dy;
+                double th = atan2(ey - cy, ex - cx);
+                if (th < 0.0) th += PDD_TWO_PI;
+                double u = th - ts;
+                if (u < 0.0) u += PDD_TWO_PI;
+                if (u >= PDD_TWO_PI) u -= PDD_TWO_PI;
+                A.side[rec] = 0;
+                A.su[rec] = u;
+            }
+            A.Y[rec] = Yn;
+            A.Z[rec] = Zn;
+            break;
+        }
+        my_steps += (unsigned long long)k;
+    }
+    // block totals
+    __shared__ unsigned long long ss[8];
+    __shared__ int sc[8];
+    for (int o = 16; o; o >>= 1) {
+        my_steps += __shfl_xor_sync(0xffffffffu, my_steps, o);
+        my_capped += __shfl_xor_sync(0xffffffffu, my_capped, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = my_steps;
+        sc[threadIdx.x >> 5] = my_capped;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        int c = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += ss[w];
+            c += sc[w];
+        }
+        atomicAdd(A.steps, t);
+        if (c) atomicAdd(A.capped, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a12
+// ---------------------------------------------------------------------------
+struct FinalArgs {
+    const int *rows, *row_sub, *knot_ptr, *rowptr;
+    const uint8_t *floating;
+    const double *ku;
+    const long *kinv_off;     // per circle (-1 when not IMQ)
+    const double *kinv;
+    double c2;
+    int paths, mc_floating;
+    const int8_t *side;
+    const double *su, *Y, *Z;
+    const int *mom_ptr;
+    double *moments, *bmean, *val, *se, *b, *se_b;
+};
+
+__global__ void __launch_bounds__(1024) k_mc_finalize(Problem P, FinalArgs F) {
+    extern __shared__ double fsm[];                   // [32 batches][ns] moments, then per-batch C
+    __shared__ double bsum[kBatches];
+    __shared__ int bcnt[kBatches];
+    const int slot = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = F.rows[slot], m = F.row_sub[i];
+    const int a = F.knot_ptr[m], ns = F.knot_ptr[m + 1] - a;
+    const bool imq = !F.floating[m];
+    double *Mb = fsm;                                 // kBatches x ns
+    double *Cb = fsm + kBatches * ns;                 // kBatches x ns
+    double acc[kMaxStencil / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxStencil / 32; ++q) acc[q] = 0.0;
+    double bs = 0.0;
+    int cnt = 0;
+    const long base = (long)slot * F.paths;
+    for (int p = warp; p < F.paths; p += kBatches) {
+        const int sd = F.side[base + p];
+        if (sd == 2) continue;
+        ++cnt;
+        const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
+        if (sd == 1) {
+            if (lane == 0) {
+                double ex, ey;
+                boundary_point(P, su, ex, ey);
+                bs += gdata(P, ex, ey, su) * yv + zv;
+            }
+        } else {
+            if (lane == 0) bs += zv;
+#pragma unroll
+            for (int q = 0; q < kMaxStencil / 32; ++q) {
+                const int l = lane + 32 * q;
+                if (l < ns) {
+                    double phi;
+                    if (imq) {
+                        const double d = su - F.ku[a + l];
+                        phi = 1.0 / sqrt(d * d + F.c2);
+                    } else {
+                        // Fourier cardinal of knot l (Eq. 18), closed form
+                        double x = remainder(su - PDD_TWO_PI * l / ns, PDD_TWO_PI);
+                        phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
+                    }
+                    acc[q] += yv * phi;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxStencil / 32; ++q) {
+        const int l = lane + 32 * q;
+        if (l < ns) Mb[warp * ns + l] = acc[q];
+    }
+    if (lane == 0) {
+        bsum[warp] = bs;
+        bcnt[warp] = cnt;
+    }
+    __syncthreads();
+    // per-batch C estimates (batch means)
+    const double *Ki = imq ? F.kinv + F.kinv_off[m] : nullptr;
+    for (int j = lane; j < ns; j += 32) {
+        double v = 0.0;
+        const int nb = bcnt[warp];
+        if (imq) {
+            for (int l = 0; l < ns; ++l) v -= Ki[l * ns + j] * Mb[warp * ns + l];
+        } else {
+            v = -Mb[warp * ns + j];
+        }
+        Cb[warp * ns + j] = nb ? v / nb : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int ntot = 0;
+        for (int w = 0; w < kBatches; ++w) ntot += bcnt[w];
+        const double inv = ntot ? 1.0 / ntot : 0.0;
+        const int off = (i < a) ? 1 : 0;
+        const long rp = F.rowptr[i];
+        for (int j = lane; j < ns; j += 32) {
+            double mean = 0.0, msum = 0.0;
+            for (int w = 0; w < kBatches; ++w) {
+                mean += bcnt[w] * Cb[w * ns + j];
+                msum += Mb[w * ns + j];
+            }
+            mean *= inv;
+            double var = 0.0;
+            for (int w = 0; w < kBatches; ++w) {
+                double f = bcnt[w] * inv, d = Cb[w * ns + j] - mean;
+                var += f * f * d * d;
+            }
+            var *= (double)kBatches / (kBatches - 1);
+            F.val[rp + off + j] = mean;
+            F.se[rp + off + j] = sqrt(var);
+            F.moments[F.mom_ptr[slot] + j] = msum * inv;
+        }
+        if (lane == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < kBatches; ++w) tot += bsum[w];
+            const double bm = tot * inv;
+            double var = 0.0;
+            for (int w = 0; w < kBatches; ++w) {
+                if (!bcnt[w]) continue;
+                double f = bcnt[w] * inv, d = bsum[w] / bcnt[w] - bm;
+                var += f * f * d * d;
+            }
+            var *= (double)kBatches / (kBatches - 1);
+            F.b[i] = bm;
+            F.bmean[slot] = bm;
+            F.se_b[i] = sqrt(var);
+        }
+    }
+}
+
+// rows integrated by Monte Carlo: flag + compaction
+__global__ void k_mc_flag(int N, const int *row_sub, const uint8_t *floating, int mc_floating, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int m = row_sub[i];
+    flag[i] = (m >= 0 && (!floating[m] || mc_floating)) ? 1 : 0;
+}
+
+__global__ void k_mc_compact(int N, const int *flag, const int *pos, const int *row_sub,
+                             const int *knot_ptr, int *rows, int *ns) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || !flag[i]) return;
+    int s = pos[i], m = row_sub[i];
+    rows[s] = i;
+    ns[s] = knot_ptr[m + 1] - knot_ptr[m];
+}
+
+void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, DevBuf<long> &koff_m,
+                        cudaStream_t st) {
+    if (cov.max_stencil > kMaxStencil) fail(PDD_EINVAL, "stencil larger than the Monte Carlo kernels support");
+    std::vector<int> per;
+    std::vector<long> off(cov.M, -1);
+    long tot = 0;
+    for (int m = 0; m < cov.M; ++m) {
+        int n = cov.h_knot_ptr[m + 1] - cov.h_knot_ptr[m];
+        if (!cov.h_floating[m] && n > 0) {
+            per.push_back(m);
+            off[m] = tot;
+            tot += (long)n * n;
+        }
+    }
+    DevBuf<long> koff_c;
+    DevBuf<int> circ, bad;
+    kinv.alloc(std::max<long>(tot, 1));
+    koff_m.alloc(cov.M);
+    bad.alloc(1);
+    PDD_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    PDD_CUDA(cudaMemcpyAsync(koff_m.p, off.data(), cov.M * sizeof(long), cudaMemcpyHostToDevice, st));
+    if (!per.empty()) {
+        std::vector<long> offc(per.size());
+        for (size_t q = 0; q < per.size(); ++q) offc[q] = off[per[q]];
+        circ.alloc(per.size());
+        koff_c.alloc(per.size());
+        PDD_CUDA(cudaMemcpyAsync(circ.p, per.data(), per.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        PDD_CUDA(cudaMemcpyAsync(koff_c.p, offc.data(), per.size() * sizeof(long), cudaMemcpyHostToDevice, st));
+        const size_t smem = (size_t)2 * cov.max_stencil * cov.max_stencil * sizeof(double);
+        PDD_CUDA(cudaFuncSetAttribute(k_imq_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, koff_c.p, c2,
+                   kinv.p, bad.p);
+    }
+    int hb = 0;
+    PDD_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaStreamSynchronize(st));
+    if (hb) fail(PDD_EINVAL, "IMQ matrix not positive definite (coincident stencil angles)");
+}
+
+template <typename R>
+static void launch_paths(const Problem &P, const PathArgs &A, int nrows, cudaStream_t st) {
+    const bool kill = P.c_kind != PDD_C_ZERO, src = P.f_kind != PDD_F_ZERO;
+    if (kill && src) PDD_LAUNCH((k_paths<R, true, true>), nrows, 256, 0, st, P, A);
+    else if (kill) PDD_LAUNCH((k_paths<R, true, false>), nrows, 256, 0, st, P, A);
+    else if (src) PDD_LAUNCH((k_paths<R, false, true>), nrows, 256, 0, st, P, A);
+    else PDD_LAUNCH((k_paths<R, false, false>), nrows, 256, 0, st, P, A);
+}
+
+McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o, pdd_system &sys,
+                    cudaStream_t st) {
+    McStats ms;
+    const int N = cov.N;
+    const int mcf = o.floating_method == PDD_FLOATING_MONTE_CARLO ? 1 : 0;
+    DevBuf<int> flag, pos;
+    flag.alloc(N + 1);
+    pos.alloc(N + 1);
+    PDD_LAUNCH(k_mc_flag, cdiv(N, 256), 256, 0, st, N, cov.row_sub.p, cov.floating.p, mcf, flag.p);
+    const int nmc = (int)exclusive_scan(flag.p, pos.p, N, st);
+    sys.n_mc = nmc;
+    ms.rows = nmc;
+    if (nmc == 0) return ms;
+    sys.mc_rows.alloc(nmc);
+    DevBuf<int> ns;
+    ns.alloc(nmc + 1);
+    sys.mom_ptr.alloc(nmc + 1);
+    PDD_LAUNCH(k_mc_compact, cdiv(N, 256), 256, 0, st, N, flag.p, pos.p, cov.row_sub.p, cov.knot_ptr.p,
+               sys.mc_rows.p, ns.p);
+    const int nmom = (int)exclusive_scan(ns.p, sys.mom_ptr.p, nmc, st);
+    sys.moments.alloc(std::max(nmom, 1));
+    sys.bmean.alloc(nmc);
+
+    // a10: IMQ inverses for every perimeter circle with a stencil
+    DevBuf<double> kinv;
+    DevBuf<long> koff_m;
+    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, st);
+
+    // a11: paths into the record scratch, in waves that bound the scratch size
+    const long P_ = o.paths;
+    const size_t per_row = (size_t)P_ * (1 + 3 * sizeof(double));
+    const int wave = (int)std::max<size_t>(1, std::min<size_t>(nmc, ((size_t)8 << 30) / per_row));
+    DevBuf<int8_t> side;
+    DevBuf<double> su, Y, Z;
+    side.alloc((size_t)wave * P_);
+    su.alloc((size_t)wave * P_);
+    Y.alloc((size_t)wave * P_);
+    Z.alloc((size_t)wave * P_);
+    DevBuf<unsigned long long> steps;
+    DevBuf<int> capped;
+    steps.alloc(1);
+    capped.alloc(1);
+    PDD_CUDA(cudaMemsetAsync(steps.p, 0, sizeof(unsigned long long), st));
+    PDD_CUDA(cudaMemsetAsync(capped.p, 0, sizeof(int), st));
+    cudaEvent_t e0, e1, e2;
+    PDD_CUDA(cudaEventCreate(&e0));
+    PDD_CUDA(cudaEventCreate(&e1));
+    PDD_CUDA(cudaEventCreate(&e2));
+    float tp = 0, tf = 0;
+    for (int w0 = 0; w0 < nmc; w0 += wave) {
+        const int nr = std::min(wave, nmc - w0);
+        PathArgs A{sys.mc_rows.p + w0, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
+                   cov.theta_s.p, o.paths, o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p};
+        PDD_CUDA(cudaEventRecord(e0, st));
+        if (o.precision == PDD_PREC_MIXED) launch_paths<float>(P, A, nr, st);
+        else launch_paths<double>(P, A, nr, st);
+        PDD_CUDA(cudaEventRecord(e1, st));
+        FinalArgs F{sys.mc_rows.p + w0, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p, cov.ku.p,
+                    koff_m.p, kinv.p, o.imq_c2, o.paths, mcf, side.p, su.p, Y.p, Z.p, sys.mom_ptr.p + w0,
+                    sys.moments.p, sys.bmean.p + w0, sys.val.p, sys.se.p, sys.b.p, sys.se_b.p};
+        const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
+        PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+        PDD_LAUNCH(k_mc_finalize, nr, 1024, fsm, st, P, F);
+        PDD_CUDA(cudaEventRecord(e2, st));
+        PDD_CUDA(cudaEventSynchronize(e2));
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+        tp += a;
+        tf += b;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    unsigned long long hs = 0;
+    int hc = 0;
+    PDD_CUDA(cudaMemcpyAsync(&hs, steps.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaMemcpyAsync(&hc, capped.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaStreamSynchronize(st));
+    ms.steps = (int64_t)hs;
+    ms.capped = hc;
+    ms.ms_paths = tp;
+    ms.ms_finalize = tf;
+    return ms;
+}
+
+}  // namespace pdd
+
+// ---------------------------------------------------------------------------
+// a14 (perimeter rows): replay each row's paths with the same Philox streams
+// (common random numbers).  The paths X do not depend on c, f or g; only the
+// weights do.  With S_q = sum_k 1{c<0} psi_q(X_k) h / (1 + c(X_k) h),
+// dY_tau/dw_q = Y_tau S_q and dZ/dw_q = sum_k f(X_k) h Y_k S_q(k).  The row adds
+// lambda_i E[(1_dOmega g + 1_Gamma u_hat) dY_q + dZ_q] to dJ/dw_q and
+// lambda_i E[1_dOmega psi^g_k(s) Y_tau] to dJ/da_k.
+// ---------------------------------------------------------------------------
+namespace pdd {
+
+struct GradArgs {
+    const double *u, *lambda;
+    const int *knot_ptr;
+    const uint8_t *floating;
+    const double *ku;
+    const long *kinv_off;
+    const double *kinv;
+    double c2;
+    int n_par;
+    double *partial;          // [slot][n_rbf + n_gcoef]
+};
+
+template <typename R, bool SRC>
+__global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradArgs G) {
+    extern __shared__ double gsm[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int nw = P.n_rbf, ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
+    double *alpha = gsm;                         // kMaxStencil
+    double *S = alpha + kMaxStencil;             // [nw][T]
+    double *dZ = S + (size_t)nw * T;             // [nw][T]
+    double *Gw = dZ + (size_t)nw * T;            // [nw][T]
+    double *Gg = Gw + (size_t)nw * T;            // [ng][T]
+    const int slot = blockIdx.x;
+    const int i = A.rows[slot], m = A.row_sub[i];
+    const int a = G.knot_ptr[m], ns = G.knot_ptr[m + 1] - a;
+    const bool imq = !G.floating[m];
+    // u_hat(u) = sum_l alpha_l phi_l(u) (IMQ) or sum_j u_j H_j(theta) (Fourier cardinals)
+    for (int l = tid; l < ns; l += T) {
+        double v = 0.0;
+        if (imq) {
+            const double *Ki = G.kinv + G.kinv_off[m];
+            for (int j = 0; j < ns; ++j) v += Ki[l * ns + j] * G.u[a + j];
+        } else {
+            v = G.u[a + l];
+        }
+        alpha[l] = v;
+    }
+    for (int q = 0; q < nw; ++q) Gw[q * T + tid] = 0.0;
+    for (int k = 0; k < ng; ++k) Gg[k * T + tid] = 0.0;
+    __syncthreads();
+    const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m];
+    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
+    const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
+    const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
+    const double inv2s = nw ? 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma) : 0.0;
+    for (int p = tid; p < A.paths; p += T) {
+        R x = (R)A.kx[i], y = (R)A.ky[i];
+        double Yv = 1.0, Zv = 0.0;
+        for (int q = 0; q < nw; ++q) {
+            S[q * T + tid] = 0.0;
+            dZ[q * T + tid] = 0.0;
+        }
+        int k = 0;
+        int side = 2;
+        double su = 0.0;
+        for (;;) {
+            if (k >= max_steps) break;
+            R xi0, xi1;
+            Num<R>::normals(A.seed, (uint32_t)i, (uint32_t)k, (uint32_t)p, xi0, xi1);
+            R bx, by;
+            Num<R>::drift(P, x, y, bx, by);
+            const double xd = (double)x, yd = (double)y;
+            double cv = 0.0;
+            if (P.c_kind == PDD_C_RBF) {
+                double s = 0.0;
+                for (int q = 0; q < nw; ++q) {
+                    const double ddx = xd - P.rbf_x[q], ddy = yd - P.rbf_y[q];
+                    s += P.rbf_w[q] * exp(-(ddx * ddx + ddy * ddy) * inv2s);
+                }
+                cv = s < 0.0 ? s : 0.0;
+            } else {
+                cv = (sizeof(R) == 8) ? killing(P, xd, yd) : (double)killing32(P, (float)x, (float)y);
+            }
+            const double fv = SRC ? ((sizeof(R) == 8) ? source(P, xd, yd) : (double)source32(P, (float)x, (float)y)) : 0.0;
+            if (nw && cv < 0.0) {
+                const double fac = A.h / (1.0 + cv * A.h);
+                for (int q = 0; q < nw; ++q) {
+                    const double ddx = xd - P.rbf_x[q], ddy = yd - P.rbf_y[q];
+                    const double psi = exp(-(ddx * ddx + ddy * ddy) * inv2s);
+                    if (SRC) dZ[q * T + tid] += fv * A.h * Yv * S[q * T + tid];
+                    S[q * T + tid] += psi * fac;
+                }
+            } else if (SRC && nw) {
+                for (int q = 0; q < nw; ++q) dZ[q * T + tid] += fv * A.h * Yv * S[q * T + tid];
+            }
+            const double Yn = Yv * (1.0 + cv * A.h);
+            const double Zn = Zv + fv * Yv * A.h;
+            const R nx = x + bx * h + sh * xi0;
+            const R ny = y + by * h + sh * xi1;
+            ++k;
+            const R ddx = nx - rcx, ddy = ny - rcy;
+            const bool out_c = !(ddx * ddx + ddy * ddy < r2);
+            const bool out_d = !inside_domain(P, (double)nx, (double)ny);
+            if (!out_c && !out_d) {
+                x = nx;
+                y = ny;
+                Yv = Yn;
+                Zv = Zn;
+                continue;
+            }
+            const double dx = (double)nx - xd, dy = (double)ny - yd;
+            double tc = 2.0, td = 2.0;
+            int ed = -1;
+            if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
+            if (out_d) {
+                if (P.dom_kind == 0) {
+                    double t;
+                    if ((double)nx <= P.dom[0]) { t = (P.dom[0] - xd) / dx; if (t < td) { td = t; ed = 3; } }
+                    if ((double)nx >= P.dom[2]) { t = (P.dom[2] - xd) / dx; if (t < td) { td = t; ed = 1; } }
+                    if ((double)ny <= P.dom[1]) { t = (P.dom[1] - yd) / dy; if (t < td) { td = t; ed = 0; } }
+                    if ((double)ny >= P.dom[3]) { t = (P.dom[3] - yd) / dy; if (t < td) { td = t; ed = 2; } }
+                } else {
+                    td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
+                    ed = 0;
+                }
+            }
+            if (td <= tc) {
+                side = 1;
+                su = boundary_s(P, xd + td * dx, yd + td * dy, ed);
+            } else {
+                const double ex = xd + tc * dx, ey = yd + tc * dy;
+                double th = atan2(ey - cy, ex - cx);
+                if (th < 0.0) th += PDD_TWO_PI;
+                double uu = th - A.theta_s[m];
+                if (uu < 0.0) uu += PDD_TWO_PI;
+                if (uu >= PDD_TWO_PI) uu -= PDD_TWO_PI;
+                side = 0;
+                su = uu;
+            }
+            Yv = Yn;
+            Zv = Zn;
+            break;
+        }
+        if (side == 2) continue;
+        double payoff;
+        if (side == 1) {
+            double ex, ey;
+            boundary_point(P, su, ex, ey);
+            payoff = gdata(P, ex, ey, su);
+            if (ng) {
+                const int kc = (P.n_gcoef + 1) / 2;
+                const double wv = PDD_TWO_PI * su / P.perimeter;
+                for (int kk = 0; kk < ng; ++kk) {
+                    const double basis = (kk < kc) ? cos(kk * wv) : sin((kk - kc + 1) * wv);
+                    Gg[kk * T + tid] += Yv * basis;
+                }
+            }
+        } else {
+            payoff = 0.0;
+            for (int l = 0; l < ns; ++l) {
+                double ph;
+                if (imq) {
+                    const double d = su - G.ku[a + l];
+                    ph = 1.0 / sqrt(d * d + G.c2);
+                } else {
+                    double xx = remainder(su - PDD_TWO_PI * l / ns, PDD_TWO_PI);
+                    ph = (xx == 0.0) ? 1.0 : sin(0.5 * ns * xx) * cos(0.5 * xx) / (sin(0.5 * xx) * ns);
+                }
+                payoff += alpha[l] * ph;
+            }
+        }
+        for (int q = 0; q < nw; ++q) Gw[q * T + tid] += payoff * Yv * S[q * T + tid] + dZ[q * T + tid];
+    }
+    __syncthreads();
+    const double scale = G.lambda[i] / A.paths;
+    for (int q = tid; q < nw + ng; q += T) {
+        const double *src = (q < nw) ? Gw + (size_t)q * T : Gg + (size_t)(q - nw) * T;
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += src[t];
+        G.partial[(long)slot * G.n_par + q] = scale * s;
+    }
+}
+
+void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o, const pdd_system &sys,
+             const double *u, const double *lambda, DevBuf<double> &partial, int &n_part, cudaStream_t st) {
+    n_part = 0;
+    const int nmc = sys.n_mc;
+    const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
+    const int ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
+    if (nmc == 0 || nw + ng == 0) return;
+    DevBuf<double> kinv;
+    DevBuf<long> koff_m;
+    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, st);
+    const int n_par = P.n_rbf + P.n_gcoef;
+    partial.alloc((size_t)nmc * n_par);
+    PDD_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double) * nmc * n_par, st));
+    DevBuf<unsigned long long> steps;
+    DevBuf<int> capped;
+    steps.alloc(1);
+    capped.alloc(1);
+    PathArgs A{sys.mc_rows.p, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p,
+               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p};
+    GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
+    const int T = 64;
+    const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);
+    if (smem > 220 * 1024) fail(PDD_EINVAL, "too many gradient parameters for the replay kernel");
+    const bool src = P.f_kind != PDD_F_ZERO;
+#define PDD_GRAD_LAUNCH(R, SRCV)                                                                          \
+    do {                                                                                                  \
+        PDD_CUDA(cudaFuncSetAttribute(k_paths_grad<R, SRCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem));                                                       \
+        PDD_LAUNCH((k_paths_grad<R, SRCV>), nmc, T, smem, st, P, A, G);                                   \
+    } while (0)
+    if (o.precision == PDD_PREC_MIXED) {
+        if (src) PDD_GRAD_LAUNCH(float, true); else PDD_GRAD_LAUNCH(float, false);
+    } else {
+        if (src) PDD_GRAD_LAUNCH(double, true); else PDD_GRAD_LAUNCH(double, false);
+    }
+#undef PDD_GRAD_LAUNCH
+    n_part = nmc;
+}
+
+}  // namespace pdd

@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars:
+  * cover, knots, row owners, CSR pattern: bit-exact (knot coordinates to
+    a few ulps: both sides call their own cos/sin);
+  * floating rows (pseudospectral): <= 1e-10 relative, normwise per row, FP64
+    and mixed (FP32 LU + FP64 refinement);
+  * Monte Carlo rows, FP64 form on identical Philox streams: raw moments and
+    b <= 1e-12 relative; C entries <= 1e-12 + 16 kappa(K) eps (the IMQ solve's
+    rounding);
+  * Monte Carlo rows, mixed form (FP32 positions): within 4 standard errors
+    of the FP64 oracle on every entry checked (the two forms draw different
+    normals), aggregate z^2 near 1;
+  * u: <= 1e-10 relative against the oracle's direct solve of its own system.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import cover as ocover
+from oracle import imq as oimq
+from oracle import krylov as okrylov
+from oracle import system as osystem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pdd():
+    import paper_2311_08946_gb300 as pkg
+    from paper_2311_08946_gb300 import build
+    build.build()
+    pkg.load()
+    return pkg
+
+
+_cache = {}
+
+
+def _oracle_cover(name, cfg):
+    key = ("cover", name)
+    if key not in _cache:
+        _cache[key] = ocover.full_cover(cfg)
+    return _cache[key]
+
+
+def _np(d):
+    return {k: v.cpu().numpy() for k, v in d.items()}
+
+
+COVERS = [("tiny", workloads.tiny), ("varcoef", workloads.varcoef), ("scaled", workloads.scaled)]
+
+
+@pytest.mark.parametrize("name,fn", COVERS)
+def test_cover_bit_exact(pdd, name, fn):
+    cfg = fn()
+    cov = pdd.Cover(cfg)
+    oc = _oracle_cover(name, cfg)
+    a = _np(cov.arrays())
+    assert (cov.M, cov.N, cov.nnz) == (oc.M, oc.N, oc.col.size)
+    assert cov.M_floating == int(oc.floating.sum())
+    assert np.array_equal(a["floating"].astype(bool), oc.floating)
+    for k in ("knot_ptr", "kowner", "row_sub", "rowptr", "col"):
+        assert np.array_equal(a[k].astype(np.int64), getattr(oc, k).astype(np.int64)), k
+    assert np.array_equal(a["kdir"].astype(bool), oc.kdir)
+    assert np.array_equal(a["cx"], oc.cx) and np.array_equal(a["cy"], oc.cy) and np.array_equal(a["r"], oc.r)
+    for k in ("kx", "ky", "ku"):
+        assert np.abs(a[k] - getattr(oc, k)).max() <= 8e-16 * max(1.0, np.abs(getattr(oc, k)).max()), k
+
+
+def _row_err(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_floating_rows_tiny(pdd, precision):
+    cfg = workloads.tiny(paths=64)
+    oc = _oracle_cover("tiny", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, precision)
+    g = _np(S.csr())
+    ref = osystem.assemble(cfg, oc, rows=[i for i in range(oc.N) if oc.row_sub[i] >= 0 and oc.floating[oc.row_sub[i]]])
+    assert len(ref.fl_rows) == 64
+    for i in ref.fl_rows:
+        a, b = oc.rowptr[i], oc.rowptr[i + 1]
+        assert _row_err(g["val"][a:b], ref.vals[a:b]) < 1e-10, i
+        assert abs(g["b"][i] - ref.b[i]) <= 1e-10 * max(abs(ref.b[i]), 1e-3 * np.abs(ref.b).max() + 1e-300)
+    st = S.stats()
+    assert st["floating_disks"] == 4 and st["floating_rows"] == 64
+    if precision == "mixed":
+        assert st["unconverged_disks"] == 0 and st["max_refine_sweeps"] >= 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_floating_rows_varcoef_sampled(pdd, precision):
+    """Full-size variable-coefficient workload; 6 disks recomputed by the oracle."""
+    cfg = workloads.varcoef(paths=64)
+    oc = _oracle_cover("varcoef", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, precision)
+    g = _np(S.csr())
+    rng = np.random.default_rng(4)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    from oracle import problem, spectral
+    op = problem.Operator(cfg["op"], oc.domain)
+    shapes = {}
+    for m in rng.choice(disks, 6, replace=False):
+        res = spectral.floating_rows(oc, op, int(m), shapes)
+        for i, (cols, v, bi) in res.items():
+            a, b = oc.rowptr[i], oc.rowptr[i + 1]
+            rc = oc.col[a:b]
+            pos = np.searchsorted(rc, cols)
+            assert _row_err(g["val"][a + pos], v) < 1e-10, (m, i)
+            assert abs(g["b"][i] - bi) <= 1e-10 * max(abs(bi), 1e-3)
+    if precision == "mixed":
+        assert S.stats()["unconverged_disks"] == 0
+
+
+def test_mc_rows_identical_streams_tiny(pdd):
+    cfg = workloads.tiny(paths=500)
+    oc = _oracle_cover("tiny", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    g = _np(S.csr())
+    mc = _np(S.mc())
+    rows = mc["rows"]
+    ref = osystem.assemble(cfg, oc, rows=list(rows), threads=4)
+    assert len(ref.mc_rows) == rows.size > 100
+    for k, i in enumerate(rows):
+        r = ref.mc_rows[int(i)]
+        got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
+        assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max()), i
+        assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
+        a, b = oc.rowptr[i], oc.rowptr[i + 1]
+        rc = oc.col[a:b]
+        pos = np.searchsorted(rc, r.cols)
+        kap = oimq.condition(r.u_stencil, 1.5) if r.u_stencil.size else 1.0
+        tol = 1e-12 + 16 * kap * np.finfo(float).eps
+        assert np.abs(g["val"][a + pos] - r.vals).max() <= tol * max(1.0, np.abs(r.vals).max()), i
+        # batch-means standard errors against the per-path ones (31 degrees of freedom)
+        ok = r.se > 0
+        if np.any(ok):
+            ratio = g["se"][a + pos][ok] / r.se[ok]
+            assert 0.4 < np.median(ratio) < 1.6
+    st = S.stats()
+    assert st["path_steps"] == sum(r.steps for r in ref.mc_rows.values())
+
+
+def test_mc_rows_identical_streams_varcoef_sampled(pdd):
+    """Full-size variable-coefficient workload (10^4 paths, h = 1e-5), 6 rows recomputed."""
+    cfg = workloads.varcoef()
+    oc = _oracle_cover("varcoef", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    mc = _np(S.mc())
+    rows = mc["rows"]
+    rng = np.random.default_rng(11)
+    pick = rng.choice(rows.size, 6, replace=False)
+    ref = osystem.assemble(cfg, oc, rows=[int(rows[k]) for k in pick], threads=6)
+    for k in pick:
+        i = int(rows[k])
+        r = ref.mc_rows[i]
+        got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
+        assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max()), i
+        assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
+
+
+def test_mc_mixed_within_standard_errors(pdd):
+    cfg = workloads.tiny(paths=2000)
+    oc = _oracle_cover("tiny", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "mixed")
+    g = _np(S.csr())
+    mc = _np(S.mc())
+    rows = [int(i) for i in mc["rows"][::4]]
+    ref = osystem.assemble(cfg, oc, rows=rows, threads=4)
+    z = []
+    for i in rows:
+        r = ref.mc_rows[i]
+        a, b = oc.rowptr[i], oc.rowptr[i + 1]
+        pos = np.searchsorted(oc.col[a:b], r.cols)
+        se = np.sqrt(g["se"][a + pos] ** 2 + r.se ** 2)
+        ok = se > 0
+        z.extend(((g["val"][a + pos] - r.vals)[ok] / se[ok]).tolist())
+        zb = (g["b"][i] - r.b) / math.hypot(g["se_b"][i], r.se_b)
+        z.append(zb)
+    z = np.array(z)
+    assert np.abs(z).max() < 4.0 + 1.5      # 4 SE with margin for the batch-means SE estimate
+    assert np.mean(np.abs(z) > 4.0) < 5e-3
+    assert 0.5 < np.mean(z * z) < 2.0
+
+
+def test_solution_tiny_against_oracle(pdd):
+    cfg = workloads.tiny(paths=300)
+    oc = _oracle_cover("tiny", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    u = S.solve(rtol=1e-14).cpu().numpy()
+    ref = osystem.assemble(cfg, oc, threads=4)
+    uo = okrylov.solve(ref.csr(), ref.b)
+    assert np.abs(u - uo).max() <= 1e-10 * np.abs(uo).max()
+    assert S.last_solve["converged"]
+
+
+def test_gmres_random_csr_against_direct(pdd):
+    import scipy.sparse as sp
+    rng = np.random.default_rng(7)
+    n = 3001
+    A = sp.random(n, n, density=8.0 / n, random_state=7, format="csr") * 0.1 + sp.eye(n) * 2.0
+    A.sort_indices()
+    b = rng.standard_normal(n)
+    rowptr = torch.tensor(A.indptr, dtype=torch.int32, device="cuda")
+    col = torch.tensor(A.indices, dtype=torch.int32, device="cuda")
+    val = torch.tensor(A.data, dtype=torch.float64, device="cuda")
+    bt = torch.tensor(b, dtype=torch.float64, device="cuda")
+    x, info = pdd.solve_csr(rowptr, col, val, bt, rtol=1e-13, restart=30)
+    xr = okrylov.solve(A, b)
+    assert info["converged"] and np.abs(x.cpu().numpy() - xr).max() <= 1e-10 * np.abs(xr).max()
+    xt, info = pdd.solve_csr(rowptr, col, val, bt, rtol=1e-13, restart=30, transpose=True)
+    xrt = okrylov.solve_transpose(A, b)
+    assert info["converged"] and np.abs(xt.cpu().numpy() - xrt).max() <= 1e-10 * np.abs(xrt).max()
+    y = pdd.spmv_csr(rowptr, col, val, bt).cpu().numpy()
+    assert np.abs(y - A @ b).max() <= 1e-13 * np.abs(A @ b).max()
+    yt = pdd.spmv_csr(rowptr, col, val, bt, transpose=True).cpu().numpy()
+    assert np.abs(yt - A.T @ b).max() <= 1e-13 * np.abs(A.T @ b).max()
+
+
+def test_solution_varcoef_residual(pdd):
+    """Full-size workload: the GPU's u solves the GPU's C u = r to the stated tolerance (FP64 check on CPU)."""
+    import scipy.sparse as sp
+    cfg = workloads.varcoef(paths=256)
+    cov = pdd.Cover(cfg)
+    S = pdd.System(cov, cfg, "mixed")
+    u = S.solve(rtol=1e-13).cpu().numpy()
+    a = _np(cov.arrays())
+    g = _np(S.csr())
+    C = sp.csr_matrix((g["val"], a["col"], a["rowptr"]), shape=(cov.N, cov.N))
+    assert np.linalg.norm(C @ u - g["b"]) <= 1.05e-13 * np.linalg.norm(g["b"])
+
+
+def test_adjoint_against_oracle(pdd):
+    from oracle import adjoint as oadj
+    cfg = workloads.grad(paths=64)
+    oc = _oracle_cover("grad", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    u = S.solve(rtol=1e-14)
+    rng = np.random.default_rng(9)
+    u_obs = np.exp(oc.kx) * np.sin(oc.ky) + 0.01 * rng.standard_normal(oc.N)
+    dJ = 2.0 * (u - torch.tensor(u_obs, device="cuda"))
+    g, lam = S.grad(u, dJ, return_lambda=True)
+    g = g.cpu().numpy()
+    ref = osystem.assemble(cfg, oc, with_grad=True)
+    uo = okrylov.solve(ref.csr(), ref.b)
+    gw, ga, lo = oadj.gradient(cfg, ref, uo, 2.0 * (uo - u_obs))
+    want = np.concatenate([gw, ga])
+    assert np.abs(lam.cpu().numpy() - lo).max() <= 1e-9 * np.abs(lo).max()
+    assert np.abs(g - want).max() <= 1e-8 * np.abs(want).max()
+
+
+def test_error_statuses(pdd):
+    cfg = workloads.tiny()
+    bad = dict(cfg)
+    bad["cover"] = dict(cfg["cover"], nx=3)        # drops a column of circles: a gap
+    with pytest.raises(pdd.PddError) as e:
+        pdd.Cover(bad)
+    assert e.value.code == "PDD_ECOVER_GAP"
+    corner = dict(cfg)
+    # a circle through the corners (0,0) and (0,1), exactly representable: degenerate junctions
+    corner["cover"] = {"kind": "explicit", "cx": np.array([0.375, 0.5]), "cy": np.array([0.5, 0.5]),
+                       "r": np.array([0.625, 0.9]), "n_knots": np.array([16, 16], np.int32),
+                       "n_r": np.array([8, 8], np.int32), "n_theta": np.array([16, 16], np.int32)}
+    with pytest.raises(pdd.PddError) as e:
+        pdd.Cover(corner)
+    assert e.value.code == "PDD_EINVAL"
