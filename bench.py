@@ -1,0 +1,455 @@
+"""Throughput of the interfacial-system hot path on GB300.
+
+One step = build_cover + assemble_G (mixed form) + solve on the
+variable-coefficient workload (Omega = [0,2]^2, hexagonal lattice of 1,003
+circles of radius 0.05, 32 knots, 32x32 disk grids, 10^4 paths per
+Monte Carlo knot, h = 1e-5): every row a1-a13 of the hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  value = knots of G assembled and solved per
+second over all ranks (each rank runs its own replica: the path has no
+cross-rank exchange).  Extra keys: the FP64 form on the same GPU, Monte Carlo
+path-steps/s, the adjoint (a14) timed on the gradient workload, errors
+against the FP64 oracle on sampled rows, the roofline of the dominant
+kernel, the oracle timed on the host cores, clocks and launch counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G-assembly knots/s + MC path-steps/s at stated err vs FP64 oracle, mixed vs FP64"
+WORKLOAD = ("varcoef: Omega=[0,2]^2, L=1/2 Lap+(sin x,cos y).grad, c=-(1+x^2+y^2), "
+            "u*=sin(pi x)cos(pi y); hex lattice R=0.05 spacing 0.07 (1003 circles); "
+            "32 knots/circle, 32x32 disk grid; 1e4 paths/knot, h=1e-5")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.fill_(1.0)          # 512 MB write, larger than the 129 MB L2
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def step(pdd, cfg, precision, stream):
+    cov = pdd.Cover(cfg, stream=stream)
+    S = pdd.System(cov, cfg, precision, stream=stream)
+    u = S.solve(rtol=1e-13, restart=64, stream=stream)
+    return cov, S, u
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2311_08946_gb300 as pdd
+    import workloads
+
+    pdd.load()
+    cfg = workloads.varcoef()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        cov, S, u = step(pdd, cfg, "mixed", stream)
+        del cov, S, u
+    torch.cuda.synchronize()
+    times, stats, solve = [], [], []
+    launches0 = pdd.launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            barrier(world)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cov, S, u = step(pdd, cfg, "mixed", stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(S.stats())
+            solve.append(S.last_solve)
+            N = cov.N
+            del cov, S, u
+    launches = (pdd.launch_count() - launches0) // max(1, args.steps)
+    ms = statistics.mean(times)
+    ms_max = max_over_ranks(ms, world)
+    value = world * N / (ms_max / 1e3)
+    st = stats[-1]
+    path_steps = st["path_steps"]
+    mc_rate = path_steps / (statistics.mean(s["ms_paths"] for s in stats) / 1e3)
+
+    # e2e: the public API with host-side inputs, result copied to pinned host memory
+    e2e_times = []
+    u_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    for _ in range(max(2, min(args.steps, 3))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cov, S, u = step(pdd, cfg, "mixed", stream)
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        del cov, S, u
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
+    h2d = 36 + 112 + 72 + 48        # domain, cover spec, operator and option structs
+    e2e = {"value": world * N / e2e_s, "unit": "knots/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": N * 8}
+
+    out = {"metric": METRIC, "value": value, "unit": "knots/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": "mixed (FP32 LU + FP64 refinement; FP32 path "
+                      "positions, FP64 weights and scores)", "knots": N, "l2": "flushed between steps "
+                      "(512 MB write); working set 4+ GB", "parallelism": f"replicas x{world}"},
+           "mc_path_steps_per_s": world * mc_rate, "path_steps_per_step": path_steps,
+           "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
+                                            "ms_refine", "ms_eval", "ms_paths", "ms_finalize")},
+           "gmres": solve[-1], "refine_sweeps_max": st["max_refine_sweeps"],
+           "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary()}
+
+    # roofline of the dominant kernel (device time from CUDA events inside the library)
+    out["roofline"] = roofline(st, cfg, N)
+
+    if not args.no_fp64 and rank == 0:
+        out["fp64_form"] = fp64_form(pdd, cfg, stream, flush)
+    if not args.no_oracle and rank == 0:
+        out["err_vs_oracle"] = errors_vs_oracle(pdd, cfg, stream)
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        out["grad"] = grad_bench(pdd, stream)
+    return out
+
+
+def roofline(st, cfg, N):
+    """Dominant kernel of the mixed step, against its own bound."""
+    pk, src = peaks()
+    stages = {"k_paths (a11)": st["ms_paths"], "k_lu (a7)": st["ms_factor"],
+              "k_lu_solve+k_residual (a8)": st["ms_refine"], "k_disk_eval (a9)": st["ms_eval"],
+              "k_disk_operator (a6)": st["ms_operator"]}
+    top = max(stages, key=stages.get)
+    n = cfg["n_r"] * cfg["n_theta"]
+    disks = st["floating_disks"]
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if top.startswith("k_lu ("):
+        flops = disks * (2.0 / 3.0) * n ** 3
+        # FP32 SIMT FMA: 152 SMs x 128 lanes x 2 flop x clock
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / (st["ms_factor"] / 1e3) / 1e12
+        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "FP32 CUDA-core FMA rate at the measured max SM clock (152x128x2xf)"}
+    if top.startswith("k_paths"):
+        # issue-bound ALU kernel: report FP64 weight updates against the FP64 rate
+        steps = st["path_steps"]
+        ach = steps / (st["ms_paths"] / 1e3) / 1e9
+        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": None, "unit": "Gpath-steps/s",
+                "frac": None, "traffic": None}
+    if top.startswith("k_lu_solve"):
+        nrhs = cfg["n_knots"] + 1
+        nc = 2 * cfg["n_r"] + 1
+        sweeps = max(1, st["max_refine_sweeps"])
+        fp64 = disks * (sweeps - 1) * 2.0 * n * ((nc - 1) + cfg["n_theta"] + 1) * nrhs
+        ach = fp64 / (st["ms_refine"] / 1e3) / 1e12
+        peak = 1.25
+        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64)",
+                "frac": ach / peak, "traffic": None, "peak_source": "nominal GB300 FP64 rate"}
+    return {"kernel": top, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+def fp64_form(pdd, cfg, stream, flush):
+    import torch
+    cov, S, u = step(pdd, cfg, "fp64", stream)      # warm
+    del cov, S, u
+    flush_l2(flush)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cov, S, u = step(pdd, cfg, "fp64", stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = S.stats()
+    res = {"value": cov.N / (ms / 1e3), "unit": "knots/s", "ms_per_step": ms,
+           "mc_path_steps_per_s": st["path_steps"] / (st["ms_paths"] / 1e3),
+           "stages_ms": {k: st[k] for k in ("ms_disks", "ms_factor", "ms_refine", "ms_paths")}}
+    # mixed vs FP64 on every floating row and on u (same GPU)
+    Sm = pdd.System(cov, cfg, "mixed", stream=stream)
+    a = {k: v.cpu() for k, v in cov.arrays().items()}
+    g64 = S.csr()["val"].cpu()
+    g32 = Sm.csr()["val"].cpu()
+    rs = a["row_sub"].numpy()
+    fl = a["floating"].numpy()
+    rp = a["rowptr"].numpy()
+    worst = 0.0
+    for i in range(cov.N):
+        m = rs[i]
+        if m >= 0 and fl[m]:
+            x, y = g64[rp[i]:rp[i + 1]].numpy(), g32[rp[i]:rp[i + 1]].numpy()
+            worst = max(worst, float(abs(x - y).max() / abs(x).max()))
+    res["mixed_vs_fp64_floating_rows_max_rel"] = worst
+    return res
+
+
+def errors_vs_oracle(pdd, cfg, stream):
+    """Sampled floating disks and Monte Carlo rows recomputed by the FP64 oracle."""
+    import numpy as np
+
+    from oracle import cover as ocover
+    from oracle import problem, spectral
+    from oracle import system as osystem
+
+    t0 = time.time()
+    cov = pdd.Cover(cfg, stream=stream)
+    out = {}
+    oc = ocover.full_cover(cfg)
+    a = {k: v.cpu().numpy() for k, v in cov.arrays().items()}
+    out["cover_bit_exact"] = bool(all(np.array_equal(a[k].astype(np.int64), getattr(oc, k).astype(np.int64))
+                                      for k in ("knot_ptr", "kowner", "row_sub", "rowptr", "col")))
+    op = problem.Operator(cfg["op"], oc.domain)
+    rng = np.random.default_rng(0)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    for prec in ("mixed", "fp64"):
+        S = pdd.System(cov, cfg, prec, stream=stream)
+        g = S.csr()["val"].cpu().numpy()
+        worst = 0.0
+        for m in rng.choice(disks, 3, replace=False):
+            for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m)).items():
+                pos = oc.rowptr[i] + np.searchsorted(oc.col[oc.rowptr[i]:oc.rowptr[i + 1]], cols)
+                worst = max(worst, float(np.abs(g[pos] - v).max() / np.abs(v).max()))
+        out[f"floating_rows_{prec}_max_rel"] = worst
+        if prec == "fp64":
+            mc = S.mc()
+            rows = mc["rows"].cpu().numpy()
+            mom = mc["moments"].cpu().numpy()
+            mp = mc["mom_ptr"].cpu().numpy()
+            pick = rng.choice(rows.size, 2, replace=False)
+            ref = osystem.assemble(cfg, oc, rows=[int(rows[k]) for k in pick], threads=2)
+            w = 0.0
+            for k in pick:
+                r = ref.mc_rows[int(rows[k])]
+                w = max(w, float(np.abs(mom[mp[k]:mp[k + 1]] - r.moments).max() / np.abs(r.moments).max()))
+            out["mc_moments_fp64_identical_streams_max_rel"] = w
+    out["oracle_seconds"] = time.time() - t0
+    return out
+
+
+def cpu_baseline(cfg, budget_s=20.0):
+    """The oracle as it stands, on the host cores, over a bounded sample of the workload."""
+    import numpy as np
+
+    from oracle import cover as ocover
+    from oracle import problem, spectral
+    from oracle import system as osystem
+
+    cores = len(os.sched_getaffinity(0))
+    oc = ocover.full_cover(cfg)
+    op = problem.Operator(cfg["op"], oc.domain)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    mc_rows = [i for i in range(oc.N) if oc.row_sub[i] >= 0 and not oc.floating[oc.row_sub[i]]]
+    rng = np.random.default_rng(1)
+    t0 = time.time()
+    nd = 0
+    fl_rows = 0
+    while time.time() - t0 < budget_s / 2 and nd < len(disks):
+        m = int(disks[rng.integers(len(disks))])
+        fl_rows += len(spectral.floating_rows(oc, op, m))
+        nd += 1
+    t_disk = (time.time() - t0) / nd
+    t1 = time.time()
+    picked = list(rng.choice(mc_rows, min(len(mc_rows), 2 * cores), replace=False))
+    ref = osystem.assemble(cfg, oc, rows=[int(i) for i in picked], threads=cores)
+    t_mc_row = (time.time() - t1) / len(picked) * cores          # per row on one core
+    steps = sum(r.steps for r in ref.mc_rows.values())
+    total = (t_disk * len(disks) + t_mc_row * len(mc_rows) / cores)
+    return {"value": oc.N / total, "unit": "knots/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nd} floating disks (Householder QR, {fl_rows} rows) + {len(picked)} Monte Carlo "
+                      f"rows (10^4 paths each, {steps} path-steps) of the workload, extrapolated to all "
+                      f"{len(disks)} disks and {len(mc_rows)} Monte Carlo rows",
+            "mc_path_steps_per_s": steps / (time.time() - t1)}
+
+
+def grad_bench(pdd, stream):
+    """a14 on the gradient workload: forward + adjoint, device time."""
+    import numpy as np
+    import torch
+
+    import workloads
+    cfg = workloads.grad(paths=1000)
+    cov = pdd.Cover(cfg, stream=stream)
+    S = pdd.System(cov, cfg, "fp64", stream=stream)
+    u = S.solve(rtol=1e-14, stream=stream)
+    a = cov.arrays()
+    u_obs = torch.exp(a["kx"]) * torch.sin(a["ky"])
+    dJ = 2.0 * (u - u_obs)
+    S.grad(u, dJ, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g = S.grad(u, dJ, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"workload": "grad: tiny geometry, 64 RBF weights of c + 32 boundary Fourier coefficients of g, "
+                        "1000 paths/knot", "ms": e0.elapsed_time(e1), "n_params": int(g.numel()),
+            "grad_norm": float(g.norm().item())}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import workloads
+    cfg = workloads.varcoef()
+    for _ in range(max(3, args.warmup) if args.warmup > 0 else 0):
+        pass
+    vals = []
+    bl = None
+    for _ in range(max(1, args.steps)):
+        bl = cpu_baseline(cfg, budget_s=max(4.0, 60.0 / max(1, args.steps)))
+        vals.append(bl["value"])
+    value = statistics.mean(vals)
+    bl["value"] = value
+    return {"metric": METRIC, "value": value, "unit": "knots/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * 30202 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"}, "impl": "reference",
+            "cpu_baseline": bl, "e2e": {"value": value, "unit": "knots/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    rank, world, _ = dist_setup(args.gpus)
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

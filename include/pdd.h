@@ -168,9 +168,13 @@ typedef struct {
     int max_refine_sweeps;    /* most refinement sweeps any disk needed              */
     int unconverged_disks;    /* disks whose refinement missed refine_tol            */
     double ms_cover_rows;     /* device time per stage (CUDA events), milliseconds   */
-    double ms_disks;
-    double ms_paths;
-    double ms_finalize;
+    double ms_disks;          /*   all floating-disk work (a6-a9)                    */
+    double ms_paths;          /*   Euler-Maruyama path kernel (a11)                  */
+    double ms_finalize;       /*   Monte Carlo finalize (a12)                         */
+    double ms_operator;       /*   collocation operator build (a6)                   */
+    double ms_factor;         /*   batched LU (a7)                                    */
+    double ms_refine;         /*   solves and refinement residuals (a8)              */
+    double ms_eval;           /*   evaluation at the knots (a9)                       */
 } pdd_assembly_stats;
 
 /*

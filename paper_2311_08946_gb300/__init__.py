@@ -80,7 +80,9 @@ class _AssemblyStats(ctypes.Structure):
                 ("capped_paths", ctypes.c_int64), ("max_refine_sweeps", ctypes.c_int),
                 ("unconverged_disks", ctypes.c_int), ("ms_cover_rows", ctypes.c_double),
                 ("ms_disks", ctypes.c_double), ("ms_paths", ctypes.c_double),
-                ("ms_finalize", ctypes.c_double)]
+                ("ms_finalize", ctypes.c_double), ("ms_operator", ctypes.c_double),
+                ("ms_factor", ctypes.c_double), ("ms_refine", ctypes.c_double),
+                ("ms_eval", ctypes.c_double)]
 
 
 class _SolveOpts(ctypes.Structure):

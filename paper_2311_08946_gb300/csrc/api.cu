@@ -258,6 +258,10 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.ms_disks = t12;
         S.ms_paths = ms.ms_paths;
         S.ms_finalize = ms.ms_finalize;
+        S.ms_operator = ds.ms_operator;
+        S.ms_factor = ds.ms_factor;
+        S.ms_refine = ds.ms_refine;
+        S.ms_eval = ds.ms_eval;
         if (ms.capped) fail(PDD_EPATH_CAP, std::to_string(ms.capped) + " paths reached the step cap");
         if (ds.unconverged)
             fail(PDD_ENOCONV, std::to_string(ds.unconverged) + " disks missed the refinement tolerance");

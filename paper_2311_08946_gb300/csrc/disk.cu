@@ -604,9 +604,13 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     for (size_t w0 = 0; w0 < disks.size(); w0 += wave) {
         const int nd = (int)std::min<size_t>(wave, disks.size() - w0);
         PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
+        StageTimer tm(st, 5);
+        tm.mark(0);
         dim3 g_op(cdiv(S.n, 8), nd);
         PDD_LAUNCH(k_disk_operator<T>, g_op, 256, 0, st, P, S, dd.p, A.p, sA, RHS.p, sR, coef.p, sC);
+        tm.mark(1);
         launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
+        tm.mark(2);
         if (!mixed) {
             PDD_LAUNCH(k_lu_solve<T>, nd, 256, 0, st, A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0,
                        (int *)nullptr, (int *)nullptr, 0.0);
@@ -625,6 +629,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                 if (s + 1 < maxs)
                     PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p);
             }
+            tm.mark(3);
             std::vector<int> hc(nd), hs(nd);
             PDD_CUDA(cudaMemcpyAsync(hc.data(), conv.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
             PDD_CUDA(cudaMemcpyAsync(hs.data(), sweeps.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -634,6 +639,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                 ds.unconverged += hc[d] ? 0 : 1;
             }
         }
+        if (!mixed) tm.mark(3);
         const int group = (S.nrhs <= 32) ? 32 : ((S.nrhs <= 64) ? 64 : 128);
         const size_t rowb = (size_t)(S.n + S.nt) * sizeof(double);
         const int per = (int)std::min<size_t>(256 / group, (180 * 1024) / rowb);
@@ -642,9 +648,14 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
         PDD_CUDA(cudaFuncSetAttribute(k_disk_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
         PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p,
                    cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.b.p);
+        tm.mark(4);
         std::vector<int> hinfo(nd);
         PDD_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));
+        ds.ms_operator += tm.ms(0, 1);
+        ds.ms_factor += tm.ms(1, 2);
+        ds.ms_refine += tm.ms(2, 3);
+        ds.ms_eval += tm.ms(3, 4);
         for (int d = 0; d < nd; ++d)
             if (hinfo[d]) fail(PDD_ENOCONV, "singular collocation matrix");
         ds.disks += nd;
@@ -680,6 +691,10 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
         all.rows += d.rows;
         all.max_sweeps = std::max(all.max_sweeps, d.max_sweeps);
         all.unconverged += d.unconverged;
+        all.ms_operator += d.ms_operator;
+        all.ms_factor += d.ms_factor;
+        all.ms_refine += d.ms_refine;
+        all.ms_eval += d.ms_eval;
     }
     return all;
 }

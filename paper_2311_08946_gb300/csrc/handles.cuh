@@ -63,6 +63,26 @@ void assemble_dirichlet(const pdd_cover &cov, const Problem &P, pdd_system &sys,
 
 struct DiskStats {
     int disks = 0, rows = 0, max_sweeps = 0, unconverged = 0;
+    float ms_operator = 0, ms_factor = 0, ms_refine = 0, ms_eval = 0;
+};
+
+// CUDA events bracketing consecutive stages on one stream
+struct StageTimer {
+    cudaEvent_t ev[8];
+    int n = 0;
+    cudaStream_t st;
+    explicit StageTimer(cudaStream_t s, int count) : n(count), st(s) {
+        for (int k = 0; k < n; ++k) PDD_CUDA(cudaEventCreate(&ev[k]));
+    }
+    void mark(int k) { PDD_CUDA(cudaEventRecord(ev[k], st)); }
+    float ms(int a, int b) {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+    ~StageTimer() {
+        for (int k = 0; k < n; ++k) cudaEventDestroy(ev[k]);
+    }
 };
 DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
                          pdd_system &sys, cudaStream_t st);
