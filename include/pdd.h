@@ -244,6 +244,32 @@ pdd_status pdd_solve_csr(int n, const int *rowptr_dev, const int *col_dev, const
                          const double *b_dev, double *u_dev, const pdd_solve_opts *opts,
                          pdd_solve_info *info, void *stream);
 
+/*
+ * pdd_solve_csr_noalloc -- pdd_solve_csr without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- a process whose device
+ * heap belongs to another allocator (a caching allocator that must not be
+ * bypassed or fragmented), a latency-critical loop that cannot absorb the
+ * device-wide synchronisation of cudaFree, or a service that must not fail
+ * with out-of-memory in the middle of a request.
+ *   Workspace: a fixed 64 MiB array in device memory, reserved by every GPU
+ *   that loads the library and held until the process exits.  The Krylov
+ *   basis, partial sums and Hessenberg state of one solve must fit in it:
+ *   about (restart + 2) * n * 8 bytes; larger requests return PDD_EINVAL with
+ *   the sizes in pdd_last_error() and touch nothing.
+ *   The first call on a device looks up the array's device address once
+ *   (with that device current); make that first call before any stream
+ *   capture on the device.
+ *   Every call uses the same array, which keeps the previous call's contents
+ *   (the solver clears what must start at zero).  Calls that overlap on the
+ *   GPU -- on different streams, or from different host threads, on the same
+ *   device -- race on the array and give wrong results: serialise them.
+ *   opts->transpose must be 0.  Arguments and results are as pdd_solve_csr.
+ */
+pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr_dev, const int *col_dev,
+                                 const double *val_dev, const double *b_dev, double *u_dev,
+                                 const pdd_solve_opts *opts, pdd_solve_info *info, void *stream);
+
 /* y = C x (or C^T x when transpose != 0) for a CSR matrix in device memory. */
 pdd_status pdd_spmv_csr(int n, const int *rowptr_dev, const int *col_dev, const double *val_dev,
                         const double *x_dev, double *y_dev, int transpose, void *stream);

@@ -96,7 +96,8 @@ class _SolveInfo(ctypes.Structure):
 
 EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy_cover",
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
-           "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_spmv_csr", "pdd_grad",
+           "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
+           "pdd_spmv_csr", "pdd_grad",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
 _lib = None
@@ -130,6 +131,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdd_destroy_system.argtypes = [vp]
     lib.pdd_solve.argtypes = [vp, vp, vp, vp, vp]
     lib.pdd_solve_csr.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.pdd_solve_csr_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pdd_spmv_csr.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp]
     lib.pdd_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = lib
@@ -361,6 +363,21 @@ def solve_csr(rowptr, col, val, b, rtol=1e-13, restart=64, max_iters=20000, tran
     _check(load().pdd_solve_csr(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(u), ctypes.byref(o),
                                 ctypes.byref(info), _stream(stream)))
     return u, {"iters": info.iters, "rel_residual": info.rel_residual, "converged": info.converged}
+
+
+def solve_csr_noalloc(rowptr, col, val, b, u, rtol=1e-13, restart=64, max_iters=20000, stream=None):
+    """pdd_solve_csr_noalloc: the CSR GMRES solve on the library's fixed device workspace.
+
+    For callers that cannot allocate device memory while they run; ``u`` is
+    a caller-owned float64 device tensor of length n.  Calls that overlap on
+    one device race on the shared workspace.
+    """
+    n = b.numel()
+    info = _SolveInfo()
+    o = _SolveOpts(restart, max_iters, rtol, 0)
+    _check(load().pdd_solve_csr_noalloc(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(u),
+                                        ctypes.byref(o), ctypes.byref(info), _stream(stream)))
+    return {"iters": info.iters, "rel_residual": info.rel_residual, "converged": info.converged}
 
 
 def spmv_csr(rowptr, col, val, x, transpose=False, stream=None):

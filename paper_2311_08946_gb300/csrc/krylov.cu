@@ -11,6 +11,8 @@
 // per restart cycle to read the true residual.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "handles.cuh"
@@ -287,3 +289,154 @@ void csr_transpose(int n, int64_t nnz, const int *rowptr, const int *col, const 
 }
 
 }  // namespace pdd
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the CSR GMRES solve.
+//
+// Some callers cannot allocate device memory while they run: a host process
+// whose device heap is owned by another allocator (a caching allocator that
+// must not be bypassed or fragmented), a latency-critical loop that cannot
+// absorb the device-wide synchronisation cudaFree implies, or a service that
+// must not meet an out-of-memory failure half-way through a request.  For them
+// pdd_solve_csr_noalloc runs the same GMRES kernels on a fixed workspace that
+// lives in this file-scope device array, reserved when the library is loaded
+// and held by every GPU that loads it until the process exits.
+// ---------------------------------------------------------------------------
+namespace pdd {
+
+static constexpr size_t kNoAllocBytes = (size_t)64 << 20;          // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static constexpr int kMaxDevices = 64;
+static void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (looked up once per device).
+static void *noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= kMaxDevices) fail(PDD_EINVAL, "device ordinal out of range");
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            set_error(cuda_msg(e, "cudaGetSymbolAddress(g_noalloc_scratch)"));
+            throw Fail{PDD_ECUDA};
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+struct NoAllocLayout {
+    size_t V, w, partial, H, cs, sn, g, y, gs, total;
+};
+
+static NoAllocLayout noalloc_layout(int n, int m, int G) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    NoAllocLayout L{};
+    size_t off = 0;
+    L.V = off; off += up(sizeof(double) * (size_t)(m + 1) * n);
+    L.w = off; off += up(sizeof(double) * (size_t)n);
+    L.partial = off; off += up(sizeof(double) * (size_t)(m + 1) * G);
+    L.H = off; off += up(sizeof(double) * (size_t)(m + 1) * m);
+    L.cs = off; off += up(sizeof(double) * (size_t)m);
+    L.sn = off; off += up(sizeof(double) * (size_t)m);
+    L.g = off; off += up(sizeof(double) * (size_t)(m + 1));
+    L.y = off; off += up(sizeof(double) * (size_t)m);
+    L.gs = off; off += up(sizeof(GState));
+    L.total = off;
+    return L;
+}
+
+// The same iteration as gmres_csr, on buffers carved from `base`.
+static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, const double *val,
+                                   const double *b, double *u, const pdd_solve_opts &o, unsigned char *base,
+                                   const NoAllocLayout &L, int m, int G, cudaStream_t st) {
+    double *V = (double *)(base + L.V), *w = (double *)(base + L.w);
+    double *partial = (double *)(base + L.partial), *H = (double *)(base + L.H);
+    double *cs = (double *)(base + L.cs), *sn = (double *)(base + L.sn);
+    double *g = (double *)(base + L.g), *y = (double *)(base + L.y);
+    GState *gs = (GState *)(base + L.gs);
+    // the array keeps the previous call's contents: clear what must start at zero
+    PDD_CUDA(cudaMemsetAsync(gs, 0, sizeof(GState), st));
+    PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
+    PDD_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, st));
+    const int vb = std::min(cdiv(n, 256), 2048);
+    const int max_iters = std::max(1, o.max_iters);
+    SolveResult res;
+    std::vector<double> hp(G);
+    for (int cycle = 0;; ++cycle) {
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
+        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, (const GState *)nullptr);
+        PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs, partial, G, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, partial, G, (double *)nullptr, gs);
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (long)j * n;
+            double *Hc = H + (long)j * (m + 1);
+            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w, gs);
+            for (int pass = 0; pass < 2; ++pass) {
+                PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V, w, partial, gs);
+                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V, w, partial, G, Hc, pass, gs);
+            }
+            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, gs);
+            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, partial, G, Hc + j + 1, gs);
+            PDD_LAUNCH(k_givens, 1, 1, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
+        }
+        PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H, m + 1, g, y, gs);
+        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V, y, gs, u);
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
+        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, (const GState *)nullptr);
+        GState hg{};
+        PDD_CUDA(cudaMemcpyAsync(hp.data(), partial, G * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GState), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        double rs = 0.0;
+        for (int q = 0; q < G; ++q) rs += hp[q];
+        const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
+        res.iters = hg.iters;
+        res.rel = rel;
+        if (hg.bnorm == 0.0 || rel <= o.rtol) {
+            res.converged = 1;
+            break;
+        }
+        if (hg.iters >= max_iters) break;
+    }
+    return res;
+}
+
+}  // namespace pdd
+
+extern "C" pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr, const int *col, const double *val,
+                                            const double *b, double *u, const pdd_solve_opts *opts,
+                                            pdd_solve_info *info, void *stream) {
+    using namespace pdd;
+    try {
+        if (!opts) fail(PDD_EINVAL, "null solve options");
+        if (opts->restart < 1 || opts->restart > 256 || opts->max_iters < 1 || !(opts->rtol > 0))
+            fail(PDD_EINVAL, "restart in [1, 256], max_iters >= 1 and rtol > 0 required");
+        if (opts->transpose) fail(PDD_EINVAL, "the allocation-free solve takes C itself (transpose = 0)");
+        if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
+        const int m = opts->restart;
+        const int G = std::max(1, std::min(1024, cdiv(n, 512)));
+        const NoAllocLayout L = noalloc_layout(n, m, G);
+        if (L.total > kNoAllocBytes)
+            fail(PDD_EINVAL, "workspace of " + std::to_string(L.total) + " bytes exceeds the fixed " +
+                                 std::to_string(kNoAllocBytes) + "-byte array: (restart + 2) * n * 8 bytes "
+                                 "must stay below about 64 MiB");
+        int dev = 0;
+        PDD_CUDA(cudaGetDevice(&dev));
+        unsigned char *base = (unsigned char *)noalloc_scratch(dev);
+        SolveResult r = gmres_csr_fixed(n, rowptr, col, val, b, u, *opts, base, L, m, G, (cudaStream_t)stream);
+        if (info) {
+            info->iters = r.iters;
+            info->rel_residual = r.rel;
+            info->converged = r.converged;
+        }
+        if (!r.converged) fail(PDD_ENOCONV, "GMRES stopped at relative residual " + std::to_string(r.rel));
+    } catch (const Fail &f) {
+        return f.st;
+    }
+    return PDD_OK;
+}
