@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
+    ap.add_argument("--no-grad", action="store_true", help="skip the adjoint (a14) leg")
     return ap.parse_args()
 
 
@@ -229,7 +230,7 @@ def run_ours(args, rank, world):
     if not args.no_oracle and rank == 0:
         out["err_vs_oracle"] = errors_vs_oracle(pdd, cfg, stream)
         out["cpu_baseline"] = cpu_baseline(cfg)
-    if rank == 0:
+    if rank == 0 and not args.no_grad:
         out["grad"] = grad_bench(pdd, stream)
     return out
 

@@ -274,6 +274,19 @@ pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr_dev, const int *col_de
 pdd_status pdd_spmv_csr(int n, const int *rowptr_dev, const int *col_dev, const double *val_dev,
                         const double *x_dev, double *y_dev, int transpose, void *stream);
 
+/*
+ * pdd_batched_gemm_sub_tf32x3 -- C_b -= A_b B_b for b < batch (row-major FP32
+ * device matrices: A_b M x K with leading dimension lda at A + b*sA, B_b K x N
+ * (ldb), C_b M x N (ldc)).  Runs on the tcgen05 tensor cores with split-TF32
+ * products (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation): relative
+ * error ~1e-6 of sum |A||B|.  It is the Schur-complement update of the
+ * recursive disk LU (a7, Eq. 41 solved by LU) and is exposed for reuse and
+ * testing.  Synchronises `stream`.
+ */
+pdd_status pdd_batched_gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A_dev,
+                                       long long sA, int lda, const float *B_dev, long long sB,
+                                       int ldb, float *C_dev, long long sC, int ldc, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Adjoint gradient (a14; not in the paper).
  * ------------------------------------------------------------------------- */

@@ -97,7 +97,7 @@ class _SolveInfo(ctypes.Structure):
 EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy_cover",
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
            "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
-           "pdd_spmv_csr", "pdd_grad",
+           "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_grad",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
 _lib = None
@@ -133,6 +133,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdd_solve_csr.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pdd_solve_csr_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pdd_spmv_csr.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp]
+    i64_ = ctypes.c_longlong
+    lib.pdd_batched_gemm_sub_tf32x3.argtypes = [i32, i32, i32, i32, vp, i64_, i32, vp, i64_, i32, vp, i64_,
+                                                i32, vp]
     lib.pdd_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
@@ -386,6 +389,16 @@ def spmv_csr(rowptr, col, val, x, transpose=False, stream=None):
     _check(load().pdd_spmv_csr(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y), 1 if transpose else 0,
                                _stream(stream)))
     return y
+
+
+def gemm_sub_tf32x3(C, A, B, stream=None):
+    """C -= A @ B in place for batched row-major float32 CUDA tensors (b, M, K) x (b, K, N)."""
+    b, M, K = A.shape
+    N = B.shape[2]
+    assert C.shape == (b, M, N) and all(t.is_contiguous() and t.dtype == torch.float32 for t in (A, B, C))
+    _check(load().pdd_batched_gemm_sub_tf32x3(b, M, N, K, _ptr(A), M * K, K, _ptr(B), K * N, N, _ptr(C), M * N,
+                                              N, _stream(stream)))
+    return C
 
 
 def launch_count() -> int:

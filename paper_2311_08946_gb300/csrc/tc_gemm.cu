@@ -1,0 +1,262 @@
+// Batched C -= A * B on the 5th-generation tensor cores (tcgen05), FP32 in and
+// out with split-TF32 products: each operand is split into hi = tf32(x) and
+// lo = tf32(x - hi); A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped
+// lo*lo term is ~2^-22 relative), accumulated in FP32 in tensor memory.
+// This is the Schur-complement update of the recursive disk LU (a7) and of
+// its triangular solves; it keeps the factors accurate to about FP32, which
+// the FP64 refinement of a8 needs (one TF32 product would leave
+// kappa(A) u_tf32 > 1 on the 32x32 and 48x64 disk grids).
+//
+// One CTA (128 threads) computes a 128 x 128 tile of C for one matrix of the
+// batch:
+//   * the K loop runs in chunks of 32; each chunk is staged by all threads
+//     into shared memory in the canonical no-swizzle K-major layout (8-row x
+//     16-byte core matrices; LBO = K-direction core stride, SBO = 8-row-group
+//     stride), hi and lo copies, double-buffered;
+//   * one thread issues 4 k-steps x 3 tcgen05.mma.kind::tf32 (M = 128,
+//     N = 128, K = 8) into a TMEM accumulator and commits them to the
+//     buffer's mbarrier;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = rows) and subtracts it from C.
+// Every mbarrier wait is bounded: on timeout the kernel records an error,
+// waits once more (bounded) for its own MMAs, frees its TMEM and returns.
+#include "handles.cuh"
+
+namespace pdd {
+
+static constexpr int kTM = 128, kTN = 128, kTK = 32;
+static constexpr int kOpBytes = kTM * kTK * 4;          // one operand copy: 16 KB
+static constexpr int kStageBytes = 4 * kOpBytes;        // A_hi, A_lo, B_hi, B_lo
+static constexpr int kTcSmem = 2 * kStageBytes + 32 * 1024;   // two stages + guard band
+static constexpr int kTmemCols = 256;                   // 128 used; the rest is headroom
+static constexpr long long kWaitLimit = 1LL << 22;   // polls before a wait is declared failed
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// shared-memory matrix descriptor, no swizzle, K-major
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+    return d;                                  // base offset 0, LBO mode 0, no swizzle
+}
+
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                   // D format F32
+           | (2u << 7)                 // A format TF32
+           | (2u << 10)                // B format TF32
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try(mbar, parity)) return true;
+    return false;
+}
+
+// element (r, k) of a rows x 32 operand tile in the canonical layout
+__device__ __forceinline__ int canon_off(int r, int k, int rows) {
+    return (k >> 2) * (rows * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_sub_tf32x3(int M, int N, int K, const float *A, long sA, int lda,
+                                                            const float *B, long sB, int ldb, float *C, long sC,
+                                                            int ldc, int *err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bz = blockIdx.z;
+    const int tm = blockIdx.y * kTM, tn = blockIdx.x * kTN;
+    A += bz * sA;
+    B += bz * sB;
+    C += bz * sC;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int nch = (K + kTK - 1) / kTK;
+    const uint32_t idesc = idesc_tf32(kTM, kTN);
+    const uint32_t lbo = kTM * 16;             // K-direction core-matrix stride (rows = 128)
+    const uint32_t sbo = 128;                  // 8-row-group stride
+    int issued = -1;                           // last chunk whose MMAs were committed (uniform)
+    for (int kc = 0; kc < nch; ++kc) {
+        const int buf = kc & 1;
+        unsigned char *st = tsm + buf * kStageBytes;
+        if (kc >= 2) {
+            if (!mbar_wait(smem_u32(&mbar[buf]), ((kc - 2) >> 1) & 1)) failed = 1;
+        }
+        __syncthreads();
+        if (failed) break;
+        float *Ahi = (float *)st, *Alo = (float *)(st + kOpBytes);
+        float *Bhi = (float *)(st + 2 * kOpBytes), *Blo = (float *)(st + 3 * kOpBytes);
+        const int k0 = kc * kTK;
+        for (int e = tid; e < kTM * kTK; e += 128) {            // A rows, K contiguous
+            const int r = e >> 5, k = e & 31;
+            const int gr = tm + r, gk = k0 + k;
+            const float v = (gr < M && gk < K) ? A[(long)gr * lda + gk] : 0.f;
+            const float hi = tf32_round(v);
+            const int off = canon_off(r, k, kTM) >> 2;
+            Ahi[off] = hi;
+            Alo[off] = tf32_round(v - hi);
+        }
+        for (int e = tid; e < kTK * kTN; e += 128) {            // B is K x N (N contiguous): stage N rows x K
+            const int k = e >> 7, j = e & 127;
+            const int gk = k0 + k, gj = tn + j;
+            const float v = (gk < K && gj < N) ? B[(long)gk * ldb + gj] : 0.f;
+            const float hi = tf32_round(v);
+            const int off = canon_off(j, k, kTN) >> 2;
+            Bhi[off] = hi;
+            Blo[off] = tf32_round(v - hi);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+            const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+#pragma unroll
+            for (int s = 0; s < kTK / 8; ++s) {
+                const uint32_t ko = s * 2 * lbo;               // 8 tf32 = two 16-byte core columns
+                const int first = (kc == 0 && s == 0) ? 0 : 1;
+                mma_tf32(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, first);
+                mma_tf32(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                mma_tf32(tmem, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+            }
+            mma_commit(smem_u32(&mbar[buf]));
+        }
+        issued = kc;
+    }
+    // all MMAs of this tile are complete once the last commit has landed
+    if (issued >= 0) {
+        const int last = issued & 1;
+        const uint32_t par = (issued >> 1) & 1;
+        bool ok = mbar_wait(smem_u32(&mbar[last]), par);
+        if (!ok) {
+            failed = 1;
+            mbar_wait(smem_u32(&mbar[last]), par);          // bounded second wait for in-flight MMAs
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!failed && issued == nch - 1 && nch > 0) {
+        const int row = tm + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                float *crow = C + (long)row * ldc + tn + c0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (tn + c0 + q < N) crow[q] -= __uint_as_float(v[q]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (tid == 0 && failed) atomicAdd(err, 1);
+}
+
+void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, int lda, const float *B, long sB,
+                     int ldb, float *C, long sC, int ldc, int *err, cudaStream_t st) {
+    if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        PDD_CUDA(cudaFuncSetAttribute(k_gemm_sub_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+        attr = true;
+    }
+    dim3 grid(cdiv(N, kTN), cdiv(M, kTM), batch);
+    if (grid.y > 65535 || grid.z > 65535) fail(PDD_EINVAL, "GEMM batch too large");
+    PDD_LAUNCH(k_gemm_sub_tf32x3, grid, 128, kTcSmem, st, M, N, K, A, sA, lda, B, sB, ldb, C, sC, ldc, err);
+}
+
+}  // namespace pdd
+
+// C ABI: the Schur-update primitive (see include/pdd.h)
+extern "C" pdd_status pdd_batched_gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long long sA,
+                                                  int lda, const float *B, long long sB, int ldb, float *C,
+                                                  long long sC, int ldc, void *stream) {
+    using namespace pdd;
+    try {
+        if (batch < 0 || M < 0 || N < 0 || K < 0 || (batch && M && N && K && (!A || !B || !C)))
+            fail(PDD_EINVAL, "negative size or null operand");
+        if (lda < K || ldb < N || ldc < N) fail(PDD_EINVAL, "leading dimension smaller than the row length");
+        cudaStream_t st = (cudaStream_t)stream;
+        DevBuf<int> err;
+        err.alloc(1);
+        PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        gemm_sub_tf32x3(batch, M, N, K, A, (long)sA, lda, B, (long)sB, ldb, C, (long)sC, ldc, err.p, st);
+        int h = 0;
+        PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its MMAs");
+    } catch (const Fail &f) {
+        return f.st;
+    }
+    return PDD_OK;
+}

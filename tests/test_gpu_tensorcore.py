@@ -1,0 +1,44 @@
+"""The tcgen05 split-TF32 GEMM (Schur update of the disk LU) against an FP64 reference.
+
+Bar: |C_gpu - C_ref| <= 2^-19 * (|C0| + |A||B|) elementwise -- the split keeps
+about 21 bits per product (the dropped lo*lo term is ~2^-22 relative), plus
+FP32 accumulation over K.
+"""
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pdd():
+    import paper_2311_08946_gb300 as pkg
+    from paper_2311_08946_gb300 import build
+    build.build()
+    pkg.load()
+    return pkg
+
+
+@pytest.mark.parametrize("b,M,N,K", [(1, 128, 128, 32), (3, 256, 128, 64), (2, 300, 200, 96),
+                                     (4, 512, 384, 512), (2, 129, 65, 33), (1, 1, 1, 1)])
+def test_gemm_sub_matches_fp64(pdd, b, M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(b, M, K, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(b, K, N, device="cuda", generator=g, dtype=torch.float32)
+    C0 = torch.randn(b, M, N, device="cuda", generator=g, dtype=torch.float32)
+    C = C0.clone()
+    pdd.gemm_sub_tf32x3(C, A, B)
+    ref = C0.double() - torch.bmm(A.double(), B.double())
+    bound = 2.0 ** -19 * (C0.double().abs() + torch.bmm(A.double().abs(), B.double().abs()))
+    err = (C.double() - ref).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+
+
+def test_gemm_sub_is_not_plain_tf32(pdd):
+    # a plain single-pass TF32 product would miss this bar by ~2^8
+    A = torch.full((1, 128, 64), 1.0 + 2.0 ** -15, device="cuda")
+    B = torch.full((1, 64, 128), 1.0 + 2.0 ** -14, device="cuda")
+    C = torch.zeros(1, 128, 128, device="cuda")
+    pdd.gemm_sub_tf32x3(C, A, B)
+    want = -64.0 * (1.0 + 2.0 ** -15) * (1.0 + 2.0 ** -14)
+    assert abs(C[0, 5, 7].item() - want) <= 64 * 2.0 ** -20
