@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the adjoint (a14) leg")
+    ap.add_argument("--lu-leaf", type=int, default=0, help="force the recursive LU leaf width (0: autotuned)")
+    ap.add_argument("--lu-tmin", type=int, default=0, help="force the tensor-core threshold (with --lu-leaf)")
     return ap.parse_args()
 
 
@@ -145,10 +147,22 @@ def flush_l2(buf):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+LU = {"lu_leaf_width": 0, "lu_tensor_min": 0}
+
+
+SOLVE_MS = []
+
+
 def step(pdd, cfg, precision, stream):
+    import torch
     cov = pdd.Cover(cfg, stream=stream)
-    S = pdd.System(cov, cfg, precision, stream=stream)
+    S = pdd.System(cov, cfg, precision, stream=stream, **LU)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     u = S.solve(rtol=1e-13, restart=64, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    SOLVE_MS.append(e0.elapsed_time(e1))
     return cov, S, u
 
 
@@ -160,6 +174,7 @@ def run_ours(args, rank, world):
     import workloads
 
     pdd.load()
+    LU["lu_leaf_width"], LU["lu_tensor_min"] = args.lu_leaf, args.lu_tmin
     cfg = workloads.varcoef()
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -186,6 +201,7 @@ def run_ours(args, rank, world):
             N = cov.N
             del cov, S, u
     launches = (pdd.launch_count() - launches0) // max(1, args.steps)
+    timed_solve_ms = statistics.mean(SOLVE_MS[-args.steps:])
     ms = statistics.mean(times)
     ms_max = max_over_ranks(ms, world)
     value = world * N / (ms_max / 1e3)
@@ -220,10 +236,14 @@ def run_ours(args, rank, world):
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
                                             "ms_refine", "ms_eval", "ms_paths", "ms_finalize")},
            "gmres": solve[-1], "refine_sweeps_max": st["max_refine_sweeps"],
+           "lu": ("blocked" if st["lu_blocked"] else
+                  f"recursive leaf={st['lu_leaf_width']} tensor_min={st['lu_tensor_min']}") +
+                 (" (forced)" if args.lu_leaf else " (autotuned)"),
+           "lu_args": f"--lu-leaf {st['lu_leaf_width']} --lu-tmin {st['lu_tensor_min']}" if not st["lu_blocked"] else "",
            "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary()}
 
     # roofline of the dominant kernel (device time from CUDA events inside the library)
-    out["roofline"] = roofline(st, cfg, N)
+    out["roofline"] = roofline(st, cfg, N, timed_solve_ms)
 
     if not args.no_fp64 and rank == 0:
         out["fp64_form"] = fp64_form(pdd, cfg, stream, flush)
@@ -235,41 +255,46 @@ def run_ours(args, rank, world):
     return out
 
 
-def roofline(st, cfg, N):
-    """Dominant kernel of the mixed step, against its own bound."""
+# Thread-instructions per Euler-Maruyama step of k_paths<float,1,1> on this workload, from
+# ncu (smsp__thread_inst_executed.sum / path-steps of the small variable-coefficient case,
+# profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
+PATHS_THREAD_INST_PER_STEP = None
+
+
+def roofline(st, cfg, N, ms_solve):
+    """Roofline of the dominant stage of the mixed step (device times from CUDA events)."""
     pk, src = peaks()
-    stages = {"k_paths (a11)": st["ms_paths"], "k_lu (a7)": st["ms_factor"],
-              "k_lu_solve+k_residual (a8)": st["ms_refine"], "k_disk_eval (a9)": st["ms_eval"],
-              "k_disk_operator (a6)": st["ms_operator"]}
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    stages = {"paths": st["ms_paths"], "factor": st["ms_factor"], "refine": st["ms_refine"],
+              "finalize": st["ms_finalize"], "operator": st["ms_operator"], "solve": ms_solve}
     top = max(stages, key=stages.get)
     n = cfg["n_r"] * cfg["n_theta"]
     disks = st["floating_disks"]
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    if top.startswith("k_lu ("):
-        flops = disks * (2.0 / 3.0) * n ** 3
-        # FP32 SIMT FMA: 152 SMs x 128 lanes x 2 flop x clock
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        ach = flops / (st["ms_factor"] / 1e3) / 1e12
-        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "FP32 CUDA-core FMA rate at the measured max SM clock (152x128x2xf)"}
-    if top.startswith("k_paths"):
-        # issue-bound ALU kernel: report FP64 weight updates against the FP64 rate
-        steps = st["path_steps"]
-        ach = steps / (st["ms_paths"] / 1e3) / 1e9
-        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": None, "unit": "Gpath-steps/s",
-                "frac": None, "traffic": None}
-    if top.startswith("k_lu_solve"):
-        nrhs = cfg["n_knots"] + 1
-        nc = 2 * cfg["n_r"] + 1
-        sweeps = max(1, st["max_refine_sweeps"])
-        fp64 = disks * (sweeps - 1) * 2.0 * n * ((nc - 1) + cfg["n_theta"] + 1) * nrhs
-        ach = fp64 / (st["ms_refine"] / 1e3) / 1e12
-        peak = 1.25
-        return {"kernel": top, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64)",
-                "frac": ach / peak, "traffic": None, "peak_source": "nominal GB300 FP64 rate"}
-    return {"kernel": top, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+    out = {"stage_ms": stages}
+    # factor: split-TF32 tensor-core Schur updates; TF32 dense peak = measured BF16 peak x 1.1/2.25
+    tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)
+    fac = {"kernel": "recursive LU (k_gemm_sub_tf32x3 + k_panel_leaf + k_trsm_leaf + k_gemm_sub_simt), a7",
+           "bound": "tensor", "achieved": disks * (2.0 / 3.0) * n ** 3 / (st["ms_factor"] / 1e3) / 1e12,
+           "peak": tf32_peak, "unit": "TFLOP/s", "traffic": None,
+           "peak_source": f"TF32 dense = {src} bf16_tflops x 1.1/2.25 (nominal ratio)"}
+    fac["frac"] = fac["achieved"] / fac["peak"]
+    # paths: issue-bound ALU kernel; peak = SM issue rate / thread-instructions per step
+    issue = 152 * 4 * 32 * sm_mhz * 1e6
+    pth = {"kernel": "k_paths<float,1,1> (a11)", "bound": "alu",
+           "achieved": st["path_steps"] / (st["ms_paths"] / 1e3) / 1e9, "unit": "Gpath-steps/s",
+           "traffic": None}
+    if PATHS_THREAD_INST_PER_STEP:
+        pth["peak"] = issue / PATHS_THREAD_INST_PER_STEP / 1e9
+        pth["frac"] = pth["achieved"] / pth["peak"]
+        pth["peak_source"] = (f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz / "
+                              f"{PATHS_THREAD_INST_PER_STEP:.0f} thread-instructions per step (ncu)")
+    else:
+        pth["peak"] = None
+        pth["frac"] = None
+    chosen = pth if top in ("paths", "finalize") else fac
+    out.update(chosen)
+    out["other"] = fac if chosen is pth else pth
+    return out
 
 
 def fp64_form(pdd, cfg, stream, flush):

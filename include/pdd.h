@@ -145,6 +145,12 @@ enum { PDD_PREC_FP64 = 0,       /* disk LU, solves and paths all in FP64        
        PDD_PREC_MIXED = 1 };    /* FP32 disk LU + FP64 refinement; FP32 path
                                    positions, FP64 weights and score sums           */
 
+enum { PDD_FACTOR_RECURSIVE_TC = 0,      /* recursive LU, Schur updates on tcgen05; with
+                                             lu_leaf_width = 0 the library times the candidate
+                                             factorisations on the first wave of each grid size
+                                             and keeps the fastest (this one included)        */
+       PDD_FACTOR_BLOCKED = 1 };          /* one CTA per disk, right-looking, CUDA cores      */
+
 enum { PDD_FLOATING_PSEUDOSPECTRAL = 0,   /* Sec. 3.3 (default)                      */
        PDD_FLOATING_MONTE_CARLO = 1 };    /* integrate floating rows by paths too     */
 
@@ -157,6 +163,14 @@ typedef struct {
     double imq_c2;            /* IMQ shape c^2 of Eq. 19 (1.5 in the paper)          */
     int max_refine;           /* refinement sweeps cap (mixed form), e.g. 12         */
     double refine_tol;        /* stop when |dx|_inf <= tol |x|_inf per column        */
+    int factor;               /* mixed form's LU: PDD_FACTOR_*                        */
+    int lu_leaf_width;        /* recursive LU leaf panel width 8/16/32; 0 = autotune */
+    int lu_tensor_min;        /* smallest GEMM side sent to tcgen05; 0 = autotune    */
+    int paths_max;            /* > paths: adaptive path counts (pilot = paths)       */
+    double se_target;         /* rows whose largest standard error (C entries and r)
+                                 exceeds it rerun with paths (se/se_target)^2 paths,
+                                 capped at paths_max (rounded up to 32); path ids
+                                 continue the pilot's Philox streams                 */
 } pdd_assembly_opts;
 
 typedef struct {
@@ -165,6 +179,8 @@ typedef struct {
     int mc_rows;              /* rows assembled by Monte Carlo                       */
     int64_t path_steps;       /* Euler-Maruyama steps taken                          */
     int64_t capped_paths;     /* paths that hit the step cap                          */
+    int64_t paths_total;      /* paths run (pilot + adaptive extension)               */
+    int extended_rows;        /* rows that ran more than the pilot count              */
     int max_refine_sweeps;    /* most refinement sweeps any disk needed              */
     int unconverged_disks;    /* disks whose refinement missed refine_tol            */
     double ms_cover_rows;     /* device time per stage (CUDA events), milliseconds   */
@@ -175,6 +191,9 @@ typedef struct {
     double ms_factor;         /*   batched LU (a7)                                    */
     double ms_refine;         /*   solves and refinement residuals (a8)              */
     double ms_eval;           /*   evaluation at the knots (a9)                       */
+    int lu_blocked;           /* mixed-form LU used: 1 blocked, 0 recursive with      */
+    int lu_leaf_width;        /*   this leaf panel width and                          */
+    int lu_tensor_min;        /*   this tensor-core threshold (autotuned or forced)   */
 } pdd_assembly_stats;
 
 /*

@@ -155,11 +155,50 @@ class McRow:
         self.u_stencil = u_stencil
 
 
+def batch_mean_se(per_path, bsamp, batches=32):
+    """Standard errors by batch means (path p in batch p mod 32), largest over the row's entries."""
+    P = bsamp.size
+    bid = np.arange(P) % batches
+    nb = np.bincount(bid, minlength=batches).astype(np.float64)
+    out = []
+    for v in list(per_path.T) + [bsamp]:
+        sums = np.bincount(bid, weights=v, minlength=batches)
+        mean = sums.sum() / P
+        bm = np.where(nb > 0, sums / np.maximum(nb, 1), 0.0)
+        f = nb / P
+        out.append(np.sqrt(batches / (batches - 1) * np.sum(f * f * (bm - mean) ** 2)))
+    return max(out)
+
+
+def adaptive_paths(P0, Pmax, se, target):
+    """Path count of the adaptive rule: P0 (se/target)^2 within [P0, Pmax], rounded up to 32."""
+    want = min(max(math.ceil(P0 * (se / target) ** 2), P0), Pmax)
+    want = ((want + 31) // 32) * 32
+    return min(want, Pmax)
+
+
 def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = "imq",
            with_grad=False, Kinv=None) -> McRow:
-    """a11 + a12 for knot i integrated in subdomain m."""
+    """a11 + a12 for knot i integrated in subdomain m.
+
+    With mc["paths_max"] > mc["paths"] and mc["se_target"] > 0 the pilot of
+    mc["paths"] paths is followed, when the row's largest batch-means standard
+    error exceeds the target, by a run of adaptive_paths(...) paths on the same
+    streams (path ids 0.. continue the pilot's).
+    """
+    P0 = int(mc["paths"])
+    row = _mc_row_paths(cov, op, i, m, mc, c2, basis, with_grad, Kinv, P0)
+    Pmax = int(mc.get("paths_max", 0))
+    tgt = float(mc.get("se_target", 0.0))
+    if Pmax > P0 and tgt > 0.0:
+        need = adaptive_paths(P0, Pmax, batch_mean_se(row.per_path, row.bsamp), tgt)
+        if need > P0:
+            row = _mc_row_paths(cov, op, i, m, mc, c2, basis, with_grad, row.Kinv, need)
+    return row
+
+
+def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis, with_grad, Kinv, P) -> McRow:
     cx, cy, r = float(cov.cx[m]), float(cov.cy[m]), float(cov.r[m])
-    P = int(mc["paths"])
     rec = walk(op, cx, cy, r, float(cov.kx[i]), float(cov.ky[i]), i, int(mc["seed"]),
                float(mc["h"]), P, with_grad=with_grad)
     if rec.capped:
@@ -193,8 +232,11 @@ def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = 
     bval = bsamp.sum() / P
     se = per_path.std(0, ddof=1) / math.sqrt(P) if P > 1 else np.zeros(b - a)
     se_b = float(bsamp.std(ddof=1) / math.sqrt(P)) if P > 1 else 0.0
-    return McRow(cols, vals, float(bval), se, se_b, moments, int(rec.steps.sum()), rec, Kinv,
-                 us)
+    row = McRow(cols, vals, float(bval), se, se_b, moments, int(rec.steps.sum()), rec, Kinv, us)
+    row.per_path = per_path
+    row.bsamp = bsamp
+    row.paths = P
+    return row
 
 
 def mc_rows(cov, op: Operator, rows, mc: dict, c2: float, threads: int = 1, basis=None,

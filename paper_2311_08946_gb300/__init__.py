@@ -71,18 +71,22 @@ class _AssemblyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("floating_method", ctypes.c_int),
                 ("paths", ctypes.c_int), ("h", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("imq_c2", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("factor", ctypes.c_int),
+                ("lu_leaf_width", ctypes.c_int), ("lu_tensor_min", ctypes.c_int),
+                ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double)]
 
 
 class _AssemblyStats(ctypes.Structure):
     _fields_ = [("floating_disks", ctypes.c_int), ("floating_rows", ctypes.c_int),
                 ("mc_rows", ctypes.c_int), ("path_steps", ctypes.c_int64),
-                ("capped_paths", ctypes.c_int64), ("max_refine_sweeps", ctypes.c_int),
+                ("capped_paths", ctypes.c_int64), ("paths_total", ctypes.c_int64),
+                ("extended_rows", ctypes.c_int), ("max_refine_sweeps", ctypes.c_int),
                 ("unconverged_disks", ctypes.c_int), ("ms_cover_rows", ctypes.c_double),
                 ("ms_disks", ctypes.c_double), ("ms_paths", ctypes.c_double),
                 ("ms_finalize", ctypes.c_double), ("ms_operator", ctypes.c_double),
                 ("ms_factor", ctypes.c_double), ("ms_refine", ctypes.c_double),
-                ("ms_eval", ctypes.c_double)]
+                ("ms_eval", ctypes.c_double), ("lu_blocked", ctypes.c_int), ("lu_leaf_width", ctypes.c_int),
+                ("lu_tensor_min", ctypes.c_int)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -231,12 +235,17 @@ def cover_struct(cfg: dict):
     return s, keep
 
 
+FACTOR = {"recursive_tc": 0, "blocked": 1}
+
+
 def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps",
-                  max_refine: int = 12, refine_tol: float = 1e-14) -> _AssemblyOpts:
+                  max_refine: int = 12, refine_tol: float = 1e-14, factor: str = "recursive_tc",
+                  lu_leaf_width: int = 0, lu_tensor_min: int = 0) -> _AssemblyOpts:
     mc = cfg["mc"]
     return _AssemblyOpts(PREC[precision], 0 if floating_method == "ps" else 1, int(mc["paths"]),
                          float(mc["h"]), int(mc["seed"]), float(cfg.get("imq_c2", 1.5)),
-                         int(max_refine), float(refine_tol))
+                         int(max_refine), float(refine_tol), FACTOR[factor], int(lu_leaf_width),
+                         int(lu_tensor_min), int(mc.get("paths_max", 0)), float(mc.get("se_target", 0.0)))
 
 
 # ---------------------------------------------------------------------------
@@ -287,14 +296,16 @@ class System:
 
     def __init__(self, cov: Cover, cfg: dict | None = None, precision: str = "fp64",
                  floating_method: str = "ps", stream=None, max_refine: int = 12,
-                 refine_tol: float = 1e-14):
+                 refine_tol: float = 1e-14, factor: str = "recursive_tc", lu_leaf_width: int = 0,
+                 lu_tensor_min: int = 0):
         lib = load()
         self.cov = cov
         self.cfg = cfg or cov.cfg
         self.precision = precision
         self.floating_method = floating_method
         self._op, self._keep = operator_struct(self.cfg["op"])
-        self._opts = assembly_opts(self.cfg, precision, floating_method, max_refine, refine_tol)
+        self._opts = assembly_opts(self.cfg, precision, floating_method, max_refine, refine_tol, factor,
+                                   lu_leaf_width, lu_tensor_min)
         h = ctypes.c_void_p()
         _check(lib.pdd_assemble_G(cov.handle, ctypes.byref(self._op), ctypes.byref(self._opts),
                                   ctypes.byref(h), _stream(stream)))

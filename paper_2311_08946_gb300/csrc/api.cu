@@ -123,6 +123,11 @@ static void check_opts(const pdd_assembly_opts *o) {
     if (!o) fail(PDD_EINVAL, "null assembly options");
     if (o->precision != PDD_PREC_FP64 && o->precision != PDD_PREC_MIXED) fail(PDD_EINVAL, "unknown precision");
     if (o->floating_method != 0 && o->floating_method != 1) fail(PDD_EINVAL, "unknown floating method");
+    if (o->factor != PDD_FACTOR_RECURSIVE_TC && o->factor != PDD_FACTOR_BLOCKED) fail(PDD_EINVAL, "unknown factorisation");
+    if (o->lu_leaf_width != 0 && o->lu_leaf_width != 8 && o->lu_leaf_width != 16 && o->lu_leaf_width != 32)
+        fail(PDD_EINVAL, "lu_leaf_width must be 0, 8, 16 or 32");
+    if (o->lu_tensor_min < 0) fail(PDD_EINVAL, "lu_tensor_min must be >= 0");
+    if (o->paths_max > 0 && o->paths_max > (1 << 28)) fail(PDD_EINVAL, "paths_max too large");
     if (o->paths <= 1 || !(o->h > 0) || !(o->imq_c2 > 0)) fail(PDD_EINVAL, "paths > 1, h > 0 and c^2 > 0 required");
 }
 
@@ -252,6 +257,8 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.mc_rows = ms.rows;
         S.path_steps = ms.steps;
         S.capped_paths = ms.capped;
+        S.paths_total = ms.paths_total;
+        S.extended_rows = ms.extended_rows;
         S.max_refine_sweeps = ds.max_sweeps;
         S.unconverged_disks = ds.unconverged;
         S.ms_cover_rows = t01;
@@ -262,6 +269,9 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.ms_factor = ds.ms_factor;
         S.ms_refine = ds.ms_refine;
         S.ms_eval = ds.ms_eval;
+        S.lu_blocked = ds.lu_blocked;
+        S.lu_leaf_width = ds.lu_leaf;
+        S.lu_tensor_min = ds.lu_tmin;
         if (ms.capped) fail(PDD_EPATH_CAP, std::to_string(ms.capped) + " paths reached the step cap");
         if (ds.unconverged)
             fail(PDD_ENOCONV, std::to_string(ds.unconverged) + " disks missed the refinement tolerance");

@@ -1,9 +1,9 @@
 // a6-a9: floating rows by Chebyshev(r) x Fourier(theta) collocation on each
 // disk (Sec. 3.3, Eq. 31-35, 40-41), batched over disks.
 //
-//   a6  k_disk_operator: rows of the collocation matrix A of L + c (row-
-//       equilibrated), the right-hand sides [A_IB H, -f] and per-node FP64
-//       coefficients for the matrix-free residual.
+//   a6  k_node_coef + k_fill_operator: per-node FP64 coefficients and row
+//       scales (one thread per node), the right-hand sides [A_IB H, -f], then
+//       the rows of the row-equilibrated collocation matrix of L + c.
 //   a7  k_lu: right-looking blocked LU with partial pivoting, one CTA per
 //       disk, panel in shared memory.  The paper factors by QR (Eq. 41);
 //       LU solves the same systems.
@@ -22,6 +22,7 @@
 //   + b_y(sin t u_r + cos t u_t/r) + c u, and d/dr carries 1/R.
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -119,13 +120,14 @@ __device__ __forceinline__ double a_entry(const Shape &S, int k, int j, int q, d
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_disk_operator(Problem P, Shape S, const DiskDesc *disks,
-                                                       T *A, long strideA, double *RHS, long strideR,
-                                                       NodeCoef *coef, long strideC) {
-    const int disk = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 8 + warp;
-    if (p >= S.n) return;
+// per node: coefficients of the polar operator, the row scale 1/max|A_pq| (the
+// nonzeros of a row are the radial line through the node, its mirror through
+// the centre, the node's ring and the diagonal) and the right-hand sides
+__global__ void __launch_bounds__(256) k_node_coef(Problem P, Shape S, const DiskDesc *disks, int nd,
+                                                   double *RHS, long strideR, NodeCoef *coef, long strideC) {
+    const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (gid >= (long)nd * S.n) return;
+    const int disk = (int)(gid / S.n), p = (int)(gid - (long)disk * S.n);
     const DiskDesc dd = disks[disk];
     const int k = p / S.nt + 1, j = p % S.nt, np = S.nc + 1, half = S.nt >> 1;
     const double rho = S.x[k];
@@ -142,21 +144,52 @@ __global__ void __launch_bounds__(256) k_disk_operator(Problem P, Shape S, const
     const double ga = 0.5 / (R2 * rho * rho);
     const double de = (-bx * st + by * ct) / (dd.R * rho);
     double amax = 0.0;
-    for (int q = lane; q < S.n; q += 32) amax = fmax(amax, fabs(a_entry(S, k, j, q, al, be, ga, de, cv, p)));
-#pragma unroll
-    for (int o = 16; o; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int l = 1; l <= S.nr; ++l) {
+        double v = al * S.D2[k * np + l] + be * S.D[k * np + l];
+        double vm = al * S.D2[k * np + S.nc - l] + be * S.D[k * np + S.nc - l];
+        if (l == k) {                              // the node's own ring crosses both lines
+            v += ga * S.F2[0] + de * S.F1[0] + cv;
+            vm += ga * S.F2[half] + de * S.F1[half];
+        }
+        amax = fmax(amax, fabs(v));
+        amax = fmax(amax, fabs(vm));
+    }
+    for (int jp = 0; jp < S.nt; ++jp) {
+        if (jp == j || jp == (j + half) % S.nt) continue;          // counted with the radial line
+        const int d = (j - jp + S.nt) % S.nt;
+        amax = fmax(amax, fabs(ga * S.F2[d] + de * S.F1[d]));
+    }
     const double sc = amax > 0.0 ? 1.0 / amax : 1.0;
-    T *Arow = A + disk * strideA + (long)p * S.n;
-    for (int q = lane; q < S.n; q += 32) Arow[q] = (T)(sc * a_entry(S, k, j, q, al, be, ga, de, cv, p));
+    coef[disk * strideC + p] = NodeCoef{al, be, ga, de, cv, sc};
     const double w0 = al * S.D2[k * np + 0] + be * S.D[k * np + 0];
     const double wN = al * S.D2[k * np + S.nc] + be * S.D[k * np + S.nc];
     double *Rrow = RHS + disk * strideR + (long)p * S.nrhs;
-    for (int col = lane; col < S.nk; col += 32)
+    for (int col = 0; col < S.nk; ++col)
         Rrow[col] = sc * (w0 * S.Hg[j * S.nk + col] + wN * S.Hg[((j + half) % S.nt) * S.nk + col]);
-    if (lane == 0) {
-        Rrow[S.nk] = -sc * fv;
-        coef[disk * strideC + p] = NodeCoef{al, be, ga, de, cv, sc};
-    }
+    Rrow[S.nk] = -sc * fv;
+}
+
+// rows of the equilibrated collocation matrix, one warp per row
+template <typename T>
+__global__ void __launch_bounds__(256) k_fill_operator(Shape S, T *A, long strideA, const NodeCoef *coef,
+                                                       long strideC) {
+    const int disk = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + warp;
+    if (p >= S.n) return;
+    const NodeCoef cf = coef[disk * strideC + p];
+    const int k = p / S.nt + 1, j = p % S.nt;
+    T *Arow = A + disk * strideA + (long)p * S.n;
+    for (int q = lane; q < S.n; q += 32)
+        Arow[q] = (T)(cf.s * a_entry(S, k, j, q, cf.alpha, cf.beta, cf.gamma, cf.delta, cf.c, p));
+}
+
+// the collocation system of every disk of the wave: node coefficients, then the matrix rows
+template <typename T>
+static void build_operator(const Problem &P, const Shape &S, const DiskDesc *dd, int nd, T *A, long sA, double *RHS,
+                           long sR, NodeCoef *coef, long sC, cudaStream_t st) {
+    PDD_LAUNCH(k_node_coef, cdiv((long)nd * S.n, 256), 256, 0, st, P, S, dd, nd, RHS, sR, coef, sC);
+    dim3 g(cdiv(S.n, 8), nd);
+    PDD_LAUNCH(k_fill_operator<T>, g, 256, 0, st, S, A, sA, coef, sC);
 }
 
 // ---------------------------------------------------------------------------
@@ -165,8 +198,9 @@ __global__ void __launch_bounds__(256) k_disk_operator(Problem P, Shape S, const
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *permAll, int *infoAll) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Pn = reinterpret_cast<T *>(smem_raw);               // panel rows x NB
-    T *Ut = Pn + (size_t)n * NB;                           // NB x 64 tile of U12
+    constexpr int LD = NB + 1;                             // padded panel rows: no bank conflicts
+    T *Pn = reinterpret_cast<T *>(smem_raw);               // panel rows x LD
+    T *Ut = Pn + (size_t)n * LD;                           // NB x 64 tile of U12
     __shared__ int piv[NB];
     __shared__ double rv[8];
     __shared__ int ri[8];
@@ -180,14 +214,14 @@ __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *p
         const int kb = min(NB, n - k0), rows = n - k0;
         for (int idx = tid; idx < rows * kb; idx += 256) {
             int r = idx / kb, c = idx - r * kb;
-            Pn[r * NB + c] = A[(long)(k0 + r) * n + k0 + c];
+            Pn[r * LD + c] = A[(long)(k0 + r) * n + k0 + c];
         }
         __syncthreads();
         for (int c = 0; c < kb; ++c) {
             double best = -1.0;
             int bi = c;
             for (int r = c + tid; r < rows; r += 256) {
-                double v = fabs((double)Pn[r * NB + c]);
+                double v = fabs((double)Pn[r * LD + c]);
                 if (v > best) { best = v; bi = r; }
             }
 #pragma unroll
@@ -214,24 +248,24 @@ __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *p
             const int p = piv[c];
             if (p != c)
                 for (int cc = tid; cc < kb; cc += 256) {
-                    T t = Pn[c * NB + cc];
-                    Pn[c * NB + cc] = Pn[p * NB + cc];
-                    Pn[p * NB + cc] = t;
+                    T t = Pn[c * LD + cc];
+                    Pn[c * LD + cc] = Pn[p * LD + cc];
+                    Pn[p * LD + cc] = t;
                 }
             __syncthreads();
-            const T d = Pn[c * NB + c];
+            const T d = Pn[c * LD + c];
             if (d == (T)0 && info == 0) info = k0 + c + 1;
             for (int r = c + 1 + tid; r < rows; r += 256) {
-                T l = (d != (T)0) ? Pn[r * NB + c] / d : (T)0;
-                Pn[r * NB + c] = l;
-                for (int cc = c + 1; cc < kb; ++cc) Pn[r * NB + cc] -= l * Pn[c * NB + cc];
+                T l = (d != (T)0) ? Pn[r * LD + c] / d : (T)0;
+                Pn[r * LD + c] = l;
+                for (int cc = c + 1; cc < kb; ++cc) Pn[r * LD + cc] -= l * Pn[c * LD + cc];
             }
             __syncthreads();
         }
         // write the panel back
         for (int idx = tid; idx < rows * kb; idx += 256) {
             int r = idx / kb, c = idx - r * kb;
-            A[(long)(k0 + r) * n + k0 + c] = Pn[r * NB + c];
+            A[(long)(k0 + r) * n + k0 + c] = Pn[r * LD + c];
         }
         // the panel's row interchanges, applied to the columns outside it
         for (int c = 0; c < kb; ++c) {
@@ -256,7 +290,7 @@ __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *p
             for (int rr = 0; rr < NB; ++rr) {
                 if (rr < kb) {
                     T v = A[(long)(k0 + rr) * n + j];
-                    for (int t = 0; t < rr; ++t) v -= Pn[rr * NB + t] * u[t];
+                    for (int t = 0; t < rr; ++t) v -= Pn[rr * LD + t] * u[t];
                     u[rr] = v;
                     A[(long)(k0 + rr) * n + j] = v;
                 }
@@ -286,7 +320,7 @@ __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *p
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         int pr = kb + rbase + ty * 4 + a;
-                        lv[a] = pr < rows ? Pn[pr * NB + t] : (T)0;
+                        lv[a] = pr < rows ? Pn[pr * LD + t] : (T)0;
                     }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) uv[b] = Ut[t * 64 + tx * 4 + b];
@@ -315,12 +349,22 @@ __global__ void __launch_bounds__(256) k_lu(T *Aall, int n, long strideA, int *p
 // ---------------------------------------------------------------------------
 // a8: multi-RHS solve with the LU factors: W = U^-1 L^-1 P R, then X = W
 // (plain form) or X += W with a per-disk convergence test (refinement).
+// Row blocks of TB: the off-diagonal part of each block is a small GEMM
+// staged through shared memory (QB-wide tiles of the factor and of the
+// solved rows), the TB x TB diagonal block is solved column by column.
 // ---------------------------------------------------------------------------
+static constexpr int kSolveTB = 32, kSolveQB = 64, kSolveMaxOut = 12;   // nrhs <= 96
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_lu_solve(const T *LUall, int n, long strideA, const int *permAll,
                                                   const double *Rall, int nrhs, long strideR,
                                                   T *Wall, double *Xall, int accumulate, int *conv,
                                                   int *sweeps, double tol) {
+    extern __shared__ __align__(16) unsigned char ssm[];
+    T *Ls = reinterpret_cast<T *>(ssm);                     // kSolveTB x kSolveQB (factor tile)
+    T *Ys = Ls + kSolveTB * kSolveQB;                       // kSolveQB x nrhs (solved rows)
+    T *Dg = Ys + kSolveQB * nrhs;                           // kSolveTB x kSolveTB diagonal block
+    T *Xs = Dg + kSolveTB * kSolveTB;                       // kSolveTB x nrhs rows being solved
     const int disk = blockIdx.x, tid = threadIdx.x;
     if (conv && conv[disk]) return;
     const T *LU = LUall + disk * strideA;
@@ -328,55 +372,80 @@ __global__ void __launch_bounds__(256) k_lu_solve(const T *LUall, int n, long st
     const double *R = Rall + disk * strideR;
     T *W = Wall + disk * strideR;
     double *X = Xall + disk * strideR;
-    constexpr int TB = 16;
-    // forward: L W = P R (unit lower)
-    for (int i0 = 0; i0 < n; i0 += TB) {
-        const int tb = min(TB, n - i0);
-        for (int o = tid; o < tb * nrhs; o += 256) {
-            int ii = o / nrhs, col = o - ii * nrhs, i = i0 + ii;
-            const T *Li = LU + (long)i * n;
-            T acc = (T)R[(long)perm[i] * nrhs + col];
-            for (int q = 0; q < i0; ++q) acc -= Li[q] * W[(long)q * nrhs + col];
-            W[(long)i * nrhs + col] = acc;
-        }
-        __syncthreads();
-        for (int col = tid; col < nrhs; col += 256) {
-            for (int ii = 1; ii < tb; ++ii) {
-                const T *Li = LU + (long)(i0 + ii) * n;
-                T acc = W[(long)(i0 + ii) * nrhs + col];
-                for (int t = 0; t < ii; ++t) acc -= Li[i0 + t] * W[(long)(i0 + t) * nrhs + col];
-                W[(long)(i0 + ii) * nrhs + col] = acc;
+    constexpr int TB = kSolveTB, QB = kSolveQB;
+    for (int pass = 0; pass < 2; ++pass) {                  // 0: L (unit lower), 1: U (upper)
+        const int nblk = (n + TB - 1) / TB;
+        for (int bi = 0; bi < nblk; ++bi) {
+            const int blk = pass == 0 ? bi : nblk - 1 - bi;
+            const int i0 = blk * TB, tb = min(TB, n - i0);
+            const int qa = pass == 0 ? 0 : i0 + tb, qb = pass == 0 ? i0 : n;   // already solved rows
+            T acc[kSolveMaxOut];
+#pragma unroll
+            for (int o = 0; o < kSolveMaxOut; ++o) acc[o] = (T)0;
+            for (int q0 = qa; q0 < qb; q0 += QB) {
+                const int qn = min(QB, qb - q0);
+                for (int e = tid; e < TB * QB; e += 256) {
+                    const int r = e / QB, q = e - r * QB;
+                    Ls[e] = (r < tb && q < qn) ? LU[(long)(i0 + r) * n + q0 + q] : (T)0;
+                }
+                for (int e = tid; e < QB * nrhs; e += 256) {
+                    const int q = e / nrhs, c = e - q * nrhs;
+                    Ys[e] = (q < qn) ? W[(long)(q0 + q) * nrhs + c] : (T)0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int o = 0; o < kSolveMaxOut; ++o) {
+                    const int e = tid + o * 256;
+                    if (e < tb * nrhs) {
+                        const int r = e / nrhs, c = e - r * nrhs;
+                        T a = acc[o];
+                        const T *lr = Ls + r * QB;
+                        for (int q = 0; q < qn; ++q) a += lr[q] * Ys[q * nrhs + c];
+                        acc[o] = a;
+                    }
+                }
+                __syncthreads();
             }
-        }
-        __syncthreads();
-    }
-    // backward: U W = W (upper, non-unit)
-    for (int iend = n; iend > 0; iend -= TB) {
-        const int i0 = max(0, iend - TB), tb = iend - i0;
-        for (int o = tid; o < tb * nrhs; o += 256) {
-            int ii = o / nrhs, col = o - ii * nrhs, i = i0 + ii;
-            const T *Ui = LU + (long)i * n;
-            T acc = W[(long)i * nrhs + col];
-            for (int q = iend; q < n; ++q) acc -= Ui[q] * W[(long)q * nrhs + col];
-            W[(long)i * nrhs + col] = acc;
-        }
-        __syncthreads();
-        for (int col = tid; col < nrhs; col += 256) {
-            for (int ii = tb - 1; ii >= 0; --ii) {
-                const int i = i0 + ii;
-                const T *Ui = LU + (long)i * n;
-                T acc = W[(long)i * nrhs + col];
-                for (int t = ii + 1; t < tb; ++t) acc -= Ui[i0 + t] * W[(long)(i0 + t) * nrhs + col];
-                W[(long)i * nrhs + col] = acc / Ui[i];
+            for (int e = tid; e < tb * tb; e += 256) {
+                const int r = e / tb, c = e - r * tb;
+                Dg[r * TB + c] = LU[(long)(i0 + r) * n + i0 + c];
             }
+#pragma unroll
+            for (int o = 0; o < kSolveMaxOut; ++o) {
+                const int e = tid + o * 256;
+                if (e < tb * nrhs) {
+                    const int r = e / nrhs, c = e - r * nrhs;
+                    const T rhs = pass == 0 ? (T)R[(long)perm[i0 + r] * nrhs + c] : W[(long)(i0 + r) * nrhs + c];
+                    Xs[r * nrhs + c] = rhs - acc[o];
+                }
+            }
+            __syncthreads();
+            // the diagonal block, in shared memory
+            for (int c = tid; c < nrhs; c += 256) {
+                if (pass == 0) {
+                    for (int ii = 1; ii < tb; ++ii) {
+                        T v = Xs[ii * nrhs + c];
+                        for (int t = 0; t < ii; ++t) v -= Dg[ii * TB + t] * Xs[t * nrhs + c];
+                        Xs[ii * nrhs + c] = v;
+                    }
+                } else {
+                    for (int ii = tb - 1; ii >= 0; --ii) {
+                        T v = Xs[ii * nrhs + c];
+                        for (int t = ii + 1; t < tb; ++t) v -= Dg[ii * TB + t] * Xs[t * nrhs + c];
+                        Xs[ii * nrhs + c] = v / Dg[ii * TB + ii];
+                    }
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < tb * nrhs; e += 256) W[(long)i0 * nrhs + e] = Xs[e];
+            __syncthreads();
         }
-        __syncthreads();
     }
     // X = W or X += W; refinement test max|W| <= tol max|X|
     double dmax = 0.0, xmax = 0.0;
     for (long o = tid; o < (long)n * nrhs; o += 256) {
-        double w = (double)W[o];
-        double xv = accumulate ? X[o] + w : w;
+        const double w = (double)W[o];
+        const double xv = accumulate ? X[o] + w : w;
         X[o] = xv;
         dmax = fmax(dmax, fabs(w));
         xmax = fmax(xmax, fabs(xv));
@@ -396,6 +465,21 @@ __global__ void __launch_bounds__(256) k_lu_solve(const T *LUall, int n, long st
         sweeps[disk] += 1;
         if (d <= tol * x) conv[disk] = 1;
     }
+}
+
+template <typename T>
+static size_t solve_smem(int nrhs) {
+    return sizeof(T) * ((size_t)kSolveTB * kSolveQB + (size_t)kSolveQB * nrhs + (size_t)kSolveTB * kSolveTB +
+                        (size_t)kSolveTB * nrhs);
+}
+
+template <typename T>
+static void launch_solve(const T *LU, int n, long sA, const int *perm, const double *R, int nrhs, long sR, T *W,
+                         double *X, int accumulate, int *conv, int *sweeps, double tol, int nd, cudaStream_t st) {
+    if (nrhs > 96) fail(PDD_EINVAL, "more than 95 knots per circle");
+    const size_t sm = solve_smem<T>(nrhs);
+    PDD_CUDA(cudaFuncSetAttribute(k_lu_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PDD_LAUNCH(k_lu_solve<T>, nd, 256, sm, st, LU, n, sA, perm, R, nrhs, sR, W, X, accumulate, conv, sweeps, tol);
 }
 
 // R = RHS - A X in FP64 without forming A (equilibrated rows)
@@ -541,16 +625,16 @@ struct ShapeTables {
 };
 
 static int lu_nb(int n, size_t elem) {
-    // panel n x NB plus an NB x 64 tile must fit in ~200 KB of shared memory
+    // panel n x (NB + 1) plus an NB x 64 tile must fit in ~200 KB of shared memory
     int nb = 32;
-    while (nb > 4 && ((size_t)n * nb + (size_t)nb * 64) * elem > 200 * 1024) nb >>= 1;
+    while (nb > 4 && ((size_t)n * (nb + 1) + (size_t)nb * 64) * elem > 200 * 1024) nb >>= 1;
     return nb;
 }
 
 template <typename T>
 static void launch_lu(T *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st) {
     const int nb = lu_nb(n, sizeof(T));
-    const size_t smem = ((size_t)n * nb + (size_t)nb * 64) * sizeof(T);
+    const size_t smem = ((size_t)n * (nb + 1) + (size_t)nb * 64) * sizeof(T);
     switch (nb) {
 #define PDD_LU_CASE(NBV)                                                                      \
     case NBV:                                                                                  \
@@ -565,6 +649,62 @@ static void launch_lu(T *A, int n, long strideA, int *perm, int *info, int nd, c
 #undef PDD_LU_CASE
         default: fail(PDD_EINVAL, "disk grid too large for the panel kernel");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the mixed-form LU: on the first wave of each grid size n, the
+// candidates (one-CTA blocked LU; recursive LU with leaf width 32/16/8 and a
+// tensor-core threshold of 64 or 128) are timed with CUDA events on a copy
+// of up to 64 of the wave's matrices; the fastest is kept for the process.
+// ---------------------------------------------------------------------------
+struct LuChoice {
+    int blocked, W, tmin;
+    float ms;
+};
+static std::map<int, LuChoice> g_lu_choice;
+static std::mutex g_lu_mu;
+
+static void run_lu_choice(const LuChoice &c, float *A, int n, long sA, int *perm, int *info, int nd, cudaStream_t st) {
+    if (c.blocked) launch_lu<float>(A, n, sA, perm, info, nd, st);
+    else lu_recursive_f32(A, n, sA, perm, info, nd, st, c.W, c.tmin);
+}
+
+static LuChoice tune_lu(float *A, int n, long sA, int nd, cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> lk(g_lu_mu);
+        auto it = g_lu_choice.find(n);
+        if (it != g_lu_choice.end()) return it->second;
+    }
+    std::vector<LuChoice> cand{{1, 0, 0, 0.f}};
+    for (int W : {32, 16, 8})
+        if ((size_t)n * (W + 1) * sizeof(float) <= 200 * 1024)
+            for (int tmin : {64, 128}) cand.push_back({0, W, tmin, 0.f});
+    const int nt = std::min(nd, 304);           // two disks per SM: the occupancy of a full wave
+    DevBuf<float> pristine, work;
+    DevBuf<int> perm, info;
+    pristine.alloc((size_t)nt * sA);
+    work.alloc((size_t)nt * sA);
+    perm.alloc((size_t)nt * n);
+    info.alloc(nt);
+    PDD_CUDA(cudaMemcpyAsync(pristine.p, A, sizeof(float) * nt * sA, cudaMemcpyDeviceToDevice, st));
+    StageTimer tm(st, 2);
+    LuChoice best{1, 0, 0, 1e30f};
+    for (auto &c : cand) {
+        float t = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {           // the first run warms the code paths
+            PDD_CUDA(cudaMemcpyAsync(work.p, pristine.p, sizeof(float) * nt * sA, cudaMemcpyDeviceToDevice, st));
+            tm.mark(0);
+            run_lu_choice(c, work.p, n, sA, perm.p, info.p, nt, st);
+            tm.mark(1);
+            PDD_CUDA(cudaStreamSynchronize(st));
+            t = tm.ms(0, 1);
+        }
+        c.ms = t;
+        if (t < best.ms) best = c;
+    }
+    std::lock_guard<std::mutex> lk(g_lu_mu);
+    g_lu_choice[n] = best;
+    return best;
 }
 
 template <typename T>
@@ -606,14 +746,32 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
         PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
         StageTimer tm(st, 5);
         tm.mark(0);
-        dim3 g_op(cdiv(S.n, 8), nd);
-        PDD_LAUNCH(k_disk_operator<T>, g_op, 256, 0, st, P, S, dd.p, A.p, sA, RHS.p, sR, coef.p, sC);
+        build_operator<T>(P, S, dd.p, nd, A.p, sA, RHS.p, sR, coef.p, sC, st);
         tm.mark(1);
-        launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
+        if constexpr (sizeof(T) == 4) {
+            if (o.factor == PDD_FACTOR_BLOCKED) {
+                launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
+                ds.lu_blocked = 1;
+            } else if (o.lu_leaf_width > 0) {
+                const LuChoice c{0, o.lu_leaf_width, o.lu_tensor_min > 0 ? o.lu_tensor_min : 128, 0.f};
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st);
+                ds.lu_blocked = 0;
+                ds.lu_leaf = c.W;
+                ds.lu_tmin = c.tmin;
+            } else {
+                const LuChoice c = tune_lu(A.p, S.n, sA, nd, st);       // cached after the first wave
+                tm.mark(1);                                            // factor time excludes tuning
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st);
+                ds.lu_blocked = c.blocked;
+                ds.lu_leaf = c.W;
+                ds.lu_tmin = c.tmin;
+            }
+        } else {
+            launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
+        }
         tm.mark(2);
         if (!mixed) {
-            PDD_LAUNCH(k_lu_solve<T>, nd, 256, 0, st, A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0,
-                       (int *)nullptr, (int *)nullptr, 0.0);
+            launch_solve<T>(A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0, nullptr, nullptr, 0.0, nd, st);
         } else {
             PDD_CUDA(cudaMemsetAsync(conv.p, 0, nd * sizeof(int), st));
             PDD_CUDA(cudaMemsetAsync(sweeps.p, 0, nd * sizeof(int), st));
@@ -624,8 +782,8 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             dim3 g_res(cdiv(S.n, 8), nd);
             for (int s = 0; s < maxs; ++s) {
                 const double *rhs_now = (s == 0) ? RHS.p : Rr.p;
-                PDD_LAUNCH(k_lu_solve<T>, nd, 256, 0, st, A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p,
-                           1, conv.p, sweeps.p, tol);
+                launch_solve<T>(A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p, 1, conv.p, sweeps.p, tol, nd,
+                                st);
                 if (s + 1 < maxs)
                     PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p);
             }
@@ -695,6 +853,11 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
         all.ms_factor += d.ms_factor;
         all.ms_refine += d.ms_refine;
         all.ms_eval += d.ms_eval;
+        if (d.lu_leaf || d.lu_blocked) {
+            all.lu_blocked = d.lu_blocked;
+            all.lu_leaf = d.lu_leaf;
+            all.lu_tmin = d.lu_tmin;
+        }
     }
     return all;
 }
@@ -881,11 +1044,10 @@ void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const d
         for (size_t w0 = 0; w0 < disks.size(); w0 += wave) {
             const int nd = (int)std::min<size_t>(wave, disks.size() - w0);
             PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
-            dim3 g_op(cdiv(S.n, 8), nd);
-            PDD_LAUNCH(k_disk_operator<double>, g_op, 256, 0, st, P, S, dd.p, A.p, sA, RHS.p, sR, coef.p, sC);
+            build_operator<double>(P, S, dd.p, nd, A.p, sA, RHS.p, sR, coef.p, sC, st);
             launch_lu<double>(A.p, S.n, sA, perm.p, info.p, nd, st);
-            PDD_LAUNCH(k_lu_solve<double>, nd, 256, 0, st, A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0,
-                       (int *)nullptr, (int *)nullptr, 0.0);
+            launch_solve<double>(A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0, nullptr, nullptr, 0.0, nd,
+                                 st);
             PDD_LAUNCH(k_adjoint_vecs, nd, 256, 0, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p, X.p, sR, u,
                        lambda, Vb.p, Eb.p);
             PDD_LAUNCH(k_lu_solve_T, nd, 256, 0, st, A.p, S.n, sA, perm.p, coef.p, sC, Eb.p, Wt.p, Zb.p);

@@ -43,6 +43,7 @@ struct pdd_system {
     int n_mc = 0;
     pdd::DevBuf<int> mc_rows, mom_ptr;
     pdd::DevBuf<double> moments, bmean;
+    pdd::DevBuf<int> mc_np;                // paths run for each Monte Carlo row
     pdd_assembly_stats stats{};
     int precision = 0;
 };
@@ -64,6 +65,7 @@ void assemble_dirichlet(const pdd_cover &cov, const Problem &P, pdd_system &sys,
 struct DiskStats {
     int disks = 0, rows = 0, max_sweeps = 0, unconverged = 0;
     float ms_operator = 0, ms_factor = 0, ms_refine = 0, ms_eval = 0;
+    int lu_blocked = 0, lu_leaf = 0, lu_tmin = 0;          // factorisation used (mixed form)
 };
 
 // CUDA events bracketing consecutive stages on one stream
@@ -88,8 +90,8 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
                          pdd_system &sys, cudaStream_t st);
 
 struct McStats {
-    int rows = 0;
-    int64_t steps = 0, capped = 0;
+    int rows = 0, extended_rows = 0;
+    int64_t steps = 0, capped = 0, paths_total = 0;
     float ms_paths = 0, ms_finalize = 0;
 };
 McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
@@ -123,6 +125,11 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
 void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
                const pdd_system &sys, const double *u, const double *dJdu, double *grad,
                double *lambda, cudaStream_t st);
+
+// recursive LU of a batch of FP32 matrices on the tensor cores (lu_rec.cu)
+// W = leaf panel width (8, 16, 32); GEMMs with M, N, K >= tensor_min go to the tensor cores
+void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st, int W,
+                      int tensor_min);
 
 // device-wide exclusive scan of int32 counts (in place into out, returns the total)
 int64_t exclusive_scan(const int *in, int *out, int n, cudaStream_t st);

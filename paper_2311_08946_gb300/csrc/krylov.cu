@@ -41,26 +41,19 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int *rowptr, const in
     if (row < n && l == 0) y[row] = s;
 }
 
-// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1
+// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1;
+// warp q of the block takes the vectors t = q, q + 8, ... (no block barriers)
 __global__ void __launch_bounds__(kDotBlock) k_dots(int n, int nv, const double *V, const double *w,
                                                     double *partial, const GState *gs) {
     if (gs && gs->stop) return;
-    __shared__ double red[kDotBlock / 32];
-    const int G = gridDim.x;
+    const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (n + G - 1) / G, a = blockIdx.x * per, b = min(n, a + per);
-    for (int t = 0; t < nv; ++t) {
+    for (int t = warp; t < nv; t += kDotBlock / 32) {
         double s = 0.0;
         const double *v = V + (long)t * n;
-        for (int r = a + threadIdx.x; r < b; r += blockDim.x) s += v[r] * w[r];
+        for (int r = a + lane; r < b; r += 32) s += v[r] * w[r];
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-            for (int q = 0; q < kDotBlock / 32; ++q) tot += red[q];
-            partial[t * G + blockIdx.x] = tot;
-        }
-        __syncthreads();
+        if (lane == 0) partial[t * G + blockIdx.x] = s;
     }
 }
 

@@ -87,13 +87,15 @@ __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const i
 struct PathArgs {
     const int *rows, *row_sub;
     const double *kx, *ky, *ccx, *ccy, *cr, *theta_s;
-    int paths;
+    int paths;                       // paths per row when npaths is null
     double h;
     uint64_t seed;
     int8_t *side;
     double *su, *Y, *Z;
     unsigned long long *steps;
     int *capped;
+    const int *npaths;               // per-row path counts (adaptive), or null
+    const long *rec_off;             // per-row record offsets, or null (slot * paths)
 };
 
 __device__ __forceinline__ double circle_exit_t(double px, double py, double dx, double dy, double ox,
@@ -151,108 +153,160 @@ __device__ __forceinline__ float killing32(const Problem &P, float x, float y) {
     return 0.f;
 }
 
-__device__ __forceinline__ float source32(const Problem &P, float x, float y) {
+// f of the manufactured solution from already evaluated b and c (FP32)
+__device__ __forceinline__ float source32_given(const Problem &P, float x, float y, float bx, float by, float cv) {
     if (P.f_kind == PDD_F_ONE) return 1.0f;
     if (P.f_kind == PDD_F_MANUFACTURED) {
         float spx, cpx, spy, cpy;
         sincospif(x, &spx, &cpx);
         sincospif(y, &spy, &cpy);
         const float pi = 3.14159265358979f;
-        float u = spx * cpy, ux = pi * cpx * cpy, uy = -pi * spx * spy;
-        float bx, by;
-        Num<float>::drift(P, x, y, bx, by);
-        return -(-pi * pi * u + bx * ux + by * uy + killing32(P, x, y) * u);
+        const float u = spx * cpy, ux = pi * cpx * cpy, uy = -pi * spx * spy;
+        return -(-pi * pi * u + bx * ux + by * uy + cv * u);
     }
     return 0.f;
 }
 
+__device__ __forceinline__ float source32(const Problem &P, float x, float y) {
+    float bx, by;
+    Num<float>::drift(P, x, y, bx, by);
+    return source32_given(P, x, y, bx, by, killing32(P, x, y));
+}
+
 template <typename R, bool KILL, bool SRC>
 __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
+    __shared__ int next_path;
     const int slot = blockIdx.x;
     const int i = A.rows[slot], m = A.row_sub[i];
     const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m], ts = A.theta_s[m];
     const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
+    // domain bounds in the position type (FP32 in the mixed form)
+    const R d0 = (R)P.dom[0], d1 = (R)P.dom[1], d2 = (R)P.dom[2], d3 = (R)P.dom[3];
+    const R dr2 = (R)(P.dom[2] * P.dom[2]);
+    const R x_start = (R)A.kx[i], y_start = (R)A.ky[i];
+    const int npath = A.npaths ? A.npaths[slot] : A.paths;
+    const long rbase = A.rec_off ? A.rec_off[slot] : (long)slot * A.paths;
     unsigned long long my_steps = 0;
     int my_capped = 0;
-    for (int p = threadIdx.x; p < A.paths; p += blockDim.x) {
-        R x = (R)A.kx[i], y = (R)A.ky[i];
-        double Yv = 1.0, Zv = 0.0;
-        int k = 0;
-        const long rec = (long)slot * A.paths + p;
-        for (;;) {
-            if (k >= max_steps) {
-                A.side[rec] = 2;
-                A.su[rec] = 0.0;
-                A.Y[rec] = 0.0;
-                A.Z[rec] = 0.0;
-                ++my_capped;
-                break;
-            }
+    if (threadIdx.x == 0) next_path = blockDim.x;
+    __syncthreads();
+    // One loop iteration is one Euler-Maruyama step of this lane's current path; a lane whose
+    // path exits writes its record and starts its next path (the row's next free path id) in
+    // the same iteration, so the lanes of a warp stay converged whatever the path lengths.
+    int p = threadIdx.x;
+    R x = x_start, y = y_start;
+    double Yv = 1.0, Zv = 0.0;
+    float e = 0.f, z = 0.f;    // mixed form: Y = Yv (1 + e), Z = Zv + Yv z (FP32 block increments)
+    int k = 0;
+    while (p < npath) {
+        const long rec = rbase + p;
+        bool done = false;
+        if (k >= max_steps) {
+            A.side[rec] = 2;
+            A.su[rec] = 0.0;
+            A.Y[rec] = 0.0;
+            A.Z[rec] = 0.0;
+            ++my_capped;
+            done = true;
+        } else {
             R xi0, xi1;
             Num<R>::normals(A.seed, (uint32_t)i, (uint32_t)k, (uint32_t)p, xi0, xi1);
             R bx, by;
             Num<R>::drift(P, x, y, bx, by);
             double Yn = Yv, Zn = Zv;
-            if (KILL) {
-                double cv = (sizeof(R) == 8) ? killing(P, (double)x, (double)y) : (double)killing32(P, (float)x, (float)y);
-                Yn = Yv * (1.0 + cv * A.h);
-            }
-            if (SRC) {
-                double fv = (sizeof(R) == 8) ? source(P, (double)x, (double)y) : (double)source32(P, (float)x, (float)y);
-                Zn = Zv + fv * Yv * A.h;
+            float en = e, zn = z;
+            if constexpr (sizeof(R) == 8) {
+                // FP64 form: the same expressions as the definition (identical streams)
+                if (KILL) Yn = Yv * (1.0 + killing(P, (double)x, (double)y) * A.h);
+                if (SRC) Zn = Zv + source(P, (double)x, (double)y) * Yv * A.h;
+            } else {
+                const float cv = KILL ? killing32(P, (float)x, (float)y) : 0.f;
+                const float hf = (float)A.h;
+                // Z_{k+1} = Z_k + f_k h Y_k and Y_{k+1} = Y_k (1 + c_k h), with Y_k = Yv (1 + e)
+                if (SRC) zn = fmaf(source32_given(P, (float)x, (float)y, (float)bx, (float)by, cv) * hf, 1.0f + e, z);
+                if (KILL) en = fmaf(cv * hf, 1.0f + e, e);
             }
             const R nx = x + bx * h + sh * xi0;
             const R ny = y + by * h + sh * xi1;
             ++k;
             const R ddx = nx - rcx, ddy = ny - rcy;
             const bool out_c = !(ddx * ddx + ddy * ddy < r2);
-            const bool out_d = !inside_domain(P, (double)nx, (double)ny);
+            bool in_d;
+            if (P.dom_kind == 0) {
+                in_d = nx > d0 && nx < d2 && ny > d1 && ny < d3;
+            } else {
+                const R ex0 = nx - d0, ey0 = ny - d1;
+                in_d = ex0 * ex0 + ey0 * ey0 < dr2;
+            }
+            const bool out_d = !in_d;
+            if constexpr (sizeof(R) == 4) {
+                if ((k & 7) == 0 || out_c || out_d) {     // fold the FP32 increments into the FP64 weights
+                    Zn = fma(Yv, (double)zn, Zv);
+                    Yn = fma(Yv, (double)en, Yv);
+                    en = 0.f;
+                    zn = 0.f;
+                }
+            }
             if (!out_c && !out_d) {
                 x = nx;
                 y = ny;
                 Yv = Yn;
                 Zv = Zn;
-                continue;
-            }
-            // exit point on the segment (in FP64 from the FP64 or FP32 end points)
-            const double xd = (double)x, yd = (double)y;
-            const double dx = (double)nx - xd, dy = (double)ny - yd;
-            double tc = 2.0, td = 2.0;
-            int ed = -1;
-            if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
-            if (out_d) {
-                if (P.dom_kind == 0) {
-                    double t;
-                    if ((double)nx <= P.dom[0]) { t = (P.dom[0] - xd) / dx; if (t < td) { td = t; ed = 3; } }
-                    if ((double)nx >= P.dom[2]) { t = (P.dom[2] - xd) / dx; if (t < td) { td = t; ed = 1; } }
-                    if ((double)ny <= P.dom[1]) { t = (P.dom[1] - yd) / dy; if (t < td) { td = t; ed = 0; } }
-                    if ((double)ny >= P.dom[3]) { t = (P.dom[3] - yd) / dy; if (t < td) { td = t; ed = 2; } }
-                } else {
-                    td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
-                    ed = 0;
-                }
-            }
-            if (td <= tc) {
-                const double ex = xd + td * dx, ey = yd + td * dy;
-                A.side[rec] = 1;
-                A.su[rec] = boundary_s(P, ex, ey, ed);
+                e = en;
+                z = zn;
             } else {
-                const double ex = xd + tc * dx, ey = yd + tc * dy;
-                double th = atan2(ey - cy, ex - cx);
-                if (th < 0.0) th += PDD_TWO_PI;
-                double u = th - ts;
-                if (u < 0.0) u += PDD_TWO_PI;
-                if (u >= PDD_TWO_PI) u -= PDD_TWO_PI;
-                A.side[rec] = 0;
-                A.su[rec] = u;
+                // exit point on the segment (in FP64 from the FP64 or FP32 end points)
+                const double xd = (double)x, yd = (double)y;
+                const double dx = (double)nx - xd, dy = (double)ny - yd;
+                double tc = 2.0, td = 2.0;
+                int ed = -1;
+                if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
+                if (out_d) {
+                    if (P.dom_kind == 0) {
+                        // the edges as the in-loop test saw them (FP32-rounded in the mixed form)
+                        const double D0 = (double)d0, D1 = (double)d1, D2 = (double)d2, D3 = (double)d3;
+                        double t;
+                        if ((double)nx <= D0) { t = (D0 - xd) / dx; if (t < td) { td = t; ed = 3; } }
+                        if ((double)nx >= D2) { t = (D2 - xd) / dx; if (t < td) { td = t; ed = 1; } }
+                        if ((double)ny <= D1) { t = (D1 - yd) / dy; if (t < td) { td = t; ed = 0; } }
+                        if ((double)ny >= D3) { t = (D3 - yd) / dy; if (t < td) { td = t; ed = 2; } }
+                    } else {
+                        td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
+                        ed = 0;
+                    }
+                }
+                if (td <= tc) {
+                    const double ex = xd + td * dx, ey = yd + td * dy;
+                    A.side[rec] = 1;
+                    A.su[rec] = boundary_s(P, ex, ey, ed);
+                } else {
+                    const double ex = xd + tc * dx, ey = yd + tc * dy;
+                    double th = atan2(ey - cy, ex - cx);
+                    if (th < 0.0) th += PDD_TWO_PI;
+                    double u = th - ts;
+                    if (u < 0.0) u += PDD_TWO_PI;
+                    if (u >= PDD_TWO_PI) u -= PDD_TWO_PI;
+                    A.side[rec] = 0;
+                    A.su[rec] = u;
+                }
+                A.Y[rec] = Yn;
+                A.Z[rec] = Zn;
+                done = true;
             }
-            A.Y[rec] = Yn;
-            A.Z[rec] = Zn;
-            break;
         }
-        my_steps += (unsigned long long)k;
+        if (done) {
+            my_steps += (unsigned long long)k;
+            p = atomicAdd(&next_path, 1);
+            x = x_start;
+            y = y_start;
+            Yv = 1.0;
+            Zv = 0.0;
+            e = 0.f;
+            z = 0.f;
+            k = 0;
+        }
     }
     // block totals
     __shared__ unsigned long long ss[8];
@@ -288,14 +342,17 @@ struct FinalArgs {
     const long *kinv_off;     // per circle (-1 when not IMQ)
     const double *kinv;
     double c2;
-    int paths, mc_floating;
+    int paths, mc_floating, mixed;
+    const int *npaths;               // per-row path counts, or null (paths)
+    const long *rec_off;             // per-row record offsets, or null (slot * paths)
+    const int *gslot;                // index of the row in the system's Monte Carlo arrays, or null (slot)
     const int8_t *side;
     const double *su, *Y, *Z;
     const int *mom_ptr;
     double *moments, *bmean, *val, *se, *b, *se_b;
 };
 
-__global__ void __launch_bounds__(1024) k_mc_finalize(Problem P, FinalArgs F) {
+__global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
     extern __shared__ double fsm[];                   // [32 batches][ns] moments, then per-batch C
     __shared__ double bsum[kBatches];
     __shared__ int bcnt[kBatches];
@@ -305,65 +362,113 @@ __global__ void __launch_bounds__(1024) k_mc_finalize(Problem P, FinalArgs F) {
     const bool imq = !F.floating[m];
     double *Mb = fsm;                                 // kBatches x ns
     double *Cb = fsm + kBatches * ns;                 // kBatches x ns
+    const int npath = F.npaths ? F.npaths[slot] : F.paths;
+    const long base = F.rec_off ? F.rec_off[slot] : (long)slot * F.paths;
+    const int gs = F.gslot ? F.gslot[slot] : slot;
+    for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each
     double acc[kMaxStencil / 32];
 #pragma unroll
     for (int q = 0; q < kMaxStencil / 32; ++q) acc[q] = 0.0;
     double bs = 0.0;
     int cnt = 0;
-    const long base = (long)slot * F.paths;
-    for (int p = warp; p < F.paths; p += kBatches) {
+    // this lane's stencil angles (IMQ) or knot angles (Fourier cardinals)
+    double uk[kMaxStencil / 32];
+    float ukf[kMaxStencil / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxStencil / 32; ++q) {
+        const int l = lane + 32 * q;
+        uk[q] = (l < ns) ? (imq ? F.ku[a + l] : PDD_TWO_PI * l / ns) : 0.0;
+        ukf[q] = (float)uk[q];
+    }
+    const float c2f = (float)F.c2;
+    // mixed form: 16 paths are summed in FP32, then folded into the FP64 accumulators
+    float accf[kMaxStencil / 32];
+    float bsf = 0.f;
+    int pend = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxStencil / 32; ++q) accf[q] = 0.f;
+    for (int p = bt; p < npath; p += kBatches) {
         const int sd = F.side[base + p];
         if (sd == 2) continue;
         ++cnt;
-        const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
         if (sd == 1) {
             if (lane == 0) {
+                const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
                 double ex, ey;
                 boundary_point(P, su, ex, ey);
                 bs += gdata(P, ex, ey, su) * yv + zv;
             }
-        } else {
-            if (lane == 0) bs += zv;
+            continue;
+        }
+        if (F.mixed && imq) {
+            const float yf = (float)F.Y[base + p];
+            const float suf = (float)F.su[base + p];
+            if (lane == 0) bsf += (float)F.Z[base + p];
 #pragma unroll
             for (int q = 0; q < kMaxStencil / 32; ++q) {
-                const int l = lane + 32 * q;
-                if (l < ns) {
-                    double phi;
-                    if (imq) {
-                        const double d = su - F.ku[a + l];
-                        phi = 1.0 / sqrt(d * d + F.c2);
-                    } else {
-                        // Fourier cardinal of knot l (Eq. 18), closed form
-                        double x = remainder(su - PDD_TWO_PI * l / ns, PDD_TWO_PI);
-                        phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
-                    }
-                    acc[q] += yv * phi;
-                }
+                const float df = suf - ukf[q];
+                accf[q] = fmaf(yf, rsqrtf(df * df + c2f), accf[q]);
             }
+            if (++pend == 16) {
+#pragma unroll
+                for (int q = 0; q < kMaxStencil / 32; ++q) {
+                    acc[q] += (double)accf[q];
+                    accf[q] = 0.f;
+                }
+                bs += (double)bsf;
+                bsf = 0.f;
+                pend = 0;
+            }
+            continue;
+        }
+        const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
+        if (lane == 0) bs += zv;
+#pragma unroll
+        for (int q = 0; q < kMaxStencil / 32; ++q) {
+            const int l = lane + 32 * q;
+            if (l >= ns) continue;
+            double phi;
+            if (imq) {
+                const double d = su - uk[q];
+                phi = 1.0 / sqrt(d * d + F.c2);
+            } else {
+                // Fourier cardinal of knot l (Eq. 18), closed form
+                const double x = remainder(su - uk[q], PDD_TWO_PI);
+                phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
+            }
+            acc[q] += yv * phi;
         }
     }
 #pragma unroll
     for (int q = 0; q < kMaxStencil / 32; ++q) {
         const int l = lane + 32 * q;
-        if (l < ns) Mb[warp * ns + l] = acc[q];
+        acc[q] += (l < ns) ? (double)accf[q] : 0.0;
+    }
+    bs += (double)bsf;
+#pragma unroll
+    for (int q = 0; q < kMaxStencil / 32; ++q) {
+        const int l = lane + 32 * q;
+        if (l < ns) Mb[bt * ns + l] = acc[q];
     }
     if (lane == 0) {
-        bsum[warp] = bs;
-        bcnt[warp] = cnt;
+        bsum[bt] = bs;
+        bcnt[bt] = cnt;
+    }
     }
     __syncthreads();
     // per-batch C estimates (batch means)
     const double *Ki = imq ? F.kinv + F.kinv_off[m] : nullptr;
-    for (int j = lane; j < ns; j += 32) {
-        double v = 0.0;
-        const int nb = bcnt[warp];
-        if (imq) {
-            for (int l = 0; l < ns; ++l) v -= Ki[l * ns + j] * Mb[warp * ns + l];
-        } else {
-            v = -Mb[warp * ns + j];
+    for (int bt = warp; bt < kBatches; bt += 16)
+        for (int j = lane; j < ns; j += 32) {
+            double v = 0.0;
+            const int nb = bcnt[bt];
+            if (imq) {
+                for (int l = 0; l < ns; ++l) v -= Ki[l * ns + j] * Mb[bt * ns + l];
+            } else {
+                v = -Mb[bt * ns + j];
+            }
+            Cb[bt * ns + j] = nb ? v / nb : 0.0;
         }
-        Cb[warp * ns + j] = nb ? v / nb : 0.0;
-    }
     __syncthreads();
     if (warp == 0) {
         int ntot = 0;
@@ -386,7 +491,7 @@ __global__ void __launch_bounds__(1024) k_mc_finalize(Problem P, FinalArgs F) {
             var *= (double)kBatches / (kBatches - 1);
             F.val[rp + off + j] = mean;
             F.se[rp + off + j] = sqrt(var);
-            F.moments[F.mom_ptr[slot] + j] = msum * inv;
+            F.moments[F.mom_ptr[gs] + j] = msum * inv;
         }
         if (lane == 0) {
             double tot = 0.0;
@@ -400,7 +505,7 @@ __global__ void __launch_bounds__(1024) k_mc_finalize(Problem P, FinalArgs F) {
             }
             var *= (double)kBatches / (kBatches - 1);
             F.b[i] = bm;
-            F.bmean[slot] = bm;
+            F.bmean[gs] = bm;
             F.se_b[i] = sqrt(var);
         }
     }
@@ -462,6 +567,23 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
     if (hb) fail(PDD_EINVAL, "IMQ matrix not positive definite (coincident stencil angles)");
 }
 
+// adaptive path count of each row from its pilot standard errors
+__global__ void k_need(int nmc, const int *rows, const int *row_sub, const int *knot_ptr, const int *rowptr,
+                       const double *se, const double *se_b, int P0, int Pmax, double target, int *need) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= nmc) return;
+    const int i = rows[slot], m = row_sub[i];
+    const int a = knot_ptr[m], ns = knot_ptr[m + 1] - a, off = (i < a) ? 1 : 0;
+    double mx = se_b[i];
+    for (int j = 0; j < ns; ++j) mx = fmax(mx, se[rowptr[i] + off + j]);
+    const double r = mx / target;
+    double want = ceil(P0 * r * r);
+    want = fmin(fmax(want, (double)P0), (double)Pmax);
+    int w = (int)want;
+    w = ((w + 31) / 32) * 32;
+    need[slot] = w > Pmax ? Pmax : w;
+}
+
 template <typename R>
 static void launch_paths(const Problem &P, const PathArgs &A, int nrows, cudaStream_t st) {
     const bool kill = P.c_kind != PDD_C_ZERO, src = P.f_kind != PDD_F_ZERO;
@@ -501,7 +623,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
 
     // a11: paths into the record scratch, in waves that bound the scratch size
     const long P_ = o.paths;
-    const size_t per_row = (size_t)P_ * (1 + 3 * sizeof(double));
+    const size_t rec_bytes = 1 + 3 * sizeof(double);
+    const size_t per_row = (size_t)P_ * rec_bytes;
     const int wave = (int)std::max<size_t>(1, std::min<size_t>(nmc, ((size_t)8 << 30) / per_row));
     DevBuf<int8_t> side;
     DevBuf<double> su, Y, Z;
@@ -520,28 +643,89 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     PDD_CUDA(cudaEventCreate(&e1));
     PDD_CUDA(cudaEventCreate(&e2));
     float tp = 0, tf = 0;
-    for (int w0 = 0; w0 < nmc; w0 += wave) {
-        const int nr = std::min(wave, nmc - w0);
-        PathArgs A{sys.mc_rows.p + w0, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
-                   cov.theta_s.p, o.paths, o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p};
+    const int mixed = o.precision == PDD_PREC_MIXED ? 1 : 0;
+    const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
+    PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    auto run_wave = [&](const int *rows, int nr, const int *np, const long *roff, const int *gsl, const int *momp,
+                        double *bmean) {
+        PathArgs A{rows, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p, o.paths,
+                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff};
         PDD_CUDA(cudaEventRecord(e0, st));
-        if (o.precision == PDD_PREC_MIXED) launch_paths<float>(P, A, nr, st);
+        if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
         PDD_CUDA(cudaEventRecord(e1, st));
-        FinalArgs F{sys.mc_rows.p + w0, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p, cov.ku.p,
-                    koff_m.p, kinv.p, o.imq_c2, o.paths, mcf, side.p, su.p, Y.p, Z.p, sys.mom_ptr.p + w0,
-                    sys.moments.p, sys.bmean.p + w0, sys.val.p, sys.se.p, sys.b.p, sys.se_b.p};
-        const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
-        PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-        PDD_LAUNCH(k_mc_finalize, nr, 1024, fsm, st, P, F);
+        FinalArgs F{rows, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p,
+                    o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p, momp, sys.moments.p, bmean,
+                    sys.val.p, sys.se.p, sys.b.p, sys.se_b.p};
+        PDD_LAUNCH(k_mc_finalize, nr, 512, fsm, st, P, F);
         PDD_CUDA(cudaEventRecord(e2, st));
         PDD_CUDA(cudaEventSynchronize(e2));
-        float a = 0, b = 0;
-        cudaEventElapsedTime(&a, e0, e1);
-        cudaEventElapsedTime(&b, e1, e2);
-        tp += a;
-        tf += b;
+        float ta = 0, tb = 0;
+        cudaEventElapsedTime(&ta, e0, e1);
+        cudaEventElapsedTime(&tb, e1, e2);
+        tp += ta;
+        tf += tb;
+    };
+    for (int w0 = 0; w0 < nmc; w0 += wave) {
+        const int nr = std::min(wave, nmc - w0);
+        run_wave(sys.mc_rows.p + w0, nr, nullptr, nullptr, nullptr, sys.mom_ptr.p + w0, sys.bmean.p + w0);
     }
+    ms.paths_total = (int64_t)nmc * P_;
+    sys.mc_np.alloc(nmc);
+    std::vector<int> need(nmc, (int)P_);
+    // adaptive path counts: rows whose largest standard error exceeds the target rerun with
+    // P0 (se/target)^2 paths (capped at paths_max); path ids continue the pilot's streams
+    if (o.paths_max > o.paths && o.se_target > 0.0) {
+        DevBuf<int> dneed;
+        dneed.alloc(nmc);
+        PDD_LAUNCH(k_need, cdiv(nmc, 256), 256, 0, st, nmc, sys.mc_rows.p, cov.row_sub.p, cov.knot_ptr.p,
+                   cov.rowptr.p, sys.se.p, sys.se_b.p, o.paths, o.paths_max, o.se_target, dneed.p);
+        PDD_CUDA(cudaMemcpyAsync(need.data(), dneed.p, nmc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> ext_slot, ext_row_host;
+        std::vector<int> hrows(nmc);
+        PDD_CUDA(cudaMemcpyAsync(hrows.data(), sys.mc_rows.p, nmc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < nmc; ++k)
+            if (need[k] > P_) ext_slot.push_back(k);
+        size_t q = 0;
+        const size_t budget = (size_t)8 << 30;
+        while (q < ext_slot.size()) {
+            std::vector<int> rows, np, gsl;
+            std::vector<long> roff;
+            size_t used = 0;
+            long off = 0;
+            while (q < ext_slot.size() && (rows.empty() || used + (size_t)need[ext_slot[q]] * rec_bytes <= budget)) {
+                const int k = ext_slot[q++];
+                rows.push_back(hrows[k]);
+                np.push_back(need[k]);
+                gsl.push_back(k);
+                roff.push_back(off);
+                off += need[k];
+                used += (size_t)need[k] * rec_bytes;
+                ms.paths_total += need[k];
+                ++ms.extended_rows;
+            }
+            DevBuf<int> drows, dnp, dgsl;
+            DevBuf<long> droff;
+            drows.alloc(rows.size());
+            dnp.alloc(rows.size());
+            dgsl.alloc(rows.size());
+            droff.alloc(rows.size());
+            PDD_CUDA(cudaMemcpyAsync(drows.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            PDD_CUDA(cudaMemcpyAsync(dnp.p, np.data(), np.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            PDD_CUDA(cudaMemcpyAsync(dgsl.p, gsl.data(), gsl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            PDD_CUDA(cudaMemcpyAsync(droff.p, roff.data(), roff.size() * sizeof(long), cudaMemcpyHostToDevice, st));
+            if ((size_t)off > side.n) {
+                side.alloc(off);
+                su.alloc(off);
+                Y.alloc(off);
+                Z.alloc(off);
+            }
+            run_wave(drows.p, (int)rows.size(), dnp.p, droff.p, dgsl.p, sys.mom_ptr.p, sys.bmean.p);
+        }
+    }
+    PDD_CUDA(cudaMemcpyAsync(sys.mc_np.p, need.data(), nmc * sizeof(int), cudaMemcpyHostToDevice, st));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
@@ -614,7 +798,8 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
     const double inv2s = nw ? 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma) : 0.0;
-    for (int p = tid; p < A.paths; p += T) {
+    const int npath = A.npaths ? A.npaths[slot] : A.paths;
+    for (int p = tid; p < npath; p += T) {
         R x = (R)A.kx[i], y = (R)A.ky[i];
         double Yv = 1.0, Zv = 0.0;
         for (int q = 0; q < nw; ++q) {
@@ -733,7 +918,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
         for (int q = 0; q < nw; ++q) Gw[q * T + tid] += payoff * Yv * S[q * T + tid] + dZ[q * T + tid];
     }
     __syncthreads();
-    const double scale = G.lambda[i] / A.paths;
+    const double scale = G.lambda[i] / npath;
     for (int q = tid; q < nw + ng; q += T) {
         const double *src = (q < nw) ? Gw + (size_t)q * T : Gg + (size_t)(q - nw) * T;
         double s = 0.0;
@@ -760,7 +945,7 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     steps.alloc(1);
     capped.alloc(1);
     PathArgs A{sys.mc_rows.p, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p,
-               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p};
+               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p, sys.mc_np.p, nullptr};
     GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
     const int T = 64;
     const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);

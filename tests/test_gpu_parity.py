@@ -75,11 +75,11 @@ def _row_err(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_floating_rows_tiny(pdd, precision):
+@pytest.mark.parametrize("precision,factor", [("fp64", "blocked"), ("mixed", "recursive_tc"), ("mixed", "blocked")])
+def test_floating_rows_tiny(pdd, precision, factor):
     cfg = workloads.tiny(paths=64)
     oc = _oracle_cover("tiny", cfg)
-    S = pdd.System(pdd.Cover(cfg), cfg, precision)
+    S = pdd.System(pdd.Cover(cfg), cfg, precision, factor=factor)
     g = _np(S.csr())
     ref = osystem.assemble(cfg, oc, rows=[i for i in range(oc.N) if oc.row_sub[i] >= 0 and oc.floating[oc.row_sub[i]]])
     assert len(ref.fl_rows) == 64
@@ -93,12 +93,12 @@ def test_floating_rows_tiny(pdd, precision):
         assert st["unconverged_disks"] == 0 and st["max_refine_sweeps"] >= 2
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_floating_rows_varcoef_sampled(pdd, precision):
+@pytest.mark.parametrize("precision,factor", [("fp64", "blocked"), ("mixed", "recursive_tc"), ("mixed", "blocked")])
+def test_floating_rows_varcoef_sampled(pdd, precision, factor):
     """Full-size variable-coefficient workload; 6 disks recomputed by the oracle."""
     cfg = workloads.varcoef(paths=64)
     oc = _oracle_cover("varcoef", cfg)
-    S = pdd.System(pdd.Cover(cfg), cfg, precision)
+    S = pdd.System(pdd.Cover(cfg), cfg, precision, factor=factor)
     g = _np(S.csr())
     rng = np.random.default_rng(4)
     disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
@@ -115,6 +115,43 @@ def test_floating_rows_varcoef_sampled(pdd, precision):
             assert abs(g["b"][i] - bi) <= 1e-10 * max(abs(bi), 1e-3)
     if precision == "mixed":
         assert S.stats()["unconverged_disks"] == 0
+
+
+@pytest.mark.parametrize("leaf,tmin", [(32, 128), (16, 64), (8, 64), (16, 1000000)])
+def test_recursive_lu_candidates(pdd, leaf, tmin):
+    """Every factorisation the autotuner may pick gives the oracle's floating rows (varcoef, 6 disks)."""
+    cfg = workloads.varcoef(paths=16)
+    oc = _oracle_cover("varcoef", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "mixed", lu_leaf_width=leaf, lu_tensor_min=tmin)
+    assert S.stats()["unconverged_disks"] == 0
+    g = _np(S.csr())
+    from oracle import problem, spectral
+    op = problem.Operator(cfg["op"], oc.domain)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    for m in np.random.default_rng(leaf).choice(disks, 3, replace=False):
+        for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m)).items():
+            pos = oc.rowptr[i] + np.searchsorted(oc.col[oc.rowptr[i]:oc.rowptr[i + 1]], cols)
+            assert _row_err(g["val"][pos], v) < 1e-10, (leaf, tmin, m, i)
+
+
+def test_floating_rows_scaled_sampled(pdd):
+    """The 48(r) x 64(theta) grid (n = 3072) of the scaled workload: recursive tensor-core LU + FP64
+    refinement on 3,600 disks; 2 disks recomputed by the oracle (Householder QR of 3072 x 3072)."""
+    cfg = workloads.scaled(paths=16)
+    oc = _oracle_cover("scaled", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "mixed")
+    g = _np(S.csr())
+    st = S.stats()
+    assert st["unconverged_disks"] == 0 and st["floating_disks"] == 3600
+    from oracle import problem, spectral
+    op = problem.Operator(cfg["op"], oc.domain)
+    rng = np.random.default_rng(2)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    for m in rng.choice(disks, 2, replace=False):
+        for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m)).items():
+            a, b = oc.rowptr[i], oc.rowptr[i + 1]
+            pos = np.searchsorted(oc.col[a:b], cols)
+            assert _row_err(g["val"][a + pos], v) < 1e-10, (m, i)
 
 
 def test_mc_rows_identical_streams_tiny(pdd):
@@ -159,6 +196,26 @@ def test_mc_rows_identical_streams_varcoef_sampled(pdd):
     for k in pick:
         i = int(rows[k])
         r = ref.mc_rows[i]
+        got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
+        assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max()), i
+        assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
+
+
+def test_mc_adaptive_path_counts_identical_streams(pdd):
+    """Adaptive path counts: the GPU and the oracle apply the rule to their own pilots (batch-means
+    standard errors) and must pick the same counts; the final estimates agree at 1e-12."""
+    cfg = workloads.tiny(paths=64)
+    cfg["mc"] = dict(cfg["mc"], paths_max=2048, se_target=0.01)
+    oc = _oracle_cover("tiny", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    mc = _np(S.mc())
+    rows = mc["rows"]
+    st = S.stats()
+    assert st["extended_rows"] > 0
+    ref = osystem.assemble(cfg, oc, rows=[int(i) for i in rows], threads=4)
+    assert st["paths_total"] == sum(r.paths for r in ref.mc_rows.values())
+    for k, i in enumerate(rows):
+        r = ref.mc_rows[int(i)]
         got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
         assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max()), i
         assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
@@ -284,3 +341,84 @@ def test_error_statuses(pdd):
     with pytest.raises(pdd.PddError) as e:
         pdd.Cover(corner)
     assert e.value.code == "PDD_EINVAL"
+
+
+def test_adjoint_against_central_differences_gpu(pdd):
+    """The GPU adjoint against central differences of the GPU's own J (same Philox streams).
+
+    Step 1e-4 (truncation O(eps^2)); the bar is the one the oracle's adjoint meets.
+    """
+    base = workloads.grad(paths=64)
+    oc = _oracle_cover("grad", base)
+    rng = np.random.default_rng(9)
+    u_obs = torch.tensor(np.exp(oc.kx) * np.sin(oc.ky) + 0.01 * rng.standard_normal(oc.N), device="cuda")
+
+    def J(cfg):
+        S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+        u = S.solve(rtol=1e-15)
+        return float(((u - u_obs) ** 2).sum().item()), S, u
+
+    J0, S, u = J(base)
+    g = S.grad(u, 2.0 * (u - u_obs)).cpu().numpy()
+    nw = base["op"]["rbf"]["w"].size
+    eps = 1e-4
+    for kind, idx in (("w", 3), ("w", 50), ("a", 1), ("a", 17)):
+        vals = []
+        for sgn in (1.0, -1.0):
+            c = workloads.grad(paths=64)
+            if kind == "w":
+                c["op"]["rbf"]["w"] = c["op"]["rbf"]["w"].copy()
+                c["op"]["rbf"]["w"][idx] += sgn * eps
+            else:
+                c["op"]["g_coef"] = c["op"]["g_coef"].copy()
+                c["op"]["g_coef"][idx] += sgn * eps
+            vals.append(J(c)[0])
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        got = g[idx] if kind == "w" else g[nw + idx]
+        assert abs(fd - got) <= 1e-6 * max(1e-2, abs(fd)), (kind, idx, fd, got)
+
+
+def test_adaptive_cover_and_rows(pdd):
+    """Batching workload: unit disk, 7,108 circles of log-normal radii, grids 16^2..64^2, c from 64
+    Gaussians.  Cover bit-exact; one disk of every grid shape and 4 Monte Carlo rows (FP64,
+    identical streams) recomputed by the oracle."""
+    cfg = workloads.adaptive(paths=200, paths_max=0)
+    oc = _oracle_cover("adaptive", cfg)
+    cov = pdd.Cover(cfg)
+    a = _np(cov.arrays())
+    assert (cov.M, cov.N, cov.nnz) == (oc.M, oc.N, oc.col.size)
+    for k in ("knot_ptr", "kowner", "row_sub", "rowptr", "col"):
+        assert np.array_equal(a[k].astype(np.int64), getattr(oc, k).astype(np.int64)), k
+    from oracle import problem, spectral
+    op = problem.Operator(cfg["op"], oc.domain)
+    for prec in ("mixed", "fp64"):
+        S = pdd.System(cov, cfg, prec)
+        g = _np(S.csr())
+        st = S.stats()
+        assert st["unconverged_disks"] == 0
+        if prec == "mixed":
+            seen = {}
+            for m in range(oc.M):
+                if oc.floating[m] and oc.sub_rows(m).size and oc.n_r[m] not in seen:
+                    seen[oc.n_r[m]] = m
+            assert len(seen) >= 5
+            for nr, m in seen.items():
+                if nr > 40:
+                    continue                   # the oracle's QR of n >= 2304 is checked on one grid below
+                for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m)).items():
+                    pos = oc.rowptr[i] + np.searchsorted(oc.col[oc.rowptr[i]:oc.rowptr[i + 1]], cols)
+                    assert _row_err(g["val"][pos], v) < 1e-10, (nr, m, i)
+            m = seen[max(seen)]
+            for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m)).items():
+                pos = oc.rowptr[i] + np.searchsorted(oc.col[oc.rowptr[i]:oc.rowptr[i + 1]], cols)
+                assert _row_err(g["val"][pos], v) < 1e-10, (max(seen), m, i)
+        else:
+            mc = _np(S.mc())
+            rows = mc["rows"]
+            pick = np.random.default_rng(3).choice(rows.size, 4, replace=False)
+            ref = osystem.assemble(cfg, oc, rows=[int(rows[k]) for k in pick], threads=4)
+            for k in pick:
+                r = ref.mc_rows[int(rows[k])]
+                got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
+                assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max())
+                assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))

@@ -21,7 +21,8 @@ Workloads (the problem is Eq. 1 with L = 1/2 Laplacian + b.grad, sigma = I):
                    16 knots; 1,000 paths, h=1e-5.
 * ``adaptive``  -- unit disk, c(x) from 64 Gaussian RBFs (clipped to <= 0), f=0,
                    g=e^x sin y; ~10^4 circles with log-normal radii in [0.02, 0.1];
-                   per-circle grids 16^2..64^2 chosen by radius.
+                   per-circle grids 16^2..64^2 chosen by radius; 10^3 pilot paths per
+                   Monte Carlo knot, up to 10^5 where its standard error exceeds 2e-3.
 * ``grad``      -- ``tiny`` geometry; parameters are 64 RBF weights of c and 32
                    Fourier coefficients of g along the boundary arclength.
 
@@ -126,7 +127,8 @@ def rbf_field(n: int = 64, seed: int = 1, sigma: float = 0.2, negative: bool = F
             "sigma": float(sigma)}
 
 
-def adaptive(paths: int = 1000, h: float = 1e-5, seed: int = 0, cells: int = 16) -> dict:
+def adaptive(paths: int = 1000, h: float = 1e-5, seed: int = 0, cells: int = 16,
+             paths_max: int = 100000, se_target: float = 2e-3) -> dict:
     """Unit disk with an adaptive cover of log-normal radii (drawn here, seed 0).
 
     The domain's bounding box [-1,1]^2 is cut into ``cells`` x ``cells`` macro
@@ -162,7 +164,9 @@ def adaptive(paths: int = 1000, h: float = 1e-5, seed: int = 0, cells: int = 16)
         "n_knots": 0, "n_r": 0, "n_theta": 0,
         "op": {"b": "zero", "c": "rbf", "f": "zero", "g": "exp_sin",
                "rbf": rbf_field(64, seed=1, sigma=0.2, negative=False)},
-        "mc": {"paths": paths, "h": h, "seed": seed},
+        # pilot of `paths` per Monte Carlo knot, then up to paths_max where the largest
+        # standard error of the row exceeds se_target
+        "mc": {"paths": paths, "h": h, "seed": seed, "paths_max": paths_max, "se_target": se_target},
         "imq_c2": 1.5,
     }
 
