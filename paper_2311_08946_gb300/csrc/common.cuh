@@ -251,13 +251,20 @@ __device__ __forceinline__ void normals64(uint64_t seed, uint32_t knot, uint32_t
     xi1 = rr * s;
 }
 
-// 24-bit uniforms for the mixed-precision form
+// 23-bit uniforms in (0, 1) for the mixed-precision form, built from the
+// mantissa bits (no conversion instruction): [1.m] - 1 = m 2^-23 with
+// m = w >> 9 (exact), plus half a step; u follows the leading bits of w like
+// the 53-bit form does
+__device__ __forceinline__ float uniform23(uint32_t w) {
+    return (__uint_as_float(0x3f800000u | (w >> 9)) - 1.0f) + 0x1p-24f;
+}
+
 __device__ __forceinline__ void normals32(uint64_t seed, uint32_t knot, uint32_t step, uint32_t path,
                                           float &xi0, float &xi1) {
     U4 w = philox10(step, path, 0u, 0u, (uint32_t)(seed & 0xffffffffu), knot);
-    float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    float rr = sqrtf(-2.0f * logf(u1));
+    const float u1 = uniform23(w.x);
+    const float u2 = uniform23(w.z);
+    const float rr = sqrtf(-2.0f * logf(u1));
     float s, c;
     sincospif(2.0f * u2, &s, &c);
     xi0 = rr * c;

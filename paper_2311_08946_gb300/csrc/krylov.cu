@@ -162,8 +162,11 @@ void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const
     PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, x, y, (const GState *)nullptr);
 }
 
+// The m Arnoldi iterations of a restart cycle (about 8 kernels each) are
+// captured once into a CUDA graph and replayed once per cycle; the stop flag
+// on the device turns the remaining kernels of a converged cycle into no-ops.
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
-                      const pdd_solve_opts &o, cudaStream_t st) {
+                      const pdd_solve_opts &o, cudaStream_t st_in) {
     const int m = std::max(1, std::min(256, o.restart));
     const int G = std::max(1, std::min(1024, cdiv(n, 512)));
     DevBuf<double> V, w, partial, H, cs, sn, g, y;
@@ -177,53 +180,98 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
     g.alloc(m + 1);
     y.alloc(m);
     gs.alloc(1);
+    // graph capture needs a capturable stream: the legacy default stream is replaced by a private one
+    cudaStream_t st = st_in;
+    bool own = false;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    if (st_in == 0 || st_in == cudaStreamLegacy) {
+        PDD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        PDD_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+        PDD_CUDA(cudaEventRecord(ev_in, st_in));
+        PDD_CUDA(cudaStreamWaitEvent(st, ev_in, 0));
+        own = true;
+    }
     PDD_CUDA(cudaMemsetAsync(gs.p, 0, sizeof(GState), st));
     PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
     PDD_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * (m + 1) * m, st));
     const int vb = std::min(cdiv(n, 256), 2048);
     SolveResult res;
     const int max_iters = std::max(1, o.max_iters);
-    for (int cycle = 0;; ++cycle) {
-        // r = b - C u  (u = 0 on the first cycle)
-        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
-        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
-        PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
-        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, partial.p, G, (double *)nullptr, gs.p);
-        for (int j = 0; j < m; ++j) {
-            double *vj = V.p + (long)j * n;
-            double *Hc = H.p + (long)j * (m + 1);
-            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
-            for (int pass = 0; pass < 2; ++pass) {
-                PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, gs.p);
-                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, G, Hc, pass, gs.p);
+    cudaGraphExec_t exec = nullptr;
+    int per_cycle = 0;
+    std::vector<double> hp(G);
+    try {
+        for (int cycle = 0;; ++cycle) {
+            // r = b - C u  (u = 0 on the first cycle)
+            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
+            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, partial.p, G, (double *)nullptr, gs.p);
+            if (!exec) {
+                const int64_t before = pdd_launch_count();
+                cudaGraph_t graph;
+                PDD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                for (int j = 0; j < m; ++j) {
+                    double *vj = V.p + (long)j * n;
+                    double *Hc = H.p + (long)j * (m + 1);
+                    PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
+                    for (int pass = 0; pass < 2; ++pass) {
+                        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, gs.p);
+                        PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, G, Hc, pass, gs.p);
+                    }
+                    PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, gs.p);
+                    PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, partial.p, G,
+                               Hc + j + 1, gs.p);
+                    PDD_LAUNCH(k_givens, 1, 1, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
+                }
+                PDD_CUDA(cudaStreamEndCapture(st, &graph));
+                PDD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                cudaGraphDestroy(graph);
+                per_cycle = (int)(pdd_launch_count() - before);
+                count_launch(-per_cycle);          // captured, not run: counted when the graph runs
             }
-            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, gs.p);
-            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, partial.p, G,
-                       Hc + j + 1, gs.p);
-            PDD_LAUNCH(k_givens, 1, 1, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
+            PDD_CUDA(cudaGraphLaunch(exec, st));
+            count_launch(per_cycle);
+            PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H.p, m + 1, g.p, y.p, gs.p);
+            PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V.p, y.p, gs.p, u);
+            // true residual
+            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
+            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
+            GState hg{};
+            PDD_CUDA(cudaMemcpyAsync(hp.data(), partial.p, G * sizeof(double), cudaMemcpyDeviceToHost, st));
+            PDD_CUDA(cudaMemcpyAsync(&hg, gs.p, sizeof(GState), cudaMemcpyDeviceToHost, st));
+            PDD_CUDA(cudaStreamSynchronize(st));
+            double rs = 0.0;
+            for (int q = 0; q < G; ++q) rs += hp[q];
+            const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
+            res.iters = hg.iters;
+            res.rel = rel;
+            if (hg.bnorm == 0.0 || rel <= o.rtol) {
+                res.converged = 1;
+                break;
+            }
+            if (hg.iters >= max_iters) break;
         }
-        PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H.p, m + 1, g.p, y.p, gs.p);
-        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V.p, y.p, gs.p, u);
-        // true residual
-        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
-        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
-        std::vector<double> hp(G);
-        GState hg{};
-        PDD_CUDA(cudaMemcpyAsync(hp.data(), partial.p, G * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PDD_CUDA(cudaMemcpyAsync(&hg, gs.p, sizeof(GState), cudaMemcpyDeviceToHost, st));
-        PDD_CUDA(cudaStreamSynchronize(st));
-        double rs = 0.0;
-        for (int q = 0; q < G; ++q) rs += hp[q];
-        const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
-        res.iters = hg.iters;
-        res.rel = rel;
-        if (hg.bnorm == 0.0 || rel <= o.rtol) {
-            res.converged = 1;
-            break;
+    } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (own) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+            cudaEventDestroy(ev_in);
         }
-        if (hg.iters >= max_iters) break;
+        throw;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (own) {
+        PDD_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+        PDD_CUDA(cudaEventRecord(ev_out, st));
+        PDD_CUDA(cudaStreamWaitEvent(st_in, ev_out, 0));
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        cudaEventDestroy(ev_in);
+        cudaEventDestroy(ev_out);
     }
     return res;
 }

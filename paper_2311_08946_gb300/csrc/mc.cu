@@ -96,6 +96,7 @@ struct PathArgs {
     int *capped;
     const int *npaths;               // per-row path counts (adaptive), or null
     const long *rec_off;             // per-row record offsets, or null (slot * paths)
+    float2 *ez;                      // mixed form: the unfolded FP32 increments (e, z) of each record
 };
 
 __device__ __forceinline__ double circle_exit_t(double px, double py, double dx, double dy, double ox,
@@ -108,6 +109,19 @@ __device__ __forceinline__ double circle_exit_t(double px, double py, double dx,
     if (disc < 0.0) disc = 0.0;
     const double sq = sqrt(disc);
     return (b >= 0.0) ? -c / (b + sq) : (sq - b) / a;
+}
+
+// first crossing of the segment P -> P + D with the circle |z - o| = rad (P inside), in R
+template <typename R>
+__device__ __forceinline__ R circle_exit_tr(R px, R py, R dx, R dy, R ox, R oy, R rad) {
+    const R qx = px - ox, qy = py - oy;
+    const R a = dx * dx + dy * dy;
+    const R b = qx * dx + qy * dy;
+    const R c = qx * qx + qy * qy - rad * rad;
+    R disc = b * b - a * c;
+    if (disc < (R)0) disc = (R)0;
+    const R sq = sqrt(disc);
+    return (b >= (R)0) ? -c / (b + sq) : (sq - b) / a;
 }
 
 template <typename R>
@@ -182,6 +196,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
+    const float hf = (float)A.h;
     // domain bounds in the position type (FP32 in the mixed form)
     const R d0 = (R)P.dom[0], d1 = (R)P.dom[1], d2 = (R)P.dom[2], d3 = (R)P.dom[3];
     const R dr2 = (R)(P.dom[2] * P.dom[2]);
@@ -200,6 +215,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     double Yv = 1.0, Zv = 0.0;
     float e = 0.f, z = 0.f;    // mixed form: Y = Yv (1 + e), Z = Zv + Yv z (FP32 block increments)
     int k = 0;
+    unsigned it = 0;           // loop iterations, equal in all active lanes
     while (p < npath) {
         const long rec = rbase + p;
         bool done = false;
@@ -208,6 +224,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
             A.su[rec] = 0.0;
             A.Y[rec] = 0.0;
             A.Z[rec] = 0.0;
+            if constexpr (sizeof(R) == 4) A.ez[rec] = make_float2(0.f, 0.f);
             ++my_capped;
             done = true;
         } else {
@@ -223,7 +240,6 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                 if (SRC) Zn = Zv + source(P, (double)x, (double)y) * Yv * A.h;
             } else {
                 const float cv = KILL ? killing32(P, (float)x, (float)y) : 0.f;
-                const float hf = (float)A.h;
                 // Z_{k+1} = Z_k + f_k h Y_k and Y_{k+1} = Y_k (1 + c_k h), with Y_k = Yv (1 + e)
                 if (SRC) zn = fmaf(source32_given(P, (float)x, (float)y, (float)bx, (float)by, cv) * hf, 1.0f + e, z);
                 if (KILL) en = fmaf(cv * hf, 1.0f + e, e);
@@ -242,7 +258,10 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
             }
             const bool out_d = !in_d;
             if constexpr (sizeof(R) == 4) {
-                if ((k & 7) == 0 || out_c || out_d) {     // fold the FP32 increments into the FP64 weights
+                // fold the FP32 increments into the FP64 weights every 8 iterations of the loop (the
+                // same iterations in every lane of the warp, so the FP64 work is not divergent); the
+                // increments left at the exit go to the record and the finalize folds them
+                if ((++it & 7) == 0) {
                     Zn = fma(Yv, (double)zn, Zv);
                     Yn = fma(Yv, (double)en, Yv);
                     en = 0.f;
@@ -257,42 +276,41 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                 e = en;
                 z = zn;
             } else {
-                // exit point on the segment (in FP64 from the FP64 or FP32 end points)
-                const double xd = (double)x, yd = (double)y;
-                const double dx = (double)nx - xd, dy = (double)ny - yd;
-                double tc = 2.0, td = 2.0;
+                // exit point on the segment, in the position type (FP64 form: FP64; mixed: FP32)
+                const R dx = nx - x, dy = ny - y;
+                R tc = (R)2, td = (R)2;
                 int ed = -1;
-                if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
+                if (out_c) tc = circle_exit_tr<R>(x, y, dx, dy, rcx, rcy, (R)rad);
                 if (out_d) {
                     if (P.dom_kind == 0) {
-                        // the edges as the in-loop test saw them (FP32-rounded in the mixed form)
-                        const double D0 = (double)d0, D1 = (double)d1, D2 = (double)d2, D3 = (double)d3;
-                        double t;
-                        if ((double)nx <= D0) { t = (D0 - xd) / dx; if (t < td) { td = t; ed = 3; } }
-                        if ((double)nx >= D2) { t = (D2 - xd) / dx; if (t < td) { td = t; ed = 1; } }
-                        if ((double)ny <= D1) { t = (D1 - yd) / dy; if (t < td) { td = t; ed = 0; } }
-                        if ((double)ny >= D3) { t = (D3 - yd) / dy; if (t < td) { td = t; ed = 2; } }
+                        R t;
+                        if (nx <= d0) { t = (d0 - x) / dx; if (t < td) { td = t; ed = 3; } }
+                        if (nx >= d2) { t = (d2 - x) / dx; if (t < td) { td = t; ed = 1; } }
+                        if (ny <= d1) { t = (d1 - y) / dy; if (t < td) { td = t; ed = 0; } }
+                        if (ny >= d3) { t = (d3 - y) / dy; if (t < td) { td = t; ed = 2; } }
                     } else {
-                        td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
+                        td = circle_exit_tr<R>(x, y, dx, dy, d0, d1, (R)P.dom[2]);
                         ed = 0;
                     }
                 }
                 if (td <= tc) {
-                    const double ex = xd + td * dx, ey = yd + td * dy;
+                    const R ex = x + td * dx, ey = y + td * dy;
                     A.side[rec] = 1;
-                    A.su[rec] = boundary_s(P, ex, ey, ed);
+                    A.su[rec] = boundary_s(P, (double)ex, (double)ey, ed);
                 } else {
-                    const double ex = xd + tc * dx, ey = yd + tc * dy;
-                    double th = atan2(ey - cy, ex - cx);
-                    if (th < 0.0) th += PDD_TWO_PI;
-                    double u = th - ts;
-                    if (u < 0.0) u += PDD_TWO_PI;
-                    if (u >= PDD_TWO_PI) u -= PDD_TWO_PI;
+                    const R ex = x + tc * dx, ey = y + tc * dy;
+                    R th = atan2(ey - rcy, ex - rcx);
+                    const R two_pi = (R)PDD_TWO_PI;
+                    if (th < (R)0) th += two_pi;
+                    R u = th - (R)ts;
+                    if (u < (R)0) u += two_pi;
+                    if (u >= two_pi) u -= two_pi;
                     A.side[rec] = 0;
-                    A.su[rec] = u;
+                    A.su[rec] = (double)u;
                 }
                 A.Y[rec] = Yn;
                 A.Z[rec] = Zn;
+                if constexpr (sizeof(R) == 4) A.ez[rec] = make_float2(en, zn);
                 done = true;
             }
         }
@@ -335,6 +353,24 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
 // ---------------------------------------------------------------------------
 // a12
 // ---------------------------------------------------------------------------
+// Dirichlet data in FP32 (mixed form's boundary scores)
+__device__ __forceinline__ float gdata32(const Problem &P, float x, float y, float s) {
+    switch (P.g_kind) {
+        case PDD_G_EXP_SIN: return expf(x) * sinf(y);
+        case PDD_G_SIN_COS: return sinpif(x) * cospif(y);
+        case PDD_G_BOUNDARY_FOURIER: {
+            const int kc = (P.n_gcoef + 1) / 2, ks = P.n_gcoef - kc;
+            const float w = s * (float)(2.0 / P.perimeter);
+            float acc = 0.f;
+            for (int k = 0; k < kc; ++k) acc += (float)P.g_coef[k] * cospif(k * w);
+            for (int k = 1; k <= ks; ++k) acc += (float)P.g_coef[kc + k - 1] * sinpif(k * w);
+            return acc;
+        }
+        case PDD_G_ONE: return 1.f;
+        default: return 0.f;
+    }
+}
+
 struct FinalArgs {
     const int *rows, *row_sub, *knot_ptr, *rowptr;
     const uint8_t *floating;
@@ -348,6 +384,7 @@ struct FinalArgs {
     const int *gslot;                // index of the row in the system's Monte Carlo arrays, or null (slot)
     const int8_t *side;
     const double *su, *Y, *Z;
+    const float2 *ez;                // mixed form: unfolded increments, Y (1 + e) and Z + Y z
     const int *mom_ptr;
     double *moments, *bmean, *val, *se, *b, *se_b;
 };
@@ -365,12 +402,6 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
     const int npath = F.npaths ? F.npaths[slot] : F.paths;
     const long base = F.rec_off ? F.rec_off[slot] : (long)slot * F.paths;
     const int gs = F.gslot ? F.gslot[slot] : slot;
-    for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each
-    double acc[kMaxStencil / 32];
-#pragma unroll
-    for (int q = 0; q < kMaxStencil / 32; ++q) acc[q] = 0.0;
-    double bs = 0.0;
-    int cnt = 0;
     // this lane's stencil angles (IMQ) or knot angles (Fourier cardinals)
     double uk[kMaxStencil / 32];
     float ukf[kMaxStencil / 32];
@@ -381,79 +412,98 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         ukf[q] = (float)uk[q];
     }
     const float c2f = (float)F.c2;
-    // mixed form: 16 paths are summed in FP32, then folded into the FP64 accumulators
-    float accf[kMaxStencil / 32];
-    float bsf = 0.f;
-    int pend = 0;
+    const bool fast = F.mixed && imq;
+    for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each (p mod 32)
+        double acc[kMaxStencil / 32];
+        float accf[kMaxStencil / 32];                      // mixed form: FP32 sums of 16 paths
 #pragma unroll
-    for (int q = 0; q < kMaxStencil / 32; ++q) accf[q] = 0.f;
-    for (int p = bt; p < npath; p += kBatches) {
-        const int sd = F.side[base + p];
-        if (sd == 2) continue;
-        ++cnt;
-        if (sd == 1) {
-            if (lane == 0) {
-                const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
-                double ex, ey;
-                boundary_point(P, su, ex, ey);
-                bs += gdata(P, ex, ey, su) * yv + zv;
-            }
-            continue;
+        for (int q = 0; q < kMaxStencil / 32; ++q) {
+            acc[q] = 0.0;
+            accf[q] = 0.f;
         }
-        if (F.mixed && imq) {
-            const float yf = (float)F.Y[base + p];
-            const float suf = (float)F.su[base + p];
-            if (lane == 0) bsf += (float)F.Z[base + p];
-#pragma unroll
-            for (int q = 0; q < kMaxStencil / 32; ++q) {
-                const float df = suf - ukf[q];
-                accf[q] = fmaf(yf, rsqrtf(df * df + c2f), accf[q]);
-            }
-            if (++pend == 16) {
-#pragma unroll
-                for (int q = 0; q < kMaxStencil / 32; ++q) {
-                    acc[q] += (double)accf[q];
-                    accf[q] = 0.f;
+        int pend = 0;
+        double bs = 0.0;
+        int cnt = 0;
+        // chunks of 32 paths of this batch: lane l loads path bt + 32 (t0 + l)
+        for (int t0 = 0; bt + kBatches * t0 < npath; t0 += 32) {
+            const int pl = bt + kBatches * (t0 + lane);
+            int sd = 2;
+            double yv = 0.0, zv = 0.0, su = 0.0;
+            if (pl < npath) {
+                sd = F.side[base + pl];
+                yv = F.Y[base + pl];
+                zv = F.Z[base + pl];
+                su = F.su[base + pl];
+                if (F.mixed) {
+                    const float2 q = F.ez[base + pl];
+                    zv = fma(yv, (double)q.y, zv);
+                    yv = fma(yv, (double)q.x, yv);
                 }
-                bs += (double)bsf;
-                bsf = 0.f;
-                pend = 0;
             }
-            continue;
+            if (sd != 2) {                                 // this lane's own contribution to r_i
+                ++cnt;
+                if (sd == 1) {
+                    double ex, ey;
+                    boundary_point(P, su, ex, ey);
+                    const double g = F.mixed ? (double)gdata32(P, (float)ex, (float)ey, (float)su) : gdata(P, ex, ey, su);
+                    bs += g * yv + zv;
+                } else {
+                    bs += zv;
+                }
+            }
+            // the chunk's interface exits, in path order, into every lane's basis sums
+            for (int src = 0; src < 32; ++src) {
+                const int s_sd = __shfl_sync(0xffffffffu, sd, src);
+                if (s_sd != 0) continue;
+                const double s_y = __shfl_sync(0xffffffffu, yv, src);
+                const double s_su = __shfl_sync(0xffffffffu, su, src);
+                if (fast) {
+                    const float yf = (float)s_y, suf = (float)s_su;
+#pragma unroll
+                    for (int q = 0; q < kMaxStencil / 32; ++q) {
+                        const float df = suf - ukf[q];
+                        accf[q] = fmaf(yf, rsqrtf(df * df + c2f), accf[q]);
+                    }
+                    if (++pend == 16) {
+#pragma unroll
+                        for (int q = 0; q < kMaxStencil / 32; ++q) {
+                            acc[q] += (double)accf[q];
+                            accf[q] = 0.f;
+                        }
+                        pend = 0;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kMaxStencil / 32; ++q) {
+                        const int l = lane + 32 * q;
+                        if (l >= ns) continue;
+                        double phi;
+                        if (imq) {
+                            const double d = s_su - uk[q];
+                            phi = 1.0 / sqrt(d * d + F.c2);
+                        } else {
+                            // Fourier cardinal of knot l (Eq. 18), closed form
+                            const double x = remainder(s_su - uk[q], PDD_TWO_PI);
+                            phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
+                        }
+                        acc[q] += s_y * phi;
+                    }
+                }
+            }
         }
-        const double yv = F.Y[base + p], zv = F.Z[base + p], su = F.su[base + p];
-        if (lane == 0) bs += zv;
 #pragma unroll
         for (int q = 0; q < kMaxStencil / 32; ++q) {
             const int l = lane + 32 * q;
-            if (l >= ns) continue;
-            double phi;
-            if (imq) {
-                const double d = su - uk[q];
-                phi = 1.0 / sqrt(d * d + F.c2);
-            } else {
-                // Fourier cardinal of knot l (Eq. 18), closed form
-                const double x = remainder(su - uk[q], PDD_TWO_PI);
-                phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
-            }
-            acc[q] += yv * phi;
+            if (l < ns) Mb[bt * ns + l] = acc[q] + (double)accf[q];
         }
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxStencil / 32; ++q) {
-        const int l = lane + 32 * q;
-        acc[q] += (l < ns) ? (double)accf[q] : 0.0;
-    }
-    bs += (double)bsf;
-#pragma unroll
-    for (int q = 0; q < kMaxStencil / 32; ++q) {
-        const int l = lane + 32 * q;
-        if (l < ns) Mb[bt * ns + l] = acc[q];
-    }
-    if (lane == 0) {
-        bsum[bt] = bs;
-        bcnt[bt] = cnt;
-    }
+        for (int o = 16; o; o >>= 1) {
+            bs += __shfl_xor_sync(0xffffffffu, bs, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        }
+        if (lane == 0) {
+            bsum[bt] = bs;
+            bcnt[bt] = cnt;
+        }
     }
     __syncthreads();
     // per-batch C estimates (batch means)
@@ -623,7 +673,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
 
     // a11: paths into the record scratch, in waves that bound the scratch size
     const long P_ = o.paths;
-    const size_t rec_bytes = 1 + 3 * sizeof(double);
+    const int mixed = o.precision == PDD_PREC_MIXED ? 1 : 0;
+    const size_t rec_bytes = 1 + 3 * sizeof(double) + (mixed ? sizeof(float2) : 0);
     const size_t per_row = (size_t)P_ * rec_bytes;
     const int wave = (int)std::max<size_t>(1, std::min<size_t>(nmc, ((size_t)8 << 30) / per_row));
     DevBuf<int8_t> side;
@@ -632,6 +683,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     su.alloc((size_t)wave * P_);
     Y.alloc((size_t)wave * P_);
     Z.alloc((size_t)wave * P_);
+    DevBuf<float2> ez;
+    if (mixed) ez.alloc((size_t)wave * P_);
     DevBuf<unsigned long long> steps;
     DevBuf<int> capped;
     steps.alloc(1);
@@ -643,19 +696,18 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     PDD_CUDA(cudaEventCreate(&e1));
     PDD_CUDA(cudaEventCreate(&e2));
     float tp = 0, tf = 0;
-    const int mixed = o.precision == PDD_PREC_MIXED ? 1 : 0;
     const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
     PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
     auto run_wave = [&](const int *rows, int nr, const int *np, const long *roff, const int *gsl, const int *momp,
                         double *bmean) {
         PathArgs A{rows, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p, o.paths,
-                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff};
+                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p};
         PDD_CUDA(cudaEventRecord(e0, st));
         if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
         PDD_CUDA(cudaEventRecord(e1, st));
         FinalArgs F{rows, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p,
-                    o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p, momp, sys.moments.p, bmean,
+                    o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p, ez.p, momp, sys.moments.p, bmean,
                     sys.val.p, sys.se.p, sys.b.p, sys.se_b.p};
         PDD_LAUNCH(k_mc_finalize, nr, 512, fsm, st, P, F);
         PDD_CUDA(cudaEventRecord(e2, st));
@@ -721,6 +773,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
                 su.alloc(off);
                 Y.alloc(off);
                 Z.alloc(off);
+                if (mixed) ez.alloc(off);
             }
             run_wave(drows.p, (int)rows.size(), dnp.p, droff.p, dgsl.p, sys.mom_ptr.p, sys.bmean.p);
         }

@@ -213,7 +213,10 @@ def test_mc_adaptive_path_counts_identical_streams(pdd):
     st = S.stats()
     assert st["extended_rows"] > 0
     ref = osystem.assemble(cfg, oc, rows=[int(i) for i in rows], threads=4)
-    assert st["paths_total"] == sum(r.paths for r in ref.mc_rows.values())
+    P0 = cfg["mc"]["paths"]
+    # the GPU counts every path it ran: the pilot of each row, then the full rerun of extended rows
+    assert st["paths_total"] == sum(P0 + (r.paths if r.paths > P0 else 0) for r in ref.mc_rows.values())
+    assert st["extended_rows"] == sum(1 for r in ref.mc_rows.values() if r.paths > P0)
     for k, i in enumerate(rows):
         r = ref.mc_rows[int(i)]
         got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
@@ -422,3 +425,21 @@ def test_adaptive_cover_and_rows(pdd):
                 got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
                 assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max())
                 assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
+
+
+def test_autograd_function_matches_pdd_grad(pdd):
+    """torch.autograd through MisfitSolve (forward: assemble + solve; backward: pdd_grad)."""
+    cfg = workloads.grad(paths=64)
+    w = torch.tensor(cfg["op"]["rbf"]["w"], dtype=torch.float64, device="cuda", requires_grad=True)
+    a = torch.tensor(cfg["op"]["g_coef"], dtype=torch.float64, device="cuda", requires_grad=True)
+    u = pdd.MisfitSolve.apply(w, a, cfg)
+    oc = _oracle_cover("grad", cfg)
+    u_obs = torch.tensor(np.exp(oc.kx) * np.sin(oc.ky), device="cuda")
+    J = ((u - u_obs) ** 2).sum()
+    J.backward()
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    u2 = S.solve(rtol=1e-14)
+    g = S.grad(u2, 2.0 * (u2 - u_obs))
+    nw = w.numel()
+    assert torch.allclose(w.grad, g[:nw], rtol=1e-9, atol=1e-12)
+    assert torch.allclose(a.grad, g[nw:], rtol=1e-9, atol=1e-12)
