@@ -482,6 +482,250 @@ static void launch_solve(const T *LU, int n, long sA, const int *perm, const dou
     PDD_LAUNCH(k_lu_solve<T>, nd, 256, sm, st, LU, n, sA, perm, R, nrhs, sR, W, X, accumulate, conv, sweeps, tol);
 }
 
+// ---------------------------------------------------------------------------
+// a8, mixed form: right-looking blocked triangular solves.  One CTA holds a
+// group of right-hand-side columns for all n rows in shared memory; for each
+// 32-row panel it applies the inverse of the panel's diagonal block (computed
+// once after the factorisation) and then subtracts the panel's contribution
+// from every row not yet solved.  Each factor entry is read from HBM once per
+// solve, and the row updates are independent FP32 FMA chains (broadcast
+// shared-memory reads of the solved panel rows).
+// ---------------------------------------------------------------------------
+static constexpr int kRlTB = 32, kRlThreads = 512;
+static constexpr size_t kRlSmemMax = 200 * 1024;
+
+// inverses of the unit-lower and upper 32x32 diagonal blocks of each LU:
+// Dinv[disk][blk][0] = inv(L_bb), Dinv[disk][blk][1] = inv(U_bb), zero-padded
+__global__ void __launch_bounds__(128) k_diag_inv(const float *LUall, int n, long strideA, int nd, float *Dinv) {
+    __shared__ float Ts[4][kRlTB][kRlTB + 1], Xs[4][kRlTB][kRlTB + 1];
+    const int w = threadIdx.x >> 5, j = threadIdx.x & 31;
+    const int nblk = (n + kRlTB - 1) / kRlTB;
+    const long item = (long)blockIdx.x * 4 + w;
+    if (item >= (long)nd * nblk * 2) return;
+    const int tri = (int)(item & 1);
+    const long db = item >> 1;
+    const int blk = (int)(db % nblk), disk = (int)(db / nblk);
+    const int i0 = blk * kRlTB, tb = min(kRlTB, n - i0);
+    const float *LU = LUall + disk * strideA;
+    for (int r = 0; r < kRlTB; ++r) Ts[w][r][j] = (r < tb && j < tb) ? LU[(long)(i0 + r) * n + i0 + j] : 0.f;
+    __syncwarp();
+    // lane j forms column j of the inverse
+    if (tri == 0) {
+        for (int i = 0; i < kRlTB; ++i) {
+            float v = (i == j) ? 1.f : 0.f;
+            if (i > j && i < tb)
+                for (int k = j; k < i; ++k) v -= Ts[w][i][k] * Xs[w][k][j];
+            Xs[w][i][j] = (i < tb && j < tb) ? v : 0.f;
+        }
+    } else {
+        for (int i = kRlTB - 1; i >= 0; --i) {
+            float v = 0.f;
+            if (i < tb && j < tb && i <= j) {
+                v = (i == j) ? 1.f : 0.f;
+                for (int k = i + 1; k <= j; ++k) v -= Ts[w][i][k] * Xs[w][k][j];
+                v /= Ts[w][i][i];
+            }
+            Xs[w][i][j] = v;
+        }
+    }
+    __syncwarp();
+    float *out = Dinv + (((long)disk * nblk + blk) * 2 + tri) * (kRlTB * kRlTB);
+    for (int r = 0; r < kRlTB; ++r) out[r * kRlTB + j] = Xs[w][r][j];
+}
+
+template <int CG>
+__device__ __forceinline__ void rl_rank1(float (&acc)[CG], float l, const float *xrow) {
+#pragma unroll
+    for (int c = 0; c < CG; c += 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(xrow + c);
+        acc[c] = fmaf(-l, x.x, acc[c]);
+        acc[c + 1] = fmaf(-l, x.y, acc[c + 1]);
+        acc[c + 2] = fmaf(-l, x.z, acc[c + 2]);
+        acc[c + 3] = fmaf(-l, x.w, acc[c + 3]);
+    }
+}
+
+// X += inv(LU) P R for the columns [blockIdx.y CG, ...) of every disk not yet
+// converged; the largest |correction| and |X| of each disk go to dmaxb/xmaxb
+// (bit patterns of non-negative doubles, ordered like the values)
+template <int CG>
+__global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUall, int n, long strideA,
+                                                            const int *permAll, const float *DinvAll,
+                                                            const double *Rall, int nrhs, long strideR,
+                                                            double *Xall, const int *conv,
+                                                            unsigned long long *dmaxb, unsigned long long *xmaxb) {
+    constexpr int NT = kRlThreads, TB = kRlTB, OUT = (TB * CG + NT - 1) / NT;
+    extern __shared__ __align__(16) float rsm[];
+    float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
+    float *Ds = rsm + (size_t)n * CG;                  // TB x TB diagonal-block inverse
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    if (conv[disk]) return;
+    const int c0 = blockIdx.y * CG, cg = min(CG, nrhs - c0);
+    const float *LU = LUall + disk * strideA;
+    const int *perm = permAll + (long)disk * n;
+    const double *R = Rall + disk * strideR;
+    double *X = Xall + disk * strideR;
+    const int nblk = (n + TB - 1) / TB;
+    const float *Dv = DinvAll + (long)disk * nblk * 2 * (TB * TB);
+    for (int e = tid; e < n * CG; e += NT) {
+        const int p = e / CG, c = e - p * CG;
+        Bs[e] = (c < cg) ? (float)R[(long)perm[p] * nrhs + c0 + c] : 0.f;
+    }
+    const bool vec = (n & 3) == 0;
+    for (int pass = 0; pass < 2; ++pass) {             // 0: L (unit lower), 1: U (upper)
+        for (int bi = 0; bi < nblk; ++bi) {
+            const int blk = pass == 0 ? bi : nblk - 1 - bi;
+            const int i0 = blk * TB, tb = min(TB, n - i0);
+            const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
+            for (int e = tid; e < TB * TB; e += NT) Ds[e] = Dt[e];
+            __syncthreads();
+            // the panel's rows: X_b = inv(T_bb) B_b
+            float o[OUT];
+#pragma unroll
+            for (int q = 0; q < OUT; ++q) {
+                const int e = tid + q * NT;
+                float v = 0.f;
+                if (e < tb * CG) {
+                    const int r = e / CG, c = e - r * CG;
+                    const float *dr = Ds + r * TB;
+                    const float *bc = Bs + (size_t)i0 * CG + c;
+                    for (int k = 0; k < tb; ++k) v = fmaf(dr[k], bc[(size_t)k * CG], v);
+                }
+                o[q] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < OUT; ++q) {
+                const int e = tid + q * NT;
+                if (e < tb * CG) Bs[(size_t)i0 * CG + e] = o[q];
+            }
+            __syncthreads();
+            // rows still to solve: B_r -= T_rb X_b
+            const int ra = pass == 0 ? i0 + tb : 0, rb = pass == 0 ? n : i0;
+            const float *xs = Bs + (size_t)i0 * CG;
+            for (int r = ra + tid; r < rb; r += NT) {
+                float acc[CG];
+                float *br = Bs + (size_t)r * CG;
+#pragma unroll
+                for (int c = 0; c < CG; c += 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(br + c);
+                    acc[c] = t.x;
+                    acc[c + 1] = t.y;
+                    acc[c + 2] = t.z;
+                    acc[c + 3] = t.w;
+                }
+                const float *lrow = LU + (long)r * n + i0;
+                if (vec && tb == TB) {
+#pragma unroll 2
+                    for (int k0 = 0; k0 < TB; k0 += 4) {
+                        const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lrow + k0));
+                        rl_rank1<CG>(acc, l4.x, xs + (size_t)(k0 + 0) * CG);
+                        rl_rank1<CG>(acc, l4.y, xs + (size_t)(k0 + 1) * CG);
+                        rl_rank1<CG>(acc, l4.z, xs + (size_t)(k0 + 2) * CG);
+                        rl_rank1<CG>(acc, l4.w, xs + (size_t)(k0 + 3) * CG);
+                    }
+                } else {
+                    for (int k = 0; k < tb; ++k) rl_rank1<CG>(acc, __ldg(lrow + k), xs + (size_t)k * CG);
+                }
+#pragma unroll
+                for (int c = 0; c < CG; c += 4)
+                    *reinterpret_cast<float4 *>(br + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+            }
+            __syncthreads();
+        }
+    }
+    // X += W; the refinement test takes max|W| and max|X| over the disk's columns
+    double dmax = 0.0, xmax = 0.0;
+    for (int e = tid; e < n * cg; e += NT) {
+        const int p = e / cg, c = e - p * cg;
+        const double w = (double)Bs[(size_t)p * CG + c];
+        double *xp = X + (long)p * nrhs + c0 + c;
+        const double xv = *xp + w;
+        *xp = xv;
+        dmax = fmax(dmax, fabs(w));
+        xmax = fmax(xmax, fabs(xv));
+    }
+    __shared__ double sd[NT / 32], sx[NT / 32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if ((tid & 31) == 0) {
+        sd[tid >> 5] = dmax;
+        sx[tid >> 5] = xmax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double d = 0.0, x = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            d = fmax(d, sd[w]);
+            x = fmax(x, sx[w]);
+        }
+        atomicMax(dmaxb + disk, (unsigned long long)__double_as_longlong(d));
+        atomicMax(xmaxb + disk, (unsigned long long)__double_as_longlong(x));
+    }
+}
+
+// per disk: count the sweep and stop refining once max|W| <= tol max|X|
+__global__ void k_refine_conv(int nd, int *conv, int *sweeps, unsigned long long *dmaxb,
+                              unsigned long long *xmaxb, double tol) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nd) return;
+    if (!conv[d]) {
+        sweeps[d] += 1;
+        if (__longlong_as_double((long long)dmaxb[d]) <= tol * __longlong_as_double((long long)xmaxb[d])) conv[d] = 1;
+    }
+    dmaxb[d] = 0ull;
+    xmaxb[d] = 0ull;
+}
+
+// column-group width of the right-looking solve for n rows and nrhs columns
+// (0: the shared-memory block does not fit; the tiled solve is used)
+static int rl_width(int n, int nrhs, int &groups) {
+    static const int widths[] = {8, 12, 20, 36, 52};
+    for (int g = 1; g <= nrhs; ++g) {
+        const int cg = (nrhs + g - 1) / g;
+        int W = 0;
+        for (int w : widths)
+            if (w >= cg) {
+                W = w;
+                break;
+            }
+        if (!W) continue;
+        const size_t sm = ((size_t)n * W + (size_t)kRlTB * kRlTB) * sizeof(float);
+        if (sm <= kRlSmemMax) {
+            groups = (nrhs + W - 1) / W;
+            return W;
+        }
+        if (W == 8) break;
+    }
+    groups = 0;
+    return 0;
+}
+
+template <int CG>
+static void launch_rl_cg(const float *LU, int n, long sA, const int *perm, const float *Dinv, const double *R,
+                         int nrhs, long sR, double *X, const int *conv, unsigned long long *dmb,
+                         unsigned long long *xmb, int nd, int groups, cudaStream_t st) {
+    const size_t sm = ((size_t)n * CG + (size_t)kRlTB * kRlTB) * sizeof(float);
+    PDD_CUDA(cudaFuncSetAttribute(k_lu_solve_rl<CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PDD_LAUNCH(k_lu_solve_rl<CG>, dim3(nd, groups), kRlThreads, sm, st, LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv,
+               dmb, xmb);
+}
+
+static void launch_rl(int W, const float *LU, int n, long sA, const int *perm, const float *Dinv, const double *R,
+                      int nrhs, long sR, double *X, const int *conv, unsigned long long *dmb,
+                      unsigned long long *xmb, int nd, int groups, cudaStream_t st) {
+    switch (W) {
+        case 8: launch_rl_cg<8>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+        case 12: launch_rl_cg<12>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+        case 20: launch_rl_cg<20>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+        case 36: launch_rl_cg<36>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+        default: launch_rl_cg<52>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+    }
+}
+
 // R = RHS - A X in FP64 without forming A (equilibrated rows)
 __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefAll, long strideC,
                                                   const double *RHSall, const double *Xall,
@@ -715,8 +959,12 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     const bool mixed = sizeof(T) == 4;
     const size_t perA = (size_t)S.n * S.n * sizeof(T);
     const size_t perR = (size_t)S.n * S.nrhs * sizeof(double);
+    int rl_groups = 0;
+    const int rlW = mixed ? rl_width(S.n, S.nrhs, rl_groups) : 0;
+    const int nblk = (S.n + kRlTB - 1) / kRlTB;
+    const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) : 0;
     const size_t perDisk = perA + perR * (mixed ? 3 : 1) + (size_t)S.n * S.nrhs * sizeof(T) +
-                           (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + 64;
+                           (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + perDinv + 64;
     size_t freeb = 0, totb = 0;
     PDD_CUDA(cudaMemGetInfo(&freeb, &totb));
     size_t budget = std::min<size_t>((size_t)(0.6 * freeb), (size_t)64 << 30);
@@ -728,6 +976,13 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     DevBuf<NodeCoef> coef;
     DevBuf<int> perm, info, conv, sweeps;
     DevBuf<DiskDesc> dd;
+    DevBuf<float> dinv;
+    DevBuf<unsigned long long> dmaxb, xmaxb;
+    if (rlW) {
+        dinv.alloc((size_t)wave * nblk * 2 * kRlTB * kRlTB);
+        dmaxb.alloc(wave);
+        xmaxb.alloc(wave);
+    }
     A.alloc((size_t)wave * S.n * S.n);
     W.alloc((size_t)wave * S.n * S.nrhs);
     RHS.alloc((size_t)wave * S.n * S.nrhs);
@@ -769,6 +1024,11 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
         } else {
             launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
         }
+        if (rlW) {
+            const long items = (long)nd * nblk * 2;
+            PDD_LAUNCH(k_diag_inv, (int)((items + 3) / 4), 128, 0, st, reinterpret_cast<const float *>(A.p), S.n, sA,
+                       nd, dinv.p);
+        }
         tm.mark(2);
         if (!mixed) {
             launch_solve<T>(A.p, S.n, sA, perm.p, RHS.p, S.nrhs, sR, W.p, X.p, 0, nullptr, nullptr, 0.0, nd, st);
@@ -780,10 +1040,20 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-14;
             const size_t rsm = (size_t)8 * ((S.nc - 1) + S.nt) * sizeof(double);
             dim3 g_res(cdiv(S.n, 8), nd);
+            if (rlW) {
+                PDD_CUDA(cudaMemsetAsync(dmaxb.p, 0, nd * sizeof(unsigned long long), st));
+                PDD_CUDA(cudaMemsetAsync(xmaxb.p, 0, nd * sizeof(unsigned long long), st));
+            }
             for (int s = 0; s < maxs; ++s) {
                 const double *rhs_now = (s == 0) ? RHS.p : Rr.p;
-                launch_solve<T>(A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p, 1, conv.p, sweeps.p, tol, nd,
-                                st);
+                if (rlW) {
+                    launch_rl(rlW, reinterpret_cast<const float *>(A.p), S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs,
+                              sR, X.p, conv.p, dmaxb.p, xmaxb.p, nd, rl_groups, st);
+                    PDD_LAUNCH(k_refine_conv, cdiv(nd, 256), 256, 0, st, nd, conv.p, sweeps.p, dmaxb.p, xmaxb.p, tol);
+                } else {
+                    launch_solve<T>(A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p, 1, conv.p, sweeps.p, tol,
+                                    nd, st);
+                }
                 if (s + 1 < maxs)
                     PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p);
             }
