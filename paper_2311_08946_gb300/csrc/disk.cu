@@ -33,6 +33,7 @@ namespace pdd {
 struct Shape {
     int nr, nt, nk, nc, n, nrhs;
     double *x, *D, *D2, *F1, *F2, *Hg;   // device tables
+    float2 *Dhl, *D2hl, *F1hl, *F2hl;    // the same tables as FP32 (hi, lo) pairs
 };
 
 struct DiskDesc {
@@ -169,18 +170,43 @@ __global__ void __launch_bounds__(256) k_node_coef(Problem P, Shape S, const Dis
     Rrow[S.nk] = -sc * fv;
 }
 
-// rows of the equilibrated collocation matrix, one warp per row
+// rows of the equilibrated collocation matrix, one warp per row: the row is
+// zeroed in shared memory, its nonzeros (the node's radial line, the mirrored
+// line and the node's ring: 2 nr + nt candidates, the crossings computed twice
+// with the same value) are evaluated in FP64, and the row is stored with
+// 16-byte writes
 template <typename T>
 __global__ void __launch_bounds__(256) k_fill_operator(Shape S, T *A, long strideA, const NodeCoef *coef,
-                                                       long strideC) {
+                                                       long strideC, int rows_per_block) {
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int disk = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 8 + warp;
+    if (warp >= rows_per_block) return;
+    const int p = blockIdx.x * rows_per_block + warp;
     if (p >= S.n) return;
+    T *row = reinterpret_cast<T *>(fsm_raw) + (size_t)warp * S.n;
+    for (int q = lane; q < S.n; q += 32) row[q] = (T)0;
+    __syncwarp();
     const NodeCoef cf = coef[disk * strideC + p];
-    const int k = p / S.nt + 1, j = p % S.nt;
+    const int k = p / S.nt + 1, j = p % S.nt, jm = (j + (S.nt >> 1)) % S.nt;
+    const int ncand = 2 * S.nr + S.nt;
+    for (int c = lane; c < ncand; c += 32) {
+        int q;
+        if (c < S.nr) q = c * S.nt + j;
+        else if (c < 2 * S.nr) q = (c - S.nr) * S.nt + jm;
+        else q = (k - 1) * S.nt + (c - 2 * S.nr);
+        row[q] = (T)(cf.s * a_entry(S, k, j, q, cf.alpha, cf.beta, cf.gamma, cf.delta, cf.c, p));
+    }
+    __syncwarp();
     T *Arow = A + disk * strideA + (long)p * S.n;
-    for (int q = lane; q < S.n; q += 32)
-        Arow[q] = (T)(cf.s * a_entry(S, k, j, q, cf.alpha, cf.beta, cf.gamma, cf.delta, cf.c, p));
+    constexpr int V = 16 / sizeof(T);
+    if (S.n % V == 0) {
+        const int nv = S.n / V;
+        const float4 *src = reinterpret_cast<const float4 *>(row);
+        float4 *dst = reinterpret_cast<float4 *>(Arow);
+        for (int q = lane; q < nv; q += 32) dst[q] = src[q];
+    } else {
+        for (int q = lane; q < S.n; q += 32) Arow[q] = row[q];
+    }
 }
 
 // the collocation system of every disk of the wave: node coefficients, then the matrix rows
@@ -188,8 +214,13 @@ template <typename T>
 static void build_operator(const Problem &P, const Shape &S, const DiskDesc *dd, int nd, T *A, long sA, double *RHS,
                            long sR, NodeCoef *coef, long sC, cudaStream_t st) {
     PDD_LAUNCH(k_node_coef, cdiv((long)nd * S.n, 256), 256, 0, st, P, S, dd, nd, RHS, sR, coef, sC);
-    dim3 g(cdiv(S.n, 8), nd);
-    PDD_LAUNCH(k_fill_operator<T>, g, 256, 0, st, S, A, sA, coef, sC);
+    const size_t row_bytes = (size_t)S.n * sizeof(T);
+    const int rpb = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(96 * 1024) / row_bytes));
+    if (row_bytes > (size_t)200 * 1024) fail(PDD_EINVAL, "disk grid too large for the operator kernel");
+    const size_t sm = rpb * row_bytes;
+    PDD_CUDA(cudaFuncSetAttribute(k_fill_operator<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 g(cdiv(S.n, rpb), nd);
+    PDD_LAUNCH(k_fill_operator<T>, g, 32 * rpb, sm, st, S, A, sA, coef, sC, rpb);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,6 +523,7 @@ static void launch_solve(const T *LU, int n, long sA, const int *perm, const dou
 // shared-memory reads of the solved panel rows).
 // ---------------------------------------------------------------------------
 static constexpr int kRlTB = 32, kRlThreads = 512;
+__device__ __forceinline__ float2 df_add(float2 a, float2 b);
 static constexpr size_t kRlSmemMax = 200 * 1024;
 
 // inverses of the unit-lower and upper 32x32 diagonal blocks of each LU:
@@ -553,7 +585,8 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
                                                             const int *permAll, const float *DinvAll,
                                                             const double *Rall, int nrhs, long strideR,
                                                             double *Xall, const int *conv,
-                                                            unsigned long long *dmaxb, unsigned long long *xmaxb) {
+                                                            unsigned long long *dmaxb, unsigned long long *xmaxb,
+                                                            float2 *Dall, int dmode) {
     constexpr int NT = kRlThreads, TB = kRlTB, OUT = (TB * CG + NT - 1) / NT;
     extern __shared__ __align__(16) float rsm[];
     float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
@@ -634,14 +667,19 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
             __syncthreads();
         }
     }
-    // X += W; the refinement test takes max|W| and max|X| over the disk's columns
+    // X += W (and D = W or D += W, in double-float, for the later residuals); the refinement test
+    // takes max|W| and max|X| over the disk's columns
     double dmax = 0.0, xmax = 0.0;
+    float2 *Dd = dmode ? Dall + disk * strideR : nullptr;
     for (int e = tid; e < n * cg; e += NT) {
         const int p = e / cg, c = e - p * cg;
-        const double w = (double)Bs[(size_t)p * CG + c];
-        double *xp = X + (long)p * nrhs + c0 + c;
-        const double xv = *xp + w;
-        *xp = xv;
+        const float w32 = Bs[(size_t)p * CG + c];
+        const double w = (double)w32;
+        const long o = (long)p * nrhs + c0 + c;
+        const double xv = X[o] + w;
+        X[o] = xv;
+        if (dmode == 1) Dd[o] = make_float2(w32, 0.f);
+        else if (dmode == 2) Dd[o] = df_add(Dd[o], make_float2(w32, 0.f));
         dmax = fmax(dmax, fabs(w));
         xmax = fmax(xmax, fabs(xv));
     }
@@ -704,53 +742,123 @@ static int rl_width(int n, int nrhs, int &groups) {
     return 0;
 }
 
+struct RlArgs {
+    const float *LU;
+    int n;
+    long sA;
+    const int *perm;
+    const float *Dinv;
+    const double *R;
+    int nrhs;
+    long sR;
+    double *X;
+    const int *conv;
+    unsigned long long *dmb, *xmb;
+    float2 *D;
+    int dmode, nd, groups;
+};
+
 template <int CG>
-static void launch_rl_cg(const float *LU, int n, long sA, const int *perm, const float *Dinv, const double *R,
-                         int nrhs, long sR, double *X, const int *conv, unsigned long long *dmb,
-                         unsigned long long *xmb, int nd, int groups, cudaStream_t st) {
-    const size_t sm = ((size_t)n * CG + (size_t)kRlTB * kRlTB) * sizeof(float);
+static void launch_rl_cg(const RlArgs &a, cudaStream_t st) {
+    const size_t sm = ((size_t)a.n * CG + (size_t)kRlTB * kRlTB) * sizeof(float);
     PDD_CUDA(cudaFuncSetAttribute(k_lu_solve_rl<CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    PDD_LAUNCH(k_lu_solve_rl<CG>, dim3(nd, groups), kRlThreads, sm, st, LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv,
-               dmb, xmb);
+    PDD_LAUNCH(k_lu_solve_rl<CG>, dim3(a.nd, a.groups), kRlThreads, sm, st, a.LU, a.n, a.sA, a.perm, a.Dinv, a.R,
+               a.nrhs, a.sR, a.X, a.conv, a.dmb, a.xmb, a.D, a.dmode);
 }
 
-static void launch_rl(int W, const float *LU, int n, long sA, const int *perm, const float *Dinv, const double *R,
-                      int nrhs, long sR, double *X, const int *conv, unsigned long long *dmb,
-                      unsigned long long *xmb, int nd, int groups, cudaStream_t st) {
+static void launch_rl(int W, const RlArgs &a, cudaStream_t st) {
     switch (W) {
-        case 8: launch_rl_cg<8>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
-        case 12: launch_rl_cg<12>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
-        case 20: launch_rl_cg<20>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
-        case 36: launch_rl_cg<36>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
-        default: launch_rl_cg<52>(LU, n, sA, perm, Dinv, R, nrhs, sR, X, conv, dmb, xmb, nd, groups, st); break;
+        case 8: launch_rl_cg<8>(a, st); break;
+        case 12: launch_rl_cg<12>(a, st); break;
+        case 20: launch_rl_cg<20>(a, st); break;
+        case 36: launch_rl_cg<36>(a, st); break;
+        default: launch_rl_cg<52>(a, st); break;
     }
 }
 
-// R = RHS - A X in FP64 without forming A (equilibrated rows)
+// ---------------------------------------------------------------------------
+// double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (Dekker 1971; Knuth's two-sum).  Products use __fmul_rn so that the
+// compiler cannot contract them into the following addition.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
+// (sh, sl) += w x, the accumulator left unnormalised
+__device__ __forceinline__ void df_acc(float &sh, float &sl, float2 w, float2 x) {
+    const float p = __fmul_rn(w.x, x.x);
+    float e = fmaf(w.x, x.x, -p);
+    e = fmaf(w.x, x.y, fmaf(w.y, x.x, e));
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl += t + e;
+}
+
+__global__ void k_split_df(const double *v, float2 *out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = df_split(v[i]);
+}
+
+// R = RHS - A X in FP64 without forming A (equilibrated rows).  A block takes
+// kResNP nodes; their combined radial and angular weights go to shared memory
+// and the (node, column) outputs are spread over all threads of the block.
+// With R1 non-null the residual is also stored as (hi, lo) FP32 pairs.
+static constexpr int kResNP = 64;
+
 __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefAll, long strideC,
                                                   const double *RHSall, const double *Xall,
-                                                  double *Rall, long strideR, const int *conv) {
+                                                  double *Rall, long strideR, const int *conv, float2 *R1all) {
     const int disk = blockIdx.y;
     if (conv[disk]) return;
-    extern __shared__ double wsm[];                 // per row: nc-1 radial + nt angular weights
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int p = blockIdx.x * 8 + ty;
+    extern __shared__ double wsm[];                 // per node: nc-1 radial + nt angular weights
     const int nw = (S.nc - 1) + S.nt, np = S.nc + 1, half = S.nt >> 1;
-    double *w = wsm + ty * nw;
-    const double *X = Xall + disk * strideR;
-    if (p < S.n) {
-        const NodeCoef cf = coefAll[disk * strideC + p];
-        const int k = p / S.nt + 1;
-        for (int l = tx; l < S.nc - 1; l += 32)      // l+1 = 1..nc-1
-            w[l] = cf.alpha * S.D2[k * np + l + 1] + cf.beta * S.D[k * np + l + 1];
-        for (int d = tx; d < S.nt; d += 32) w[S.nc - 1 + d] = cf.gamma * S.F2[d] + cf.delta * S.F1[d];
+    const int p0 = blockIdx.x * kResNP, npb = min(kResNP, S.n - p0);
+    for (int e = threadIdx.x; e < npb * nw; e += blockDim.x) {
+        const int pl = e / nw, l = e - pl * nw;
+        const NodeCoef cf = coefAll[disk * strideC + p0 + pl];
+        const int k = (p0 + pl) / S.nt + 1;
+        double v;
+        if (l < S.nc - 1) {
+            v = cf.alpha * S.D2[k * np + l + 1] + cf.beta * S.D[k * np + l + 1];
+        } else {
+            const int d = l - (S.nc - 1);
+            v = cf.gamma * S.F2[d] + cf.delta * S.F1[d];
+        }
+        wsm[e] = v;
     }
-    __syncwarp();
-    if (p >= S.n) return;
-    const NodeCoef cf = coefAll[disk * strideC + p];
-    const int k = p / S.nt + 1, j = p % S.nt;
-    const int jm = (j + half) % S.nt;
-    for (int col = tx; col < S.nrhs; col += 32) {
+    __syncthreads();
+    const double *X = Xall + disk * strideR;
+    for (int e = threadIdx.x; e < npb * S.nrhs; e += blockDim.x) {
+        const int pl = e / S.nrhs, col = e - pl * S.nrhs, p = p0 + pl;
+        const double *w = wsm + pl * nw;
+        const NodeCoef cf = coefAll[disk * strideC + p];
+        const int k = p / S.nt + 1, j = p % S.nt;
+        const int jm = (j + half) % S.nt;
         double acc = cf.c * X[(long)p * S.nrhs + col];
         for (int l = 1; l <= S.nr; ++l) {
             acc += w[l - 1] * X[(long)((l - 1) * S.nt + j) * S.nrhs + col];
@@ -763,8 +871,78 @@ __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefA
             d += (d < 0) ? S.nt : 0;
             acc += wa[d] * X[(rb + jp) * S.nrhs + col];
         }
-        Rall[disk * strideR + (long)p * S.nrhs + col] =
-            RHSall[disk * strideR + (long)p * S.nrhs + col] - cf.s * acc;
+        const long o = disk * strideR + (long)p * S.nrhs + col;
+        const double r = RHSall[o] - cf.s * acc;
+        Rall[o] = r;
+        if (R1all) R1all[o] = df_split(r);
+    }
+}
+
+// Later refinement sweeps: with X = X1 + D (X1 the first solve's FP32 result,
+// D the sum of the later FP32 corrections), R = R1 - A D where R1 = RHS - A X1
+// came from k_residual.  |D| is about the first solve's error, so A D needs
+// far fewer digits than the first residual; it is formed in double-float
+// arithmetic on the FP32 pipes (FP64 runs at a small fraction of the FP32
+// rate on this part).  The result is rounded to FP32, the precision in which
+// the triangular solves read it.
+__global__ void __launch_bounds__(256) k_residual_df(Shape S, const NodeCoef *coefAll, long strideC,
+                                                     const float2 *R1all, const float2 *Dall, double *Rall,
+                                                     long strideR, const int *conv) {
+    const int disk = blockIdx.y;
+    if (conv[disk]) return;
+    extern __shared__ float2 wdf[];                 // per node: weights, then (c, s)
+    const int nw = (S.nc - 1) + S.nt, np = S.nc + 1, half = S.nt >> 1;
+    const int p0 = blockIdx.x * kResNP, npb = min(kResNP, S.n - p0);
+    float2 *cab = wdf + (size_t)kResNP * nw;        // per node: alpha, beta, gamma, delta, c, s
+    for (int pl = threadIdx.x; pl < npb; pl += blockDim.x) {
+        const NodeCoef cf = coefAll[disk * strideC + p0 + pl];
+        cab[6 * pl + 0] = df_split(cf.alpha);
+        cab[6 * pl + 1] = df_split(cf.beta);
+        cab[6 * pl + 2] = df_split(cf.gamma);
+        cab[6 * pl + 3] = df_split(cf.delta);
+        cab[6 * pl + 4] = df_split(cf.c);
+        cab[6 * pl + 5] = df_split(cf.s);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < npb * nw; e += blockDim.x) {
+        const int pl = e / nw, l = e - pl * nw;
+        const int k = (p0 + pl) / S.nt + 1;
+        const float2 *cf = cab + 6 * pl;
+        float2 v;
+        if (l < S.nc - 1) {
+            v = df_add(df_mul(cf[0], S.D2hl[k * np + l + 1]), df_mul(cf[1], S.Dhl[k * np + l + 1]));
+        } else {
+            const int d = l - (S.nc - 1);
+            v = df_add(df_mul(cf[2], S.F2hl[d]), df_mul(cf[3], S.F1hl[d]));
+        }
+        wdf[e] = v;
+    }
+    __syncthreads();
+    const float2 *D = Dall + disk * strideR;
+    for (int e = threadIdx.x; e < npb * S.nrhs; e += blockDim.x) {
+        const int pl = e / S.nrhs, col = e - pl * S.nrhs, p = p0 + pl;
+        const float2 *w = wdf + pl * nw;
+        const int k = p / S.nt + 1, j = p % S.nt;
+        const int jm = (j + half) % S.nt;
+        const float2 x0 = D[(long)p * S.nrhs + col];
+        const float2 c0 = df_mul(cab[6 * pl + 4], x0);
+        float sh = c0.x, sl = c0.y;
+        for (int l = 1; l <= S.nr; ++l) {
+            df_acc(sh, sl, w[l - 1], D[(long)((l - 1) * S.nt + j) * S.nrhs + col]);
+            df_acc(sh, sl, w[S.nc - l - 1], D[(long)((l - 1) * S.nt + jm) * S.nrhs + col]);
+        }
+        const float2 *wa = w + S.nc - 1;
+        const long rb = (long)(k - 1) * S.nt;
+        for (int jp = 0; jp < S.nt; ++jp) {
+            int d = j - jp;
+            d += (d < 0) ? S.nt : 0;
+            df_acc(sh, sl, wa[d], D[(rb + jp) * S.nrhs + col]);
+        }
+        const float h = sh + sl;
+        const float2 ad = df_mul(cab[6 * pl + 5], make_float2(h, sl - (h - sh)));
+        const long o = disk * strideR + (long)p * S.nrhs + col;
+        const float2 r = df_add(R1all[o], make_float2(-ad.x, -ad.y));
+        Rall[o] = (double)r.x;
     }
 }
 
@@ -852,6 +1030,7 @@ __global__ void __launch_bounds__(256) k_disk_eval(Shape S, const DiskDesc *disk
 // ---------------------------------------------------------------------------
 struct ShapeTables {
     DevBuf<double> x, D, D2, F1, F2, Hg;
+    DevBuf<float2> Dhl, D2hl, F1hl, F2hl;
     Shape S{};
     void build(int nr, int nt, int nk, cudaStream_t st) {
         const int nc = 2 * nr + 1, np = nc + 1;
@@ -864,7 +1043,16 @@ struct ShapeTables {
         PDD_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * np * np, st));
         PDD_LAUNCH(k_shape_tables, 1, 256, 0, st, nr, nt, nk, x.p, D.p, F1.p, F2.p, Hg.p);
         PDD_LAUNCH(k_matmul_sq, cdiv((long)np * np, 256), 256, 0, st, D.p, D2.p, np);
-        S = Shape{nr, nt, nk, nc, nr * nt, nk + 1, x.p, D.p, D2.p, F1.p, F2.p, Hg.p};
+        Dhl.alloc((size_t)np * np);
+        D2hl.alloc((size_t)np * np);
+        F1hl.alloc(nt);
+        F2hl.alloc(nt);
+        PDD_LAUNCH(k_split_df, cdiv((long)np * np, 256), 256, 0, st, D.p, Dhl.p, np * np);
+        PDD_LAUNCH(k_split_df, cdiv((long)np * np, 256), 256, 0, st, D2.p, D2hl.p, np * np);
+        PDD_LAUNCH(k_split_df, cdiv(nt, 256), 256, 0, st, F1.p, F1hl.p, nt);
+        PDD_LAUNCH(k_split_df, cdiv(nt, 256), 256, 0, st, F2.p, F2hl.p, nt);
+        S = Shape{nr, nt, nk, nc, nr * nt, nk + 1, x.p, D.p, D2.p, F1.p, F2.p, Hg.p,
+                  Dhl.p, D2hl.p, F1hl.p, F2hl.p};
     }
 };
 
@@ -962,7 +1150,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     int rl_groups = 0;
     const int rlW = mixed ? rl_width(S.n, S.nrhs, rl_groups) : 0;
     const int nblk = (S.n + kRlTB - 1) / kRlTB;
-    const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) : 0;
+    const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) + 2 * perR : 0;
     const size_t perDisk = perA + perR * (mixed ? 3 : 1) + (size_t)S.n * S.nrhs * sizeof(T) +
                            (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + perDinv + 64;
     size_t freeb = 0, totb = 0;
@@ -978,10 +1166,13 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     DevBuf<DiskDesc> dd;
     DevBuf<float> dinv;
     DevBuf<unsigned long long> dmaxb, xmaxb;
+    DevBuf<float2> R1hl, Dhl;
     if (rlW) {
         dinv.alloc((size_t)wave * nblk * 2 * kRlTB * kRlTB);
         dmaxb.alloc(wave);
         xmaxb.alloc(wave);
+        R1hl.alloc((size_t)wave * S.n * S.nrhs);
+        Dhl.alloc((size_t)wave * S.n * S.nrhs);
     }
     A.alloc((size_t)wave * S.n * S.n);
     W.alloc((size_t)wave * S.n * S.nrhs);
@@ -1038,8 +1229,12 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             PDD_CUDA(cudaMemsetAsync(X.p, 0, (size_t)nd * sR * sizeof(double), st));
             const int maxs = std::max(1, o.max_refine);
             const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-14;
-            const size_t rsm = (size_t)8 * ((S.nc - 1) + S.nt) * sizeof(double);
-            dim3 g_res(cdiv(S.n, 8), nd);
+            const int nw = (S.nc - 1) + S.nt;
+            const size_t rsm = (size_t)kResNP * nw * sizeof(double);
+            const size_t rsm_df = ((size_t)kResNP * nw + 6 * kResNP) * sizeof(float2);
+            PDD_CUDA(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+            PDD_CUDA(cudaFuncSetAttribute(k_residual_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm_df));
+            dim3 g_res(cdiv(S.n, kResNP), nd);
             if (rlW) {
                 PDD_CUDA(cudaMemsetAsync(dmaxb.p, 0, nd * sizeof(unsigned long long), st));
                 PDD_CUDA(cudaMemsetAsync(xmaxb.p, 0, nd * sizeof(unsigned long long), st));
@@ -1047,15 +1242,26 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             for (int s = 0; s < maxs; ++s) {
                 const double *rhs_now = (s == 0) ? RHS.p : Rr.p;
                 if (rlW) {
-                    launch_rl(rlW, reinterpret_cast<const float *>(A.p), S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs,
-                              sR, X.p, conv.p, dmaxb.p, xmaxb.p, nd, rl_groups, st);
+                    const RlArgs ra{reinterpret_cast<const float *>(A.p), S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs, sR,
+                                    X.p, conv.p, dmaxb.p, xmaxb.p, Dhl.p, s == 0 ? 0 : (s == 1 ? 1 : 2), nd,
+                                    rl_groups};
+                    launch_rl(rlW, ra, st);
                     PDD_LAUNCH(k_refine_conv, cdiv(nd, 256), 256, 0, st, nd, conv.p, sweeps.p, dmaxb.p, xmaxb.p, tol);
+                    if (s + 1 < maxs) {
+                        if (s == 0)
+                            PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p,
+                                       R1hl.p);
+                        else
+                            PDD_LAUNCH(k_residual_df, g_res, 256, rsm_df, st, S, coef.p, sC, R1hl.p, Dhl.p, Rr.p, sR,
+                                       conv.p);
+                    }
                 } else {
                     launch_solve<T>(A.p, S.n, sA, perm.p, rhs_now, S.nrhs, sR, W.p, X.p, 1, conv.p, sweeps.p, tol,
                                     nd, st);
+                    if (s + 1 < maxs)
+                        PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p,
+                                   (float2 *)nullptr);
                 }
-                if (s + 1 < maxs)
-                    PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p);
             }
             tm.mark(3);
             std::vector<int> hc(nd), hs(nd);

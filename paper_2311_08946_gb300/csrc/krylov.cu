@@ -41,32 +41,66 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int *rowptr, const in
     if (row < n && l == 0) y[row] = s;
 }
 
-// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1;
-// warp q of the block takes the vectors t = q, q + 8, ... (no block barriers)
+// sum of partial[0 .. G) by one warp (fixed lane assignment and shuffle tree: deterministic)
+__device__ __forceinline__ double warp_sum_partials(const double *partial, int G) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int q = lane; q < G; q += 32) s += partial[q];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1.  Every thread
+// takes rows of the block's chunk; four vectors at a time give four independent loads per row.
+static constexpr int kMaxDots = 257;
 __global__ void __launch_bounds__(kDotBlock) k_dots(int n, int nv, const double *V, const double *w,
                                                     double *partial, const GState *gs) {
     if (gs && gs->stop) return;
+    __shared__ double red[kDotBlock / 32][kMaxDots];
     const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (n + G - 1) / G, a = blockIdx.x * per, b = min(n, a + per);
-    for (int t = warp; t < nv; t += kDotBlock / 32) {
-        double s = 0.0;
-        const double *v = V + (long)t * n;
-        for (int r = a + lane; r < b; r += 32) s += v[r] * w[r];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) partial[t * G + blockIdx.x] = s;
+    for (int t0 = 0; t0 < nv; t0 += 4) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const double *v0 = V + (long)t0 * n;
+        const int nq = min(4, nv - t0);
+        for (int r = a + threadIdx.x; r < b; r += kDotBlock) {
+            const double wr = w[r];
+            s0 += v0[r] * wr;
+            if (nq > 1) s1 += v0[(long)n + r] * wr;
+            if (nq > 2) s2 += v0[2l * n + r] * wr;
+            if (nq > 3) s3 += v0[3l * n + r] * wr;
+        }
+        for (int o = 16; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        }
+        if (lane == 0) {
+            red[warp][t0] = s0;
+            if (nq > 1) red[warp][t0 + 1] = s1;
+            if (nq > 2) red[warp][t0 + 2] = s2;
+            if (nq > 3) red[warp][t0 + 3] = s3;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nv; t += kDotBlock) {
+        double v = 0.0;
+        for (int q = 0; q < kDotBlock / 32; ++q) v += red[q][t];
+        partial[t * G + blockIdx.x] = v;
     }
 }
 
-// h[t] = sum_blk partial[t][blk]; w -= sum_t V[t] h[t]; column j of H gets h (+= when add)
+// h[t] = sum_blk partial[t][blk] (one warp per t); w -= sum_t V[t] h[t]; column j of H gets h (+= when add)
 __global__ void __launch_bounds__(kDotBlock) k_orth(int n, int nv, const double *V, double *w,
                                                     const double *partial, int G, double *Hcol, int add,
                                                     const GState *gs) {
     if (gs && gs->stop) return;
-    __shared__ double h[257];
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < G; ++q) s += partial[t * G + q];
-        h[t] = s;
+    __shared__ double h[kMaxDots];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < nv; t += kDotBlock / 32) {
+        const double s = warp_sum_partials(partial + (long)t * G, G);
+        if (lane == 0) h[t] = s;
     }
     __syncthreads();
     if (blockIdx.x == 0)
@@ -84,40 +118,56 @@ __global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w,
                                                          const GState *gs) {
     if (gs && gs->stop) return;
     __shared__ double nrm;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < G; ++q) s += partial[q];
-        nrm = sqrt(s);
-        if (blockIdx.x == 0 && Hsub) *Hsub = nrm;
+    if (threadIdx.x < 32) {
+        const double s = warp_sum_partials(partial, G);
+        if (threadIdx.x == 0) {
+            nrm = sqrt(s);
+            if (blockIdx.x == 0 && Hsub) *Hsub = nrm;
+        }
     }
     __syncthreads();
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) v[r] = w[r] * inv;
 }
 
-// apply the previous rotations to column j, make a new one, update g and the stop flag
+// apply the previous rotations to column j, make a new one, update g and the stop flag; one
+// warp stages the column and the rotations in shared memory, lane 0 runs the recurrence
 __global__ void k_givens(double *H, int ldh, double *cs, double *sn, double *g, int j, double rtol,
                          int max_iters, GState *gs) {
     if (gs->stop) return;
+    __shared__ double hs[kMaxDots], cc[kMaxDots], ss[kMaxDots];
     double *hc = H + (long)j * ldh;                  // column j stored contiguously (ldh = m+1)
-    for (int i = 0; i < j; ++i) {
-        double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
-        hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-        hc[i] = t;
+    for (int i = threadIdx.x; i <= j + 1; i += 32) hs[i] = hc[i];
+    for (int i = threadIdx.x; i < j; i += 32) {
+        cc[i] = cs[i];
+        ss[i] = sn[i];
     }
-    const double a = hc[j], b = hc[j + 1];
-    const double den = hypot(a, b);
-    const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    hc[j] = den;
-    hc[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    gs->iters += 1;
-    gs->k_used = j + 1;
-    gs->res = fabs(g[j + 1]);
-    if (gs->res <= rtol * gs->bnorm || gs->iters >= max_iters || b == 0.0) gs->stop = 1;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        double hi = hs[0];
+        for (int i = 0; i < j; ++i) {
+            const double hn = hs[i + 1];
+            const double t = cc[i] * hi + ss[i] * hn;
+            hi = -ss[i] * hi + cc[i] * hn;
+            hs[i] = t;
+        }
+        // hi is the rotated entry j
+        const double a = hi, b = hs[j + 1];
+        const double den = hypot(a, b);
+        const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+        cs[j] = c;
+        sn[j] = s;
+        hs[j] = den;
+        hs[j + 1] = 0.0;
+        g[j + 1] = -s * g[j];
+        g[j] = c * g[j];
+        gs->iters += 1;
+        gs->k_used = j + 1;
+        gs->res = fabs(g[j + 1]);
+        if (gs->res <= rtol * gs->bnorm || gs->iters >= max_iters || b == 0.0) gs->stop = 1;
+    }
+    __syncwarp();
+    for (int i = threadIdx.x; i <= j + 1; i += 32) hc[i] = hs[i];
 }
 
 // y = H^-1 g (upper triangular k x k), single thread; then stop is cleared for the next cycle
@@ -146,8 +196,8 @@ __global__ void k_residual_vec(int n, const double *b, double *r) {
 
 __global__ void k_cycle_start(GState *gs, const double *partial, int G, double *g, int m, double rtol,
                               int max_iters, int first) {
-    double s = 0.0;
-    for (int q = 0; q < G; ++q) s += partial[q];
+    const double s = warp_sum_partials(partial, G);
+    if (threadIdx.x != 0) return;
     const double beta = sqrt(s);
     if (first) gs->bnorm = beta;                      // x0 = 0, so r0 = b
     for (int i = 0; i <= m; ++i) g[i] = 0.0;
@@ -206,7 +256,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
             PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
             PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
-            PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+            PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
             PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, partial.p, G, (double *)nullptr, gs.p);
             if (!exec) {
                 const int64_t before = pdd_launch_count();
@@ -223,7 +273,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
                     PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, gs.p);
                     PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, partial.p, G,
                                Hc + j + 1, gs.p);
-                    PDD_LAUNCH(k_givens, 1, 1, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
+                    PDD_LAUNCH(k_givens, 1, 32, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
                 }
                 PDD_CUDA(cudaStreamEndCapture(st, &graph));
                 PDD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -410,7 +460,7 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
         PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, (const GState *)nullptr);
-        PDD_LAUNCH(k_cycle_start, 1, 1, 0, st, gs, partial, G, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+        PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs, partial, G, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
         PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, partial, G, (double *)nullptr, gs);
         for (int j = 0; j < m; ++j) {
             double *vj = V + (long)j * n;
@@ -422,7 +472,7 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
             }
             PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, gs);
             PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, partial, G, Hc + j + 1, gs);
-            PDD_LAUNCH(k_givens, 1, 1, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
+            PDD_LAUNCH(k_givens, 1, 32, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
         }
         PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H, m + 1, g, y, gs);
         PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V, y, gs, u);
