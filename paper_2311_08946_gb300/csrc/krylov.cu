@@ -41,91 +41,83 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int *rowptr, const in
     if (row < n && l == 0) y[row] = s;
 }
 
-// sum of partial[0 .. G) by one warp (fixed lane assignment and shuffle tree: deterministic)
-__device__ __forceinline__ double warp_sum_partials(const double *partial, int G) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int q = lane; q < G; q += 32) s += partial[q];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
-// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1.  Every thread
-// takes rows of the block's chunk; four vectors at a time give four independent loads per row.
+// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1; the last block to
+// finish adds the partials of every vector in block order into hsum[t] (deterministic) and
+// re-arms the counter.  Each thread takes rows of the block's chunk, eight vectors at a time
+// (eight independent loads per row).
 static constexpr int kMaxDots = 257;
-__global__ void __launch_bounds__(kDotBlock) k_dots(int n, int nv, const double *V, const double *w,
-                                                    double *partial, const GState *gs) {
+static constexpr int kDotThreads = 128;
+__global__ void __launch_bounds__(kDotThreads) k_dots(int n, int nv, const double *V, const double *w,
+                                                      double *partial, double *hsum, unsigned *cnt,
+                                                      const GState *gs) {
     if (gs && gs->stop) return;
-    __shared__ double red[kDotBlock / 32][kMaxDots];
+    __shared__ double red[kDotThreads / 32][kMaxDots];
+    __shared__ bool last;
     const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (n + G - 1) / G, a = blockIdx.x * per, b = min(n, a + per);
-    for (int t0 = 0; t0 < nv; t0 += 4) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int t0 = 0; t0 < nv; t0 += 8) {
+        double s[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q] = 0.0;
+        const int nq = min(8, nv - t0);
         const double *v0 = V + (long)t0 * n;
-        const int nq = min(4, nv - t0);
-        for (int r = a + threadIdx.x; r < b; r += kDotBlock) {
+        for (int r = a + threadIdx.x; r < b; r += kDotThreads) {
             const double wr = w[r];
-            s0 += v0[r] * wr;
-            if (nq > 1) s1 += v0[(long)n + r] * wr;
-            if (nq > 2) s2 += v0[2l * n + r] * wr;
-            if (nq > 3) s3 += v0[3l * n + r] * wr;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < nq) s[q] += v0[(long)q * n + r] * wr;
         }
-        for (int o = 16; o; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
-        }
-        if (lane == 0) {
-            red[warp][t0] = s0;
-            if (nq > 1) red[warp][t0 + 1] = s1;
-            if (nq > 2) red[warp][t0 + 2] = s2;
-            if (nq > 3) red[warp][t0 + 3] = s3;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double v = s[q];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && q < nq) red[warp][t0 + q] = v;
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nv; t += kDotBlock) {
+    for (int t = threadIdx.x; t < nv; t += kDotThreads) {
         double v = 0.0;
-        for (int q = 0; q < kDotBlock / 32; ++q) v += red[q][t];
-        partial[t * G + blockIdx.x] = v;
+        for (int q = 0; q < kDotThreads / 32; ++q) v += red[q][t];
+        partial[(long)t * G + blockIdx.x] = v;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == (unsigned)G - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = warp; t < nv; t += kDotThreads / 32) {
+        double v = 0.0;
+        for (int q = lane; q < G; q += 32) v += __ldcg(partial + (long)t * G + q);
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) hsum[t] = v;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
 }
 
-// h[t] = sum_blk partial[t][blk] (one warp per t); w -= sum_t V[t] h[t]; column j of H gets h (+= when add)
+// w -= sum_t V[t] h[t] with h = hsum; column j of H gets h (+= when add)
 __global__ void __launch_bounds__(kDotBlock) k_orth(int n, int nv, const double *V, double *w,
-                                                    const double *partial, int G, double *Hcol, int add,
-                                                    const GState *gs) {
+                                                    const double *hsum, double *Hcol, int add, const GState *gs) {
     if (gs && gs->stop) return;
     __shared__ double h[kMaxDots];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = warp; t < nv; t += kDotBlock / 32) {
-        const double s = warp_sum_partials(partial + (long)t * G, G);
-        if (lane == 0) h[t] = s;
-    }
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) h[t] = hsum[t];
     __syncthreads();
     if (blockIdx.x == 0)
         for (int t = threadIdx.x; t < nv; t += blockDim.x) Hcol[t] = add ? Hcol[t] + h[t] : h[t];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         double s = w[r];
+#pragma unroll 8
         for (int t = 0; t < nv; ++t) s -= V[(long)t * n + r] * h[t];
         w[r] = s;
     }
 }
 
-// v = w / |w|, with |w| from the partials; Hsub = |w|
-__global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w, double *v,
-                                                         const double *partial, int G, double *Hsub,
-                                                         const GState *gs) {
+// v = w / |w| with |w|^2 = hsum[0]; Hsub = |w|
+__global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w, double *v, const double *hsum,
+                                                         double *Hsub, const GState *gs) {
     if (gs && gs->stop) return;
-    __shared__ double nrm;
-    if (threadIdx.x < 32) {
-        const double s = warp_sum_partials(partial, G);
-        if (threadIdx.x == 0) {
-            nrm = sqrt(s);
-            if (blockIdx.x == 0 && Hsub) *Hsub = nrm;
-        }
-    }
-    __syncthreads();
+    const double nrm = sqrt(hsum[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && Hsub) *Hsub = nrm;
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) v[r] = w[r] * inv;
 }
@@ -194,11 +186,10 @@ __global__ void k_residual_vec(int n, const double *b, double *r) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = b[i] - r[i];
 }
 
-__global__ void k_cycle_start(GState *gs, const double *partial, int G, double *g, int m, double rtol,
-                              int max_iters, int first) {
-    const double s = warp_sum_partials(partial, G);
+__global__ void k_cycle_start(GState *gs, const double *hsum, double *g, int m, double rtol, int max_iters,
+                              int first) {
     if (threadIdx.x != 0) return;
-    const double beta = sqrt(s);
+    const double beta = sqrt(hsum[0]);
     if (first) gs->bnorm = beta;                      // x0 = 0, so r0 = b
     for (int i = 0; i <= m; ++i) g[i] = 0.0;
     g[0] = beta;
@@ -218,12 +209,15 @@ void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
                       const pdd_solve_opts &o, cudaStream_t st_in) {
     const int m = std::max(1, std::min(256, o.restart));
-    const int G = std::max(1, std::min(1024, cdiv(n, 512)));
-    DevBuf<double> V, w, partial, H, cs, sn, g, y;
+    const int G = std::max(1, std::min(1024, cdiv(n, kDotThreads)));
+    DevBuf<double> V, w, partial, hsum, H, cs, sn, g, y;
+    DevBuf<unsigned> cnt;
     DevBuf<GState> gs;
     V.alloc((size_t)(m + 1) * n);
     w.alloc(n);
     partial.alloc((size_t)(m + 1) * G);
+    hsum.alloc(m + 1);
+    cnt.alloc(1);
     H.alloc((size_t)(m + 1) * m);
     cs.alloc(m);
     sn.alloc(m);
@@ -242,6 +236,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
         own = true;
     }
     PDD_CUDA(cudaMemsetAsync(gs.p, 0, sizeof(GState), st));
+    PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
     PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
     PDD_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * (m + 1) * m, st));
     const int vb = std::min(cdiv(n, 256), 2048);
@@ -249,15 +244,14 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
     const int max_iters = std::max(1, o.max_iters);
     cudaGraphExec_t exec = nullptr;
     int per_cycle = 0;
-    std::vector<double> hp(G);
     try {
         for (int cycle = 0;; ++cycle) {
             // r = b - C u  (u = 0 on the first cycle)
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
             PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
-            PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs.p, partial.p, G, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
-            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, partial.p, G, (double *)nullptr, gs.p);
+            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs.p, hsum.p, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, hsum.p, (double *)nullptr, gs.p);
             if (!exec) {
                 const int64_t before = pdd_launch_count();
                 cudaGraph_t graph;
@@ -267,12 +261,12 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
                     double *Hc = H.p + (long)j * (m + 1);
                     PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
                     for (int pass = 0; pass < 2; ++pass) {
-                        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, gs.p);
-                        PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, partial.p, G, Hc, pass, gs.p);
+                        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, j + 1, V.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
+                        PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, hsum.p, Hc, pass, gs.p);
                     }
-                    PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, gs.p);
-                    PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, partial.p, G,
-                               Hc + j + 1, gs.p);
+                    PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
+                    PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, hsum.p, Hc + j + 1,
+                               gs.p);
                     PDD_LAUNCH(k_givens, 1, 32, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
                 }
                 PDD_CUDA(cudaStreamEndCapture(st, &graph));
@@ -288,13 +282,12 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
             // true residual
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
             PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w.p, w.p, partial.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
             GState hg{};
-            PDD_CUDA(cudaMemcpyAsync(hp.data(), partial.p, G * sizeof(double), cudaMemcpyDeviceToHost, st));
+            double rs = 0.0;
+            PDD_CUDA(cudaMemcpyAsync(&rs, hsum.p, sizeof(double), cudaMemcpyDeviceToHost, st));
             PDD_CUDA(cudaMemcpyAsync(&hg, gs.p, sizeof(GState), cudaMemcpyDeviceToHost, st));
             PDD_CUDA(cudaStreamSynchronize(st));
-            double rs = 0.0;
-            for (int q = 0; q < G; ++q) rs += hp[q];
             const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
             res.iters = hg.iters;
             res.rel = rel;
@@ -419,7 +412,7 @@ static void *noalloc_scratch(int dev) {
 }
 
 struct NoAllocLayout {
-    size_t V, w, partial, H, cs, sn, g, y, gs, total;
+    size_t V, w, partial, hsum, cnt, H, cs, sn, g, y, gs, total;
 };
 
 static NoAllocLayout noalloc_layout(int n, int m, int G) {
@@ -429,6 +422,8 @@ static NoAllocLayout noalloc_layout(int n, int m, int G) {
     L.V = off; off += up(sizeof(double) * (size_t)(m + 1) * n);
     L.w = off; off += up(sizeof(double) * (size_t)n);
     L.partial = off; off += up(sizeof(double) * (size_t)(m + 1) * G);
+    L.hsum = off; off += up(sizeof(double) * (size_t)(m + 1));
+    L.cnt = off; off += up(sizeof(unsigned));
     L.H = off; off += up(sizeof(double) * (size_t)(m + 1) * m);
     L.cs = off; off += up(sizeof(double) * (size_t)m);
     L.sn = off; off += up(sizeof(double) * (size_t)m);
@@ -445,46 +440,47 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
                                    const NoAllocLayout &L, int m, int G, cudaStream_t st) {
     double *V = (double *)(base + L.V), *w = (double *)(base + L.w);
     double *partial = (double *)(base + L.partial), *H = (double *)(base + L.H);
+    double *hsum = (double *)(base + L.hsum);
+    unsigned *cnt = (unsigned *)(base + L.cnt);
     double *cs = (double *)(base + L.cs), *sn = (double *)(base + L.sn);
     double *g = (double *)(base + L.g), *y = (double *)(base + L.y);
     GState *gs = (GState *)(base + L.gs);
     // the array keeps the previous call's contents: clear what must start at zero
     PDD_CUDA(cudaMemsetAsync(gs, 0, sizeof(GState), st));
+    PDD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), st));
     PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
     PDD_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, st));
     const int vb = std::min(cdiv(n, 256), 2048);
     const int max_iters = std::max(1, o.max_iters);
     SolveResult res;
-    std::vector<double> hp(G);
     for (int cycle = 0;; ++cycle) {
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, (const GState *)nullptr);
-        PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs, partial, G, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
-        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, partial, G, (double *)nullptr, gs);
+        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
+        PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs, hsum, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, hsum, (double *)nullptr, gs);
         for (int j = 0; j < m; ++j) {
             double *vj = V + (long)j * n;
             double *Hc = H + (long)j * (m + 1);
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w, gs);
             for (int pass = 0; pass < 2; ++pass) {
-                PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, j + 1, V, w, partial, gs);
-                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V, w, partial, G, Hc, pass, gs);
+                PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, j + 1, V, w, partial, hsum, cnt, gs);
+                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V, w, hsum, Hc, pass, gs);
             }
-            PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, gs);
-            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, partial, G, Hc + j + 1, gs);
+            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, gs);
+            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, hsum, Hc + j + 1, gs);
             PDD_LAUNCH(k_givens, 1, 32, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
         }
         PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H, m + 1, g, y, gs);
         PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V, y, gs, u);
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, G, kDotBlock, 0, st, n, 1, w, w, partial, (const GState *)nullptr);
+        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
         GState hg{};
-        PDD_CUDA(cudaMemcpyAsync(hp.data(), partial, G * sizeof(double), cudaMemcpyDeviceToHost, st));
+        double rs = 0.0;
+        PDD_CUDA(cudaMemcpyAsync(&rs, hsum, sizeof(double), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GState), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));
-        double rs = 0.0;
-        for (int q = 0; q < G; ++q) rs += hp[q];
         const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
         res.iters = hg.iters;
         res.rel = rel;
@@ -510,7 +506,7 @@ extern "C" pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr, const int 
         if (opts->transpose) fail(PDD_EINVAL, "the allocation-free solve takes C itself (transpose = 0)");
         if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
         const int m = opts->restart;
-        const int G = std::max(1, std::min(1024, cdiv(n, 512)));
+        const int G = std::max(1, std::min(1024, cdiv(n, kDotThreads)));
         const NoAllocLayout L = noalloc_layout(n, m, G);
         if (L.total > kNoAllocBytes)
             fail(PDD_EINVAL, "workspace of " + std::to_string(L.total) + " bytes exceeds the fixed " +

@@ -7,17 +7,19 @@
 // the FP64 refinement of a8 needs (one TF32 product would leave
 // kappa(A) u_tf32 > 1 on the 32x32 and 48x64 disk grids).
 //
-// One CTA (128 threads) computes a 128 x 128 tile of C for one matrix of the
+// One CTA (256 threads) computes a 128 x 128 tile of C for one matrix of the
 // batch:
-//   * the K loop runs in chunks of 32; each chunk is staged by all threads
-//     into shared memory in the canonical no-swizzle K-major layout (8-row x
-//     16-byte core matrices; LBO = K-direction core stride, SBO = 8-row-group
-//     stride), hi and lo copies, double-buffered;
+//   * the K loop runs in chunks of 32; each chunk is loaded with 16-byte
+//     loads into registers while the tensor cores work on the previous one,
+//     split, and stored into shared memory in the canonical no-swizzle
+//     K-major layout (8-row x 16-byte core matrices; LBO = K-direction core
+//     stride, SBO = 8-row-group stride), hi and lo copies, double-buffered;
 //   * one thread issues 4 k-steps x 3 tcgen05.mma.kind::tf32 (M = 128,
 //     N = 128, K = 8) into a TMEM accumulator and commits them to the
 //     buffer's mbarrier;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-//     lanes 32w..32w+31 = rows) and subtracts it from C.
+//     lanes 32(w mod 4).. = rows, and one half of the columns) and subtracts
+//     it from C.
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // waits once more (bounded) for its own MMAs, frees its TMEM and returns.
 #include "handles.cuh"
@@ -27,8 +29,8 @@ namespace pdd {
 static constexpr int kTM = 128, kTN = 128, kTK = 32;
 static constexpr int kOpBytes = kTM * kTK * 4;          // one operand copy: 16 KB
 static constexpr int kStageBytes = 4 * kOpBytes;        // A_hi, A_lo, B_hi, B_lo
-static constexpr int kTcSmem = 2 * kStageBytes + 32 * 1024;   // two stages + guard band
-static constexpr int kTmemCols = 256;                   // 128 used; the rest is headroom
+static constexpr int kTcSmem = 2 * kStageBytes;        // two stages
+static constexpr int kTmemCols = 128;                   // one 128 x 128 FP32 accumulator
 static constexpr long long kWaitLimit = 1LL << 22;   // polls before a wait is declared failed
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -97,9 +99,143 @@ __device__ __forceinline__ int canon_off(int r, int k, int rows) {
     return (k >> 2) * (rows * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 
-__global__ void __launch_bounds__(128, 1) k_gemm_sub_tf32x3(int M, int N, int K, const float *A, long sA, int lda,
-                                                            const float *B, long sB, int ldb, float *C, long sC,
-                                                            int ldc, int *err) {
+static constexpr int kTcThreads = 256;
+
+// One K chunk of the two operands in registers (vector path): thread (warp w, lane l) holds
+//   A: 4 float4 = rows 8 ((i >> 1) 8 + w) + (l & 7), k = 4 ((l >> 3) + 4 (i & 1)) .. + 3
+//   B: 4 float4 = row k = (l >> 3) + 4 w, columns 4 ((l & 7) + 8 i) .. + 3
+// so that a warp's global loads cover whole 32-byte sectors and its shared-memory stores
+// into the canonical layout hit 32 different banks.
+struct Chunk {
+    float4 a[4], b[4];
+};
+
+__device__ __forceinline__ void load_chunk_vec(Chunk &c, const float *A, int lda, const float *B, int ldb, int M,
+                                               int N, int K, int tm, int tn, int k0, int w, int l) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 8 * ((i >> 1) * 8 + w) + (l & 7), k = 4 * ((l >> 3) + 4 * (i & 1));
+        const int gr = tm + r, gk = k0 + k;
+        c.a[i] = (gr < M && gk < K) ? __ldg(reinterpret_cast<const float4 *>(A + (long)gr * lda + gk))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = (l >> 3) + 4 * w, j = 4 * ((l & 7) + 8 * i);
+        const int gk = k0 + k, gj = tn + j;
+        c.b[i] = (gk < K && gj < N) ? __ldg(reinterpret_cast<const float4 *>(B + (long)gk * ldb + gj))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ float4 split_hi(float4 v) {
+    return make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+}
+
+__device__ __forceinline__ float4 split_lo(float4 v, float4 h) {
+    return make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z), tf32_round(v.w - h.w));
+}
+
+__device__ __forceinline__ float pick4(float4 v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void store_chunk_vec(const Chunk &c, float *Ahi, float *Alo, float *Bhi, float *Blo, int w,
+                                                int l) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 8 * ((i >> 1) * 8 + w) + (l & 7), k = 4 * ((l >> 3) + 4 * (i & 1));
+        const int off = canon_off(r, k, kTM) >> 2;
+        const float4 h = split_hi(c.a[i]);
+        *reinterpret_cast<float4 *>(Ahi + off) = h;
+        *reinterpret_cast<float4 *>(Alo + off) = split_lo(c.a[i], h);
+    }
+    const int rot = (l >> 1) & 3;            // element order rotated per lane: conflict-free stores
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = (l >> 3) + 4 * w, j0 = 4 * ((l & 7) + 8 * i);
+        const float4 h = split_hi(c.b[i]);
+        const float4 lo = split_lo(c.b[i], h);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ee = (e + rot) & 3;
+            const int off = canon_off(j0 + ee, k, kTN) >> 2;
+            Bhi[off] = pick4(h, ee);
+            Blo[off] = pick4(lo, ee);
+        }
+    }
+}
+
+// scalar staging for shapes or addresses that are not 16-byte aligned
+__device__ __forceinline__ void stage_scalar(const float *A, int lda, const float *B, int ldb, int M, int N, int K,
+                                             int tm, int tn, int k0, float *Ahi, float *Alo, float *Bhi, float *Blo,
+                                             int tid) {
+    for (int e = tid; e < kTM * kTK; e += kTcThreads) {
+        const int r = e >> 5, k = e & 31;
+        const int gr = tm + r, gk = k0 + k;
+        const float v = (gr < M && gk < K) ? A[(long)gr * lda + gk] : 0.f;
+        const float hi = tf32_round(v);
+        const int off = canon_off(r, k, kTM) >> 2;
+        Ahi[off] = hi;
+        Alo[off] = tf32_round(v - hi);
+    }
+    for (int e = tid; e < kTK * kTN; e += kTcThreads) {
+        const int k = e >> 7, j = e & 127;
+        const int gk = k0 + k, gj = tn + j;
+        const float v = (gk < K && gj < N) ? B[(long)gk * ldb + gj] : 0.f;
+        const float hi = tf32_round(v);
+        const int off = canon_off(j, k, kTN) >> 2;
+        Bhi[off] = hi;
+        Blo[off] = tf32_round(v - hi);
+    }
+}
+
+// C (tile rows tm.., columns tn..) -= the TMEM accumulator; warp w reads TMEM lanes 32 (w & 3) ..
+// (rows) and the column half (w >> 2)
+template <bool VEC>
+__device__ __forceinline__ void epilogue(uint32_t tmem, float *C, int ldc, int M, int N, int tm, int tn, int w,
+                                         int l) {
+    const int row = tm + (w & 3) * 32 + l;
+#pragma unroll 1
+    for (int c0 = (w >> 2) * 64; c0 < (w >> 2) * 64 + 64; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M) {
+            float *crow = C + (long)row * ldc + tn + c0;
+            if (VEC && tn + c0 + 32 <= N) {
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    float4 cv = *reinterpret_cast<float4 *>(crow + q);
+                    cv.x -= __uint_as_float(v[q]);
+                    cv.y -= __uint_as_float(v[q + 1]);
+                    cv.z -= __uint_as_float(v[q + 2]);
+                    cv.w -= __uint_as_float(v[q + 3]);
+                    *reinterpret_cast<float4 *>(crow + q) = cv;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (tn + c0 + q < N) crow[q] -= __uint_as_float(v[q]);
+            }
+        }
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_sub_tf32x3(int M, int N, int K, const float *A, long sA,
+                                                                   int lda, const float *B, long sB, int ldb,
+                                                                   float *C, long sC, int ldc, int *err) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
@@ -131,35 +267,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_sub_tf32x3(int M, int N, int K,
     const uint32_t lbo = kTM * 16;             // K-direction core-matrix stride (rows = 128)
     const uint32_t sbo = 128;                  // 8-row-group stride
     int issued = -1;                           // last chunk whose MMAs were committed (uniform)
+    Chunk cur;
+    if (VEC && nch > 0) load_chunk_vec(cur, A, lda, B, ldb, M, N, K, tm, tn, 0, warp, lane);
     for (int kc = 0; kc < nch; ++kc) {
         const int buf = kc & 1;
         unsigned char *st = tsm + buf * kStageBytes;
-        if (kc >= 2) {
+        if (kc >= 2 && tid == 0) {
             if (!mbar_wait(smem_u32(&mbar[buf]), ((kc - 2) >> 1) & 1)) failed = 1;
         }
         __syncthreads();
         if (failed) break;
         float *Ahi = (float *)st, *Alo = (float *)(st + kOpBytes);
         float *Bhi = (float *)(st + 2 * kOpBytes), *Blo = (float *)(st + 3 * kOpBytes);
-        const int k0 = kc * kTK;
-        for (int e = tid; e < kTM * kTK; e += 128) {            // A rows, K contiguous
-            const int r = e >> 5, k = e & 31;
-            const int gr = tm + r, gk = k0 + k;
-            const float v = (gr < M && gk < K) ? A[(long)gr * lda + gk] : 0.f;
-            const float hi = tf32_round(v);
-            const int off = canon_off(r, k, kTM) >> 2;
-            Ahi[off] = hi;
-            Alo[off] = tf32_round(v - hi);
-        }
-        for (int e = tid; e < kTK * kTN; e += 128) {            // B is K x N (N contiguous): stage N rows x K
-            const int k = e >> 7, j = e & 127;
-            const int gk = k0 + k, gj = tn + j;
-            const float v = (gk < K && gj < N) ? B[(long)gk * ldb + gj] : 0.f;
-            const float hi = tf32_round(v);
-            const int off = canon_off(j, k, kTN) >> 2;
-            Bhi[off] = hi;
-            Blo[off] = tf32_round(v - hi);
-        }
+        if (VEC) store_chunk_vec(cur, Ahi, Alo, Bhi, Blo, warp, lane);
+        else stage_scalar(A, lda, B, ldb, M, N, K, tm, tn, kc * kTK, Ahi, Alo, Bhi, Blo, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -177,9 +298,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_sub_tf32x3(int M, int N, int K,
             mma_commit(smem_u32(&mbar[buf]));
         }
         issued = kc;
+        // the next chunk's loads are in flight while the tensor cores work on this one
+        if (VEC && kc + 1 < nch) load_chunk_vec(cur, A, lda, B, ldb, M, N, K, tm, tn, (kc + 1) * kTK, warp, lane);
     }
     // all MMAs of this tile are complete once the last commit has landed
-    if (issued >= 0) {
+    if (issued >= 0 && tid == 0) {
         const int last = issued & 1;
         const uint32_t par = (issued >> 1) & 1;
         bool ok = mbar_wait(smem_u32(&mbar[last]), par);
@@ -188,33 +311,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_sub_tf32x3(int M, int N, int K,
             mbar_wait(smem_u32(&mbar[last]), par);          // bounded second wait for in-flight MMAs
         }
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (!failed && issued == nch - 1 && nch > 0) {
-        const int row = tm + warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
-                float *crow = C + (long)row * ldc + tn + c0;
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (tn + c0 + q < N) crow[q] -= __uint_as_float(v[q]);
-            }
-        }
-    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!failed && issued == nch - 1 && nch > 0) epilogue<VEC>(tmem, C, ldc, M, N, tm, tn, warp, lane);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -227,12 +326,22 @@ void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, in
     if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
     static bool attr = false;
     if (!attr) {
-        PDD_CUDA(cudaFuncSetAttribute(k_gemm_sub_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+        PDD_CUDA(cudaFuncSetAttribute(k_gemm_sub_tf32x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+        PDD_CUDA(cudaFuncSetAttribute(k_gemm_sub_tf32x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
         attr = true;
     }
     dim3 grid(cdiv(N, kTN), cdiv(M, kTM), batch);
     if (grid.y > 65535 || grid.z > 65535) fail(PDD_EINVAL, "GEMM batch too large");
-    PDD_LAUNCH(k_gemm_sub_tf32x3, grid, 128, kTcSmem, st, M, N, K, A, sA, lda, B, sB, ldb, C, sC, ldc, err);
+    // 16-byte vector path: every row start and the K and N extents on 4-float boundaries
+    auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    const bool vec = al16(A) && al16(B) && al16(C) && lda % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 && sA % 4 == 0 &&
+                     sB % 4 == 0 && sC % 4 == 0 && K % 4 == 0 && N % 4 == 0;
+    if (vec)
+        PDD_LAUNCH(k_gemm_sub_tf32x3<true>, grid, kTcThreads, kTcSmem, st, M, N, K, A, sA, lda, B, sB, ldb, C, sC,
+                   ldc, err);
+    else
+        PDD_LAUNCH(k_gemm_sub_tf32x3<false>, grid, kTcThreads, kTcSmem, st, M, N, K, A, sA, lda, B, sB, ldb, C, sC,
+                   ldc, err);
 }
 
 }  // namespace pdd

@@ -19,8 +19,11 @@ def pdd():
     return pkg
 
 
+# aligned shapes take the 16-byte staging path (ragged tiles at the M, N and K edges included:
+# 260 x 132 x 68, 96 x 200 x 36); odd extents take the scalar path
 @pytest.mark.parametrize("b,M,N,K", [(1, 128, 128, 32), (3, 256, 128, 64), (2, 300, 200, 96),
-                                     (4, 512, 384, 512), (2, 129, 65, 33), (1, 1, 1, 1)])
+                                     (4, 512, 384, 512), (3, 260, 132, 68), (2, 96, 200, 36),
+                                     (2, 129, 65, 33), (1, 1, 1, 1)])
 def test_gemm_sub_matches_fp64(pdd, b, M, N, K):
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(b, M, K, device="cuda", generator=g, dtype=torch.float32)
