@@ -565,15 +565,27 @@ __global__ void __launch_bounds__(128) k_diag_inv(const float *LUall, int n, lon
     for (int r = 0; r < kRlTB; ++r) out[r * kRlTB + j] = Xs[w][r][j];
 }
 
-template <int CG>
-__device__ __forceinline__ void rl_rank1(float (&acc)[CG], float l, const float *xrow) {
+// the 32 factor entries T[r, i0 .. i0+31] of one row (16-byte loads; zero for rows past rb)
+__device__ __forceinline__ void rl_fetch(float4 (&l)[kRlTB / 4], const float *LU, int n, int r, int rb, int i0) {
+    const float4 *src = reinterpret_cast<const float4 *>(LU + (long)(r < rb ? r : 0) * n + i0);
 #pragma unroll
-    for (int c = 0; c < CG; c += 4) {
-        const float4 x = *reinterpret_cast<const float4 *>(xrow + c);
-        acc[c] = fmaf(-l, x.x, acc[c]);
-        acc[c + 1] = fmaf(-l, x.y, acc[c + 1]);
-        acc[c + 2] = fmaf(-l, x.z, acc[c + 2]);
-        acc[c + 3] = fmaf(-l, x.w, acc[c + 3]);
+    for (int q = 0; q < kRlTB / 4; ++q) l[q] = r < rb ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int CG>
+__device__ __forceinline__ void rl_rank4(float (&acc)[CG], float4 l, const float *xs) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const float lk = kk == 0 ? l.x : (kk == 1 ? l.y : (kk == 2 ? l.z : l.w));
+        const float *xr = xs + (size_t)kk * CG;
+#pragma unroll
+        for (int c = 0; c < CG; c += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(xr + c);
+            acc[c] = fmaf(-lk, x.x, acc[c]);
+            acc[c + 1] = fmaf(-lk, x.y, acc[c + 1]);
+            acc[c + 2] = fmaf(-lk, x.z, acc[c + 2]);
+            acc[c + 3] = fmaf(-lk, x.w, acc[c + 3]);
+        }
     }
 }
 
@@ -582,11 +594,11 @@ __device__ __forceinline__ void rl_rank1(float (&acc)[CG], float l, const float 
 // (bit patterns of non-negative doubles, ordered like the values)
 template <int CG>
 __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUall, int n, long strideA,
-                                                            const int *permAll, const float *DinvAll,
-                                                            const double *Rall, int nrhs, long strideR,
-                                                            double *Xall, const int *conv,
-                                                            unsigned long long *dmaxb, unsigned long long *xmaxb,
-                                                            float2 *Dall, int dmode) {
+                                                               const int *permAll, const float *DinvAll,
+                                                               const double *Rall, int nrhs, long strideR,
+                                                               double *Xall, const int *conv,
+                                                               unsigned long long *dmaxb, unsigned long long *xmaxb,
+                                                               float2 *Dall, int dmode) {
     constexpr int NT = kRlThreads, TB = kRlTB, OUT = (TB * CG + NT - 1) / NT;
     extern __shared__ __align__(16) float rsm[];
     float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
@@ -609,6 +621,12 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
         for (int bi = 0; bi < nblk; ++bi) {
             const int blk = pass == 0 ? bi : nblk - 1 - bi;
             const int i0 = blk * TB, tb = min(TB, n - i0);
+            const int ra = pass == 0 ? i0 + tb : 0, rb = pass == 0 ? n : i0;
+            const bool full = vec && tb == TB;
+            // this thread's first row of the update: its factor entries are in flight during the
+            // diagonal step
+            float4 lv[TB / 4];
+            if (full) rl_fetch(lv, LU, n, ra + tid, rb, i0);
             const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
             for (int e = tid; e < TB * TB; e += NT) Ds[e] = Dt[e];
             __syncthreads();
@@ -633,8 +651,7 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
                 if (e < tb * CG) Bs[(size_t)i0 * CG + e] = o[q];
             }
             __syncthreads();
-            // rows still to solve: B_r -= T_rb X_b
-            const int ra = pass == 0 ? i0 + tb : 0, rb = pass == 0 ? n : i0;
+            // rows still to solve: B_r -= T_rb X_b; the next row's entries load during this row's FMAs
             const float *xs = Bs + (size_t)i0 * CG;
             for (int r = ra + tid; r < rb; r += NT) {
                 float acc[CG];
@@ -647,18 +664,30 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
                     acc[c + 2] = t.z;
                     acc[c + 3] = t.w;
                 }
-                const float *lrow = LU + (long)r * n + i0;
-                if (vec && tb == TB) {
-#pragma unroll 2
-                    for (int k0 = 0; k0 < TB; k0 += 4) {
-                        const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lrow + k0));
-                        rl_rank1<CG>(acc, l4.x, xs + (size_t)(k0 + 0) * CG);
-                        rl_rank1<CG>(acc, l4.y, xs + (size_t)(k0 + 1) * CG);
-                        rl_rank1<CG>(acc, l4.z, xs + (size_t)(k0 + 2) * CG);
-                        rl_rank1<CG>(acc, l4.w, xs + (size_t)(k0 + 3) * CG);
+                if (full) {
+                    float4 ln[TB / 4];
+                    const bool more = r + NT < rb;
+                    if (more) rl_fetch(ln, LU, n, r + NT, rb, i0);
+#pragma unroll
+                    for (int q = 0; q < TB / 4; ++q) rl_rank4<CG>(acc, lv[q], xs + (size_t)(4 * q) * CG);
+                    if (more) {
+#pragma unroll
+                        for (int q = 0; q < TB / 4; ++q) lv[q] = ln[q];
                     }
                 } else {
-                    for (int k = 0; k < tb; ++k) rl_rank1<CG>(acc, __ldg(lrow + k), xs + (size_t)k * CG);
+                    const float *lrow = LU + (long)r * n + i0;
+                    for (int k = 0; k < tb; ++k) {
+                        const float lk = __ldg(lrow + k);
+                        const float *xr = xs + (size_t)k * CG;
+#pragma unroll
+                        for (int c = 0; c < CG; c += 4) {
+                            const float4 x = *reinterpret_cast<const float4 *>(xr + c);
+                            acc[c] = fmaf(-lk, x.x, acc[c]);
+                            acc[c + 1] = fmaf(-lk, x.y, acc[c + 1]);
+                            acc[c + 2] = fmaf(-lk, x.z, acc[c + 2]);
+                            acc[c + 3] = fmaf(-lk, x.w, acc[c + 3]);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < CG; c += 4)
@@ -1109,8 +1138,8 @@ static LuChoice tune_lu(float *A, int n, long sA, int nd, cudaStream_t st) {
     }
     std::vector<LuChoice> cand{{1, 0, 0, 0.f}};
     for (int W : {32, 16, 8})
-        if ((size_t)n * (W + 1) * sizeof(float) <= 200 * 1024)
-            for (int tmin : {64, 128}) cand.push_back({0, W, tmin, 0.f});
+        if ((size_t)n * ((W + 1) * sizeof(float) + sizeof(int)) <= 200 * 1024)
+            for (int tmin : {32, 64, 128}) cand.push_back({0, W, tmin, 0.f});
     const int nt = std::min(nd, 304);           // two disks per SM: the occupancy of a full wave
     DevBuf<float> pristine, work;
     DevBuf<int> perm, info;

@@ -41,58 +41,59 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int *rowptr, const in
     if (row < n && l == 0) y[row] = s;
 }
 
-// partial[t * G + blk] = sum over this block's rows of V[t] . w, t = 0..nv-1; the last block to
-// finish adds the partials of every vector in block order into hsum[t] (deterministic) and
-// re-arms the counter.  Each thread takes rows of the block's chunk, eight vectors at a time
-// (eight independent loads per row).
+// partial[t * G + bx] = sum over the rows of block column bx of V[t] . w.  The grid is
+// (row chunks G) x (groups of eight vectors); each thread takes rows of its chunk for the eight
+// vectors of its group (independent loads).  The last block of a vector group to finish adds the
+// group's partials in block order into hsum[t] (deterministic) and re-arms the group's counter.
 static constexpr int kMaxDots = 257;
-static constexpr int kDotThreads = 128;
+static constexpr int kDotThreads = 128, kDotVec = 8;
+static constexpr int kDotGroups = (kMaxDots + kDotVec - 1) / kDotVec;
 __global__ void __launch_bounds__(kDotThreads) k_dots(int n, int nv, const double *V, const double *w,
                                                       double *partial, double *hsum, unsigned *cnt,
                                                       const GState *gs) {
     if (gs && gs->stop) return;
-    __shared__ double red[kDotThreads / 32][kMaxDots];
+    __shared__ double red[kDotThreads / 32][kDotVec];
     __shared__ bool last;
     const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = blockIdx.y * kDotVec, nq = min(kDotVec, nv - t0);
     const int per = (n + G - 1) / G, a = blockIdx.x * per, b = min(n, a + per);
-    for (int t0 = 0; t0 < nv; t0 += 8) {
-        double s[8];
+    double s[kDotVec];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) s[q] = 0.0;
-        const int nq = min(8, nv - t0);
-        const double *v0 = V + (long)t0 * n;
-        for (int r = a + threadIdx.x; r < b; r += kDotThreads) {
-            const double wr = w[r];
+    for (int q = 0; q < kDotVec; ++q) s[q] = 0.0;
+    const double *v0 = V + (long)t0 * n;
+    for (int r = a + threadIdx.x; r < b; r += kDotThreads) {
+        const double wr = w[r];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < nq) s[q] += v0[(long)q * n + r] * wr;
-        }
+        for (int q = 0; q < kDotVec; ++q)
+            if (q < nq) s[q] += v0[(long)q * n + r] * wr;
+    }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            double v = s[q];
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && q < nq) red[warp][t0 + q] = v;
-        }
+    for (int q = 0; q < kDotVec; ++q) {
+        double v = s[q];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nv; t += kDotThreads) {
+    if (threadIdx.x < nq) {
         double v = 0.0;
-        for (int q = 0; q < kDotThreads / 32; ++q) v += red[q][t];
-        partial[(long)t * G + blockIdx.x] = v;
+        for (int q = 0; q < kDotThreads / 32; ++q) v += red[q][threadIdx.x];
+        partial[(long)(t0 + threadIdx.x) * G + blockIdx.x] = v;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == (unsigned)G - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(cnt + blockIdx.y, 1u) == (unsigned)G - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int t = warp; t < nv; t += kDotThreads / 32) {
+    for (int q = warp; q < nq; q += kDotThreads / 32) {
+        const double *pp = partial + (long)(t0 + q) * G;
         double v = 0.0;
-        for (int q = lane; q < G; q += 32) v += __ldcg(partial + (long)t * G + q);
+#pragma unroll 4
+        for (int i = lane; i < G; i += 32) v += __ldcg(pp + i);
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) hsum[t] = v;
+        if (lane == 0) hsum[t0 + q] = v;
     }
-    if (threadIdx.x == 0) *cnt = 0u;
+    if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
 // w -= sum_t V[t] h[t] with h = hsum; column j of H gets h (+= when add)
@@ -106,8 +107,14 @@ __global__ void __launch_bounds__(kDotBlock) k_orth(int n, int nv, const double 
         for (int t = threadIdx.x; t < nv; t += blockDim.x) Hcol[t] = add ? Hcol[t] + h[t] : h[t];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         double s = w[r];
-#pragma unroll 8
-        for (int t = 0; t < nv; ++t) s -= V[(long)t * n + r] * h[t];
+        for (int t0 = 0; t0 < nv; t0 += 16) {            // sixteen independent loads in flight
+            double v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = (t0 + q < nv) ? V[(long)(t0 + q) * n + r] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (t0 + q < nv) s -= v[q] * h[t0 + q];
+        }
         w[r] = s;
     }
 }
@@ -209,7 +216,7 @@ void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
                       const pdd_solve_opts &o, cudaStream_t st_in) {
     const int m = std::max(1, std::min(256, o.restart));
-    const int G = std::max(1, std::min(1024, cdiv(n, kDotThreads)));
+    const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));
     DevBuf<double> V, w, partial, hsum, H, cs, sn, g, y;
     DevBuf<unsigned> cnt;
     DevBuf<GState> gs;
@@ -217,7 +224,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
     w.alloc(n);
     partial.alloc((size_t)(m + 1) * G);
     hsum.alloc(m + 1);
-    cnt.alloc(1);
+    cnt.alloc(kDotGroups);
     H.alloc((size_t)(m + 1) * m);
     cs.alloc(m);
     sn.alloc(m);
@@ -236,7 +243,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
         own = true;
     }
     PDD_CUDA(cudaMemsetAsync(gs.p, 0, sizeof(GState), st));
-    PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
+    PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned) * kDotGroups, st));
     PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
     PDD_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * (m + 1) * m, st));
     const int vb = std::min(cdiv(n, 256), 2048);
@@ -249,7 +256,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
             // r = b - C u  (u = 0 on the first cycle)
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
             PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
             PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs.p, hsum.p, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
             PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, hsum.p, (double *)nullptr, gs.p);
             if (!exec) {
@@ -261,10 +268,10 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
                     double *Hc = H.p + (long)j * (m + 1);
                     PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
                     for (int pass = 0; pass < 2; ++pass) {
-                        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, j + 1, V.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
+                        PDD_LAUNCH(k_dots, dim3(G, cdiv(j + 1, kDotVec)), kDotThreads, 0, st, n, j + 1, V.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
                         PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, hsum.p, Hc, pass, gs.p);
                     }
-                    PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
+                    PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
                     PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, hsum.p, Hc + j + 1,
                                gs.p);
                     PDD_LAUNCH(k_givens, 1, 32, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
@@ -282,7 +289,7 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
             // true residual
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
             PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
+            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
             GState hg{};
             double rs = 0.0;
             PDD_CUDA(cudaMemcpyAsync(&rs, hsum.p, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -423,7 +430,7 @@ static NoAllocLayout noalloc_layout(int n, int m, int G) {
     L.w = off; off += up(sizeof(double) * (size_t)n);
     L.partial = off; off += up(sizeof(double) * (size_t)(m + 1) * G);
     L.hsum = off; off += up(sizeof(double) * (size_t)(m + 1));
-    L.cnt = off; off += up(sizeof(unsigned));
+    L.cnt = off; off += up(sizeof(unsigned) * kDotGroups);
     L.H = off; off += up(sizeof(double) * (size_t)(m + 1) * m);
     L.cs = off; off += up(sizeof(double) * (size_t)m);
     L.sn = off; off += up(sizeof(double) * (size_t)m);
@@ -447,7 +454,7 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
     GState *gs = (GState *)(base + L.gs);
     // the array keeps the previous call's contents: clear what must start at zero
     PDD_CUDA(cudaMemsetAsync(gs, 0, sizeof(GState), st));
-    PDD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), st));
+    PDD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * kDotGroups, st));
     PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
     PDD_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, st));
     const int vb = std::min(cdiv(n, 256), 2048);
@@ -456,7 +463,7 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
     for (int cycle = 0;; ++cycle) {
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
+        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
         PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs, hsum, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
         PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, hsum, (double *)nullptr, gs);
         for (int j = 0; j < m; ++j) {
@@ -464,10 +471,10 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
             double *Hc = H + (long)j * (m + 1);
             PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w, gs);
             for (int pass = 0; pass < 2; ++pass) {
-                PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, j + 1, V, w, partial, hsum, cnt, gs);
+                PDD_LAUNCH(k_dots, dim3(G, cdiv(j + 1, kDotVec)), kDotThreads, 0, st, n, j + 1, V, w, partial, hsum, cnt, gs);
                 PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V, w, hsum, Hc, pass, gs);
             }
-            PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, gs);
+            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, gs);
             PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, hsum, Hc + j + 1, gs);
             PDD_LAUNCH(k_givens, 1, 32, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
         }
@@ -475,7 +482,7 @@ static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, con
         PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V, y, gs, u);
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, G, kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
+        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
         GState hg{};
         double rs = 0.0;
         PDD_CUDA(cudaMemcpyAsync(&rs, hsum, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -506,7 +513,7 @@ extern "C" pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr, const int 
         if (opts->transpose) fail(PDD_EINVAL, "the allocation-free solve takes C itself (transpose = 0)");
         if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
         const int m = opts->restart;
-        const int G = std::max(1, std::min(1024, cdiv(n, kDotThreads)));
+        const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));
         const NoAllocLayout L = noalloc_layout(n, m, G);
         if (L.total > kNoAllocBytes)
             fail(PDD_EINVAL, "workspace of " + std::to_string(L.total) + " bytes exceeds the fixed " +

@@ -22,6 +22,8 @@ namespace pdd {
 void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, int lda, const float *B, long sB,
                      int ldb, float *C, long sC, int ldc, int *err, cudaStream_t st);
 
+__device__ __forceinline__ void apply_panel_swaps(float *A, int n, int k0, int w, const int *piv, int tid, int nt);
+
 // factor columns [k0, k0+w) of rows [k0, n); perm tracks P A = L U
 template <int W>
 __global__ void __launch_bounds__(256) k_panel_leaf(float *Aall, int n, long strideA, int k0, int w, int *permAll,
@@ -35,10 +37,12 @@ __global__ void __launch_bounds__(256) k_panel_leaf(float *Aall, int n, long str
     float *A = Aall + disk * strideA;
     int *perm = permAll + (long)disk * n;
     const int rows = n - k0;
+    int *ps = reinterpret_cast<int *>(pn + (size_t)rows * LD);   // perm[k0 ..], stored at the end
     for (int idx = tid; idx < rows * w; idx += 256) {
         const int r = idx / w, c = idx - r * w;
         pn[r * LD + c] = A[(long)(k0 + r) * n + k0 + c];
     }
+    for (int r = tid; r < rows; r += 256) ps[r] = perm[k0 + r];
     __syncthreads();
     int info = 0;
     for (int c = 0; c < w; ++c) {
@@ -63,9 +67,9 @@ __global__ void __launch_bounds__(256) k_panel_leaf(float *Aall, int n, long str
                 if (rv[q] > b || (rv[q] == b && ri[q] < i0)) { b = rv[q]; i0 = ri[q]; }
             piv[c] = i0;
             if (i0 != c) {
-                const int t = perm[k0 + c];
-                perm[k0 + c] = perm[k0 + i0];
-                perm[k0 + i0] = t;
+                const int t = ps[c];
+                ps[c] = ps[i0];
+                ps[i0] = t;
             }
         }
         __syncthreads();
@@ -89,12 +93,19 @@ __global__ void __launch_bounds__(256) k_panel_leaf(float *Aall, int n, long str
         const int r = idx / w, c = idx - r * w;
         A[(long)(k0 + r) * n + k0 + c] = pn[r * LD + c];
     }
-    // the panel's interchanges, applied to every column outside it
+    for (int r = tid; r < rows; r += 256) perm[k0 + r] = ps[r];
+    __syncthreads();
+    apply_panel_swaps(A, n, k0, w, piv, tid, 256);
+    if (tid == 0 && info && infoAll[disk] == 0) infoAll[disk] = info;
+}
+
+// the w pivots of a factored panel, applied to every column outside it
+__device__ __forceinline__ void apply_panel_swaps(float *A, int n, int k0, int w, const int *piv, int tid, int nt) {
     for (int c = 0; c < w; ++c) {
         const int p = piv[c];
         if (p != c) {
             float *ra = A + (long)(k0 + c) * n, *rb = A + (long)(k0 + p) * n;
-            for (int j = tid; j < n - w; j += 256) {
+            for (int j = tid; j < n - w; j += nt) {
                 const int col = j < k0 ? j : j + w;
                 const float t = ra[col];
                 ra[col] = rb[col];
@@ -103,6 +114,167 @@ __global__ void __launch_bounds__(256) k_panel_leaf(float *Aall, int n, long str
         }
         __syncthreads();
     }
+}
+
+// The same panel factorisation with the panel in registers: thread t owns panel rows t and
+// t + 512 (panels of at most 1024 rows), all W columns.  Per column: block argmax (lowest row
+// index among equal magnitudes), the two rows exchanged through shared memory, and the rank-1
+// update of the owned rows from the pivot row (register FMAs).
+static constexpr int kPanelThreads = 512, kPanelRows = 2;
+
+template <int W>
+__global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(float *Aall, int n, long strideA, int k0, int w,
+                                                                int *permAll, int *infoAll) {
+    constexpr int NT = kPanelThreads, R = kPanelRows, NW = NT / 32;
+    __shared__ float xch[2][W];
+    __shared__ float rv[NW];
+    __shared__ int ri[NW];
+    __shared__ int piv[W];
+    __shared__ int ps[NT * R];                            // perm[k0 ..], swapped here, stored at the end
+    const int disk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *A = Aall + disk * strideA;
+    int *perm = permAll + (long)disk * n;
+    const int rows = n - k0;
+    for (int r = tid; r < rows; r += NT) ps[r] = perm[k0 + r];
+    float a[R][W];
+    const bool vec = (n & 3) == 0 && (k0 & 3) == 0 && w == W;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * NT;
+        const float *src = A + (long)(k0 + r) * n + k0;
+        if (vec) {
+#pragma unroll
+            for (int c = 0; c < W; c += 4) {
+                const float4 v = r < rows ? *reinterpret_cast<const float4 *>(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                a[i][c] = v.x;
+                a[i][c + 1] = v.y;
+                a[i][c + 2] = v.z;
+                a[i][c + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < W; ++c) a[i][c] = (r < rows && c < w) ? src[c] : 0.f;
+        }
+    }
+    int info = 0;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+        if (c >= w) break;
+        float best = -1.f;
+        int bi = 0x7fffffff;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * NT;
+            if (r >= c && r < rows) {
+                const float v = fabsf(a[i][c]);
+                if (v > best || (v == best && r < bi)) {
+                    best = v;
+                    bi = r;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            rv[warp] = best;
+            ri[warp] = bi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < NW ? rv[lane] : -1.f;
+            bi = lane < NW ? ri[lane] : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                piv[c] = bi;
+                if (bi != c) {
+                    const int t = ps[c];
+                    ps[c] = ps[bi];
+                    ps[bi] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int p = piv[c];
+        // rows c and p through shared memory: xch[0] = row c, xch[1] = row p (the new row c); row c
+        // (c < W <= NT) is thread c's first row, row p is row p / NT of thread p % NT
+        const int po = p % NT;
+        if (tid == c) {
+#pragma unroll
+            for (int cc = 0; cc < W; ++cc) xch[0][cc] = a[0][cc];
+        }
+        if (tid == po) {
+            if (p < NT) {
+#pragma unroll
+                for (int cc = 0; cc < W; ++cc) xch[1][cc] = a[0][cc];
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < W; ++cc) xch[1][cc] = a[R - 1][cc];
+            }
+        }
+        __syncthreads();
+        if (p != c) {
+            if (tid == c) {
+#pragma unroll
+                for (int cc = 0; cc < W; ++cc) a[0][cc] = xch[1][cc];
+            }
+            if (tid == po) {
+                if (p < NT) {
+#pragma unroll
+                    for (int cc = 0; cc < W; ++cc) a[0][cc] = xch[0][cc];
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < W; ++cc) a[R - 1][cc] = xch[0][cc];
+                }
+            }
+        }
+        const float d = xch[1][c];
+        if (d == 0.f && info == 0) info = k0 + c + 1;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = tid + i * NT;
+            if (r > c && r < rows) {
+                const float l = (d != 0.f) ? a[i][c] / d : 0.f;
+                a[i][c] = l;
+#pragma unroll
+                for (int cc = c + 1; cc < W; ++cc) a[i][cc] -= l * xch[1][cc];
+            }
+        }
+        __syncthreads();                                  // xch is rewritten by the next column
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * NT;
+        if (r < rows) {
+            float *dst = A + (long)(k0 + r) * n + k0;
+            if (vec) {
+#pragma unroll
+                for (int c = 0; c < W; c += 4)
+                    *reinterpret_cast<float4 *>(dst + c) = make_float4(a[i][c], a[i][c + 1], a[i][c + 2], a[i][c + 3]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (c < w) dst[c] = a[i][c];
+            }
+        }
+    }
+    for (int r = tid; r < rows; r += NT) perm[k0 + r] = ps[r];
+    __syncthreads();
+    apply_panel_swaps(A, n, k0, w, piv, tid, NT);
     if (tid == 0 && info && infoAll[disk] == 0) infoAll[disk] = info;
 }
 
@@ -203,7 +375,14 @@ struct RecLU {
     }
 
     void leaf(int k0, int w) {
-        const size_t smem = (size_t)(n - k0) * (W + 1) * sizeof(float);
+        if (n - k0 <= kPanelThreads * kPanelRows) {
+            switch (W) {
+                case 32: PDD_LAUNCH(k_panel_reg<32>, nd, kPanelThreads, 0, st, A, n, sA, k0, w, perm, info); return;
+                case 16: PDD_LAUNCH(k_panel_reg<16>, nd, kPanelThreads, 0, st, A, n, sA, k0, w, perm, info); return;
+                default: PDD_LAUNCH(k_panel_reg<8>, nd, kPanelThreads, 0, st, A, n, sA, k0, w, perm, info); return;
+            }
+        }
+        const size_t smem = (size_t)(n - k0) * ((W + 1) * sizeof(float) + sizeof(int));
         switch (W) {
 #define PDD_LEAF(WV)                                                                                      \
     case WV:                                                                                              \
@@ -267,7 +446,8 @@ void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int n
     PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     PDD_LAUNCH(k_iota_perm, cdiv((long)n * nd, 256), 256, 0, st, n, nd, perm, info);
     if (W != 8 && W != 16 && W != 32) fail(PDD_EINVAL, "panel width must be 8, 16 or 32");
-    if ((size_t)n * (W + 1) * sizeof(float) > 200 * 1024) fail(PDD_EINVAL, "disk grid too large for the panel width");
+    if ((size_t)n * ((W + 1) * sizeof(float) + sizeof(int)) > 200 * 1024)
+        fail(PDD_EINVAL, "disk grid too large for the panel width");
     RecLU r{A, n, strideA, perm, info, err.p, nd, W, st, tensor_min};
     r.lu(0, n);
     int h = 0;

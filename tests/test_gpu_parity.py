@@ -117,7 +117,7 @@ def test_floating_rows_varcoef_sampled(pdd, precision, factor):
         assert S.stats()["unconverged_disks"] == 0
 
 
-@pytest.mark.parametrize("leaf,tmin", [(32, 128), (16, 64), (8, 64), (16, 1000000)])
+@pytest.mark.parametrize("leaf,tmin", [(32, 128), (32, 32), (16, 64), (8, 32), (16, 1000000)])
 def test_recursive_lu_candidates(pdd, leaf, tmin):
     """Every factorisation the autotuner may pick gives the oracle's floating rows (varcoef, 6 disks)."""
     cfg = workloads.varcoef(paths=16)
