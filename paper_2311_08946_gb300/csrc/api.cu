@@ -6,6 +6,8 @@
 #include <cstring>
 #include <string>
 
+#include <vector>
+
 #include "handles.cuh"
 
 namespace pdd {
@@ -43,6 +45,17 @@ void ProblemHolder::set(const pdd_domain &dom, const pdd_operator &op, cudaStrea
         P.rbf_y = rbf_y.p;
         P.rbf_w = rbf_w.p;
         P.rbf_sigma = op.rbf_sigma;
+        std::vector<float> f32(3 * (size_t)op.n_rbf);
+        for (int q = 0; q < op.n_rbf; ++q) {
+            f32[q] = (float)op.rbf_x[q];
+            f32[op.n_rbf + q] = (float)op.rbf_y[q];
+            f32[2 * op.n_rbf + q] = (float)op.rbf_w[q];
+        }
+        rbf32.alloc(f32.size());
+        PDD_CUDA(cudaMemcpyAsync(rbf32.p, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        P.rbf32 = rbf32.p;
+        P.rbf_inv2s2 = (float)(1.0 / (2.0 * op.rbf_sigma * op.rbf_sigma));
     }
     if (op.g_kind == PDD_G_BOUNDARY_FOURIER) {
         if (op.n_gcoef <= 0 || !op.g_coef) fail(PDD_EINVAL, "g = boundary Fourier needs coefficients");

@@ -84,6 +84,8 @@ struct Problem {
     int n_gcoef;
     const double *g_coef;                  // device
     double perimeter;
+    const float *rbf32;                    // device: the RBF centres and weights as FP32, x[n] y[n] w[n]
+    float rbf_inv2s2;                      // 1 / (2 sigma^2) in FP32
 };
 
 #define PDD_PI 3.141592653589793
@@ -251,6 +253,19 @@ __device__ __forceinline__ void normals64(uint64_t seed, uint32_t knot, uint32_t
     xi1 = rr * s;
 }
 
+// FP32 sine and cosine for the mixed form: the argument is reduced to [-pi, pi]
+// (where the hardware approximations __sinf/__cosf/__sincosf keep an absolute
+// error near 2^-21) and the approximation is taken there
+__device__ __forceinline__ float reduce_2pi(float x) {
+    return x - 6.28318530717958647692f * rintf(x * 0.159154943091895335769f);
+}
+
+// sin(pi x) and cos(pi x): x - 2 round(x / 2) is exact, then as above
+__device__ __forceinline__ void fast_sincospi(float x, float &s, float &c) {
+    const float t = x - 2.0f * rintf(0.5f * x);
+    __sincosf(3.14159265358979323846f * t, &s, &c);
+}
+
 // 23-bit uniforms in (0, 1) for the mixed-precision form, built from the
 // mantissa bits (no conversion instruction): [1.m] - 1 = m 2^-23 with
 // m = w >> 9 (exact), plus half a step; u follows the leading bits of w like
@@ -264,9 +279,9 @@ __device__ __forceinline__ void normals32(uint64_t seed, uint32_t knot, uint32_t
     U4 w = philox10(step, path, 0u, 0u, (uint32_t)(seed & 0xffffffffu), knot);
     const float u1 = uniform23(w.x);
     const float u2 = uniform23(w.z);
-    const float rr = sqrtf(-2.0f * logf(u1));
+    const float rr = sqrtf(-2.0f * __logf(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    fast_sincospi(2.0f * u2, s, c);
     xi0 = rr * c;
     xi1 = rr * s;
 }

@@ -599,10 +599,11 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
                                                                double *Xall, const int *conv,
                                                                unsigned long long *dmaxb, unsigned long long *xmaxb,
                                                                float2 *Dall, int dmode) {
-    constexpr int NT = kRlThreads, TB = kRlTB, OUT = (TB * CG + NT - 1) / NT;
+    constexpr int NT = kRlThreads, TB = kRlTB;
+    static_assert(CG / 4 <= NT / 32, "one warp per column quad of the diagonal step");
     extern __shared__ __align__(16) float rsm[];
     float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
-    float *Ds = rsm + (size_t)n * CG;                  // TB x TB diagonal-block inverse
+    float *Ds = rsm + (size_t)n * CG;                  // TB x (TB + 1) diagonal-block inverse (padded rows)
     const int disk = blockIdx.x, tid = threadIdx.x;
     if (conv[disk]) return;
     const int c0 = blockIdx.y * CG, cg = min(CG, nrhs - c0);
@@ -627,29 +628,29 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
             // diagonal step
             float4 lv[TB / 4];
             if (full) rl_fetch(lv, LU, n, ra + tid, rb, i0);
+            // the panel's rows X_b = inv(T_bb) B_b: warp q takes columns 4q .. 4q+3, lane i the
+            // panel row i; the row of the inverse comes from global memory into registers and the
+            // panel's right-hand sides are read as broadcasts
+            const int warp = tid >> 5, lane = tid & 31;
+            const bool dtask = warp < CG / 4 && lane < tb;
             const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
-            for (int e = tid; e < TB * TB; e += NT) Ds[e] = Dt[e];
+            for (int e = tid; e < TB * TB; e += NT) Ds[(e >> 5) * (TB + 1) + (e & 31)] = Dt[e];
             __syncthreads();
-            // the panel's rows: X_b = inv(T_bb) B_b
-            float o[OUT];
-#pragma unroll
-            for (int q = 0; q < OUT; ++q) {
-                const int e = tid + q * NT;
-                float v = 0.f;
-                if (e < tb * CG) {
-                    const int r = e / CG, c = e - r * CG;
-                    const float *dr = Ds + r * TB;
-                    const float *bc = Bs + (size_t)i0 * CG + c;
-                    for (int k = 0; k < tb; ++k) v = fmaf(dr[k], bc[(size_t)k * CG], v);
+            float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (dtask) {
+                const float *bc = Bs + (size_t)i0 * CG + 4 * warp;
+                const float *dr = Ds + lane * (TB + 1);
+                for (int k = 0; k < tb; ++k) {
+                    const float d = dr[k];
+                    const float4 b = *reinterpret_cast<const float4 *>(bc + (size_t)k * CG);
+                    xo.x = fmaf(d, b.x, xo.x);
+                    xo.y = fmaf(d, b.y, xo.y);
+                    xo.z = fmaf(d, b.z, xo.z);
+                    xo.w = fmaf(d, b.w, xo.w);
                 }
-                o[q] = v;
             }
             __syncthreads();
-#pragma unroll
-            for (int q = 0; q < OUT; ++q) {
-                const int e = tid + q * NT;
-                if (e < tb * CG) Bs[(size_t)i0 * CG + e] = o[q];
-            }
+            if (dtask) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * warp) = xo;
             __syncthreads();
             // rows still to solve: B_r -= T_rb X_b; the next row's entries load during this row's FMAs
             const float *xs = Bs + (size_t)i0 * CG;
@@ -760,7 +761,7 @@ static int rl_width(int n, int nrhs, int &groups) {
                 break;
             }
         if (!W) continue;
-        const size_t sm = ((size_t)n * W + (size_t)kRlTB * kRlTB) * sizeof(float);
+        const size_t sm = ((size_t)n * W + (size_t)kRlTB * (kRlTB + 1)) * sizeof(float);
         if (sm <= kRlSmemMax) {
             groups = (nrhs + W - 1) / W;
             return W;
@@ -789,7 +790,7 @@ struct RlArgs {
 
 template <int CG>
 static void launch_rl_cg(const RlArgs &a, cudaStream_t st) {
-    const size_t sm = ((size_t)a.n * CG + (size_t)kRlTB * kRlTB) * sizeof(float);
+    const size_t sm = ((size_t)a.n * CG + (size_t)kRlTB * (kRlTB + 1)) * sizeof(float);
     PDD_CUDA(cudaFuncSetAttribute(k_lu_solve_rl<CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     PDD_LAUNCH(k_lu_solve_rl<CG>, dim3(a.nd, a.groups), kRlThreads, sm, st, a.LU, a.n, a.sA, a.perm, a.Dinv, a.R,
                a.nrhs, a.sR, a.X, a.conv, a.dmb, a.xmb, a.D, a.dmode);

@@ -54,6 +54,7 @@ namespace pdd {
 struct ProblemHolder {
     Problem P{};
     DevBuf<double> rbf_x, rbf_y, rbf_w, g_coef;
+    DevBuf<float> rbf32;
     void set(const pdd_domain &dom, const pdd_operator &op, cudaStream_t st);
 };
 

@@ -143,8 +143,8 @@ struct Num<float> {
     }
     __device__ static void drift(const Problem &P, float x, float y, float &bx, float &by) {
         if (P.b_kind == PDD_B_SINX_COSY) {
-            bx = sinf(x);
-            by = cosf(y);
+            bx = __sinf(reduce_2pi(x));
+            by = __cosf(reduce_2pi(y));
         } else {
             bx = 0.f;
             by = 0.f;
@@ -157,10 +157,11 @@ __device__ __forceinline__ float killing32(const Problem &P, float x, float y) {
     if (P.c_kind == PDD_C_QUADRATIC) return -(1.0f + x * x + y * y);
     if (P.c_kind == PDD_C_RBF) {
         float s = 0.f;
-        const float inv = (float)(1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma));
-        for (int q = 0; q < P.n_rbf; ++q) {
-            float dx = x - (float)P.rbf_x[q], dy = y - (float)P.rbf_y[q];
-            s += (float)P.rbf_w[q] * expf(-(dx * dx + dy * dy) * inv);
+        const int nr = P.n_rbf;
+        const float *cx = P.rbf32, *cy = P.rbf32 + nr, *cw = P.rbf32 + 2 * nr;
+        for (int q = 0; q < nr; ++q) {
+            const float dx = x - cx[q], dy = y - cy[q];
+            s += cw[q] * __expf(-(dx * dx + dy * dy) * P.rbf_inv2s2);
         }
         return s < 0.f ? s : 0.f;
     }
@@ -172,8 +173,8 @@ __device__ __forceinline__ float source32_given(const Problem &P, float x, float
     if (P.f_kind == PDD_F_ONE) return 1.0f;
     if (P.f_kind == PDD_F_MANUFACTURED) {
         float spx, cpx, spy, cpy;
-        sincospif(x, &spx, &cpx);
-        sincospif(y, &spy, &cpy);
+        fast_sincospi(x, spx, cpx);
+        fast_sincospi(y, spy, cpy);
         const float pi = 3.14159265358979f;
         const float u = spx * cpy, ux = pi * cpx * cpy, uy = -pi * spx * spy;
         return -(-pi * pi * u + bx * ux + by * uy + cv * u);

@@ -9,8 +9,8 @@
 //
 // One CTA (256 threads) computes a 128 x 128 tile of C for one matrix of the
 // batch:
-//   * the K loop runs in chunks of 32; each chunk is loaded with 16-byte
-//     loads into registers while the tensor cores work on the previous one,
+//   * the K loop runs in chunks of 16; each chunk is loaded with 16-byte
+//     loads into registers two chunks ahead of the tensor cores,
 //     split, and stored into shared memory in the canonical no-swizzle
 //     K-major layout (8-row x 16-byte core matrices; LBO = K-direction core
 //     stride, SBO = 8-row-group stride), hi and lo copies, double-buffered;
@@ -20,16 +20,18 @@
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32(w mod 4).. = rows, and one half of the columns) and subtracts
 //     it from C.
+//   * 64 KB of shared memory and 128 TMEM columns per CTA: two CTAs share an
+//     SM, so one's prologue and epilogue overlap the other's MMAs.
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // waits once more (bounded) for its own MMAs, frees its TMEM and returns.
 #include "handles.cuh"
 
 namespace pdd {
 
-static constexpr int kTM = 128, kTN = 128, kTK = 32;
-static constexpr int kOpBytes = kTM * kTK * 4;          // one operand copy: 16 KB
+static constexpr int kTM = 128, kTN = 128, kTK = 16;
+static constexpr int kOpBytes = kTM * kTK * 4;          // one operand copy: 8 KB
 static constexpr int kStageBytes = 4 * kOpBytes;        // A_hi, A_lo, B_hi, B_lo
-static constexpr int kTcSmem = 2 * kStageBytes;        // two stages
+static constexpr int kTcSmem = 2 * kStageBytes;        // two stages (64 KB: two CTAs per SM)
 static constexpr int kTmemCols = 128;                   // one 128 x 128 FP32 accumulator
 static constexpr long long kWaitLimit = 1LL << 22;   // polls before a wait is declared failed
 
@@ -101,28 +103,31 @@ __device__ __forceinline__ int canon_off(int r, int k, int rows) {
 
 static constexpr int kTcThreads = 256;
 
-// One K chunk of the two operands in registers (vector path): thread (warp w, lane l) holds
-//   A: 4 float4 = rows 8 ((i >> 1) 8 + w) + (l & 7), k = 4 ((l >> 3) + 4 (i & 1)) .. + 3
-//   B: 4 float4 = row k = (l >> 3) + 4 w, columns 4 ((l & 7) + 8 i) .. + 3
+// One K chunk (16) of the two operands in registers (vector path): thread (warp w, lane l) holds
+//   A: 2 float4 = rows 8 (8 i + w) + (l & 7), k = 4 (l >> 3) .. + 3
+//   B: 2 float4 = row k = (l >> 3) + 4 (w >> 1), columns 4 ((l & 7) + 8 (2 (w & 1) + i)) .. + 3
 // so that a warp's global loads cover whole 32-byte sectors and its shared-memory stores
 // into the canonical layout hit 32 different banks.
 struct Chunk {
-    float4 a[4], b[4];
+    float4 a[2], b[2];
 };
+
+__device__ __forceinline__ int chunk_a_row(int i, int w, int l) { return 8 * (8 * i + w) + (l & 7); }
+__device__ __forceinline__ int chunk_a_k(int l) { return 4 * (l >> 3); }
+__device__ __forceinline__ int chunk_b_k(int w, int l) { return (l >> 3) + 4 * (w >> 1); }
+__device__ __forceinline__ int chunk_b_j(int i, int w, int l) { return 4 * ((l & 7) + 8 * (2 * (w & 1) + i)); }
 
 __device__ __forceinline__ void load_chunk_vec(Chunk &c, const float *A, int lda, const float *B, int ldb, int M,
                                                int N, int K, int tm, int tn, int k0, int w, int l) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = 8 * ((i >> 1) * 8 + w) + (l & 7), k = 4 * ((l >> 3) + 4 * (i & 1));
-        const int gr = tm + r, gk = k0 + k;
+    for (int i = 0; i < 2; ++i) {
+        const int gr = tm + chunk_a_row(i, w, l), gk = k0 + chunk_a_k(l);
         c.a[i] = (gr < M && gk < K) ? __ldg(reinterpret_cast<const float4 *>(A + (long)gr * lda + gk))
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int k = (l >> 3) + 4 * w, j = 4 * ((l & 7) + 8 * i);
-        const int gk = k0 + k, gj = tn + j;
+    for (int i = 0; i < 2; ++i) {
+        const int gk = k0 + chunk_b_k(w, l), gj = tn + chunk_b_j(i, w, l);
         c.b[i] = (gk < K && gj < N) ? __ldg(reinterpret_cast<const float4 *>(B + (long)gk * ldb + gj))
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -143,17 +148,16 @@ __device__ __forceinline__ float pick4(float4 v, int e) {
 __device__ __forceinline__ void store_chunk_vec(const Chunk &c, float *Ahi, float *Alo, float *Bhi, float *Blo, int w,
                                                 int l) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = 8 * ((i >> 1) * 8 + w) + (l & 7), k = 4 * ((l >> 3) + 4 * (i & 1));
-        const int off = canon_off(r, k, kTM) >> 2;
+    for (int i = 0; i < 2; ++i) {
+        const int off = canon_off(chunk_a_row(i, w, l), chunk_a_k(l), kTM) >> 2;
         const float4 h = split_hi(c.a[i]);
         *reinterpret_cast<float4 *>(Ahi + off) = h;
         *reinterpret_cast<float4 *>(Alo + off) = split_lo(c.a[i], h);
     }
     const int rot = (l >> 1) & 3;            // element order rotated per lane: conflict-free stores
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int k = (l >> 3) + 4 * w, j0 = 4 * ((l & 7) + 8 * i);
+    for (int i = 0; i < 2; ++i) {
+        const int k = chunk_b_k(w, l), j0 = chunk_b_j(i, w, l);
         const float4 h = split_hi(c.b[i]);
         const float4 lo = split_lo(c.b[i], h);
 #pragma unroll
@@ -171,7 +175,7 @@ __device__ __forceinline__ void stage_scalar(const float *A, int lda, const floa
                                              int tm, int tn, int k0, float *Ahi, float *Alo, float *Bhi, float *Blo,
                                              int tid) {
     for (int e = tid; e < kTM * kTK; e += kTcThreads) {
-        const int r = e >> 5, k = e & 31;
+        const int r = e / kTK, k = e % kTK;
         const int gr = tm + r, gk = k0 + k;
         const float v = (gr < M && gk < K) ? A[(long)gr * lda + gk] : 0.f;
         const float hi = tf32_round(v);
@@ -233,7 +237,7 @@ __device__ __forceinline__ void epilogue(uint32_t tmem, float *C, int ldc, int M
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_sub_tf32x3(int M, int N, int K, const float *A, long sA,
+__global__ void __launch_bounds__(kTcThreads, 2) k_gemm_sub_tf32x3(int M, int N, int K, const float *A, long sA,
                                                                    int lda, const float *B, long sB, int ldb,
                                                                    float *C, long sC, int ldc, int *err) {
     extern __shared__ __align__(1024) unsigned char tsm[];
@@ -267,8 +271,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_sub_tf32x3(int M, int N,
     const uint32_t lbo = kTM * 16;             // K-direction core-matrix stride (rows = 128)
     const uint32_t sbo = 128;                  // 8-row-group stride
     int issued = -1;                           // last chunk whose MMAs were committed (uniform)
-    Chunk cur;
+    Chunk cur, nxt;                            // chunks kc and kc + 1 in flight
     if (VEC && nch > 0) load_chunk_vec(cur, A, lda, B, ldb, M, N, K, tm, tn, 0, warp, lane);
+    if (VEC && nch > 1) load_chunk_vec(nxt, A, lda, B, ldb, M, N, K, tm, tn, kTK, warp, lane);
     for (int kc = 0; kc < nch; ++kc) {
         const int buf = kc & 1;
         unsigned char *st = tsm + buf * kStageBytes;
@@ -298,8 +303,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_sub_tf32x3(int M, int N,
             mma_commit(smem_u32(&mbar[buf]));
         }
         issued = kc;
-        // the next chunk's loads are in flight while the tensor cores work on this one
-        if (VEC && kc + 1 < nch) load_chunk_vec(cur, A, lda, B, ldb, M, N, K, tm, tn, (kc + 1) * kTK, warp, lane);
+        // two chunks' loads are in flight while the tensor cores work on this one
+        if (VEC) {
+            cur = nxt;
+            if (kc + 2 < nch) load_chunk_vec(nxt, A, lda, B, ldb, M, N, K, tm, tn, (kc + 2) * kTK, warp, lane);
+        }
     }
     // all MMAs of this tile are complete once the last commit has landed
     if (issued >= 0 && tid == 0) {
