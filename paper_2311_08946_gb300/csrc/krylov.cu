@@ -5,10 +5,10 @@
 // Layout: the Krylov basis V is (m+1) x n row-major (each basis vector
 // contiguous); dot products are block partial sums reduced in a fixed order
 // (deterministic).  Orthogonalisation is classical Gram-Schmidt applied
-// twice (CGS2).  The Hessenberg matrix, Givens rotations and the residual
-// estimate live on the device; after convergence every kernel of the cycle
-// sees the stop flag and returns at once, so the host synchronises only once
-// per restart cycle to read the true residual.
+// twice (CGS2).  The m Arnoldi iterations of a restart cycle run in one
+// cooperative kernel (k_arnoldi_fused); the Hessenberg matrix, Givens
+// rotations and the residual estimate live on the device, and the host
+// synchronises once per restart cycle to read the true residual.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -96,29 +96,6 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int n, int nv, const doubl
     if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
-// w -= sum_t V[t] h[t] with h = hsum; column j of H gets h (+= when add)
-__global__ void __launch_bounds__(kDotBlock) k_orth(int n, int nv, const double *V, double *w,
-                                                    const double *hsum, double *Hcol, int add, const GState *gs) {
-    if (gs && gs->stop) return;
-    __shared__ double h[kMaxDots];
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) h[t] = hsum[t];
-    __syncthreads();
-    if (blockIdx.x == 0)
-        for (int t = threadIdx.x; t < nv; t += blockDim.x) Hcol[t] = add ? Hcol[t] + h[t] : h[t];
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        double s = w[r];
-        for (int t0 = 0; t0 < nv; t0 += 16) {            // sixteen independent loads in flight
-            double v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = (t0 + q < nv) ? V[(long)(t0 + q) * n + r] : 0.0;
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-                if (t0 + q < nv) s -= v[q] * h[t0 + q];
-        }
-        w[r] = s;
-    }
-}
-
 // v = w / |w| with |w|^2 = hsum[0]; Hsub = |w|
 __global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w, double *v, const double *hsum,
                                                          double *Hsub, const GState *gs) {
@@ -127,46 +104,6 @@ __global__ void __launch_bounds__(kDotBlock) k_normalize(int n, const double *w,
     if (blockIdx.x == 0 && threadIdx.x == 0 && Hsub) *Hsub = nrm;
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) v[r] = w[r] * inv;
-}
-
-// apply the previous rotations to column j, make a new one, update g and the stop flag; one
-// warp stages the column and the rotations in shared memory, lane 0 runs the recurrence
-__global__ void k_givens(double *H, int ldh, double *cs, double *sn, double *g, int j, double rtol,
-                         int max_iters, GState *gs) {
-    if (gs->stop) return;
-    __shared__ double hs[kMaxDots], cc[kMaxDots], ss[kMaxDots];
-    double *hc = H + (long)j * ldh;                  // column j stored contiguously (ldh = m+1)
-    for (int i = threadIdx.x; i <= j + 1; i += 32) hs[i] = hc[i];
-    for (int i = threadIdx.x; i < j; i += 32) {
-        cc[i] = cs[i];
-        ss[i] = sn[i];
-    }
-    __syncwarp();
-    if (threadIdx.x == 0) {
-        double hi = hs[0];
-        for (int i = 0; i < j; ++i) {
-            const double hn = hs[i + 1];
-            const double t = cc[i] * hi + ss[i] * hn;
-            hi = -ss[i] * hi + cc[i] * hn;
-            hs[i] = t;
-        }
-        // hi is the rotated entry j
-        const double a = hi, b = hs[j + 1];
-        const double den = hypot(a, b);
-        const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-        cs[j] = c;
-        sn[j] = s;
-        hs[j] = den;
-        hs[j + 1] = 0.0;
-        g[j + 1] = -s * g[j];
-        g[j] = c * g[j];
-        gs->iters += 1;
-        gs->k_used = j + 1;
-        gs->res = fabs(g[j + 1]);
-        if (gs->res <= rtol * gs->bnorm || gs->iters >= max_iters || b == 0.0) gs->stop = 1;
-    }
-    __syncwarp();
-    for (int i = threadIdx.x; i <= j + 1; i += 32) hc[i] = hs[i];
 }
 
 // y = H^-1 g (upper triangular k x k), single thread; then stop is cleared for the next cycle
@@ -210,16 +147,268 @@ void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const
     PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, x, y, (const GState *)nullptr);
 }
 
-// The m Arnoldi iterations of a restart cycle (about 8 kernels each) are
-// captured once into a CUDA graph and replayed once per cycle; the stop flag
-// on the device turns the remaining kernels of a converged cycle into no-ops.
+// ---------------------------------------------------------------------------
+// One restart cycle's Arnoldi iterations in a single cooperative launch.
+// Block b owns rows [b per, (b+1) per): it computes w = C v_j on them, their
+// partial dot products with the basis, their part of the CGS2 updates and of
+// |w|; partial sums meet in global memory and are added in block order after
+// a grid barrier (deterministic).  Block 0 keeps the Hessenberg column, the
+// Givens rotations and g in shared memory and writes the stop flag that every
+// block reads after the iteration's last barrier.  Four grid barriers per
+// iteration; each is a bounded spin that records an error and returns.
+// ---------------------------------------------------------------------------
+static constexpr int kFusedThreads = 512;
+static constexpr long long kBarrierLimit = 1LL << 20;   // polls (an L2 read and >= 64 ns each) before giving up
+
+struct FusedArnoldi {
+    int n, m;
+    const int *rowptr, *col;
+    const double *val;
+    double *V, *w, *part;        // part: 3 x kMaxDots x gridDim.x partial sums
+    double *H, *cs, *sn, *g;     // H column-major (ldh = m + 1)
+    GState *gs;
+    unsigned *bar;               // [0] arrivals, [1] generation
+    int *err;
+    double rtol;
+    int max_iters;
+};
+
+__device__ __forceinline__ bool grid_barrier(const FusedArnoldi &F) {
+    __shared__ int s_bad;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = F.bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(F.bar, 1u) == gridDim.x - 1) {
+            atomicExch(F.bar, 0u);
+            __threadfence();
+            atomicAdd(F.bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g0) {
+                if (++it > kBarrierLimit) {
+                    atomicExch(F.err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_bad = *(volatile int *)F.err;
+    }
+    __syncthreads();
+    return s_bad == 0;
+}
+
+__device__ __forceinline__ double warp_sum(double s) {
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F) {
+    constexpr int NW = kFusedThreads / 32;
+    __shared__ double h[kMaxDots], hcol[kMaxDots + 1], cs[kMaxDots], sn[kMaxDots], gv[kMaxDots + 1];
+    __shared__ double red[NW];
+    __shared__ int s_stop;
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n = F.n, m = F.m, ldh = m + 1;
+    const int per = (n + G - 1) / G, r0 = min(n, b * per), r1 = min(n, r0 + per);
+    if (b == 0)
+        for (int i = tid; i <= m; i += kFusedThreads) gv[i] = F.g[i];
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) s_stop = __ldcg(&F.gs->stop);
+        __syncthreads();
+        if (s_stop) break;
+        // w = C v_j on this block's rows, 8 lanes per row; v_j was written by every block
+        // (every lane of a warp runs the same number of slots: the shuffles below use the full mask)
+        const double *vj = F.V + (long)j * n;
+        for (int base = r0; base < r1; base += kFusedThreads / 8) {
+            const int row = base + (tid >> 3), l = tid & 7;
+            double s = 0.0;
+            if (row < r1)
+                for (int k = F.rowptr[row] + l; k < F.rowptr[row + 1]; k += 8) s += F.val[k] * __ldcg(vj + F.col[k]);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            if (row < r1 && l == 0) F.w[row] = s;
+        }
+        __syncthreads();
+        // two passes of classical Gram-Schmidt against v_0 .. v_j
+        for (int pass = 0; pass < 2; ++pass) {
+            double *pp = F.part + (long)pass * kMaxDots * G;
+            for (int t = warp; t <= j; t += NW) {
+                const double *vt = F.V + (long)t * n;
+                double s = 0.0;
+                for (int r = r0 + lane; r < r1; r += 32) s += vt[r] * F.w[r];
+                s = warp_sum(s);
+                if (lane == 0) pp[(long)t * G + b] = s;
+            }
+            if (!grid_barrier(F)) return;
+            for (int t = warp; t <= j; t += NW) {
+                double s = 0.0;
+                for (int q = lane; q < G; q += 32) s += __ldcg(pp + (long)t * G + q);
+                s = warp_sum(s);
+                if (lane == 0) h[t] = s;
+            }
+            __syncthreads();
+            if (b == 0)
+                for (int t = tid; t <= j; t += kFusedThreads) hcol[t] = pass ? hcol[t] + h[t] : h[t];
+            for (int r = r0 + tid; r < r1; r += kFusedThreads) {
+                double s = F.w[r];
+                for (int t = 0; t <= j; ++t) s -= F.V[(long)t * n + r] * h[t];
+                F.w[r] = s;
+            }
+            __syncthreads();
+        }
+        // |w|
+        {
+            double s = 0.0;
+            for (int r = r0 + tid; r < r1; r += kFusedThreads) s += F.w[r] * F.w[r];
+            s = warp_sum(s);
+            if (lane == 0) red[warp] = s;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int q = 0; q < NW; ++q) t += red[q];
+                F.part[2L * kMaxDots * G + b] = t;
+            }
+        }
+        if (!grid_barrier(F)) return;
+        if (warp == 0) {
+            const double s = warp_sum([&] {
+                double a = 0.0;
+                for (int q = lane; q < G; q += 32) a += __ldcg(F.part + 2L * kMaxDots * G + q);
+                return a;
+            }());
+            if (lane == 0) red[0] = s;
+        }
+        __syncthreads();
+        const double nrm = sqrt(red[0]);
+        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        double *vn = F.V + (long)(j + 1) * n;
+        for (int r = r0 + tid; r < r1; r += kFusedThreads) vn[r] = F.w[r] * inv;
+        if (b == 0 && tid == 0) {
+            // Givens: the previous rotations on column j, a new one, g and the stop flag
+            hcol[j + 1] = nrm;
+            double hi = hcol[0];
+            for (int i = 0; i < j; ++i) {
+                const double hn = hcol[i + 1];
+                const double t = cs[i] * hi + sn[i] * hn;
+                hi = -sn[i] * hi + cs[i] * hn;
+                hcol[i] = t;
+            }
+            const double a = hi, bb = hcol[j + 1];
+            const double den = hypot(a, bb);
+            const double c = den > 0.0 ? a / den : 1.0, sv = den > 0.0 ? bb / den : 0.0;
+            cs[j] = c;
+            sn[j] = sv;
+            hcol[j] = den;
+            hcol[j + 1] = 0.0;
+            gv[j + 1] = -sv * gv[j];
+            gv[j] = c * gv[j];
+            GState *gs = F.gs;
+            gs->iters += 1;
+            gs->k_used = j + 1;
+            gs->res = fabs(gv[j + 1]);
+            if (gs->res <= F.rtol * gs->bnorm || gs->iters >= F.max_iters || bb == 0.0) gs->stop = 1;
+        }
+        if (b == 0) {
+            __syncthreads();
+            double *Hc = F.H + (long)j * ldh;
+            for (int i = tid; i <= j + 1; i += kFusedThreads) Hc[i] = hcol[i];
+            for (int i = tid; i <= j + 1; i += kFusedThreads) F.g[i] = gv[i];
+        }
+        if (!grid_barrier(F)) return;
+    }
+}
+
+// buffers of one GMRES(m) solve; gmres_csr allocates them, the allocation-free entry point carves
+// them from its fixed array
+struct GmresBufs {
+    double *V, *w, *partial, *hsum, *H, *cs, *sn, *g, *y, *fpart;
+    unsigned *cnt, *bar;
+    GState *gs;
+    int *err;
+};
+
+static int fused_grid(int n) {
+    static int per_sm = 0, sms = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!per_sm) {
+        int dev = 0;
+        PDD_CUDA(cudaGetDevice(&dev));
+        PDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_fused, kFusedThreads, 0));
+        if (per_sm < 1) fail(PDD_ECUDA, "the fused Arnoldi kernel does not fit on an SM");
+    }
+    return std::max(1, std::min(sms, cdiv(n, 64)));     // one block per SM: co-resident, cheap barriers
+}
+
+static SolveResult gmres_run(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
+                             const pdd_solve_opts &o, const GmresBufs &B, int m, int G, cudaStream_t st) {
+    PDD_CUDA(cudaMemsetAsync(B.gs, 0, sizeof(GState), st));
+    PDD_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(unsigned) * kDotGroups, st));
+    PDD_CUDA(cudaMemsetAsync(B.bar, 0, sizeof(unsigned) * 2, st));
+    PDD_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), st));
+    PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
+    PDD_CUDA(cudaMemsetAsync(B.H, 0, sizeof(double) * (m + 1) * m, st));
+    const int vb = std::min(cdiv(n, 256), 2048);
+    const int max_iters = std::max(1, o.max_iters);
+    const int Gf = fused_grid(n);
+    FusedArnoldi F{n, m, rowptr, col, val, B.V, B.w, B.fpart, B.H, B.cs, B.sn, B.g, B.gs, B.bar, B.err, o.rtol,
+                   max_iters};
+    SolveResult res;
+    for (int cycle = 0;; ++cycle) {
+        // r = b - C u  (u = 0 on the first cycle)
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, B.w, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, B.w);
+        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, B.w, B.w, B.partial, B.hsum, B.cnt,
+                   (const GState *)nullptr);
+        PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, B.gs, B.hsum, B.g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
+        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, B.w, B.V, B.hsum, (double *)nullptr, B.gs);
+        void *args[] = {&F};
+        PDD_CUDA(cudaLaunchCooperativeKernel((const void *)k_arnoldi_fused, dim3(Gf), dim3(kFusedThreads), args, 0,
+                                             st));
+        count_launch();
+        PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, B.H, m + 1, B.g, B.y, B.gs);
+        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, B.V, B.y, B.gs, u);
+        // true residual
+        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, B.w, (const GState *)nullptr);
+        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, B.w);
+        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, B.w, B.w, B.partial, B.hsum, B.cnt,
+                   (const GState *)nullptr);
+        GState hg{};
+        double rs = 0.0;
+        int herr = 0;
+        PDD_CUDA(cudaMemcpyAsync(&rs, B.hsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaMemcpyAsync(&hg, B.gs, sizeof(GState), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        if (herr) fail(PDD_ECUDA, "GMRES grid barrier timed out");
+        const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
+        res.iters = hg.iters;
+        res.rel = rel;
+        if (hg.bnorm == 0.0 || rel <= o.rtol) {
+            res.converged = 1;
+            break;
+        }
+        if (hg.iters >= max_iters) break;
+    }
+    return res;
+}
+
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
-                      const pdd_solve_opts &o, cudaStream_t st_in) {
+                      const pdd_solve_opts &o, cudaStream_t st) {
     const int m = std::max(1, std::min(256, o.restart));
     const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));
-    DevBuf<double> V, w, partial, hsum, H, cs, sn, g, y;
-    DevBuf<unsigned> cnt;
+    const int Gf = fused_grid(n);
+    DevBuf<double> V, w, partial, hsum, H, cs, sn, g, y, fpart;
+    DevBuf<unsigned> cnt, bar;
     DevBuf<GState> gs;
+    DevBuf<int> err;
     V.alloc((size_t)(m + 1) * n);
     w.alloc(n);
     partial.alloc((size_t)(m + 1) * G);
@@ -231,99 +420,11 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
     g.alloc(m + 1);
     y.alloc(m);
     gs.alloc(1);
-    // graph capture needs a capturable stream: the legacy default stream is replaced by a private one
-    cudaStream_t st = st_in;
-    bool own = false;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    if (st_in == 0 || st_in == cudaStreamLegacy) {
-        PDD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        PDD_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-        PDD_CUDA(cudaEventRecord(ev_in, st_in));
-        PDD_CUDA(cudaStreamWaitEvent(st, ev_in, 0));
-        own = true;
-    }
-    PDD_CUDA(cudaMemsetAsync(gs.p, 0, sizeof(GState), st));
-    PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned) * kDotGroups, st));
-    PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
-    PDD_CUDA(cudaMemsetAsync(H.p, 0, sizeof(double) * (m + 1) * m, st));
-    const int vb = std::min(cdiv(n, 256), 2048);
-    SolveResult res;
-    const int max_iters = std::max(1, o.max_iters);
-    cudaGraphExec_t exec = nullptr;
-    int per_cycle = 0;
-    try {
-        for (int cycle = 0;; ++cycle) {
-            // r = b - C u  (u = 0 on the first cycle)
-            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
-            PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
-            PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs.p, hsum.p, g.p, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
-            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p, hsum.p, (double *)nullptr, gs.p);
-            if (!exec) {
-                const int64_t before = pdd_launch_count();
-                cudaGraph_t graph;
-                PDD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                for (int j = 0; j < m; ++j) {
-                    double *vj = V.p + (long)j * n;
-                    double *Hc = H.p + (long)j * (m + 1);
-                    PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w.p, gs.p);
-                    for (int pass = 0; pass < 2; ++pass) {
-                        PDD_LAUNCH(k_dots, dim3(G, cdiv(j + 1, kDotVec)), kDotThreads, 0, st, n, j + 1, V.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
-                        PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V.p, w.p, hsum.p, Hc, pass, gs.p);
-                    }
-                    PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, gs.p);
-                    PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w.p, V.p + (long)(j + 1) * n, hsum.p, Hc + j + 1,
-                               gs.p);
-                    PDD_LAUNCH(k_givens, 1, 32, 0, st, H.p, m + 1, cs.p, sn.p, g.p, j, o.rtol, max_iters, gs.p);
-                }
-                PDD_CUDA(cudaStreamEndCapture(st, &graph));
-                PDD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-                cudaGraphDestroy(graph);
-                per_cycle = (int)(pdd_launch_count() - before);
-                count_launch(-per_cycle);          // captured, not run: counted when the graph runs
-            }
-            PDD_CUDA(cudaGraphLaunch(exec, st));
-            count_launch(per_cycle);
-            PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H.p, m + 1, g.p, y.p, gs.p);
-            PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V.p, y.p, gs.p, u);
-            // true residual
-            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w.p, (const GState *)nullptr);
-            PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w.p);
-            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w.p, w.p, partial.p, hsum.p, cnt.p, (const GState *)nullptr);
-            GState hg{};
-            double rs = 0.0;
-            PDD_CUDA(cudaMemcpyAsync(&rs, hsum.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-            PDD_CUDA(cudaMemcpyAsync(&hg, gs.p, sizeof(GState), cudaMemcpyDeviceToHost, st));
-            PDD_CUDA(cudaStreamSynchronize(st));
-            const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
-            res.iters = hg.iters;
-            res.rel = rel;
-            if (hg.bnorm == 0.0 || rel <= o.rtol) {
-                res.converged = 1;
-                break;
-            }
-            if (hg.iters >= max_iters) break;
-        }
-    } catch (...) {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (own) {
-            cudaStreamSynchronize(st);
-            cudaStreamDestroy(st);
-            cudaEventDestroy(ev_in);
-        }
-        throw;
-    }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (own) {
-        PDD_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
-        PDD_CUDA(cudaEventRecord(ev_out, st));
-        PDD_CUDA(cudaStreamWaitEvent(st_in, ev_out, 0));
-        cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
-        cudaEventDestroy(ev_in);
-        cudaEventDestroy(ev_out);
-    }
-    return res;
+    fpart.alloc((size_t)3 * kMaxDots * Gf);
+    bar.alloc(2);
+    err.alloc(1);
+    const GmresBufs B{V.p, w.p, partial.p, hsum.p, H.p, cs.p, sn.p, g.p, y.p, fpart.p, cnt.p, bar.p, gs.p, err.p};
+    return gmres_run(n, rowptr, col, val, b, u, o, B, m, G, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,10 +520,10 @@ static void *noalloc_scratch(int dev) {
 }
 
 struct NoAllocLayout {
-    size_t V, w, partial, hsum, cnt, H, cs, sn, g, y, gs, total;
+    size_t V, w, partial, hsum, cnt, H, cs, sn, g, y, gs, fpart, bar, err, total;
 };
 
-static NoAllocLayout noalloc_layout(int n, int m, int G) {
+static NoAllocLayout noalloc_layout(int n, int m, int G, int Gf) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     NoAllocLayout L{};
     size_t off = 0;
@@ -437,6 +538,9 @@ static NoAllocLayout noalloc_layout(int n, int m, int G) {
     L.g = off; off += up(sizeof(double) * (size_t)(m + 1));
     L.y = off; off += up(sizeof(double) * (size_t)m);
     L.gs = off; off += up(sizeof(GState));
+    L.fpart = off; off += up(sizeof(double) * (size_t)3 * kMaxDots * Gf);
+    L.bar = off; off += up(sizeof(unsigned) * 2);
+    L.err = off; off += up(sizeof(int));
     L.total = off;
     return L;
 }
@@ -445,59 +549,12 @@ static NoAllocLayout noalloc_layout(int n, int m, int G) {
 static SolveResult gmres_csr_fixed(int n, const int *rowptr, const int *col, const double *val,
                                    const double *b, double *u, const pdd_solve_opts &o, unsigned char *base,
                                    const NoAllocLayout &L, int m, int G, cudaStream_t st) {
-    double *V = (double *)(base + L.V), *w = (double *)(base + L.w);
-    double *partial = (double *)(base + L.partial), *H = (double *)(base + L.H);
-    double *hsum = (double *)(base + L.hsum);
-    unsigned *cnt = (unsigned *)(base + L.cnt);
-    double *cs = (double *)(base + L.cs), *sn = (double *)(base + L.sn);
-    double *g = (double *)(base + L.g), *y = (double *)(base + L.y);
-    GState *gs = (GState *)(base + L.gs);
-    // the array keeps the previous call's contents: clear what must start at zero
-    PDD_CUDA(cudaMemsetAsync(gs, 0, sizeof(GState), st));
-    PDD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * kDotGroups, st));
-    PDD_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
-    PDD_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, st));
-    const int vb = std::min(cdiv(n, 256), 2048);
-    const int max_iters = std::max(1, o.max_iters);
-    SolveResult res;
-    for (int cycle = 0;; ++cycle) {
-        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
-        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
-        PDD_LAUNCH(k_cycle_start, 1, 32, 0, st, gs, hsum, g, m, o.rtol, max_iters, cycle == 0 ? 1 : 0);
-        PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V, hsum, (double *)nullptr, gs);
-        for (int j = 0; j < m; ++j) {
-            double *vj = V + (long)j * n;
-            double *Hc = H + (long)j * (m + 1);
-            PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, vj, w, gs);
-            for (int pass = 0; pass < 2; ++pass) {
-                PDD_LAUNCH(k_dots, dim3(G, cdiv(j + 1, kDotVec)), kDotThreads, 0, st, n, j + 1, V, w, partial, hsum, cnt, gs);
-                PDD_LAUNCH(k_orth, vb, kDotBlock, 0, st, n, j + 1, V, w, hsum, Hc, pass, gs);
-            }
-            PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, gs);
-            PDD_LAUNCH(k_normalize, vb, kDotBlock, 0, st, n, w, V + (long)(j + 1) * n, hsum, Hc + j + 1, gs);
-            PDD_LAUNCH(k_givens, 1, 32, 0, st, H, m + 1, cs, sn, g, j, o.rtol, max_iters, gs);
-        }
-        PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, H, m + 1, g, y, gs);
-        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, V, y, gs, u);
-        PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, w, (const GState *)nullptr);
-        PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, w);
-        PDD_LAUNCH(k_dots, dim3(G, 1), kDotThreads, 0, st, n, 1, w, w, partial, hsum, cnt, (const GState *)nullptr);
-        GState hg{};
-        double rs = 0.0;
-        PDD_CUDA(cudaMemcpyAsync(&rs, hsum, sizeof(double), cudaMemcpyDeviceToHost, st));
-        PDD_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GState), cudaMemcpyDeviceToHost, st));
-        PDD_CUDA(cudaStreamSynchronize(st));
-        const double rel = hg.bnorm > 0.0 ? std::sqrt(rs) / hg.bnorm : 0.0;
-        res.iters = hg.iters;
-        res.rel = rel;
-        if (hg.bnorm == 0.0 || rel <= o.rtol) {
-            res.converged = 1;
-            break;
-        }
-        if (hg.iters >= max_iters) break;
-    }
-    return res;
+    const GmresBufs B{(double *)(base + L.V), (double *)(base + L.w), (double *)(base + L.partial),
+                      (double *)(base + L.hsum), (double *)(base + L.H), (double *)(base + L.cs),
+                      (double *)(base + L.sn), (double *)(base + L.g), (double *)(base + L.y),
+                      (double *)(base + L.fpart), (unsigned *)(base + L.cnt), (unsigned *)(base + L.bar),
+                      (GState *)(base + L.gs), (int *)(base + L.err)};
+    return gmres_run(n, rowptr, col, val, b, u, o, B, m, G, st);
 }
 
 }  // namespace pdd
@@ -514,7 +571,7 @@ extern "C" pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr, const int 
         if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
         const int m = opts->restart;
         const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));
-        const NoAllocLayout L = noalloc_layout(n, m, G);
+        const NoAllocLayout L = noalloc_layout(n, m, G, fused_grid(n));
         if (L.total > kNoAllocBytes)
             fail(PDD_EINVAL, "workspace of " + std::to_string(L.total) + " bytes exceeds the fixed " +
                                  std::to_string(kNoAllocBytes) + "-byte array: (restart + 2) * n * 8 bytes "
