@@ -34,6 +34,7 @@ struct Shape {
     int nr, nt, nk, nc, n, nrhs;
     double *x, *D, *D2, *F1, *F2, *Hg;   // device tables
     float2 *Dhl, *D2hl, *F1hl, *F2hl;    // the same tables as FP32 (hi, lo) pairs
+    float2 *Hghl;
 };
 
 struct DiskDesc {
@@ -1055,12 +1056,100 @@ __global__ void __launch_bounds__(256) k_disk_eval(Shape S, const DiskDesc *disk
     }
 }
 
+// mixed form: the same evaluation with the 1024-term sums in double-float
+// arithmetic (the weights are built in FP64 and split; X comes split by
+// k_split_x).  A block takes one disk, its knots eight at a time; the
+// (knot, column) outputs are spread over all threads.
+static constexpr int kEvalKnots = 8;
+
+__global__ void k_split_x(long count, const double *X, float2 *Xhl) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < count; e += (long)gridDim.x * blockDim.x)
+        Xhl[e] = df_split(X[e]);
+}
+
+__global__ void __launch_bounds__(256) k_disk_eval_df(Shape S, const DiskDesc *disks, const int *sub_rows,
+                                                      const double *kx, const double *ky, const int *rowptr,
+                                                      const float2 *Xhl, long strideR, int kper, double *val,
+                                                      double *b) {
+    extern __shared__ float2 edf[];                 // kper (<= kEvalKnots) x (n + nt) weights
+    __shared__ double lr[kEvalKnots][130];          // radial barycentric weights, l = 0..nc
+    __shared__ double sa[kEvalKnots][130];          // angular cardinals at the grid angles
+    __shared__ double rho_s[kEvalKnots];
+    const int disk = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const DiskDesc dd = disks[disk];
+    const float2 *X = Xhl + disk * strideR;
+    const int nE = S.n + S.nt, half = S.nt >> 1;
+    for (int r0 = dd.row_begin; r0 < dd.row_end; r0 += kper) {
+        const int nkn = min(kper, dd.row_end - r0);
+        // radial and angular weights of each knot: warp g takes knot g
+        if (warp < nkn) {
+            const int i = sub_rows[r0 + warp];
+            const double dx = kx[i] - dd.cx, dy = ky[i] - dd.cy;
+            const double rho = sqrt(dx * dx + dy * dy) / dd.R;
+            const double phi = atan2(dy, dx);
+            for (int l = lane; l <= S.nc; l += 32) {
+                const double wl = ((l & 1) ? -1.0 : 1.0) * ((l == 0 || l == S.nc) ? 0.5 : 1.0);
+                const double d = rho - S.x[l];
+                lr[warp][l] = (d == 0.0) ? 0.0 : wl / d;
+            }
+            for (int a = lane; a < S.nt; a += 32) sa[warp][a] = fourier_cardinal_cf(phi - PDD_TWO_PI * a / S.nt, S.nt);
+            if (lane == 0) rho_s[warp] = rho;
+        }
+        __syncthreads();
+        if (warp < nkn && lane == 0) {             // normalise (barycentric formula, 2nd kind)
+            const double rho = rho_s[warp];
+            int hit = -1;
+            double den = 0.0;
+            for (int l = 0; l <= S.nc; ++l) {
+                if (rho == S.x[l]) hit = l;
+                den += lr[warp][l];
+            }
+            for (int l = 0; l <= S.nc; ++l)
+                lr[warp][l] = (hit >= 0) ? (l == hit ? 1.0 : 0.0) : lr[warp][l] / den;
+        }
+        __syncthreads();
+        // E[k][a] = l_{k+1} S_a + l_{nc-1-k} S_{a+half};  E_B[a] = l_0 S_a + l_nc S_{a+half}
+        for (int e = tid; e < nkn * nE; e += blockDim.x) {
+            const int g = e / nE, q = e - g * nE;
+            double v;
+            if (q < S.n) {
+                const int kk = q / S.nt, a = q - kk * S.nt;
+                v = lr[g][kk + 1] * sa[g][a] + lr[g][S.nc - 1 - kk] * sa[g][(a + half) % S.nt];
+            } else {
+                const int a = q - S.n;
+                v = lr[g][0] * sa[g][a] + lr[g][S.nc] * sa[g][(a + half) % S.nt];
+            }
+            edf[e] = df_split(v);
+        }
+        __syncthreads();
+        for (int o = tid; o < nkn * S.nrhs; o += blockDim.x) {
+            const int g = o / S.nrhs, col = o - g * S.nrhs;
+            const float2 *E = edf + g * nE;
+            float sh = 0.f, sl = 0.f;
+            for (int q = 0; q < S.n; ++q) df_acc(sh, sl, E[q], X[(long)q * S.nrhs + col]);
+            const int i = sub_rows[r0 + g];
+            if (col < S.nk) {
+                // boundary ring: G_j = -H_j on the circle
+                for (int a = 0; a < S.nt; ++a) {
+                    const float2 hg = S.Hghl[a * S.nk + col];
+                    df_acc(sh, sl, E[S.n + a], make_float2(-hg.x, -hg.y));
+                }
+                const int off = (i < dd.knot_base) ? 1 : 0;
+                val[rowptr[i] + off + col] = (double)sh + (double)sl;
+            } else {
+                b[i] = (double)sh + (double)sl;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 struct ShapeTables {
     DevBuf<double> x, D, D2, F1, F2, Hg;
-    DevBuf<float2> Dhl, D2hl, F1hl, F2hl;
+    DevBuf<float2> Dhl, D2hl, F1hl, F2hl, Hghl;
     Shape S{};
     void build(int nr, int nt, int nk, cudaStream_t st) {
         const int nc = 2 * nr + 1, np = nc + 1;
@@ -1081,8 +1170,10 @@ struct ShapeTables {
         PDD_LAUNCH(k_split_df, cdiv((long)np * np, 256), 256, 0, st, D2.p, D2hl.p, np * np);
         PDD_LAUNCH(k_split_df, cdiv(nt, 256), 256, 0, st, F1.p, F1hl.p, nt);
         PDD_LAUNCH(k_split_df, cdiv(nt, 256), 256, 0, st, F2.p, F2hl.p, nt);
+        Hghl.alloc((size_t)nt * nk);
+        PDD_LAUNCH(k_split_df, cdiv(nt * nk, 256), 256, 0, st, Hg.p, Hghl.p, nt * nk);
         S = Shape{nr, nt, nk, nc, nr * nt, nk + 1, x.p, D.p, D2.p, F1.p, F2.p, Hg.p,
-                  Dhl.p, D2hl.p, F1hl.p, F2hl.p};
+                  Dhl.p, D2hl.p, F1hl.p, F2hl.p, Hghl.p};
     }
 };
 
@@ -1304,14 +1395,29 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             }
         }
         if (!mixed) tm.mark(3);
-        const int group = (S.nrhs <= 32) ? 32 : ((S.nrhs <= 64) ? 64 : 128);
-        const size_t rowb = (size_t)(S.n + S.nt) * sizeof(double);
-        const int per = (int)std::min<size_t>(256 / group, (180 * 1024) / rowb);
-        if (per < 1 || S.nc + 1 > 130 || S.nt > 130) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
-        const size_t esm = per * rowb;
-        PDD_CUDA(cudaFuncSetAttribute(k_disk_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-        PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p,
-                   cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.b.p);
+        if (S.nc + 1 > 130 || S.nt > 130) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
+        if (rlW) {
+            // mixed form: double-float sums on X split into FP32 pairs (the correction buffer is free now)
+            const long cnt = (long)nd * sR;
+            PDD_LAUNCH(k_split_x, (int)std::min<long>(cdiv(cnt, 256), 4096), 256, 0, st, cnt, X.p, Dhl.p);
+            const size_t rowdf = (size_t)(S.n + S.nt) * sizeof(float2);
+            // knots per pass: all (knot, column) outputs of a pass in one sweep of the 256 threads
+            const int kper = (int)std::min<size_t>(std::max(1, std::min(kEvalKnots, 256 / S.nrhs)), (200 * 1024) / rowdf);
+            if (kper < 1) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
+            const size_t esm = kper * rowdf;
+            PDD_CUDA(cudaFuncSetAttribute(k_disk_eval_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+            PDD_LAUNCH(k_disk_eval_df, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p, cov.rowptr.p,
+                       Dhl.p, sR, kper, sys.val.p, sys.b.p);
+        } else {
+            const int group = (S.nrhs <= 32) ? 32 : ((S.nrhs <= 64) ? 64 : 128);
+            const size_t rowb = (size_t)(S.n + S.nt) * sizeof(double);
+            const int per = (int)std::min<size_t>(256 / group, (180 * 1024) / rowb);
+            if (per < 1) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
+            const size_t esm = per * rowb;
+            PDD_CUDA(cudaFuncSetAttribute(k_disk_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+            PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p,
+                       cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.b.p);
+        }
         tm.mark(4);
         std::vector<int> hinfo(nd);
         PDD_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -222,33 +222,63 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
         __syncthreads();
         if (s_stop) break;
         // w = C v_j on this block's rows, 8 lanes per row; v_j was written by every block
-        // (every lane of a warp runs the same number of slots: the shuffles below use the full mask)
+        // (every lane of a warp runs the same number of slots: the shuffles below use the full mask);
+        // the row's column indices and values are loaded before the gathers
         const double *vj = F.V + (long)j * n;
         for (int base = r0; base < r1; base += kFusedThreads / 8) {
             const int row = base + (tid >> 3), l = tid & 7;
             double s = 0.0;
-            if (row < r1)
-                for (int k = F.rowptr[row] + l; k < F.rowptr[row + 1]; k += 8) s += F.val[k] * __ldcg(vj + F.col[k]);
+            if (row < r1) {
+                const int ka = F.rowptr[row], kb = F.rowptr[row + 1];
+                for (int k0 = ka + l; k0 < kb; k0 += 32) {
+                    int c[4];
+                    double a[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = k0 + 8 * q;
+                        c[q] = k < kb ? F.col[k] : 0;
+                        a[q] = k < kb ? F.val[k] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s += a[q] * __ldcg(vj + c[q]);
+                }
+            }
             s += __shfl_xor_sync(0xffffffffu, s, 4);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             if (row < r1 && l == 0) F.w[row] = s;
         }
         __syncthreads();
-        // two passes of classical Gram-Schmidt against v_0 .. v_j
+        // two passes of classical Gram-Schmidt against v_0 .. v_j; eight loads in flight per lane
         for (int pass = 0; pass < 2; ++pass) {
             double *pp = F.part + (long)pass * kMaxDots * G;
             for (int t = warp; t <= j; t += NW) {
                 const double *vt = F.V + (long)t * n;
                 double s = 0.0;
-                for (int r = r0 + lane; r < r1; r += 32) s += vt[r] * F.w[r];
+                for (int rb = r0 + lane; rb < r1; rb += 256) {
+                    double v[8], x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = rb + 32 * q;
+                        v[q] = r < r1 ? vt[r] : 0.0;
+                        x[q] = r < r1 ? F.w[r] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) s += v[q] * x[q];
+                }
                 s = warp_sum(s);
                 if (lane == 0) pp[(long)t * G + b] = s;
             }
             if (!grid_barrier(F)) return;
             for (int t = warp; t <= j; t += NW) {
                 double s = 0.0;
-                for (int q = lane; q < G; q += 32) s += __ldcg(pp + (long)t * G + q);
+                for (int qb = lane; qb < G; qb += 256) {
+                    double v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = qb + 32 * q < G ? __ldcg(pp + (long)t * G + qb + 32 * q) : 0.0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) s += v[q];
+                }
                 s = warp_sum(s);
                 if (lane == 0) h[t] = s;
             }
@@ -257,7 +287,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
                 for (int t = tid; t <= j; t += kFusedThreads) hcol[t] = pass ? hcol[t] + h[t] : h[t];
             for (int r = r0 + tid; r < r1; r += kFusedThreads) {
                 double s = F.w[r];
-                for (int t = 0; t <= j; ++t) s -= F.V[(long)t * n + r] * h[t];
+                for (int t0 = 0; t0 <= j; t0 += 8) {
+                    double v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = t0 + q <= j ? F.V[(long)(t0 + q) * n + r] : 0.0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (t0 + q <= j) s -= v[q] * h[t0 + q];
+                }
                 F.w[r] = s;
             }
             __syncthreads();

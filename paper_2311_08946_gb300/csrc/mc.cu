@@ -453,17 +453,18 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                 }
             }
             // the chunk's interface exits, in path order, into every lane's basis sums
-            for (int src = 0; src < 32; ++src) {
-                const int s_sd = __shfl_sync(0xffffffffu, sd, src);
-                if (s_sd != 0) continue;
-                const double s_y = __shfl_sync(0xffffffffu, yv, src);
-                const double s_su = __shfl_sync(0xffffffffu, su, src);
-                if (fast) {
-                    const float yf = (float)s_y, suf = (float)s_su;
+            if (fast) {
+                // mixed form: each lane converts its own record once; FP32 values are shuffled
+                const float yf = (float)yv, suf = (float)su;
+                for (int src = 0; src < 32; ++src) {
+                    const int s_sd = __shfl_sync(0xffffffffu, sd, src);
+                    const float s_yf = __shfl_sync(0xffffffffu, yf, src);
+                    const float s_suf = __shfl_sync(0xffffffffu, suf, src);
+                    if (s_sd != 0) continue;
 #pragma unroll
                     for (int q = 0; q < kMaxStencil / 32; ++q) {
-                        const float df = suf - ukf[q];
-                        accf[q] = fmaf(yf, rsqrtf(df * df + c2f), accf[q]);
+                        const float df = s_suf - ukf[q];
+                        accf[q] = fmaf(s_yf, rsqrtf(df * df + c2f), accf[q]);
                     }
                     if (++pend == 16) {
 #pragma unroll
@@ -473,7 +474,13 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                         }
                         pend = 0;
                     }
-                } else {
+                }
+            } else {
+                for (int src = 0; src < 32; ++src) {
+                    const int s_sd = __shfl_sync(0xffffffffu, sd, src);
+                    const double s_y = __shfl_sync(0xffffffffu, yv, src);
+                    const double s_su = __shfl_sync(0xffffffffu, su, src);
+                    if (s_sd != 0) continue;
 #pragma unroll
                     for (int q = 0; q < kMaxStencil / 32; ++q) {
                         const int l = lane + 32 * q;
