@@ -234,7 +234,8 @@ def run_ours(args, rank, world):
                       "(512 MB write); working set 4+ GB", "parallelism": f"replicas x{world}"},
            "mc_path_steps_per_s": world * mc_rate, "path_steps_per_step": path_steps,
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
-                                            "ms_refine", "ms_eval", "ms_paths", "ms_finalize")},
+                                            "ms_refine", "ms_eval", "ms_paths", "ms_finalize", "ms_trisolve",
+                                            "ms_tc_gemm")},
            "gmres": solve[-1], "refine_sweeps_max": st["max_refine_sweeps"],
            "lu": ("blocked" if st["lu_blocked"] else
                   f"recursive leaf={st['lu_leaf_width']} tensor_min={st['lu_tensor_min']}") +
@@ -243,7 +244,7 @@ def run_ours(args, rank, world):
            "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary()}
 
     # roofline of the dominant kernel (device time from CUDA events inside the library)
-    out["roofline"] = roofline(st, cfg, N, timed_solve_ms)
+    out["roofline"] = roofline(stats, cfg, N, timed_solve_ms)
 
     if not args.no_fp64 and rank == 0:
         out["fp64_form"] = fp64_form(pdd, cfg, stream, flush)
@@ -256,44 +257,61 @@ def run_ours(args, rank, world):
 
 
 # Thread-instructions per Euler-Maruyama step of k_paths<float,1,1> on this workload, from
-# ncu (smsp__thread_inst_executed.sum / path-steps of the small variable-coefficient case,
-# profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
+# ncu (smsp__thread_inst_executed.sum / path-steps of the variable-coefficient case at 4096 paths
+# per knot, profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
 PATHS_THREAD_INST_PER_STEP = None
+# DRAM bytes (read + write) of one launch from the same captures, or None: the first sweep of
+# k_lu_solve_rl<36> on the 864 disks of the workload (profiles/k_lu_solve_rl_varcoef_mixed.md).
+TRISOLVE_DRAM_BYTES_PER_LAUNCH = 4.21e9 + 0.262e9
+# FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
+FP32_LANES_PER_SM = 128
 
 
-def roofline(st, cfg, N, ms_solve):
-    """Roofline of the dominant stage of the mixed step (device times from CUDA events)."""
+def roofline(stats, cfg, N, ms_solve):
+    """Rooflines of the three heaviest kernels, each from its own device time (CUDA events around
+    its launches inside the library, on the stream they run on); the dominant one is the line's
+    roofline, the others go under "others"."""
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    stages = {"paths": st["ms_paths"], "factor": st["ms_factor"], "refine": st["ms_refine"],
-              "finalize": st["ms_finalize"], "operator": st["ms_operator"], "solve": ms_solve}
-    top = max(stages, key=stages.get)
-    n = cfg["n_r"] * cfg["n_theta"]
-    disks = st["floating_disks"]
-    out = {"stage_ms": stages}
-    # factor: split-TF32 tensor-core Schur updates; TF32 dense peak = measured BF16 peak x 1.1/2.25
-    tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)
-    fac = {"kernel": "recursive LU (k_gemm_sub_tf32x3 + k_panel_leaf + k_trsm_leaf + k_gemm_sub_simt), a7",
-           "bound": "tensor", "achieved": disks * (2.0 / 3.0) * n ** 3 / (st["ms_factor"] / 1e3) / 1e12,
-           "peak": tf32_peak, "unit": "TFLOP/s", "traffic": None,
-           "peak_source": f"TF32 dense = {src} bf16_tflops x 1.1/2.25 (nominal ratio)"}
-    fac["frac"] = fac["achieved"] / fac["peak"]
-    # paths: issue-bound ALU kernel; peak = SM issue rate / thread-instructions per step
+    st = stats[-1]
+    mean = lambda k: statistics.mean(s[k] for s in stats)
+    n, nrhs = cfg["n_r"] * cfg["n_theta"], cfg["n_knots"] + 1
     issue = 152 * 4 * 32 * sm_mhz * 1e6
-    pth = {"kernel": "k_paths<float,1,1> (a11)", "bound": "alu",
-           "achieved": st["path_steps"] / (st["ms_paths"] / 1e3) / 1e9, "unit": "Gpath-steps/s",
+    fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    out = {"stage_ms": {"paths": mean("ms_paths"), "factor": mean("ms_factor"), "refine": mean("ms_refine"),
+                        "finalize": mean("ms_finalize"), "operator": mean("ms_operator"), "eval": mean("ms_eval"),
+                        "solve": ms_solve}}
+    # a11: the path kernel, bound by instruction issue (and the INT32 high-multiply pipe of Philox)
+    pth = {"kernel": "k_paths<float,1,1> (a11)", "bound": "alu", "ms": mean("ms_paths"),
+           "achieved": st["path_steps"] / (mean("ms_paths") / 1e3) / 1e9, "unit": "Gpath-steps/s",
            "traffic": None}
     if PATHS_THREAD_INST_PER_STEP:
         pth["peak"] = issue / PATHS_THREAD_INST_PER_STEP / 1e9
-        pth["frac"] = pth["achieved"] / pth["peak"]
         pth["peak_source"] = (f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz / "
                               f"{PATHS_THREAD_INST_PER_STEP:.0f} thread-instructions per step (ncu)")
     else:
         pth["peak"] = None
-        pth["frac"] = None
-    chosen = pth if top in ("paths", "finalize") else fac
-    out.update(chosen)
-    out["other"] = fac if chosen is pth else pth
+    # a8: right-looking triangular solves, FP32 FMA (2 n^2 (n_k+1) flop per disk and sweep)
+    tri_flop = st["disk_solves"] * 2.0 * n * n * nrhs
+    tri = {"kernel": "k_lu_solve_rl<36> (a8)", "bound": "alu", "ms": mean("ms_trisolve"),
+           "achieved": tri_flop / (mean("ms_trisolve") / 1e3) / 1e12 if mean("ms_trisolve") else None,
+           "unit": "TFLOP/s", "peak": fp32_peak,
+           "peak_source": f"FP32 FMA: 152 SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz",
+           "traffic": TRISOLVE_DRAM_BYTES_PER_LAUNCH,
+           "factor_bytes_per_s": st["disk_solves"] * 4.0 * n * n / (mean("ms_trisolve") / 1e3) / 1e9
+           if mean("ms_trisolve") else None}
+    # a7: split-TF32 Schur updates on tcgen05 (useful 2MNK flop; three TF32 products each)
+    tf32_peak = pk["bf16_tflops"] * (1.1 / 2.25)
+    gem = {"kernel": "k_gemm_sub_tf32x3 (a7)", "bound": "tensor", "ms": mean("ms_tc_gemm"),
+           "achieved": st["tc_gemm_flop"] / (mean("ms_tc_gemm") / 1e3) / 1e12 if mean("ms_tc_gemm") else None,
+           "unit": "TFLOP/s", "peak": tf32_peak / 3.0, "traffic": None,
+           "peak_source": f"TF32 dense = {src} bf16_tflops x 1.1/2.25 (nominal ratio), / 3 products per useful flop"}
+    ks = [pth, tri, gem]
+    for k in ks:
+        k["frac"] = (k["achieved"] / k["peak"]) if (k.get("achieved") and k.get("peak")) else None
+    ks.sort(key=lambda k: -(k["ms"] or 0.0))
+    out.update(ks[0])
+    out["others"] = ks[1:]
     return out
 
 

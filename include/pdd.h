@@ -194,6 +194,12 @@ typedef struct {
     int lu_blocked;           /* mixed-form LU used: 1 blocked, 0 recursive with      */
     int lu_leaf_width;        /*   this leaf panel width and                          */
     int lu_tensor_min;        /*   this tensor-core threshold (autotuned or forced)   */
+    double ms_trisolve;       /* mixed form: device time of the triangular-solve     */
+                              /*   launches alone (CUDA events around each, a8)      */
+    double ms_tc_gemm;        /* mixed form: device time of the tensor-core Schur    */
+                              /*   update launches alone (a7)                        */
+    int64_t disk_solves;      /* (disk, sweep) triangular solves run (a8)            */
+    double tc_gemm_flop;      /* useful flops (2MNK per matrix) of those launches    */
 } pdd_assembly_stats;
 
 /*

@@ -86,7 +86,8 @@ class _AssemblyStats(ctypes.Structure):
                 ("ms_finalize", ctypes.c_double), ("ms_operator", ctypes.c_double),
                 ("ms_factor", ctypes.c_double), ("ms_refine", ctypes.c_double),
                 ("ms_eval", ctypes.c_double), ("lu_blocked", ctypes.c_int), ("lu_leaf_width", ctypes.c_int),
-                ("lu_tensor_min", ctypes.c_int)]
+                ("lu_tensor_min", ctypes.c_int), ("ms_trisolve", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double),
+                ("disk_solves", ctypes.c_int64), ("tc_gemm_flop", ctypes.c_double)]
 
 
 class _SolveOpts(ctypes.Structure):

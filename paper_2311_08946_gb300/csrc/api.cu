@@ -285,6 +285,10 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.lu_blocked = ds.lu_blocked;
         S.lu_leaf_width = ds.lu_leaf;
         S.lu_tensor_min = ds.lu_tmin;
+        S.ms_trisolve = ds.ms_trisolve;
+        S.ms_tc_gemm = ds.ms_tc_gemm;
+        S.disk_solves = ds.disk_solves;
+        S.tc_gemm_flop = ds.tc_gemm_flop;
         if (ms.capped) fail(PDD_EPATH_CAP, std::to_string(ms.capped) + " paths reached the step cap");
         if (ds.unconverged)
             fail(PDD_ENOCONV, std::to_string(ds.unconverged) + " disks missed the refinement tolerance");

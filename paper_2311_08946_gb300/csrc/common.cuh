@@ -253,16 +253,24 @@ __device__ __forceinline__ void normals64(uint64_t seed, uint32_t knot, uint32_t
     xi1 = rr * s;
 }
 
+// round to the nearest integer with FP32 additions (exact for |x| < 2^22):
+// adding and subtracting 1.5 2^23 leaves x rounded to an integer, on the FMA
+// pipe instead of a round instruction
+__device__ __forceinline__ float round_fma(float x) {
+    const float big = 12582912.0f;
+    return __fsub_rn(__fadd_rn(x, big), big);
+}
+
 // FP32 sine and cosine for the mixed form: the argument is reduced to [-pi, pi]
 // (where the hardware approximations __sinf/__cosf/__sincosf keep an absolute
 // error near 2^-21) and the approximation is taken there
 __device__ __forceinline__ float reduce_2pi(float x) {
-    return x - 6.28318530717958647692f * rintf(x * 0.159154943091895335769f);
+    return x - 6.28318530717958647692f * round_fma(x * 0.159154943091895335769f);
 }
 
 // sin(pi x) and cos(pi x): x - 2 round(x / 2) is exact, then as above
 __device__ __forceinline__ void fast_sincospi(float x, float &s, float &c) {
-    const float t = x - 2.0f * rintf(0.5f * x);
+    const float t = x - 2.0f * round_fma(0.5f * x);
     __sincosf(3.14159265358979323846f * t, &s, &c);
 }
 

@@ -891,16 +891,41 @@ __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefA
         const int k = p / S.nt + 1, j = p % S.nt;
         const int jm = (j + half) % S.nt;
         double acc = cf.c * X[(long)p * S.nrhs + col];
-        for (int l = 1; l <= S.nr; ++l) {
-            acc += w[l - 1] * X[(long)((l - 1) * S.nt + j) * S.nrhs + col];
-            acc += w[S.nc - l - 1] * X[(long)((l - 1) * S.nt + jm) * S.nrhs + col];
+        // the radial line and its mirror, then the ring; eight loads in flight, summed in order
+        const long ls = (long)S.nt * S.nrhs;
+        const double *xj = X + (long)j * S.nrhs + col, *xjm = X + (long)jm * S.nrhs + col;
+        for (int l0 = 1; l0 <= S.nr; l0 += 4) {
+            double a[4], bm[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = l0 + u <= S.nr;
+                a[u] = ok ? xj[(l0 + u - 1) * ls] : 0.0;
+                bm[u] = ok ? xjm[(l0 + u - 1) * ls] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u;
+                if (l <= S.nr) {
+                    acc += w[l - 1] * a[u];
+                    acc += w[S.nc - l - 1] * bm[u];
+                }
+            }
         }
         const double *wa = w + S.nc - 1;
-        const long rb = (long)(k - 1) * S.nt;
-        for (int jp = 0; jp < S.nt; ++jp) {
-            int d = j - jp;
-            d += (d < 0) ? S.nt : 0;
-            acc += wa[d] * X[(rb + jp) * S.nrhs + col];
+        const double *xr = X + (long)(k - 1) * S.nt * S.nrhs + col;
+        for (int jp0 = 0; jp0 < S.nt; jp0 += 8) {
+            double xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = jp0 + u < S.nt ? xr[(long)(jp0 + u) * S.nrhs] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int jp = jp0 + u;
+                if (jp < S.nt) {
+                    int d = j - jp;
+                    d += (d < 0) ? S.nt : 0;
+                    acc += wa[d] * xv[u];
+                }
+            }
         }
         const long o = disk * strideR + (long)p * S.nrhs + col;
         const double r = RHSall[o] - cf.s * acc;
@@ -958,16 +983,42 @@ __global__ void __launch_bounds__(256) k_residual_df(Shape S, const NodeCoef *co
         const float2 x0 = D[(long)p * S.nrhs + col];
         const float2 c0 = df_mul(cab[6 * pl + 4], x0);
         float sh = c0.x, sl = c0.y;
-        for (int l = 1; l <= S.nr; ++l) {
-            df_acc(sh, sl, w[l - 1], D[(long)((l - 1) * S.nt + j) * S.nrhs + col]);
-            df_acc(sh, sl, w[S.nc - l - 1], D[(long)((l - 1) * S.nt + jm) * S.nrhs + col]);
+        // the radial line and its mirror, then the ring; eight loads in flight, summed in order
+        const long ls = (long)S.nt * S.nrhs;
+        const float2 *dj = D + (long)j * S.nrhs + col, *djm = D + (long)jm * S.nrhs + col;
+        for (int l0 = 1; l0 <= S.nr; l0 += 4) {
+            float2 a[4], bm[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = l0 + u <= S.nr;
+                a[u] = ok ? dj[(l0 + u - 1) * ls] : make_float2(0.f, 0.f);
+                bm[u] = ok ? djm[(l0 + u - 1) * ls] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u;
+                if (l <= S.nr) {
+                    df_acc(sh, sl, w[l - 1], a[u]);
+                    df_acc(sh, sl, w[S.nc - l - 1], bm[u]);
+                }
+            }
         }
         const float2 *wa = w + S.nc - 1;
-        const long rb = (long)(k - 1) * S.nt;
-        for (int jp = 0; jp < S.nt; ++jp) {
-            int d = j - jp;
-            d += (d < 0) ? S.nt : 0;
-            df_acc(sh, sl, wa[d], D[(rb + jp) * S.nrhs + col]);
+        const float2 *dr = D + (long)(k - 1) * S.nt * S.nrhs + col;
+        for (int jp0 = 0; jp0 < S.nt; jp0 += 8) {
+            float2 xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                xv[u] = jp0 + u < S.nt ? dr[(long)(jp0 + u) * S.nrhs] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int jp = jp0 + u;
+                if (jp < S.nt) {
+                    int d = j - jp;
+                    d += (d < 0) ? S.nt : 0;
+                    df_acc(sh, sl, wa[d], xv[u]);
+                }
+            }
         }
         const float h = sh + sl;
         const float2 ad = df_mul(cab[6 * pl + 5], make_float2(h, sl - (h - sh)));
@@ -1126,7 +1177,16 @@ __global__ void __launch_bounds__(256) k_disk_eval_df(Shape S, const DiskDesc *d
             const int g = o / S.nrhs, col = o - g * S.nrhs;
             const float2 *E = edf + g * nE;
             float sh = 0.f, sl = 0.f;
-            for (int q = 0; q < S.n; ++q) df_acc(sh, sl, E[q], X[(long)q * S.nrhs + col]);
+            const float2 *xc = X + col;
+            for (int q0 = 0; q0 < S.n; q0 += 8) {             // eight loads in flight
+                float2 xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    xv[u] = q0 + u < S.n ? xc[(long)(q0 + u) * S.nrhs] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u < S.n) df_acc(sh, sl, E[q0 + u], xv[u]);
+            }
             const int i = sub_rows[r0 + g];
             if (col < S.nk) {
                 // boundary ring: G_j = -H_j on the circle
@@ -1217,9 +1277,10 @@ struct LuChoice {
 static std::map<int, LuChoice> g_lu_choice;
 static std::mutex g_lu_mu;
 
-static void run_lu_choice(const LuChoice &c, float *A, int n, long sA, int *perm, int *info, int nd, cudaStream_t st) {
+static void run_lu_choice(const LuChoice &c, float *A, int n, long sA, int *perm, int *info, int nd, cudaStream_t st,
+                          float *ms_gemm = nullptr, double *gemm_flop = nullptr) {
     if (c.blocked) launch_lu<float>(A, n, sA, perm, info, nd, st);
-    else lu_recursive_f32(A, n, sA, perm, info, nd, st, c.W, c.tmin);
+    else lu_recursive_f32(A, n, sA, perm, info, nd, st, c.W, c.tmin, ms_gemm, gemm_flop);
 }
 
 static LuChoice tune_lu(float *A, int n, long sA, int nd, cudaStream_t st) {
@@ -1321,14 +1382,14 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                 ds.lu_blocked = 1;
             } else if (o.lu_leaf_width > 0) {
                 const LuChoice c{0, o.lu_leaf_width, o.lu_tensor_min > 0 ? o.lu_tensor_min : 128, 0.f};
-                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st);
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &ds.ms_tc_gemm, &ds.tc_gemm_flop);
                 ds.lu_blocked = 0;
                 ds.lu_leaf = c.W;
                 ds.lu_tmin = c.tmin;
             } else {
                 const LuChoice c = tune_lu(A.p, S.n, sA, nd, st);       // cached after the first wave
                 tm.mark(1);                                            // factor time excludes tuning
-                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st);
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &ds.ms_tc_gemm, &ds.tc_gemm_flop);
                 ds.lu_blocked = c.blocked;
                 ds.lu_leaf = c.W;
                 ds.lu_tmin = c.tmin;
@@ -1356,6 +1417,14 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             PDD_CUDA(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
             PDD_CUDA(cudaFuncSetAttribute(k_residual_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm_df));
             dim3 g_res(cdiv(S.n, kResNP), nd);
+            std::vector<cudaEvent_t> sev(rlW ? 2 * maxs : 0);
+            for (cudaEvent_t &e : sev) PDD_CUDA(cudaEventCreate(&e));
+            struct EvFree {
+                std::vector<cudaEvent_t> &v;
+                ~EvFree() {
+                    for (cudaEvent_t e : v) cudaEventDestroy(e);
+                }
+            } ev_free{sev};
             if (rlW) {
                 PDD_CUDA(cudaMemsetAsync(dmaxb.p, 0, nd * sizeof(unsigned long long), st));
                 PDD_CUDA(cudaMemsetAsync(xmaxb.p, 0, nd * sizeof(unsigned long long), st));
@@ -1366,7 +1435,9 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                     const RlArgs ra{reinterpret_cast<const float *>(A.p), S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs, sR,
                                     X.p, conv.p, dmaxb.p, xmaxb.p, Dhl.p, s == 0 ? 0 : (s == 1 ? 1 : 2), nd,
                                     rl_groups};
+                    PDD_CUDA(cudaEventRecord(sev[2 * s], st));
                     launch_rl(rlW, ra, st);
+                    PDD_CUDA(cudaEventRecord(sev[2 * s + 1], st));
                     PDD_LAUNCH(k_refine_conv, cdiv(nd, 256), 256, 0, st, nd, conv.p, sweeps.p, dmaxb.p, xmaxb.p, tol);
                     if (s + 1 < maxs) {
                         if (s == 0)
@@ -1392,7 +1463,14 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             for (int d = 0; d < nd; ++d) {
                 ds.max_sweeps = std::max(ds.max_sweeps, hs[d]);
                 ds.unconverged += hc[d] ? 0 : 1;
+                ds.disk_solves += hs[d];
             }
+            if (rlW)
+                for (int s = 0; s < maxs; ++s) {
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, sev[2 * s], sev[2 * s + 1]);
+                    ds.ms_trisolve += t;
+                }
         }
         if (!mixed) tm.mark(3);
         if (S.nc + 1 > 130 || S.nt > 130) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
@@ -1465,6 +1543,10 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
         all.ms_factor += d.ms_factor;
         all.ms_refine += d.ms_refine;
         all.ms_eval += d.ms_eval;
+        all.ms_trisolve += d.ms_trisolve;
+        all.ms_tc_gemm += d.ms_tc_gemm;
+        all.disk_solves += d.disk_solves;
+        all.tc_gemm_flop += d.tc_gemm_flop;
         if (d.lu_leaf || d.lu_blocked) {
             all.lu_blocked = d.lu_blocked;
             all.lu_leaf = d.lu_leaf;

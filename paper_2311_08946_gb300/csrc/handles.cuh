@@ -67,6 +67,9 @@ struct DiskStats {
     int disks = 0, rows = 0, max_sweeps = 0, unconverged = 0;
     float ms_operator = 0, ms_factor = 0, ms_refine = 0, ms_eval = 0;
     int lu_blocked = 0, lu_leaf = 0, lu_tmin = 0;          // factorisation used (mixed form)
+    float ms_trisolve = 0, ms_tc_gemm = 0;                 // kernel-only device times (mixed form)
+    int64_t disk_solves = 0;                               // (disk, sweep) triangular solves
+    double tc_gemm_flop = 0;                               // useful flops of the tensor-core launches
 };
 
 // CUDA events bracketing consecutive stages on one stream
@@ -130,7 +133,7 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
 // recursive LU of a batch of FP32 matrices on the tensor cores (lu_rec.cu)
 // W = leaf panel width (8, 16, 32); GEMMs with M, N, K >= tensor_min go to the tensor cores
 void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st, int W,
-                      int tensor_min);
+                      int tensor_min, float *ms_gemm = nullptr, double *gemm_flop = nullptr);
 
 // device-wide exclusive scan of int32 counts (in place into out, returns the total)
 int64_t exclusive_scan(const int *in, int *out, int n, cudaStream_t st);

@@ -14,6 +14,7 @@
 // is the same factorisation P A = L U as the one-CTA right-looking kernel,
 // to FP32 rounding; FP64 iterative refinement (a8) follows.
 #include <algorithm>
+#include <vector>
 
 #include "handles.cuh"
 
@@ -361,13 +362,25 @@ struct RecLU {
     int nd, W;
     cudaStream_t st;
     int tensor_min;     // smallest M, N and K sent to the tensor cores
+    std::vector<cudaEvent_t> *gev;   // event pairs around the tensor-core launches, or null
+    double flop;                     // useful flops sent to the tensor cores
 
     float *at(int r, int c) const { return A + (long)r * n + c; }
 
     void gemm(int r, int c, int M, int N, int K, int ar, int ac, int br, int bc) {
         if (M <= 0 || N <= 0 || K <= 0) return;
         if (M >= tensor_min && N >= tensor_min && K >= tensor_min) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (gev) {
+                PDD_CUDA(cudaEventCreate(&e0));
+                PDD_CUDA(cudaEventCreate(&e1));
+                gev->push_back(e0);
+                gev->push_back(e1);
+                PDD_CUDA(cudaEventRecord(e0, st));
+            }
             gemm_sub_tf32x3(nd, M, N, K, at(ar, ac), sA, n, at(br, bc), sA, n, at(r, c), sA, n, err, st);
+            if (gev) PDD_CUDA(cudaEventRecord(e1, st));
+            flop += 2.0 * M * N * K * nd;
         } else {
             dim3 g(cdiv(N, 64), cdiv(M, 64), nd);
             PDD_LAUNCH(k_gemm_sub_simt, g, 256, 0, st, M, N, K, at(ar, ac), n, at(br, bc), n, at(r, c), n, sA);
@@ -440,7 +453,7 @@ __global__ void k_iota_perm(int n, int nd, int *perm, int *info) {
 }
 
 void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st, int W,
-                      int tensor_min) {
+                      int tensor_min, float *ms_gemm, double *gemm_flop) {
     DevBuf<int> err;
     err.alloc(1);
     PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
@@ -448,11 +461,28 @@ void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int n
     if (W != 8 && W != 16 && W != 32) fail(PDD_EINVAL, "panel width must be 8, 16 or 32");
     if ((size_t)n * ((W + 1) * sizeof(float) + sizeof(int)) > 200 * 1024)
         fail(PDD_EINVAL, "disk grid too large for the panel width");
-    RecLU r{A, n, strideA, perm, info, err.p, nd, W, st, tensor_min};
-    r.lu(0, n);
+    std::vector<cudaEvent_t> gev;
+    RecLU r{A, n, strideA, perm, info, err.p, nd, W, st, tensor_min, ms_gemm ? &gev : nullptr, 0.0};
+    try {
+        r.lu(0, n);
+    } catch (...) {
+        for (cudaEvent_t e : gev) cudaEventDestroy(e);
+        throw;
+    }
     int h = 0;
     PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PDD_CUDA(cudaStreamSynchronize(st));
+    if (ms_gemm) {
+        float tot = 0.f;
+        for (size_t k = 0; k + 1 < gev.size(); k += 2) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, gev[k], gev[k + 1]);
+            tot += t;
+        }
+        *ms_gemm += tot;
+    }
+    if (gemm_flop) *gemm_flop += r.flop;
+    for (cudaEvent_t e : gev) cudaEventDestroy(e);
     if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its MMAs");
 }
 
