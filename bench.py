@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-grad", action="store_true", help="skip the adjoint (a14) leg")
     ap.add_argument("--lu-leaf", type=int, default=0, help="force the recursive LU leaf width (0: autotuned)")
     ap.add_argument("--lu-tmin", type=int, default=0, help="force the tensor-core threshold (with --lu-leaf)")
+    ap.add_argument("--precond", choices=["none", "ras"], default="none",
+                    help="GMRES right preconditioner (RAS: Eq. 42-45)")
     return ap.parse_args()
 
 
@@ -148,6 +150,7 @@ def flush_l2(buf):
 # our arm
 # ---------------------------------------------------------------------------
 LU = {"lu_leaf_width": 0, "lu_tensor_min": 0}
+SOLVE = {"precond": "none"}
 
 
 SOLVE_MS = []
@@ -159,7 +162,7 @@ def step(pdd, cfg, precision, stream):
     S = pdd.System(cov, cfg, precision, stream=stream, **LU)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    u = S.solve(rtol=1e-13, restart=64, stream=stream)
+    u = S.solve(rtol=1e-13, restart=64, stream=stream, precond=SOLVE["precond"])
     e1.record(stream)
     e1.synchronize()
     SOLVE_MS.append(e0.elapsed_time(e1))
@@ -175,6 +178,7 @@ def run_ours(args, rank, world):
 
     pdd.load()
     LU["lu_leaf_width"], LU["lu_tensor_min"] = args.lu_leaf, args.lu_tmin
+    SOLVE["precond"] = args.precond
     cfg = workloads.varcoef()
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -236,7 +240,7 @@ def run_ours(args, rank, world):
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
                                             "ms_refine", "ms_eval", "ms_paths", "ms_finalize", "ms_trisolve",
                                             "ms_tc_gemm")},
-           "gmres": solve[-1], "refine_sweeps_max": st["max_refine_sweeps"],
+           "gmres": dict(solve[-1], precond=args.precond), "refine_sweeps_max": st["max_refine_sweeps"],
            "lu": ("blocked" if st["lu_blocked"] else
                   f"recursive leaf={st['lu_leaf_width']} tensor_min={st['lu_tensor_min']}") +
                  (" (forced)" if args.lu_leaf else " (autotuned)"),

@@ -238,15 +238,28 @@ pdd_status pdd_system_stats(const pdd_system *sys, pdd_assembly_stats *stats);
 void pdd_destroy_system(pdd_system *sys);
 
 /* ---------------------------------------------------------------------------
- * Global solve (a13): restarted GMRES(m) in FP64 (Sec. 4, Eq. 45 without the
- * preconditioner) on a CSR sparse matrix-vector product.
+ * Global solve (a13): restarted GMRES(m) in FP64 (Sec. 4) on a CSR sparse
+ * matrix-vector product, optionally right-preconditioned (Eq. 45) by the
+ * one-level restricted additive Schwarz operator of Eq. 42-44.
  * ------------------------------------------------------------------------- */
+
+enum {
+    PDD_PRECOND_NONE = 0,
+    /* M^-1 = sum_p R_p^T D_p C_p^-1 R_p (Eq. 44) over subsets w_p = the rows
+     * assigned to subdomain p (Sec. 3.2) plus their neighbours in the graph of
+     * C, the knots of circle p; D_p the partition of unity of Eq. 43.  The C_p
+     * (at most 128 x 128) are inverted once per solve in FP32; the iteration
+     * and its stopping test stay FP64.  pdd_solve only (it needs the cover). */
+    PDD_PRECOND_RAS = 1
+};
 
 typedef struct {
     int restart;              /* Krylov subspace size m (1..256)                    */
     int max_iters;            /* total inner iterations cap                          */
     double rtol;              /* stop at |r - C u|_2 <= rtol |r|_2                   */
     int transpose;            /* 1: solve C^T u = r instead                          */
+    int precond;              /* PDD_PRECOND_*; pdd_solve_csr and the allocation-    */
+                              /*   free entry point take PDD_PRECOND_NONE only       */
 } pdd_solve_opts;
 
 typedef struct {
@@ -258,6 +271,15 @@ typedef struct {
 /* Solve the system's C u = r; u_dev [N] caller-owned device memory. */
 pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *u_dev,
                      pdd_solve_info *info, void *stream);
+
+/*
+ * pdd_ras_apply -- y = M_RAS^-1 v (Eq. 44) for the system's C and cover, the
+ * operator pdd_solve applies with PDD_PRECOND_RAS; v_dev, y_dev [N] double
+ * in device memory.  Builds the operator for the call (same subsets, same
+ * FP32 inverses).  PDD_EINVAL for subsets over 128 knots, PDD_ENOCONV for a
+ * singular C_p.
+ */
+pdd_status pdd_ras_apply(const pdd_system *sys, const double *v_dev, double *y_dev, void *stream);
 
 /*
  * pdd_solve_csr -- the same solver on any square CSR matrix in device memory

@@ -92,7 +92,10 @@ class _AssemblyStats(ctypes.Structure):
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("transpose", ctypes.c_int)]
+                ("transpose", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+PRECOND = {"none": 0, "ras": 1}
 
 
 class _SolveInfo(ctypes.Structure):
@@ -102,7 +105,7 @@ class _SolveInfo(ctypes.Structure):
 EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy_cover",
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
            "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
-           "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_grad",
+           "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_grad", "pdd_ras_apply",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
 _lib = None
@@ -340,14 +343,22 @@ class System:
         return {f: getattr(s, f) for f, _ in s._fields_}
 
     def solve(self, rtol: float = 1e-13, restart: int = 64, max_iters: int = 20000, out=None,
-              stream=None):
+              stream=None, precond: str = "none"):
+        """GMRES(restart) on C u = r; precond "ras": right-preconditioned by the RAS operator (Eq. 45)."""
         u = out if out is not None else torch.empty(self.cov.N, dtype=torch.float64, device="cuda")
         info = _SolveInfo()
-        o = _SolveOpts(restart, max_iters, rtol, 0)
+        o = _SolveOpts(restart, max_iters, rtol, 0, PRECOND[precond])
         _check(load().pdd_solve(self._h, ctypes.byref(o), _ptr(u), ctypes.byref(info), _stream(stream)))
         self.last_solve = {"iters": info.iters, "rel_residual": info.rel_residual,
                            "converged": info.converged}
         return u
+
+    def ras_apply(self, v: torch.Tensor, stream=None) -> torch.Tensor:
+        """y = M_RAS^-1 v (Eq. 44), the operator of solve(precond="ras")."""
+        v = v.contiguous()
+        y = torch.empty_like(v)
+        _check(load().pdd_ras_apply(self._h, _ptr(v), _ptr(y), _stream(stream)))
+        return y
 
     def grad(self, u: torch.Tensor, dJdu: torch.Tensor, stream=None, return_lambda=False):
         """dJ/d(theta) = [RBF weights of c, boundary Fourier coefficients of g]."""
@@ -374,7 +385,7 @@ def solve_csr(rowptr, col, val, b, rtol=1e-13, restart=64, max_iters=20000, tran
     n = b.numel()
     u = torch.empty(n, dtype=torch.float64, device="cuda")
     info = _SolveInfo()
-    o = _SolveOpts(restart, max_iters, rtol, 1 if transpose else 0)
+    o = _SolveOpts(restart, max_iters, rtol, 1 if transpose else 0, 0)
     _check(load().pdd_solve_csr(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(u), ctypes.byref(o),
                                 ctypes.byref(info), _stream(stream)))
     return u, {"iters": info.iters, "rel_residual": info.rel_residual, "converged": info.converged}
@@ -389,7 +400,7 @@ def solve_csr_noalloc(rowptr, col, val, b, u, rtol=1e-13, restart=64, max_iters=
     """
     n = b.numel()
     info = _SolveInfo()
-    o = _SolveOpts(restart, max_iters, rtol, 0)
+    o = _SolveOpts(restart, max_iters, rtol, 0, 0)
     _check(load().pdd_solve_csr_noalloc(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(u),
                                         ctypes.byref(o), ctypes.byref(info), _stream(stream)))
     return {"iters": info.iters, "rel_residual": info.rel_residual, "converged": info.converged}

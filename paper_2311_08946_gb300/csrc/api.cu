@@ -336,12 +336,14 @@ static void check_solve_opts(const pdd_solve_opts *o) {
     if (!o) fail(PDD_EINVAL, "null solve options");
     if (o->restart < 1 || o->restart > 256 || o->max_iters < 1 || !(o->rtol > 0))
         fail(PDD_EINVAL, "restart in [1, 256], max_iters >= 1 and rtol > 0 required");
+    if (o->precond != PDD_PRECOND_NONE && o->precond != PDD_PRECOND_RAS) fail(PDD_EINVAL, "unknown preconditioner");
 }
 
 pdd_status pdd_solve_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
                          const pdd_solve_opts *opts, pdd_solve_info *info, void *stream) {
     API_BEGIN
     check_solve_opts(opts);
+    if (opts->precond != PDD_PRECOND_NONE) fail(PDD_EINVAL, "the RAS preconditioner needs the cover: use pdd_solve");
     if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
     cudaStream_t st = (cudaStream_t)stream;
     SolveResult r;
@@ -373,7 +375,34 @@ pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *
         set_error("null system");
         return PDD_EINVAL;
     }
-    return pdd_solve_csr(sys->N, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, sys->b.p, u, opts, info, stream);
+    if (!opts || opts->precond == PDD_PRECOND_NONE)
+        return pdd_solve_csr(sys->N, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, sys->b.p, u, opts, info, stream);
+    API_BEGIN
+    check_solve_opts(opts);
+    if (opts->transpose) fail(PDD_EINVAL, "the preconditioned solve takes C itself (transpose = 0)");
+    if (!u) fail(PDD_EINVAL, "null u");
+    cudaStream_t st = (cudaStream_t)stream;
+    RasPrecond M;
+    M.build(*sys->cov, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, st);
+    const SolveResult r = gmres_csr(sys->N, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, sys->b.p, u, *opts, st, &M);
+    if (info) {
+        info->iters = r.iters;
+        info->rel_residual = r.rel;
+        info->converged = r.converged;
+    }
+    if (!r.converged) fail(PDD_ENOCONV, "GMRES stopped at relative residual " + std::to_string(r.rel));
+    API_END
+}
+
+pdd_status pdd_ras_apply(const pdd_system *sys, const double *v, double *y, void *stream) {
+    API_BEGIN
+    if (!sys || !v || !y) fail(PDD_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    RasPrecond M;
+    M.build(*sys->cov, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, st);
+    M.apply(v, y, st);
+    PDD_CUDA(cudaStreamSynchronize(st));
+    API_END
 }
 
 pdd_status pdd_spmv_csr(int n, const int *rowptr, const int *col, const double *val, const double *x, double *y,

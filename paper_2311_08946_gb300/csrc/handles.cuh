@@ -106,8 +106,17 @@ struct SolveResult {
     double rel = 0;
     int converged = 0;
 };
+// one-level RAS preconditioner of Eq. 42-44 (ras.cu)
+struct RasPrecond {
+    int P = 0, N = 0, NP = 0;                  // subsets, rows, padded subset size
+    DevBuf<int> wptr, widx, p1, l1, p2, l2;
+    DevBuf<float> cinvT, z;
+    void build(const pdd_cover &cov, const int *rowptr, const int *col, const double *val, cudaStream_t st);
+    void apply(const double *v, double *y, cudaStream_t st) const;
+};
+
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b,
-                      double *u, const pdd_solve_opts &o, cudaStream_t st);
+                      double *u, const pdd_solve_opts &o, cudaStream_t st, const RasPrecond *M = nullptr);
 void spmv_csr(int n, const int *rowptr, const int *col, const double *val, const double *x,
               double *y, cudaStream_t st);
 // explicit transpose of a CSR pattern + values (rows of the result sorted)

@@ -1,6 +1,6 @@
 // a13: the global solve C u = r (Eq. 28) in FP64 by restarted GMRES(m)
-// (Sec. 4; Eq. 45 without the RAS preconditioner) on a CSR sparse
-// matrix-vector product.
+// (Sec. 4) on a CSR sparse matrix-vector product, plain or right-
+// preconditioned (Eq. 45) by the RAS operator of ras.cu.
 //
 // Layout: the Krylov basis V is (m+1) x n row-major (each basis vector
 // contiguous); dot products are block partial sums reduced in a fixed order
@@ -171,6 +171,12 @@ struct FusedArnoldi {
     int *err;
     double rtol;
     int max_iters;
+    // right preconditioner (Eq. 44-45); ras_P = 0: none
+    int ras_P, ras_NP;
+    const int *ras_wptr, *ras_widx, *ras_p1, *ras_l1, *ras_p2, *ras_l2;
+    const float *ras_cinvT;
+    float *ras_z;
+    double *ras_Z;               // z_j = M^-1 v_j of the cycle, m x n (flexible GMRES)
 };
 
 __device__ __forceinline__ bool grid_barrier(const FusedArnoldi &F) {
@@ -211,6 +217,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
     constexpr int NW = kFusedThreads / 32;
     __shared__ double h[kMaxDots], hcol[kMaxDots + 1], cs[kMaxDots], sn[kMaxDots], gv[kMaxDots + 1];
     __shared__ double red[NW];
+    __shared__ float vs[128];
     __shared__ int s_stop;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = F.n, m = F.m, ldh = m + 1;
@@ -222,9 +229,37 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
         __syncthreads();
         if (s_stop) break;
         // w = C v_j on this block's rows, 8 lanes per row; v_j was written by every block
+        const double *vj = F.V + (long)j * n;
+        if (F.ras_P) {
+            // z_j = M^-1 v_j (Eq. 44): this block's subsets z_p = C_p^-1 (R_p v_j), then the gather of
+            // its own rows; w = C z_j below (right preconditioning, Eq. 45).  z_j is kept: the cycle
+            // ends with u += Z y (the flexible form, exact for the products actually taken, which the
+            // FP32 local solves make only nearly linear in v)
+            const int NP = F.ras_NP;
+            for (int p = b; p < F.ras_P; p += G) {
+                const int wb = F.ras_wptr[p], np_ = F.ras_wptr[p + 1] - wb;
+                for (int q = tid; q < NP; q += kFusedThreads) vs[q] = q < np_ ? (float)__ldcg(vj + F.ras_widx[wb + q]) : 0.f;
+                __syncthreads();
+                const float *ci = F.ras_cinvT + (long)p * NP * NP;
+                for (int a = tid; a < NP; a += kFusedThreads) {
+                    float s = 0.f;
+                    for (int q = 0; q < np_; ++q) s = fmaf(ci[(long)q * NP + a], vs[q], s);
+                    F.ras_z[(long)p * NP + a] = s;
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(F)) return;
+            double *zj = F.ras_Z + (long)j * n;
+            for (int r = r0 + tid; r < r1; r += kFusedThreads) {
+                const int q2 = F.ras_p2[r];
+                const double a = (double)__ldcg(F.ras_z + (long)F.ras_p1[r] * NP + F.ras_l1[r]);
+                zj[r] = q2 >= 0 ? 0.5 * (a + (double)__ldcg(F.ras_z + (long)q2 * NP + F.ras_l2[r])) : a;
+            }
+            if (!grid_barrier(F)) return;
+            vj = zj;
+        }
         // (every lane of a warp runs the same number of slots: the shuffles below use the full mask);
         // the row's column indices and values are loaded before the gathers
-        const double *vj = F.V + (long)j * n;
         for (int base = r0; base < r1; base += kFusedThreads / 8) {
             const int row = base + (tid >> 3), l = tid & 7;
             double s = 0.0;
@@ -385,7 +420,8 @@ static int fused_grid(int n) {
 }
 
 static SolveResult gmres_run(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
-                             const pdd_solve_opts &o, const GmresBufs &B, int m, int G, cudaStream_t st) {
+                             const pdd_solve_opts &o, const GmresBufs &B, int m, int G, cudaStream_t st,
+                             const RasPrecond *Mr = nullptr, double *Z = nullptr) {
     PDD_CUDA(cudaMemsetAsync(B.gs, 0, sizeof(GState), st));
     PDD_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(unsigned) * kDotGroups, st));
     PDD_CUDA(cudaMemsetAsync(B.bar, 0, sizeof(unsigned) * 2, st));
@@ -396,7 +432,20 @@ static SolveResult gmres_run(int n, const int *rowptr, const int *col, const dou
     const int max_iters = std::max(1, o.max_iters);
     const int Gf = fused_grid(n);
     FusedArnoldi F{n, m, rowptr, col, val, B.V, B.w, B.fpart, B.H, B.cs, B.sn, B.g, B.gs, B.bar, B.err, o.rtol,
-                   max_iters};
+                   max_iters, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (Mr) {
+        F.ras_P = Mr->P;
+        F.ras_NP = Mr->NP;
+        F.ras_wptr = Mr->wptr.p;
+        F.ras_widx = Mr->widx.p;
+        F.ras_p1 = Mr->p1.p;
+        F.ras_l1 = Mr->l1.p;
+        F.ras_p2 = Mr->p2.p;
+        F.ras_l2 = Mr->l2.p;
+        F.ras_cinvT = Mr->cinvT.p;
+        F.ras_z = Mr->z.p;
+        F.ras_Z = Z;
+    }
     SolveResult res;
     for (int cycle = 0;; ++cycle) {
         // r = b - C u  (u = 0 on the first cycle)
@@ -411,7 +460,8 @@ static SolveResult gmres_run(int n, const int *rowptr, const int *col, const dou
                                              st));
         count_launch();
         PDD_LAUNCH(k_upper_solve, 1, 1, 0, st, B.H, m + 1, B.g, B.y, B.gs);
-        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, B.V, B.y, B.gs, u);
+        // u += Z y (preconditioned: the z_j = M^-1 v_j of the cycle) or V y
+        PDD_LAUNCH(k_xupdate, vb, 256, 0, st, n, Mr ? Z : B.V, B.y, B.gs, u);
         // true residual
         PDD_LAUNCH(k_spmv, cdiv(n, kRowsPerBlock), 256, 0, st, n, rowptr, col, val, u, B.w, (const GState *)nullptr);
         PDD_LAUNCH(k_residual_vec, vb, 256, 0, st, n, b, B.w);
@@ -438,7 +488,7 @@ static SolveResult gmres_run(int n, const int *rowptr, const int *col, const dou
 }
 
 SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
-                      const pdd_solve_opts &o, cudaStream_t st) {
+                      const pdd_solve_opts &o, cudaStream_t st, const RasPrecond *Mr) {
     const int m = std::max(1, std::min(256, o.restart));
     const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));
     const int Gf = fused_grid(n);
@@ -461,7 +511,9 @@ SolveResult gmres_csr(int n, const int *rowptr, const int *col, const double *va
     bar.alloc(2);
     err.alloc(1);
     const GmresBufs B{V.p, w.p, partial.p, hsum.p, H.p, cs.p, sn.p, g.p, y.p, fpart.p, cnt.p, bar.p, gs.p, err.p};
-    return gmres_run(n, rowptr, col, val, b, u, o, B, m, G, st);
+    DevBuf<double> Z;
+    if (Mr) Z.alloc((size_t)m * n);
+    return gmres_run(n, rowptr, col, val, b, u, o, B, m, G, st, Mr, Z.p);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,6 +657,7 @@ extern "C" pdd_status pdd_solve_csr_noalloc(int n, const int *rowptr, const int 
         if (opts->restart < 1 || opts->restart > 256 || opts->max_iters < 1 || !(opts->rtol > 0))
             fail(PDD_EINVAL, "restart in [1, 256], max_iters >= 1 and rtol > 0 required");
         if (opts->transpose) fail(PDD_EINVAL, "the allocation-free solve takes C itself (transpose = 0)");
+        if (opts->precond != PDD_PRECOND_NONE) fail(PDD_EINVAL, "the allocation-free solve takes no preconditioner");
         if (n <= 0 || !rowptr || !col || !val || !b || !u) fail(PDD_EINVAL, "null array or n <= 0");
         const int m = opts->restart;
         const int G = std::max(1, std::min(1024, cdiv(n, 2 * kDotThreads)));

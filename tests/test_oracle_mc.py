@@ -9,6 +9,9 @@
 * g = 1, f = c = 0: every perimeter row satisfies 1 + sum_j C_ij = r_i up to
   the IMQ interpolation error of the constant.
 * The direct solve's residual; GMRES against the direct solve.
+* The RAS preconditioner (Eq. 42-45): partition of unity, M^-1 = I when C = I,
+  M^-1 = C^-1 when one subset holds every knot, and right-preconditioned GMRES
+  against the direct solve in fewer iterations than plain GMRES.
 * The adjoint gradient against central finite differences (common random numbers).
 """
 import math
@@ -19,6 +22,7 @@ import textwrap
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import workloads
 from oracle import adjoint, cover, imq, krylov, mc, problem, system
@@ -141,6 +145,42 @@ def test_direct_and_gmres_solves():
     ug, it, rel = krylov.gmres(C, S.b, restart=30, rtol=1e-13)
     assert rel <= 1e-13
     assert np.abs(ug - u).max() < 1e-11
+
+
+def test_ras_preconditioner_special_cases():
+    cfg = workloads.tiny(paths=100)
+    cov = cover.full_cover(cfg)
+    S = system.assemble(cfg, cov)
+    C = S.csr()
+    n = C.shape[0]
+    W = krylov.ras_subsets(cov.knot_ptr, cov.row_sub)
+    # every knot lies in its own circle's subset and, unless it is a Dirichlet row, in its owner's:
+    # the partition of unity of Eq. 43 weighs it by 1/2 or 1
+    apply, mult = krylov.ras_operator(C, W)
+    want = 1.0 + (np.asarray(cov.row_sub) >= 0)
+    assert np.array_equal(mult, want)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(n)
+    # C = I: every C_p is the identity, so M^-1 v = sum_p R_p^T D_p R_p v = v
+    apply_i, _ = krylov.ras_operator(sp.identity(n, format="csr"), W)
+    assert np.abs(apply_i(v) - v).max() <= 1e-15
+    # a single subset holding every knot: M^-1 = C^-1
+    apply_1, _ = krylov.ras_operator(C, [np.arange(n)])
+    assert np.abs(apply_1(v) - np.linalg.solve(C.toarray(), v)).max() <= 1e-12 * np.abs(v).max() * 1e3
+
+
+def test_ras_gmres_against_direct_solve():
+    cfg = workloads.tiny(paths=100)
+    cov = cover.full_cover(cfg)
+    S = system.assemble(cfg, cov)
+    C = S.csr()
+    u = krylov.solve(C, S.b)
+    apply, _ = krylov.ras_operator(C, krylov.ras_subsets(cov.knot_ptr, cov.row_sub))
+    up, it_p, rel_p = krylov.gmres(C, S.b, restart=30, rtol=1e-13, M=apply)
+    _, it_0, _ = krylov.gmres(C, S.b, restart=30, rtol=1e-13)
+    assert rel_p <= 1e-13
+    assert np.abs(up - u).max() < 1e-11
+    assert it_p < it_0, (it_p, it_0)
 
 
 def _J(cfg, u_obs, cov):
