@@ -45,8 +45,8 @@ def parse():
     ap.add_argument("--no-grad", action="store_true", help="skip the adjoint (a14) leg")
     ap.add_argument("--lu-leaf", type=int, default=0, help="force the recursive LU leaf width (0: autotuned)")
     ap.add_argument("--lu-tmin", type=int, default=0, help="force the tensor-core threshold (with --lu-leaf)")
-    ap.add_argument("--precond", choices=["none", "ras"], default="none",
-                    help="GMRES right preconditioner (RAS: Eq. 42-45)")
+    ap.add_argument("--precond", choices=["none", "ras"], default="ras",
+                    help="GMRES right preconditioner (RAS: Eq. 42-45, as the paper solves)")
     return ap.parse_args()
 
 
@@ -150,7 +150,7 @@ def flush_l2(buf):
 # our arm
 # ---------------------------------------------------------------------------
 LU = {"lu_leaf_width": 0, "lu_tensor_min": 0}
-SOLVE = {"precond": "none"}
+SOLVE = {"precond": "ras"}
 
 
 SOLVE_MS = []
@@ -234,7 +234,8 @@ def run_ours(args, rank, world):
            "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 LU + FP64 refinement; FP32 path "
-                      "positions, FP64 weights and scores)", "knots": N, "l2": "flushed between steps "
+                      "positions, FP64 weights and scores)", "solve": f"FP64 GMRES(64), rtol 1e-13, precond "
+                      f"{args.precond}", "knots": N, "l2": "flushed between steps "
                       "(512 MB write); working set 4+ GB", "parallelism": f"replicas x{world}"},
            "mc_path_steps_per_s": world * mc_rate, "path_steps_per_step": path_steps,
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
@@ -263,7 +264,7 @@ def run_ours(args, rank, world):
 # Thread-instructions per Euler-Maruyama step of k_paths<float,1,1> on this workload, from
 # ncu (smsp__thread_inst_executed.sum / path-steps of the variable-coefficient case at 4096 paths
 # per knot, profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
-PATHS_THREAD_INST_PER_STEP = None
+PATHS_THREAD_INST_PER_STEP = 224.0
 # DRAM bytes (read + write) of one launch from the same captures, or None: the first sweep of
 # k_lu_solve_rl<36> on the 864 disks of the workload (profiles/k_lu_solve_rl_varcoef_mixed.md).
 TRISOLVE_DRAM_BYTES_PER_LAUNCH = 4.21e9 + 0.262e9

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
     constexpr int NW = kFusedThreads / 32;
     __shared__ double h[kMaxDots], hcol[kMaxDots + 1], cs[kMaxDots], sn[kMaxDots], gv[kMaxDots + 1];
     __shared__ double red[NW];
-    __shared__ float vs[128];
+    __shared__ float vs[4 * 128];
     __shared__ int s_stop;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = F.n, m = F.m, ldh = m + 1;
@@ -236,15 +236,27 @@ __global__ void __launch_bounds__(kFusedThreads) k_arnoldi_fused(FusedArnoldi F)
             // ends with u += Z y (the flexible form, exact for the products actually taken, which the
             // FP32 local solves make only nearly linear in v)
             const int NP = F.ras_NP;
-            for (int p = b; p < F.ras_P; p += G) {
-                const int wb = F.ras_wptr[p], np_ = F.ras_wptr[p + 1] - wb;
-                for (int q = tid; q < NP; q += kFusedThreads) vs[q] = q < np_ ? (float)__ldcg(vj + F.ras_widx[wb + q]) : 0.f;
+            // four groups of 128 threads take four subsets at a time: group g of block b the subsets
+            // b + G (4 k + g); eight loads of C_p^-1 in flight per thread
+            const int grp = tid >> 7, gt = tid & 127;
+            for (int k0 = 0; b + G * k0 < F.ras_P; k0 += 4) {
+                const int p = b + G * (k0 + grp);
+                const bool has = p < F.ras_P;
+                const int wb = has ? F.ras_wptr[p] : 0, np_ = has ? F.ras_wptr[p + 1] - wb : 0;
+                if (gt < NP) vs[grp * 128 + gt] = gt < np_ ? (float)__ldcg(vj + F.ras_widx[wb + gt]) : 0.f;
                 __syncthreads();
-                const float *ci = F.ras_cinvT + (long)p * NP * NP;
-                for (int a = tid; a < NP; a += kFusedThreads) {
+                if (has && gt < NP) {
+                    const float *ci = F.ras_cinvT + (long)p * NP * NP + gt;
+                    const float *vv = vs + grp * 128;
                     float s = 0.f;
-                    for (int q = 0; q < np_; ++q) s = fmaf(ci[(long)q * NP + a], vs[q], s);
-                    F.ras_z[(long)p * NP + a] = s;
+                    for (int q0 = 0; q0 < np_; q0 += 8) {
+                        float c[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) c[u] = q0 + u < np_ ? ci[(long)(q0 + u) * NP] : 0.f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) s = fmaf(c[u], vv[q0 + u < 128 ? q0 + u : 0], s);
+                    }
+                    F.ras_z[(long)p * NP + gt] = s;
                 }
                 __syncthreads();
             }
