@@ -62,7 +62,17 @@ class _Walk(ctypes.Structure):
     _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("knot", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("h", ctypes.c_double), ("n_paths", ctypes.c_int),
-                ("max_steps", ctypes.c_int)]
+                ("max_steps", ctypes.c_int), ("shift", ctypes.c_double)]
+
+
+# c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi boundary shift in units of |sigma^T n| sqrt(h)
+# (the double nearest to it; a test recomputes it from the zeta function)
+GM_C0 = 0.5825971579390108
+
+
+def boundary_shift(mc: dict) -> float:
+    """Shift of the boundaries for the stopped Euler scheme: c0 sqrt(h) with sigma = I, or 0."""
+    return GM_C0 * math.sqrt(float(mc["h"])) if mc.get("boundary_shift", False) else 0.0
 
 
 def lib():
@@ -118,7 +128,7 @@ def max_steps_for(r, h):
 
 
 def walk(op: Operator, cx, cy, r, x0, y0, knot, seed, h, n_paths, with_grad=False,
-         max_steps=None) -> PathRecords:
+         max_steps=None, shift=0.0) -> PathRecords:
     dom = op.domain
     nr = op.rbf_w.size if with_grad else 0
     rec = PathRecords(n_paths, nr)
@@ -128,7 +138,7 @@ def walk(op: Operator, cx, cy, r, x0, y0, knot, seed, h, n_paths, with_grad=Fals
                     int(op.rbf_w.size), _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]),
                     op.rbf_sigma)
     ms = max_steps_for(r, h) if max_steps is None else int(max_steps)
-    w = _Walk(cx, cy, r, x0, y0, int(knot), int(seed), h, int(n_paths), ms)
+    w = _Walk(cx, cy, r, x0, y0, int(knot), int(seed), h, int(n_paths), ms, float(shift))
     got = lib().oracle_walk_knot(ctypes.byref(prob), ctypes.byref(w), _ptr(rec.side),
                                  _ptr(rec.edge), _ptr(rec.ex), _ptr(rec.ey), _ptr(rec.etheta),
                                  _ptr(rec.Y), _ptr(rec.Z), _ptr(rec.steps), _ptr(rec.dY),
@@ -200,7 +210,7 @@ def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = 
 def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis, with_grad, Kinv, P) -> McRow:
     cx, cy, r = float(cov.cx[m]), float(cov.cy[m]), float(cov.r[m])
     rec = walk(op, cx, cy, r, float(cov.kx[i]), float(cov.ky[i]), i, int(mc["seed"]),
-               float(mc["h"]), P, with_grad=with_grad)
+               float(mc["h"]), P, with_grad=with_grad, shift=boundary_shift(mc))
     if rec.capped:
         raise RuntimeError(f"EPATH_CAP: {rec.capped} paths of knot {i} hit the step cap")
     a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])

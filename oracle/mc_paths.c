@@ -17,6 +17,14 @@
  * X_k -> X_{k+1} first meets the circle or dOmega (smaller segment parameter;
  * a tie goes to dOmega).  The weights are the ones after the exit step.
  *
+ * Boundary shift (the Gobet-Menozzi stopped-diffusion correction, Stoch.
+ * Proc. Appl. 120 (2010); the paper's perimeter subdomains use it, Sec. 5):
+ * with shift = c0 |sigma^T n| sqrt(h) > 0 (sigma = I; c0 = -zeta(1/2)/sqrt(2 pi)
+ * = 0.5826) the exit test uses the disk and the domain shrunk by `shift`, the
+ * piece left first is chosen as above on the shrunk boundaries, and the path
+ * is scored at the projection of its first point outside onto that piece of
+ * the true boundary (radial for circles, onto the edge for the square).
+ *
  * Normals: Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo32, knot) and
  * counter (step, path, 0, 0).  The four 32-bit words (a, b, c, d) give two
  * 53-bit uniforms u1 = ((a << 21) ^ (b >> 11) + 0.5) 2^-53 and likewise u2
@@ -50,6 +58,7 @@ typedef struct {
     double h;
     int n_paths;
     int max_steps;
+    double shift;            /* 0: plain exit; > 0: shrunk boundaries, projected exit point */
 } oracle_walk;
 
 static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -163,7 +172,15 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
                      double *dY, double *dZ)
 {
     const double sh = sqrt(w->h);
-    const double r2 = w->r * w->r;
+    const double dl = w->shift > 0.0 ? w->shift : 0.0;
+    const double rs = w->r - dl;                         /* shrunk circle and domain */
+    const double r2 = rs * rs;
+    oracle_problem ps = *p;
+    if (p->dom_kind == 0) {
+        ps.dom[0] += dl; ps.dom[1] += dl; ps.dom[2] -= dl; ps.dom[3] -= dl;
+    } else {
+        ps.dom[2] -= dl;
+    }
     int capped = 0;
     double S[256], dZacc[256];      /* running sums for the RBF-weight derivatives */
     int nr = (dY != NULL) ? p->n_rbf : 0;
@@ -206,34 +223,57 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
             ++k;
             double ddx = nx - w->cx, ddy = ny - w->cy;
             int out_c = !(ddx * ddx + ddy * ddy < r2);
-            int out_d = !inside_domain(p, nx, ny);
+            int out_d = !inside_domain(&ps, nx, ny);
             if (!out_c && !out_d) { x = nx; y = ny; Y = Yn; Z = Zn; continue; }
             double dx = nx - x, dy = ny - y;
             double tc = 2.0, td = 2.0;
             int ed = -1;
-            if (out_c) tc = circle_exit_t(x, y, dx, dy, w->cx, w->cy, w->r);
+            if (out_c) tc = circle_exit_t(x, y, dx, dy, w->cx, w->cy, rs);
             if (out_d) {
-                if (p->dom_kind == 0) {
+                if (ps.dom_kind == 0) {
                     double t;
-                    if (nx <= p->dom[0]) { t = (p->dom[0] - x) / dx; if (t < td) { td = t; ed = 3; } }
-                    if (nx >= p->dom[2]) { t = (p->dom[2] - x) / dx; if (t < td) { td = t; ed = 1; } }
-                    if (ny <= p->dom[1]) { t = (p->dom[1] - y) / dy; if (t < td) { td = t; ed = 0; } }
-                    if (ny >= p->dom[3]) { t = (p->dom[3] - y) / dy; if (t < td) { td = t; ed = 2; } }
+                    if (nx <= ps.dom[0]) { t = (ps.dom[0] - x) / dx; if (t < td) { td = t; ed = 3; } }
+                    if (nx >= ps.dom[2]) { t = (ps.dom[2] - x) / dx; if (t < td) { td = t; ed = 1; } }
+                    if (ny <= ps.dom[1]) { t = (ps.dom[1] - y) / dy; if (t < td) { td = t; ed = 0; } }
+                    if (ny >= ps.dom[3]) { t = (ps.dom[3] - y) / dy; if (t < td) { td = t; ed = 2; } }
                 } else {
-                    td = circle_exit_t(x, y, dx, dy, p->dom[0], p->dom[1], p->dom[2]);
+                    td = circle_exit_t(x, y, dx, dy, ps.dom[0], ps.dom[1], ps.dom[2]);
                     ed = 0;
                 }
             }
             if (td <= tc) {
                 side[path] = 1; edge[path] = (int8_t)ed;
-                ex[path] = x + td * dx; ey[path] = y + td * dy;
+                if (dl > 0.0) {
+                    /* projection of the first point outside onto the true boundary piece */
+                    if (p->dom_kind == 0) {
+                        double qx = nx < p->dom[0] ? p->dom[0] : (nx > p->dom[2] ? p->dom[2] : nx);
+                        double qy = ny < p->dom[1] ? p->dom[1] : (ny > p->dom[3] ? p->dom[3] : ny);
+                        if (ed == 0) qy = p->dom[1];
+                        else if (ed == 1) qx = p->dom[2];
+                        else if (ed == 2) qy = p->dom[3];
+                        else qx = p->dom[0];
+                        ex[path] = qx; ey[path] = qy;
+                    } else {
+                        double th = atan2(ny - p->dom[1], nx - p->dom[0]);
+                        ex[path] = p->dom[0] + p->dom[2] * cos(th);
+                        ey[path] = p->dom[1] + p->dom[2] * sin(th);
+                    }
+                } else {
+                    ex[path] = x + td * dx; ey[path] = y + td * dy;
+                }
                 etheta[path] = 0.0;
             } else {
                 side[path] = 0; edge[path] = -1;
-                ex[path] = x + tc * dx; ey[path] = y + tc * dy;
-                double th = atan2(ey[path] - w->cy, ex[path] - w->cx);
+                double qx = x + tc * dx, qy = y + tc * dy;
+                if (dl > 0.0) { qx = nx; qy = ny; }          /* radial projection below */
+                double th = atan2(qy - w->cy, qx - w->cx);
                 if (th < 0.0) th += 2.0 * M_PI;
                 etheta[path] = th;
+                if (dl > 0.0) {
+                    ex[path] = w->cx + w->r * cos(th); ey[path] = w->cy + w->r * sin(th);
+                } else {
+                    ex[path] = qx; ey[path] = qy;
+                }
             }
             Ytau[path] = Yn; Ztau[path] = Zn; steps[path] = k;
             for (int q = 0; q < nr; ++q) {

@@ -73,7 +73,7 @@ class _AssemblyOpts(ctypes.Structure):
                 ("imq_c2", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("factor", ctypes.c_int),
                 ("lu_leaf_width", ctypes.c_int), ("lu_tensor_min", ctypes.c_int),
-                ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double)]
+                ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double), ("boundary_shift", ctypes.c_int)]
 
 
 class _AssemblyStats(ctypes.Structure):
@@ -249,7 +249,8 @@ def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps
     return _AssemblyOpts(PREC[precision], 0 if floating_method == "ps" else 1, int(mc["paths"]),
                          float(mc["h"]), int(mc["seed"]), float(cfg.get("imq_c2", 1.5)),
                          int(max_refine), float(refine_tol), FACTOR[factor], int(lu_leaf_width),
-                         int(lu_tensor_min), int(mc.get("paths_max", 0)), float(mc.get("se_target", 0.0)))
+                         int(lu_tensor_min), int(mc.get("paths_max", 0)), float(mc.get("se_target", 0.0)),
+                         1 if mc.get("boundary_shift", False) else 0)
 
 
 # ---------------------------------------------------------------------------

@@ -97,7 +97,11 @@ struct PathArgs {
     const int *npaths;               // per-row path counts (adaptive), or null
     const long *rec_off;             // per-row record offsets, or null (slot * paths)
     float2 *ez;                      // mixed form: the unfolded FP32 increments (e, z) of each record
+    double shift;                    // Gobet-Menozzi boundary shift c0 sqrt(h), or 0 (plain exit)
 };
+
+// c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi shift in units of |sigma^T n| sqrt(h) (sigma = I)
+static constexpr double kGmC0 = 0.5825971579390108;
 
 __device__ __forceinline__ double circle_exit_t(double px, double py, double dx, double dy, double ox,
                                                 double oy, double rad) {
@@ -194,13 +198,19 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     const int slot = blockIdx.x;
     const int i = A.rows[slot], m = A.row_sub[i];
     const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m], ts = A.theta_s[m];
-    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
+    // exit tests against the disk and the domain shrunk by the boundary shift (0: the true ones)
+    const double rs = rad - A.shift;
+    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rs * rs);
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
     const float hf = (float)A.h;
-    // domain bounds in the position type (FP32 in the mixed form)
-    const R d0 = (R)P.dom[0], d1 = (R)P.dom[1], d2 = (R)P.dom[2], d3 = (R)P.dom[3];
-    const R dr2 = (R)(P.dom[2] * P.dom[2]);
+    // domain bounds in the position type (FP32 in the mixed form): square (x0, y0, x1, y1) or disk
+    // (cx, cy, R); the shift moves the edges inward and shrinks R
+    const bool sq_dom = P.dom_kind == 0;
+    const R d0 = (R)(sq_dom ? P.dom[0] + A.shift : P.dom[0]), d1 = (R)(sq_dom ? P.dom[1] + A.shift : P.dom[1]);
+    const R d2 = (R)(sq_dom ? P.dom[2] - A.shift : P.dom[2] - A.shift), d3 = (R)(P.dom[3] - A.shift);
+    const double drs = P.dom[2] - A.shift;
+    const R dr2 = (R)(drs * drs);
     const R x_start = (R)A.kx[i], y_start = (R)A.ky[i];
     const int npath = A.npaths ? A.npaths[slot] : A.paths;
     const long rbase = A.rec_off ? A.rec_off[slot] : (long)slot * A.paths;
@@ -277,29 +287,45 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                 e = en;
                 z = zn;
             } else {
-                // exit point on the segment, in the position type (FP64 form: FP64; mixed: FP32)
+                // exit point on the segment, in the position type (FP64 form: FP64; mixed: FP32); with
+                // the boundary shift the piece crossed first (on the shrunk boundaries) is scored at the
+                // projection of the first point outside onto the true boundary
                 const R dx = nx - x, dy = ny - y;
                 R tc = (R)2, td = (R)2;
                 int ed = -1;
-                if (out_c) tc = circle_exit_tr<R>(x, y, dx, dy, rcx, rcy, (R)rad);
+                if (out_c) tc = circle_exit_tr<R>(x, y, dx, dy, rcx, rcy, (R)rs);
                 if (out_d) {
-                    if (P.dom_kind == 0) {
+                    if (sq_dom) {
                         R t;
                         if (nx <= d0) { t = (d0 - x) / dx; if (t < td) { td = t; ed = 3; } }
                         if (nx >= d2) { t = (d2 - x) / dx; if (t < td) { td = t; ed = 1; } }
                         if (ny <= d1) { t = (d1 - y) / dy; if (t < td) { td = t; ed = 0; } }
                         if (ny >= d3) { t = (d3 - y) / dy; if (t < td) { td = t; ed = 2; } }
                     } else {
-                        td = circle_exit_tr<R>(x, y, dx, dy, d0, d1, (R)P.dom[2]);
+                        td = circle_exit_tr<R>(x, y, dx, dy, d0, d1, (R)drs);
                         ed = 0;
                     }
                 }
+                const bool proj = A.shift > 0.0;
                 if (td <= tc) {
-                    const R ex = x + td * dx, ey = y + td * dy;
+                    R ex = x + td * dx, ey = y + td * dy;
+                    if (proj) {
+                        ex = nx;
+                        ey = ny;
+                        if (sq_dom) {
+                            const R x0 = (R)P.dom[0], y0 = (R)P.dom[1], x1 = (R)P.dom[2], y1 = (R)P.dom[3];
+                            ex = ex < x0 ? x0 : (ex > x1 ? x1 : ex);
+                            ey = ey < y0 ? y0 : (ey > y1 ? y1 : ey);
+                            if (ed == 0) ey = y0;
+                            else if (ed == 1) ex = x1;
+                            else if (ed == 2) ey = y1;
+                            else ex = x0;
+                        }                                  // disk domain: the arclength is the angle's
+                    }
                     A.side[rec] = 1;
                     A.su[rec] = boundary_s(P, (double)ex, (double)ey, ed);
                 } else {
-                    const R ex = x + tc * dx, ey = y + tc * dy;
+                    const R ex = proj ? nx : x + tc * dx, ey = proj ? ny : y + tc * dy;
                     R th = atan2(ey - rcy, ex - rcx);
                     const R two_pi = (R)PDD_TWO_PI;
                     if (th < (R)0) th += two_pi;
@@ -709,7 +735,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     auto run_wave = [&](const int *rows, int nr, const int *np, const long *roff, const int *gsl, const int *momp,
                         double *bmean) {
         PathArgs A{rows, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p, o.paths,
-                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p};
+                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p,
+                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0};
         PDD_CUDA(cudaEventRecord(e0, st));
         if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
@@ -855,7 +882,18 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     for (int k = 0; k < ng; ++k) Gg[k * T + tid] = 0.0;
     __syncthreads();
     const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m];
-    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rad * rad);
+    // the same exit rule as k_paths: disk and domain shrunk by the boundary shift (0: plain)
+    const double rs = rad - A.shift;
+    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rs * rs);
+    Problem Ps = P;
+    if (P.dom_kind == 0) {
+        Ps.dom[0] += A.shift;
+        Ps.dom[1] += A.shift;
+        Ps.dom[2] -= A.shift;
+        Ps.dom[3] -= A.shift;
+    } else {
+        Ps.dom[2] -= A.shift;
+    }
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
     const double inv2s = nw ? 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma) : 0.0;
@@ -907,7 +945,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
             ++k;
             const R ddx = nx - rcx, ddy = ny - rcy;
             const bool out_c = !(ddx * ddx + ddy * ddy < r2);
-            const bool out_d = !inside_domain(P, (double)nx, (double)ny);
+            const bool out_d = !inside_domain(Ps, (double)nx, (double)ny);
             if (!out_c && !out_d) {
                 x = nx;
                 y = ny;
@@ -918,24 +956,38 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
             const double dx = (double)nx - xd, dy = (double)ny - yd;
             double tc = 2.0, td = 2.0;
             int ed = -1;
-            if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rad);
+            if (out_c) tc = circle_exit_t(xd, yd, dx, dy, cx, cy, rs);
             if (out_d) {
-                if (P.dom_kind == 0) {
+                if (Ps.dom_kind == 0) {
                     double t;
-                    if ((double)nx <= P.dom[0]) { t = (P.dom[0] - xd) / dx; if (t < td) { td = t; ed = 3; } }
-                    if ((double)nx >= P.dom[2]) { t = (P.dom[2] - xd) / dx; if (t < td) { td = t; ed = 1; } }
-                    if ((double)ny <= P.dom[1]) { t = (P.dom[1] - yd) / dy; if (t < td) { td = t; ed = 0; } }
-                    if ((double)ny >= P.dom[3]) { t = (P.dom[3] - yd) / dy; if (t < td) { td = t; ed = 2; } }
+                    if ((double)nx <= Ps.dom[0]) { t = (Ps.dom[0] - xd) / dx; if (t < td) { td = t; ed = 3; } }
+                    if ((double)nx >= Ps.dom[2]) { t = (Ps.dom[2] - xd) / dx; if (t < td) { td = t; ed = 1; } }
+                    if ((double)ny <= Ps.dom[1]) { t = (Ps.dom[1] - yd) / dy; if (t < td) { td = t; ed = 0; } }
+                    if ((double)ny >= Ps.dom[3]) { t = (Ps.dom[3] - yd) / dy; if (t < td) { td = t; ed = 2; } }
                 } else {
-                    td = circle_exit_t(xd, yd, dx, dy, P.dom[0], P.dom[1], P.dom[2]);
+                    td = circle_exit_t(xd, yd, dx, dy, Ps.dom[0], Ps.dom[1], Ps.dom[2]);
                     ed = 0;
                 }
             }
+            const bool proj = A.shift > 0.0;
             if (td <= tc) {
                 side = 1;
-                su = boundary_s(P, xd + td * dx, yd + td * dy, ed);
+                double ex = xd + td * dx, ey = yd + td * dy;
+                if (proj) {                          // projection onto the true boundary
+                    ex = (double)nx;
+                    ey = (double)ny;
+                    if (P.dom_kind == 0) {
+                        ex = ex < P.dom[0] ? P.dom[0] : (ex > P.dom[2] ? P.dom[2] : ex);
+                        ey = ey < P.dom[1] ? P.dom[1] : (ey > P.dom[3] ? P.dom[3] : ey);
+                        if (ed == 0) ey = P.dom[1];
+                        else if (ed == 1) ex = P.dom[2];
+                        else if (ed == 2) ey = P.dom[3];
+                        else ex = P.dom[0];
+                    }
+                }
+                su = boundary_s(P, ex, ey, ed);
             } else {
-                const double ex = xd + tc * dx, ey = yd + tc * dy;
+                const double ex = proj ? (double)nx : xd + tc * dx, ey = proj ? (double)ny : yd + tc * dy;
                 double th = atan2(ey - cy, ex - cx);
                 if (th < 0.0) th += PDD_TWO_PI;
                 double uu = th - A.theta_s[m];
@@ -1006,7 +1058,8 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     steps.alloc(1);
     capped.alloc(1);
     PathArgs A{sys.mc_rows.p, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p,
-               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p, sys.mc_np.p, nullptr};
+               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p, sys.mc_np.p, nullptr,
+               nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0};
     GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
     const int T = 64;
     const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);

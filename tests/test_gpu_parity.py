@@ -154,8 +154,12 @@ def test_floating_rows_scaled_sampled(pdd):
             assert _row_err(g["val"][a + pos], v) < 1e-10, (m, i)
 
 
-def test_mc_rows_identical_streams_tiny(pdd):
+@pytest.mark.parametrize("shift", [False, True], ids=["plain", "boundary_shift"])
+def test_mc_rows_identical_streams_tiny(pdd, shift):
+    """FP64 form on the oracle's Philox streams; with the Gobet-Menozzi boundary shift both sides stop
+    at the shrunk boundaries and score the projected exit point."""
     cfg = workloads.tiny(paths=500)
+    cfg["mc"]["boundary_shift"] = shift
     oc = _oracle_cover("tiny", cfg)
     S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
     g = _np(S.csr())
@@ -247,6 +251,31 @@ def test_mc_mixed_within_standard_errors(pdd):
     assert np.mean(np.abs(z) > 4.0) < 5e-3      # 4 SE (batch-means SE has 31 degrees of freedom)
     assert np.abs(z).max() < 6.0
     assert 0.6 < np.mean(z * z) < 1.6
+
+
+def test_mc_mixed_boundary_shift_within_standard_errors(pdd):
+    """Mixed form with the boundary shift against the oracle's FP64 shifted scheme on independent
+    streams: within 4 standard errors."""
+    cfg = workloads.tiny(paths=2000)
+    cfg["mc"]["boundary_shift"] = True
+    cfg["mc"]["h"] = 4e-4
+    oc = _oracle_cover("tiny", cfg)
+    cfg1 = dict(cfg, mc=dict(cfg["mc"], seed=1))
+    S = pdd.System(pdd.Cover(cfg1), cfg1, "mixed")
+    g = _np(S.csr())
+    mc = _np(S.mc())
+    rows = [int(i) for i in mc["rows"][::4]]
+    ref = osystem.assemble(cfg, oc, rows=rows, threads=4)
+    z = []
+    for i in rows:
+        r = ref.mc_rows[i]
+        a, b = oc.rowptr[i], oc.rowptr[i + 1]
+        pos = np.searchsorted(oc.col[a:b], r.cols)
+        ok = r.se > 0
+        z.extend(((g["val"][a + pos] - r.vals)[ok] / np.hypot(g["se"][a + pos], r.se)[ok]).tolist())
+    z = np.array(z)
+    assert np.abs(z).max() < 6.0 and np.mean(np.abs(z) > 4.0) < 5e-3
+    assert 0.5 < np.mean(z * z) < 1.7
 
 
 def test_mc_mixed_same_stream_tracks_fp64(pdd):

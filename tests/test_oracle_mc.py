@@ -103,6 +103,33 @@ def test_mean_exit_time_from_disk():
         assert np.all(rec.side == 0)
 
 
+def test_boundary_shift_removes_the_exit_bias():
+    """Gobet-Menozzi: stopping at the disk shrunk by c0 sqrt(h) (c0 = -zeta(1/2)/sqrt(2 pi)) takes
+    the mean exit time's O(sqrt h) overshoot down to O(h).  At sqrt(h) = R/10 the plain scheme
+    overshoots by ~10 % of (R^2 - rho^2)/2; the shifted one is within 4 SE + 2 h."""
+    cfg, cov = _disk_cover()
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "one", "g": "zero"}, cov.domain)
+    R = cov.r[0]
+    h = (0.1 * R) ** 2
+    shift = mc.boundary_shift({"h": h, "boundary_shift": True})
+    from scipy.special import zeta
+    assert abs(mc.GM_C0 - (-zeta(0.5)) / math.sqrt(2.0 * math.pi)) <= 2e-16
+    assert abs(shift - mc.GM_C0 * 0.1 * R) < 1e-15
+    for rho in (0.0, 0.5):
+        x0 = cov.cx[0] + R * rho
+        exact = 0.5 * (R * R - (R * rho) ** 2)
+        plain = mc.walk(op, cov.cx[0], cov.cy[0], R, x0, cov.cy[0], 7, 3, h, 40000)
+        shifted = mc.walk(op, cov.cx[0], cov.cy[0], R, x0, cov.cy[0], 7, 3, h, 40000, shift=shift)
+        bias_p = plain.Z.mean() - exact
+        bias_s = shifted.Z.mean() - exact
+        se = shifted.Z.std(ddof=1) / math.sqrt(shifted.Z.size)
+        assert bias_p > 0.05 * exact, (rho, bias_p)
+        assert abs(bias_s) < 4 * se + 2 * h, (rho, bias_s, se)
+        # exit points lie on the circle itself (projection onto the true boundary)
+        d = np.hypot(shifted.ex - cov.cx[0], shifted.ey - cov.cy[0])
+        assert np.abs(d - R).max() < 1e-12
+
+
 def test_harmonic_measure_is_poisson_kernel():
     from oracle import spectral
     cfg, cov = _disk_cover()
