@@ -566,49 +566,24 @@ __global__ void __launch_bounds__(128) k_diag_inv(const float *LUall, int n, lon
     for (int r = 0; r < kRlTB; ++r) out[r * kRlTB + j] = Xs[w][r][j];
 }
 
-// the 32 factor entries T[r, i0 .. i0+31] of one row (16-byte loads; zero for rows past rb)
-__device__ __forceinline__ void rl_fetch(float4 (&l)[kRlTB / 4], const float *LU, int n, int r, int rb, int i0) {
-    const float4 *src = reinterpret_cast<const float4 *>(LU + (long)(r < rb ? r : 0) * n + i0);
-#pragma unroll
-    for (int q = 0; q < kRlTB / 4; ++q) l[q] = r < rb ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-template <int CG>
-__device__ __forceinline__ void rl_rank4(float (&acc)[CG], float4 l, const float *xs) {
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const float lk = kk == 0 ? l.x : (kk == 1 ? l.y : (kk == 2 ? l.z : l.w));
-        const float *xr = xs + (size_t)kk * CG;
-#pragma unroll
-        for (int c = 0; c < CG; c += 4) {
-            const float4 x = *reinterpret_cast<const float4 *>(xr + c);
-            acc[c] = fmaf(-lk, x.x, acc[c]);
-            acc[c + 1] = fmaf(-lk, x.y, acc[c + 1]);
-            acc[c + 2] = fmaf(-lk, x.z, acc[c + 2]);
-            acc[c + 3] = fmaf(-lk, x.w, acc[c + 3]);
-        }
-    }
-}
-
 // X += inv(LU) P R for the columns [blockIdx.y CG, ...) of every disk not yet
 // converged; the largest |correction| and |X| of each disk go to dmaxb/xmaxb
 // (bit patterns of non-negative doubles, ordered like the values)
 template <int CG>
-__global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUall, int n, long strideA,
+__global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTall, int n, long strideA,
                                                                const int *permAll, const float *DinvAll,
                                                                const double *Rall, int nrhs, long strideR,
                                                                double *Xall, const int *conv,
                                                                unsigned long long *dmaxb, unsigned long long *xmaxb,
                                                                float2 *Dall, int dmode) {
     constexpr int NT = kRlThreads, TB = kRlTB;
-    static_assert(CG / 4 <= NT / 32, "one warp per column quad of the diagonal step");
     extern __shared__ __align__(16) float rsm[];
     float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
     float *Ds = rsm + (size_t)n * CG;                  // TB x (TB + 1) diagonal-block inverse (padded rows)
     const int disk = blockIdx.x, tid = threadIdx.x;
     if (conv[disk]) return;
     const int c0 = blockIdx.y * CG, cg = min(CG, nrhs - c0);
-    const float *LU = LUall + disk * strideA;
+    const float *LUT = LUTall + disk * strideA;      // the factors transposed
     const int *perm = permAll + (long)disk * n;
     const double *R = Rall + disk * strideR;
     double *X = Xall + disk * strideR;
@@ -618,82 +593,129 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
         const int p = e / CG, c = e - p * CG;
         Bs[e] = (c < cg) ? (float)R[(long)perm[p] * nrhs + c0 + c] : 0.f;
     }
-    const bool vec = (n & 3) == 0;
+    const bool vec = true;
     for (int pass = 0; pass < 2; ++pass) {             // 0: L (unit lower), 1: U (upper)
         for (int bi = 0; bi < nblk; ++bi) {
             const int blk = pass == 0 ? bi : nblk - 1 - bi;
             const int i0 = blk * TB, tb = min(TB, n - i0);
             const int ra = pass == 0 ? i0 + tb : 0, rb = pass == 0 ? n : i0;
             const bool full = vec && tb == TB;
-            // this thread's first row of the update: its factor entries are in flight during the
-            // diagonal step
-            float4 lv[TB / 4];
-            if (full) rl_fetch(lv, LU, n, ra + tid, rb, i0);
             // the panel's rows X_b = inv(T_bb) B_b: warp q takes columns 4q .. 4q+3, lane i the
             // panel row i; the row of the inverse comes from global memory into registers and the
             // panel's right-hand sides are read as broadcasts
             const int warp = tid >> 5, lane = tid & 31;
-            const bool dtask = warp < CG / 4 && lane < tb;
             const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
             for (int e = tid; e < TB * TB; e += NT) Ds[(e >> 5) * (TB + 1) + (e & 31)] = Dt[e];
             __syncthreads();
-            float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (dtask) {
-                const float *bc = Bs + (size_t)i0 * CG + 4 * warp;
-                const float *dr = Ds + lane * (TB + 1);
-                for (int k = 0; k < tb; ++k) {
-                    const float d = dr[k];
-                    const float4 b = *reinterpret_cast<const float4 *>(bc + (size_t)k * CG);
-                    xo.x = fmaf(d, b.x, xo.x);
-                    xo.y = fmaf(d, b.y, xo.y);
-                    xo.z = fmaf(d, b.z, xo.z);
-                    xo.w = fmaf(d, b.w, xo.w);
+            // warps take the column quads in turn (two passes when CG / 4 exceeds the warp count)
+            constexpr int NQ = CG / 4, NW = NT / 32, QP = (NQ + NW - 1) / NW;
+            float4 xo[QP];
+#pragma unroll
+            for (int qp = 0; qp < QP; ++qp) {
+                const int q = warp + qp * NW;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < NQ && lane < tb) {
+                    const float *bc = Bs + (size_t)i0 * CG + 4 * q;
+                    const float *dr = Ds + lane * (TB + 1);
+                    for (int k = 0; k < tb; ++k) {
+                        const float d = dr[k];
+                        const float4 b = *reinterpret_cast<const float4 *>(bc + (size_t)k * CG);
+                        v.x = fmaf(d, b.x, v.x);
+                        v.y = fmaf(d, b.y, v.y);
+                        v.z = fmaf(d, b.z, v.z);
+                        v.w = fmaf(d, b.w, v.w);
+                    }
                 }
+                xo[qp] = v;
             }
             __syncthreads();
-            if (dtask) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * warp) = xo;
+#pragma unroll
+            for (int qp = 0; qp < QP; ++qp) {
+                const int q = warp + qp * NW;
+                if (q < NQ && lane < tb) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * q) = xo[qp];
+            }
             __syncthreads();
-            // rows still to solve: B_r -= T_rb X_b; the next row's entries load during this row's FMAs
+            // rows still to solve: B_r -= T_rb X_b, two rows per thread so that each broadcast read of
+            // a solved row feeds both
             const float *xs = Bs + (size_t)i0 * CG;
-            for (int r = ra + tid; r < rb; r += NT) {
-                float acc[CG];
-                float *br = Bs + (size_t)r * CG;
+            for (int base = ra; base < rb; base += 2 * NT) {
+                // the rows of this pass paired as (t, t + half): no thread carries an empty second row
+                const int m = min(2 * NT, rb - base), half = (m + 1) >> 1;
+                if (tid >= half) continue;
+                const int r = base + tid, r2 = r + half;
+                const bool two = r2 < base + m;
+                float acc0[CG], acc1[CG];
+                float *b0 = Bs + (size_t)r * CG, *b1 = Bs + (size_t)(two ? r2 : r) * CG;
 #pragma unroll
                 for (int c = 0; c < CG; c += 4) {
-                    const float4 t = *reinterpret_cast<const float4 *>(br + c);
-                    acc[c] = t.x;
-                    acc[c + 1] = t.y;
-                    acc[c + 2] = t.z;
-                    acc[c + 3] = t.w;
+                    const float4 t0 = *reinterpret_cast<const float4 *>(b0 + c);
+                    const float4 t1 = *reinterpret_cast<const float4 *>(b1 + c);
+                    acc0[c] = t0.x;
+                    acc0[c + 1] = t0.y;
+                    acc0[c + 2] = t0.z;
+                    acc0[c + 3] = t0.w;
+                    acc1[c] = t1.x;
+                    acc1[c + 1] = t1.y;
+                    acc1[c + 2] = t1.z;
+                    acc1[c + 3] = t1.w;
                 }
+                // factor entries T[r][i0 + k] = LUT[(i0 + k) n + r]: consecutive rows, consecutive addresses
+                const float *l0 = LUT + (long)i0 * n + r, *l1 = LUT + (long)i0 * n + (two ? r2 : r);
                 if (full) {
-                    float4 ln[TB / 4];
-                    const bool more = r + NT < rb;
-                    if (more) rl_fetch(ln, LU, n, r + NT, rb, i0);
+#pragma unroll 1
+                    for (int k0 = 0; k0 < TB; k0 += 4) {
+                        float a0[4], a1[4];
 #pragma unroll
-                    for (int q = 0; q < TB / 4; ++q) rl_rank4<CG>(acc, lv[q], xs + (size_t)(4 * q) * CG);
-                    if (more) {
+                        for (int kk = 0; kk < 4; ++kk) {
+                            a0[kk] = __ldg(l0 + (long)(k0 + kk) * n);
+                            a1[kk] = __ldg(l1 + (long)(k0 + kk) * n);
+                        }
+#pragma unroll 1
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const float m0 = kk == 0 ? a0[0] : (kk == 1 ? a0[1] : (kk == 2 ? a0[2] : a0[3]));
+                            const float m1 = kk == 0 ? a1[0] : (kk == 1 ? a1[1] : (kk == 2 ? a1[2] : a1[3]));
+                            const float *xr = xs + (size_t)(k0 + kk) * CG;
 #pragma unroll
-                        for (int q = 0; q < TB / 4; ++q) lv[q] = ln[q];
+                            for (int c = 0; c < CG; c += 4) {
+                                const float4 x = *reinterpret_cast<const float4 *>(xr + c);
+                                acc0[c] = fmaf(-m0, x.x, acc0[c]);
+                                acc0[c + 1] = fmaf(-m0, x.y, acc0[c + 1]);
+                                acc0[c + 2] = fmaf(-m0, x.z, acc0[c + 2]);
+                                acc0[c + 3] = fmaf(-m0, x.w, acc0[c + 3]);
+                                acc1[c] = fmaf(-m1, x.x, acc1[c]);
+                                acc1[c + 1] = fmaf(-m1, x.y, acc1[c + 1]);
+                                acc1[c + 2] = fmaf(-m1, x.z, acc1[c + 2]);
+                                acc1[c + 3] = fmaf(-m1, x.w, acc1[c + 3]);
+                            }
+                        }
                     }
                 } else {
-                    const float *lrow = LU + (long)r * n + i0;
                     for (int k = 0; k < tb; ++k) {
-                        const float lk = __ldg(lrow + k);
+                        const float m0 = __ldg(l0 + (long)k * n), m1 = __ldg(l1 + (long)k * n);
                         const float *xr = xs + (size_t)k * CG;
 #pragma unroll
                         for (int c = 0; c < CG; c += 4) {
                             const float4 x = *reinterpret_cast<const float4 *>(xr + c);
-                            acc[c] = fmaf(-lk, x.x, acc[c]);
-                            acc[c + 1] = fmaf(-lk, x.y, acc[c + 1]);
-                            acc[c + 2] = fmaf(-lk, x.z, acc[c + 2]);
-                            acc[c + 3] = fmaf(-lk, x.w, acc[c + 3]);
+                            acc0[c] = fmaf(-m0, x.x, acc0[c]);
+                            acc0[c + 1] = fmaf(-m0, x.y, acc0[c + 1]);
+                            acc0[c + 2] = fmaf(-m0, x.z, acc0[c + 2]);
+                            acc0[c + 3] = fmaf(-m0, x.w, acc0[c + 3]);
+                            acc1[c] = fmaf(-m1, x.x, acc1[c]);
+                            acc1[c + 1] = fmaf(-m1, x.y, acc1[c + 1]);
+                            acc1[c + 2] = fmaf(-m1, x.z, acc1[c + 2]);
+                            acc1[c + 3] = fmaf(-m1, x.w, acc1[c + 3]);
                         }
                     }
                 }
 #pragma unroll
                 for (int c = 0; c < CG; c += 4)
-                    *reinterpret_cast<float4 *>(br + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                    *reinterpret_cast<float4 *>(b0 + c) = make_float4(acc0[c], acc0[c + 1], acc0[c + 2], acc0[c + 3]);
+                if (two) {
+#pragma unroll
+                    for (int c = 0; c < CG; c += 4)
+                        *reinterpret_cast<float4 *>(b1 + c) =
+                            make_float4(acc1[c], acc1[c + 1], acc1[c + 2], acc1[c + 3]);
+                }
             }
             __syncthreads();
         }
@@ -737,13 +759,40 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUal
 }
 
 // per disk: count the sweep and stop refining once max|W| <= tol max|X|
+// AT = A^T for every disk (32 x 32 tiles through shared memory): the solve then reads the factor
+// entries of consecutive rows from consecutive addresses
+__global__ void __launch_bounds__(256) k_transpose_f32(const float *Aall, float *ATall, int n, long strideA) {
+    __shared__ float t[32][33];
+    const int disk = blockIdx.z, bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const float *A = Aall + disk * strideA;
+    float *AT = ATall + disk * strideA;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int gr = by + r, gc = bx + tx;
+        t[r][tx] = (gr < n && gc < n) ? A[(long)gr * n + gc] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int gr = bx + r, gc = by + tx;
+        if (gr < n && gc < n) AT[(long)gr * n + gc] = t[tx][r];
+    }
+}
+
+// per disk: count the sweep and stop refining once the correction just applied, or the next one
+// predicted from the contraction of the last two (|W_s|^2 / |W_{s-1}|, when they contract), is at
+// most tol max|X|
 __global__ void k_refine_conv(int nd, int *conv, int *sweeps, unsigned long long *dmaxb,
-                              unsigned long long *xmaxb, double tol) {
+                              unsigned long long *xmaxb, double *dprev, double tol) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nd) return;
     if (!conv[d]) {
         sweeps[d] += 1;
-        if (__longlong_as_double((long long)dmaxb[d]) <= tol * __longlong_as_double((long long)xmaxb[d])) conv[d] = 1;
+        const double w = __longlong_as_double((long long)dmaxb[d]);
+        const double x = __longlong_as_double((long long)xmaxb[d]);
+        const double wp = sweeps[d] > 1 ? dprev[d] : 0.0;
+        const bool predicted = wp > 0.0 && w < wp && w * (w / wp) <= tol * x;
+        if (w <= tol * x || predicted) conv[d] = 1;
+        dprev[d] = w;
     }
     dmaxb[d] = 0ull;
     xmaxb[d] = 0ull;
@@ -1332,7 +1381,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     int rl_groups = 0;
     const int rlW = mixed ? rl_width(S.n, S.nrhs, rl_groups) : 0;
     const int nblk = (S.n + kRlTB - 1) / kRlTB;
-    const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) + 2 * perR : 0;
+    const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) + 2 * perR + perA : 0;
     const size_t perDisk = perA + perR * (mixed ? 3 : 1) + (size_t)S.n * S.nrhs * sizeof(T) +
                            (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + perDinv + 64;
     size_t freeb = 0, totb = 0;
@@ -1346,13 +1395,16 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     DevBuf<NodeCoef> coef;
     DevBuf<int> perm, info, conv, sweeps;
     DevBuf<DiskDesc> dd;
-    DevBuf<float> dinv;
+    DevBuf<float> dinv, AT;
     DevBuf<unsigned long long> dmaxb, xmaxb;
+    DevBuf<double> dprev;
     DevBuf<float2> R1hl, Dhl;
     if (rlW) {
         dinv.alloc((size_t)wave * nblk * 2 * kRlTB * kRlTB);
+        AT.alloc((size_t)wave * S.n * S.n);
         dmaxb.alloc(wave);
         xmaxb.alloc(wave);
+        dprev.alloc(wave);
         R1hl.alloc((size_t)wave * S.n * S.nrhs);
         Dhl.alloc((size_t)wave * S.n * S.nrhs);
     }
@@ -1401,6 +1453,8 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             const long items = (long)nd * nblk * 2;
             PDD_LAUNCH(k_diag_inv, (int)((items + 3) / 4), 128, 0, st, reinterpret_cast<const float *>(A.p), S.n, sA,
                        nd, dinv.p);
+            PDD_LAUNCH(k_transpose_f32, dim3(cdiv(S.n, 32), cdiv(S.n, 32), nd), 256, 0, st,
+                       reinterpret_cast<const float *>(A.p), AT.p, S.n, sA);
         }
         tm.mark(2);
         if (!mixed) {
@@ -1432,13 +1486,14 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             for (int s = 0; s < maxs; ++s) {
                 const double *rhs_now = (s == 0) ? RHS.p : Rr.p;
                 if (rlW) {
-                    const RlArgs ra{reinterpret_cast<const float *>(A.p), S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs, sR,
+                    const RlArgs ra{AT.p, S.n, sA, perm.p, dinv.p, rhs_now, S.nrhs, sR,
                                     X.p, conv.p, dmaxb.p, xmaxb.p, Dhl.p, s == 0 ? 0 : (s == 1 ? 1 : 2), nd,
                                     rl_groups};
                     PDD_CUDA(cudaEventRecord(sev[2 * s], st));
                     launch_rl(rlW, ra, st);
                     PDD_CUDA(cudaEventRecord(sev[2 * s + 1], st));
-                    PDD_LAUNCH(k_refine_conv, cdiv(nd, 256), 256, 0, st, nd, conv.p, sweeps.p, dmaxb.p, xmaxb.p, tol);
+                    PDD_LAUNCH(k_refine_conv, cdiv(nd, 256), 256, 0, st, nd, conv.p, sweeps.p, dmaxb.p, xmaxb.p, dprev.p,
+                               tol);
                     if (s + 1 < maxs) {
                         if (s == 0)
                             PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p,
