@@ -662,13 +662,21 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                 // factor entries T[r][i0 + k] = LUT[(i0 + k) n + r]: consecutive rows, consecutive addresses
                 const float *l0 = LUT + (long)i0 * n + r, *l1 = LUT + (long)i0 * n + (two ? r2 : r);
                 if (full) {
+                    float a0[4], a1[4];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        a0[kk] = __ldg(l0 + (long)kk * n);
+                        a1[kk] = __ldg(l1 + (long)kk * n);
+                    }
 #pragma unroll 1
                     for (int k0 = 0; k0 < TB; k0 += 4) {
-                        float a0[4], a1[4];
+                        // the next chunk's entries are in flight during this chunk's FMAs
+                        float b0[4], b1[4];
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            a0[kk] = __ldg(l0 + (long)(k0 + kk) * n);
-                            a1[kk] = __ldg(l1 + (long)(k0 + kk) * n);
+                            const int kn = k0 + 4 + kk < TB ? k0 + 4 + kk : kk;
+                            b0[kk] = __ldg(l0 + (long)kn * n);
+                            b1[kk] = __ldg(l1 + (long)kn * n);
                         }
 #pragma unroll 1
                         for (int kk = 0; kk < 4; ++kk) {
@@ -687,6 +695,11 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                                 acc1[c + 2] = fmaf(-m1, x.z, acc1[c + 2]);
                                 acc1[c + 3] = fmaf(-m1, x.w, acc1[c + 3]);
                             }
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            a0[kk] = b0[kk];
+                            a1[kk] = b1[kk];
                         }
                     }
                 } else {

@@ -197,21 +197,39 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     __shared__ int next_path;
     const int slot = blockIdx.x;
     const int i = A.rows[slot], m = A.row_sub[i];
-    const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m], ts = A.theta_s[m];
-    // exit tests against the disk and the domain shrunk by the boundary shift (0: the true ones)
-    const double rs = rad - A.shift;
-    const R rcx = (R)cx, rcy = (R)cy, r2 = (R)(rs * rs);
+    const double rad = A.cr[m], ts = A.theta_s[m];
+    // exit tests against the disk and the domain shrunk by the boundary shift (0: the true ones), in
+    // the position type; computed once into shared memory so that the loop reads them instead of
+    // recomputing FP64 expressions: circle centre, r^2, r, the square's (x0, y0, x1, y1) or the
+    // disk domain's (cx, cy, R) and R^2, the starting point and the step constants
+    __shared__ R kc[14];
+    if (threadIdx.x == 0) {
+        const double rs = rad - A.shift, sft = A.shift;
+        const bool sqd = P.dom_kind == 0;
+        kc[0] = (R)A.ccx[m];
+        kc[1] = (R)A.ccy[m];
+        kc[2] = (R)(rs * rs);
+        kc[3] = (R)rs;
+        kc[4] = (R)(sqd ? P.dom[0] + sft : P.dom[0]);
+        kc[5] = (R)(sqd ? P.dom[1] + sft : P.dom[1]);
+        kc[6] = (R)(P.dom[2] - sft);
+        kc[7] = (R)(P.dom[3] - sft);
+        kc[8] = (R)((P.dom[2] - sft) * (P.dom[2] - sft));
+        kc[9] = (R)A.kx[i];
+        kc[10] = (R)A.ky[i];
+        kc[11] = (R)A.h;
+        kc[12] = Num<R>::sq((R)A.h);
+        kc[13] = (R)ts;
+    }
+    __syncthreads();
+    const R rcx = kc[0], rcy = kc[1], r2 = kc[2];
     const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
-    const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
-    const float hf = (float)A.h;
-    // domain bounds in the position type (FP32 in the mixed form): square (x0, y0, x1, y1) or disk
-    // (cx, cy, R); the shift moves the edges inward and shrinks R
+    const R h = kc[11], sh = kc[12];
+    const float hf = (float)kc[11];
     const bool sq_dom = P.dom_kind == 0;
-    const R d0 = (R)(sq_dom ? P.dom[0] + A.shift : P.dom[0]), d1 = (R)(sq_dom ? P.dom[1] + A.shift : P.dom[1]);
-    const R d2 = (R)(sq_dom ? P.dom[2] - A.shift : P.dom[2] - A.shift), d3 = (R)(P.dom[3] - A.shift);
-    const double drs = P.dom[2] - A.shift;
-    const R dr2 = (R)(drs * drs);
-    const R x_start = (R)A.kx[i], y_start = (R)A.ky[i];
+    const R d0 = kc[4], d1 = kc[5], d2 = kc[6], d3 = kc[7];
+    const R dr2 = kc[8];
+    const R x_start = kc[9], y_start = kc[10];
     const int npath = A.npaths ? A.npaths[slot] : A.paths;
     const long rbase = A.rec_off ? A.rec_off[slot] : (long)slot * A.paths;
     unsigned long long my_steps = 0;
@@ -293,7 +311,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                 const R dx = nx - x, dy = ny - y;
                 R tc = (R)2, td = (R)2;
                 int ed = -1;
-                if (out_c) tc = circle_exit_tr<R>(x, y, dx, dy, rcx, rcy, (R)rs);
+                if (out_c) tc = circle_exit_tr<R>(x, y, dx, dy, rcx, rcy, kc[3]);
                 if (out_d) {
                     if (sq_dom) {
                         R t;
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                         if (ny <= d1) { t = (d1 - y) / dy; if (t < td) { td = t; ed = 0; } }
                         if (ny >= d3) { t = (d3 - y) / dy; if (t < td) { td = t; ed = 2; } }
                     } else {
-                        td = circle_exit_tr<R>(x, y, dx, dy, d0, d1, (R)drs);
+                        td = circle_exit_tr<R>(x, y, dx, dy, d0, d1, d2);
                         ed = 0;
                     }
                 }
@@ -329,7 +347,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                     R th = atan2(ey - rcy, ex - rcx);
                     const R two_pi = (R)PDD_TWO_PI;
                     if (th < (R)0) th += two_pi;
-                    R u = th - (R)ts;
+                    R u = th - kc[13];
                     if (u < (R)0) u += two_pi;
                     if (u >= two_pi) u -= two_pi;
                     A.side[rec] = 0;
