@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the adjoint (a14) leg")
+    ap.add_argument("--no-poisson46", action="store_true",
+                    help="skip the leg on the paper's Poisson test (Eq. 46, [-50,50]^2)")
     ap.add_argument("--lu-leaf", type=int, default=0, help="force the recursive LU leaf width (0: autotuned)")
     ap.add_argument("--lu-tmin", type=int, default=0, help="force the tensor-core threshold (with --lu-leaf)")
     ap.add_argument("--precond", choices=["none", "ras"], default="ras",
@@ -258,6 +260,8 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0 and not args.no_grad:
         out["grad"] = grad_bench(pdd, stream)
+    if rank == 0 and not args.no_poisson46:
+        out["poisson46"] = poisson46_leg(pdd, stream, flush)
     return out
 
 
@@ -267,7 +271,7 @@ def run_ours(args, rank, world):
 PATHS_THREAD_INST_PER_STEP = 224.0
 # DRAM bytes (read + write) of one launch from the same captures, or None: the first sweep of
 # k_lu_solve_rl<36> on the 864 disks of the workload (profiles/k_lu_solve_rl_varcoef_mixed.md).
-TRISOLVE_DRAM_BYTES_PER_LAUNCH = 4.21e9 + 0.262e9
+TRISOLVE_DRAM_BYTES_PER_LAUNCH = 4.209e9 + 0.209e9
 # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
 FP32_LANES_PER_SM = 128
 
@@ -351,6 +355,71 @@ def fp64_form(pdd, cfg, stream, flush):
             x, y = g64[rp[i]:rp[i + 1]].numpy(), g32[rp[i]:rp[i + 1]].numpy()
             worst = max(worst, float(abs(x - y).max() / abs(x).max()))
     res["mixed_vs_fp64_floating_rows_max_rel"] = worst
+    return res
+
+
+# The [-50,50]^2 column of the paper's Table 1 (Sec. 5): 1152 A64FX cores, 96 MPI processes,
+# METIS + MUMPS RAS, Gobet-Menozzi paths with pathwise variance reduction.
+TABLE1_50 = {"subdomains": 100, "N": 3636, "sparsity": 0.02066, "rho_C_minus_I": 0.9558,
+             "max_offdiag_C": 0.0445, "kappa2_C": 84.0, "rms_error": 3.72e-5, "gmres_iters": 19,
+             "total_s": 76.0, "solve_s": 1.55}
+
+
+def poisson46_leg(pdd, stream, flush, steps=3):
+    """The paper's Poisson test (Eq. 46) on [-50,50]^2 at its Sec. 5 parameters (5,000 paths per
+    Monte Carlo knot, h = 0.015, boundary shift, 44 knots, 22 x 44 disk nodes, c^2 = 1.5):
+    throughput of the same step, and the statistics of Table 1 computed from the GPU's C, r and u
+    (rho(C - I), max off-diagonal C_ij, kappa_2(C) on the host in FP64)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+
+    import workloads
+    cfg = workloads.poisson46()
+    for _ in range(2):
+        cov, S, u = step(pdd, cfg, "mixed", stream)
+        del cov, S, u
+    times = []
+    for _ in range(steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cov, S, u = step(pdd, cfg, "mixed", stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    st = S.stats()
+    a = {k: v.cpu().numpy() for k, v in cov.arrays().items()}
+    g = {k: v.cpu().numpy() for k, v in S.csr().items()}
+    un = u.cpu().numpy()
+    N = cov.N
+    C = sp.csr_matrix((g["val"], a["col"], a["rowptr"]), shape=(N, N))
+    kx, ky = a["kx"], a["ky"]
+    # u46 of Eq. 46 at the knots (the exact solution, evaluated here for the error statistics)
+    s_ = np.sqrt(1.0 + kx * kx / 100.0 + ky * ky / 50.0)
+    w_ = np.sin(3.0 * kx / 25.0 + ky / 20.0) + np.sin(kx / 20.0 - 3.0 * ky / 25.0)
+    uex = 3.0 + np.sin(s_) / 3.0 + np.tanh(w_) / 3.0
+    err = un - uex
+    Cd = C.toarray()
+    sv = np.linalg.svd(Cd, compute_uv=False)
+    ev = np.linalg.eigvals(Cd - np.eye(N))
+    off = Cd - np.diag(np.diag(Cd))
+    res = {"workload": "poisson46: Omega=[-50,50]^2, Lap u = F with u = Eq. 46; 10x10 square lattice "
+                       "of radius-9 circles (pitch 10); 44 knots/circle, 22x44 disk grid; 5000 paths/knot, "
+                       "h=0.015, boundary shift; c^2=1.5",
+           "value": N / (ms / 1e3), "unit": "knots/s", "ms_per_step": ms, "steps": steps,
+           "mc_path_steps_per_s": st["path_steps"] / (st["ms_paths"] / 1e3),
+           "path_steps_per_step": st["path_steps"],
+           "stages_ms": {k: st[k] for k in ("ms_disks", "ms_factor", "ms_refine", "ms_paths", "ms_finalize")},
+           "gmres": dict(S.last_solve, precond=SOLVE["precond"]),
+           "subdomains": cov.M, "N": N, "sparsity": C.nnz / float(N) ** 2,
+           "rho_C_minus_I": float(np.abs(ev).max()), "max_offdiag_C": float(off.max()),
+           "kappa2_C": float(sv[0] / sv[-1]),
+           "rms_error": float(np.sqrt(np.mean(err * err))), "max_error": float(np.abs(err).max()),
+           "table1_column_50": TABLE1_50}
+    del cov, S, u
     return res
 
 

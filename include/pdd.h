@@ -60,11 +60,16 @@ enum { PDD_B_ZERO = 0, PDD_B_SINX_COSY = 1 };                 /* b = (sin x, cos
 enum { PDD_C_ZERO = 0, PDD_C_QUADRATIC = 1,                    /* c = -(1+x^2+y^2)    */
        PDD_C_RBF = 2 };              /* c = min(0, sum_p w_p exp(-|x-x_p|^2/(2 s^2))) */
 enum { PDD_F_ZERO = 0, PDD_F_ONE = 1,
-       PDD_F_MANUFACTURED = 2 };     /* f = -(L u* + c u*), u* = sin(pi x) cos(pi y)  */
+       PDD_F_MANUFACTURED = 2,       /* f = -(L u* + c u*), u* = sin(pi x) cos(pi y)  */
+       PDD_F_EQ46 = 3 };             /* f = -(L u46 + c u46), u46 = exact solution of
+                                        the Poisson test, Eq. 46:
+                                        3 + sin(sqrt(1+x^2/100+y^2/50))/3
+                                          + tanh(sin(3x/25+y/20) + sin(x/20-3y/25))/3 */
 enum { PDD_G_EXP_SIN = 0,            /* g = e^x sin y                                 */
        PDD_G_SIN_COS = 1,            /* g = sin(pi x) cos(pi y)                       */
        PDD_G_BOUNDARY_FOURIER = 2,   /* g(s) = sum_k a_k cos(2 pi k s/P) + b_k sin(.)  */
-       PDD_G_ONE = 3, PDD_G_ZERO = 4 };
+       PDD_G_ONE = 3, PDD_G_ZERO = 4,
+       PDD_G_EQ46 = 5 };             /* g = u46 (Eq. 46)                              */
 
 typedef struct {
     int b_kind, c_kind, f_kind, g_kind;

@@ -38,7 +38,7 @@ _lib = None
 
 B_KIND = {"zero": 0, "sinx_cosy": 1}
 C_KIND = {"zero": 0, "quadratic": 1, "rbf": 2}
-F_KIND = {"zero": 0, "one": 1, "manufactured": 2}
+F_KIND = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3}
 
 
 def build(force: bool = False) -> str:

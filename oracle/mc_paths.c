@@ -44,7 +44,7 @@ typedef struct {
     double dom[4];
     int b_kind;              /* 0 zero, 1 (sin x, cos y) */
     int c_kind;              /* 0 zero, 1 -(1+x^2+y^2), 2 rbf */
-    int f_kind;              /* 0 zero, 1 one, 2 manufactured sin(pi x)cos(pi y) */
+    int f_kind;              /* 0 zero, 1 one, 2 manufactured sin(pi x)cos(pi y), 3 Eq. 46 */
     int n_rbf;
     const double *rbf_x, *rbf_y, *rbf_w;
     double rbf_sigma;
@@ -128,6 +128,27 @@ static double killing(const oracle_problem *p, double x, double y)
     return 0.0;
 }
 
+/* Exact solution of the Poisson test (Eq. 46) with its gradient and Laplacian:
+ * u = 3 + sin(s)/3 + tanh(w)/3, s = sqrt(1 + x^2/100 + y^2/50),
+ * w = sin(3x/25 + y/20) + sin(x/20 - 3y/25) (chain rule as in problem.py). */
+static void u46(double x, double y, double *u, double *ux, double *uy, double *lap)
+{
+    double s = sqrt(1.0 + x * x / 100.0 + y * y / 50.0);
+    double sx = x / (100.0 * s), sy = y / (50.0 * s);
+    double g2s = sx * sx + sy * sy;
+    double lap_s = (1.0 / 100.0 + 1.0 / 50.0 - g2s) / s;
+    double a = 3.0 * x / 25.0 + y / 20.0, b = x / 20.0 - 3.0 * y / 25.0;
+    double w = sin(a) + sin(b);
+    double wx = 3.0 / 25.0 * cos(a) + cos(b) / 20.0;
+    double wy = cos(a) / 20.0 - 3.0 / 25.0 * cos(b);
+    double lap_w = -((3.0 / 25.0) * (3.0 / 25.0) + (1.0 / 20.0) * (1.0 / 20.0)) * w;
+    double t = tanh(w), sech2 = 1.0 - t * t;
+    *u = 3.0 + sin(s) / 3.0 + t / 3.0;
+    *ux = (cos(s) * sx + sech2 * wx) / 3.0;
+    *uy = (cos(s) * sy + sech2 * wy) / 3.0;
+    *lap = (cos(s) * lap_s - sin(s) * g2s + sech2 * (lap_w - 2.0 * t * (wx * wx + wy * wy))) / 3.0;
+}
+
 static double source(const oracle_problem *p, double x, double y)
 {
     if (p->f_kind == 1) return 1.0;
@@ -139,6 +160,12 @@ static double source(const oracle_problem *p, double x, double y)
         double bx, by;
         drift(p, x, y, &bx, &by);
         return -(-pi * pi * u + bx * ux + by * uy + killing(p, x, y) * u);
+    }
+    if (p->f_kind == 3) {
+        double u, ux, uy, lap, bx, by;
+        u46(x, y, &u, &ux, &uy, &lap);
+        drift(p, x, y, &bx, &by);
+        return -(0.5 * lap + bx * ux + by * uy + killing(p, x, y) * u);
     }
     return 0.0;
 }

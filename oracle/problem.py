@@ -7,11 +7,16 @@ Every workload uses sigma = I, so L = (1/2) Laplacian + b.grad.
 Families (names are shared with ``workloads.py``):
   b: zero | sinx_cosy                 b = (sin x, cos y)
   c: zero | quadratic | rbf           c = -(1+x^2+y^2) | min(0, sum_p w_p exp(-|x-x_p|^2/(2 s^2)))
-  f: zero | one | manufactured        f = -(L u* + c u*) for u* = sin(pi x) cos(pi y)
-  g: exp_sin | sin_cos | boundary_fourier | one | zero
+  f: zero | one | manufactured | eq46
+       manufactured: f = -(L u* + c u*) for u* = sin(pi x) cos(pi y)
+       eq46:         f = -(L u46 + c u46) for u46, the exact solution of the Poisson
+                     test (Eq. 46); with b = c = 0 this is -(1/2) Lap u46, i.e. the
+                     paper's Lap u = F with f = -F/2
+  g: exp_sin | sin_cos | boundary_fourier | one | zero | eq46 (g = u46)
 
-Pins: tests check the manufactured f against finite differences of u*, and
-that e^x sin y is harmonic (the Laplacian of the closed form vanishes).
+Pins: tests check both manufactured sources against finite differences of
+their exact solutions, u46 at points where it has a closed value, and that
+e^x sin y is harmonic (the Laplacian of the closed form vanishes).
 Test infrastructure only.
 """
 from __future__ import annotations
@@ -144,6 +149,37 @@ class Operator:
     def u_star(x, y):
         return np.sin(math.pi * x) * np.cos(math.pi * y)
 
+    # -- exact solution of the Poisson test, Eq. 46 -----------------------------
+    @staticmethod
+    def u46(x, y):
+        """u46 = 3 + sin(s)/3 + tanh(w)/3 with s = sqrt(1 + x^2/100 + y^2/50) and
+        w = sin(3x/25 + y/20) + sin(x/20 - 3y/25) (Eq. 46); returns u, u_x, u_y, Lap u.
+
+        Chain rule: Lap sin(s) = cos(s) Lap s - sin(s) |grad s|^2 with
+        Lap s = (1/100 + 1/50 - |grad s|^2) / s, and Lap tanh(w) = sech^2(w)
+        (Lap w - 2 tanh(w) |grad w|^2) with Lap w = -((3/25)^2 + (1/20)^2) w.
+        """
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        s = np.sqrt(1.0 + x * x / 100.0 + y * y / 50.0)
+        sx = x / (100.0 * s)
+        sy = y / (50.0 * s)
+        g2s = sx * sx + sy * sy
+        lap_s = (1.0 / 100.0 + 1.0 / 50.0 - g2s) / s
+        a = 3.0 * x / 25.0 + y / 20.0
+        b = x / 20.0 - 3.0 * y / 25.0
+        w = np.sin(a) + np.sin(b)
+        wx = 3.0 / 25.0 * np.cos(a) + np.cos(b) / 20.0
+        wy = np.cos(a) / 20.0 - 3.0 / 25.0 * np.cos(b)
+        lap_w = -((3.0 / 25.0) ** 2 + (1.0 / 20.0) ** 2) * w
+        t = np.tanh(w)
+        sech2 = 1.0 - t * t
+        u = 3.0 + np.sin(s) / 3.0 + t / 3.0
+        ux = (np.cos(s) * sx + sech2 * wx) / 3.0
+        uy = (np.cos(s) * sy + sech2 * wy) / 3.0
+        lap = (np.cos(s) * lap_s - np.sin(s) * g2s + sech2 * (lap_w - 2.0 * t * (wx * wx + wy * wy))) / 3.0
+        return u, ux, uy, lap
+
     def f(self, x, y):
         x = np.asarray(x, np.float64)
         y = np.asarray(y, np.float64)
@@ -159,6 +195,10 @@ class Operator:
             half_lap = -pi * pi * u            # (1/2)(u_xx + u_yy) = (1/2)(-2 pi^2 u)
             bx, by = self.b(x, y)
             return -(half_lap + bx * ux + by * uy + self.c(x, y) * u)
+        if self.f_kind == "eq46":
+            u, ux, uy, lap = self.u46(x, y)
+            bx, by = self.b(x, y)
+            return -(0.5 * lap + bx * ux + by * uy + self.c(x, y) * u)
         raise ValueError(self.f_kind)
 
     # -- Dirichlet data --------------------------------------------------------
@@ -180,6 +220,8 @@ class Operator:
             return np.exp(x) * np.sin(y)
         if self.g_kind == "sin_cos":
             return self.u_star(x, y)
+        if self.g_kind == "eq46":
+            return self.u46(x, y)[0]
         if self.g_kind == "one":
             return np.ones_like(x)
         if self.g_kind == "zero":

@@ -30,8 +30,8 @@ PDD_STATUS = {0: "PDD_OK", 1: "PDD_EINVAL", 2: "PDD_ECOVER_GAP", 3: "PDD_ECIRCLE
 
 _B = {"zero": 0, "sinx_cosy": 1}
 _C = {"zero": 0, "quadratic": 1, "rbf": 2}
-_F = {"zero": 0, "one": 1, "manufactured": 2}
-_G = {"exp_sin": 0, "sin_cos": 1, "boundary_fourier": 2, "one": 3, "zero": 4}
+_F = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3}
+_G = {"exp_sin": 0, "sin_cos": 1, "boundary_fourier": 2, "one": 3, "zero": 4, "eq46": 5}
 _COVER = {"square_lattice": 0, "hex_lattice": 1, "explicit": 2}
 PREC = {"fp64": 0, "mixed": 1}
 

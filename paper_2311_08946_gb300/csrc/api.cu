@@ -127,8 +127,8 @@ static void check_spec(const pdd_cover_spec *s) {
 
 static void check_op(const pdd_operator *op) {
     if (!op) fail(PDD_EINVAL, "null operator");
-    if (op->b_kind < 0 || op->b_kind > 1 || op->c_kind < 0 || op->c_kind > 2 || op->f_kind < 0 || op->f_kind > 2 ||
-        op->g_kind < 0 || op->g_kind > 4)
+    if (op->b_kind < 0 || op->b_kind > 1 || op->c_kind < 0 || op->c_kind > 2 || op->f_kind < 0 || op->f_kind > 3 ||
+        op->g_kind < 0 || op->g_kind > 5)
         fail(PDD_EINVAL, "unknown coefficient family");
 }
 

@@ -126,6 +126,40 @@ __device__ __forceinline__ double killing(const Problem &P, double x, double y) 
     return 0.0;
 }
 
+// exact solution of the Poisson test (Eq. 46) with its gradient and Laplacian:
+// u = 3 + sin(s)/3 + tanh(w)/3, s = sqrt(1 + x^2/100 + y^2/50), w = sin(a) + sin(b),
+// a = 3x/25 + y/20, b = x/20 - 3y/25.  Lap s = (1/100 + 1/50 - |grad s|^2)/s and
+// Lap w = -((3/25)^2 + (1/20)^2) w; tanh'' = -2 tanh sech^2.
+__device__ __forceinline__ void sincos_t(double v, double *s, double *c) { sincos(v, s, c); }
+__device__ __forceinline__ void sincos_t(float v, float *s, float *c) { sincosf(v, s, c); }
+__device__ __forceinline__ double sqrt_t(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
+__device__ __forceinline__ double tanh_t(double v) { return tanh(v); }
+__device__ __forceinline__ float tanh_t(float v) { return tanhf(v); }
+
+template <typename T>
+__device__ __forceinline__ void u46_derivs(T x, T y, T &u, T &ux, T &uy, T &lap) {
+    const T s = sqrt_t(T(1) + x * x * T(0.01) + y * y * T(0.02));
+    const T rs = T(1) / s;
+    const T sx = x * T(0.01) * rs, sy = y * T(0.02) * rs;
+    const T g2s = sx * sx + sy * sy;
+    const T lap_s = (T(0.03) - g2s) * rs;
+    const T a = x * T(0.12) + y * T(0.05), b = x * T(0.05) - y * T(0.12);
+    T sa, ca, sb, cb, ss, cs;
+    sincos_t(a, &sa, &ca);
+    sincos_t(b, &sb, &cb);
+    sincos_t(s, &ss, &cs);
+    const T w = sa + sb;
+    const T wx = T(0.12) * ca + T(0.05) * cb, wy = T(0.05) * ca - T(0.12) * cb;
+    const T lap_w = T(-0.0169) * w;
+    const T t = tanh_t(w), sech2 = T(1) - t * t;
+    const T third = T(1) / T(3);
+    u = T(3) + (ss + t) * third;
+    ux = (cs * sx + sech2 * wx) * third;
+    uy = (cs * sy + sech2 * wy) * third;
+    lap = (cs * lap_s - ss * g2s + sech2 * (lap_w - T(2) * t * (wx * wx + wy * wy))) * third;
+}
+
 __device__ __forceinline__ double source(const Problem &P, double x, double y) {
     if (P.f_kind == PDD_F_ONE) return 1.0;
     if (P.f_kind == PDD_F_MANUFACTURED) {
@@ -138,6 +172,12 @@ __device__ __forceinline__ double source(const Problem &P, double x, double y) {
         double bx, by;
         drift(P, x, y, bx, by);
         return -(-PDD_PI * PDD_PI * u + bx * ux + by * uy + killing(P, x, y) * u);
+    }
+    if (P.f_kind == PDD_F_EQ46) {
+        double u, ux, uy, lap, bx, by;
+        u46_derivs(x, y, u, ux, uy, lap);
+        drift(P, x, y, bx, by);
+        return -(0.5 * lap + bx * ux + by * uy + killing(P, x, y) * u);
     }
     return 0.0;
 }
@@ -196,6 +236,11 @@ __device__ __forceinline__ double gdata(const Problem &P, double x, double y, do
         }
         case PDD_G_BOUNDARY_FOURIER: return g_fourier(P, s);
         case PDD_G_ONE: return 1.0;
+        case PDD_G_EQ46: {
+            double u, ux, uy, lap;
+            u46_derivs(x, y, u, ux, uy, lap);
+            return u;
+        }
         default: return 0.0;
     }
 }

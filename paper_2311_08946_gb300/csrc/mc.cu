@@ -183,6 +183,11 @@ __device__ __forceinline__ float source32_given(const Problem &P, float x, float
         const float u = spx * cpy, ux = pi * cpx * cpy, uy = -pi * spx * spy;
         return -(-pi * pi * u + bx * ux + by * uy + cv * u);
     }
+    if (P.f_kind == PDD_F_EQ46) {
+        float u, ux, uy, lap;
+        u46_derivs(x, y, u, ux, uy, lap);
+        return -(0.5f * lap + bx * ux + by * uy + cv * u);
+    }
     return 0.f;
 }
 
@@ -412,6 +417,11 @@ __device__ __forceinline__ float gdata32(const Problem &P, float x, float y, flo
             return acc;
         }
         case PDD_G_ONE: return 1.f;
+        case PDD_G_EQ46: {
+            float u, ux, uy, lap;
+            u46_derivs(x, y, u, ux, uy, lap);
+            return u;
+        }
         default: return 0.f;
     }
 }

@@ -51,7 +51,8 @@ def _np(d):
     return {k: v.cpu().numpy() for k, v in d.items()}
 
 
-COVERS = [("tiny", workloads.tiny), ("varcoef", workloads.varcoef), ("scaled", workloads.scaled)]
+COVERS = [("tiny", workloads.tiny), ("varcoef", workloads.varcoef), ("scaled", workloads.scaled),
+          ("poisson46", workloads.poisson46)]
 
 
 @pytest.mark.parametrize("name,fn", COVERS)
@@ -115,6 +116,80 @@ def test_floating_rows_varcoef_sampled(pdd, precision, factor):
             assert abs(g["b"][i] - bi) <= 1e-10 * max(abs(bi), 1e-3)
     if precision == "mixed":
         assert S.stats()["unconverged_disks"] == 0
+
+
+@pytest.mark.parametrize("precision,factor", [("fp64", "blocked"), ("mixed", "recursive_tc")])
+def test_floating_rows_poisson46_sampled(pdd, precision, factor):
+    """The paper's Poisson test (Eq. 46) on [-50,50]^2: 968-node disks (22 x 44, not a multiple
+    of the LU panel width), 44 knots; 4 disks recomputed by the oracle.  The collocation matrix
+    has kappa ~ 1e5 (Sec. 5), so rows agree to ~kappa u, inside 1e-9."""
+    cfg = workloads.poisson46(paths=16)
+    oc = _oracle_cover("poisson46", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, precision, factor=factor)
+    g = _np(S.csr())
+    rng = np.random.default_rng(46)
+    disks = [m for m in range(oc.M) if oc.floating[m] and oc.sub_rows(m).size]
+    from oracle import problem, spectral
+    op = problem.Operator(cfg["op"], oc.domain)
+    shapes = {}
+    for m in rng.choice(disks, 4, replace=False):
+        for i, (cols, v, bi) in spectral.floating_rows(oc, op, int(m), shapes).items():
+            a, b = oc.rowptr[i], oc.rowptr[i + 1]
+            pos = np.searchsorted(oc.col[a:b], cols)
+            assert _row_err(g["val"][a + pos], v) < 1e-9, (m, i)
+            assert abs(g["b"][i] - bi) <= 1e-9 * max(abs(bi), 1e-3)
+    if precision == "mixed":
+        assert S.stats()["unconverged_disks"] == 0
+
+
+def test_mc_rows_identical_streams_poisson46_sampled(pdd):
+    """Eq. 46 workload with the boundary shift at h = 0.015 (256 paths per knot), FP64 form on
+    the oracle's streams; 6 Monte Carlo rows recomputed."""
+    cfg = workloads.poisson46(paths=256)
+    oc = _oracle_cover("poisson46", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    mc = _np(S.mc())
+    rows = mc["rows"]
+    rng = np.random.default_rng(12)
+    pick = rng.choice(rows.size, 6, replace=False)
+    ref = osystem.assemble(cfg, oc, rows=[int(rows[k]) for k in pick], threads=6)
+    for k in pick:
+        i = int(rows[k])
+        r = ref.mc_rows[i]
+        got = mc["moments"][mc["mom_ptr"][k]:mc["mom_ptr"][k + 1]]
+        assert np.abs(got - r.moments).max() <= 1e-12 * max(1.0, np.abs(r.moments).max()), i
+        assert abs(mc["bmean"][k] - r.b) <= 1e-12 * max(1.0, abs(r.b))
+
+
+def test_solution_poisson46_against_oracle(pdd):
+    """Whole path on the Eq. 46 workload (32 paths per knot, FP64 form, identical streams): the GPU's
+    u against the oracle's assembled-and-solved u; kappa_2(C) ~ 1e2 (Table 1), so 1e-9."""
+    cfg = workloads.poisson46(paths=32)
+    oc = _oracle_cover("poisson46", cfg)
+    S = pdd.System(pdd.Cover(cfg), cfg, "fp64")
+    u = S.solve(rtol=1e-14).cpu().numpy()
+    ref = osystem.assemble(cfg, oc, threads=8)
+    uo = okrylov.solve(ref.csr(), ref.b)
+    assert np.abs(u - uo).max() <= 1e-9 * np.abs(uo).max()
+    assert S.last_solve["converged"]
+
+
+def test_poisson46_full_size_accuracy(pdd):
+    """Sec. 5 parameters (5,000 paths per knot, h = 0.015, boundary shift), mixed form with RAS:
+    the interfacial solution against u46 at the knots.  Without the paper's pathwise variance
+    reduction the error is the Monte Carlo one: 32 paths give RMS ~2e-2 on the oracle, so 5,000
+    give ~2e-3; the bound leaves a factor 2.5."""
+    cfg = workloads.poisson46()
+    cov = pdd.Cover(cfg)
+    S = pdd.System(cov, cfg, "mixed")
+    u = S.solve(rtol=1e-12, precond="ras").cpu().numpy()
+    a = _np(cov.arrays())
+    from oracle import problem
+    uex = problem.Operator.u46(a["kx"], a["ky"])[0]
+    rms = float(np.sqrt(np.mean((u - uex) ** 2)))
+    assert S.last_solve["converged"]
+    assert rms < 5e-3, rms
+    assert S.stats()["unconverged_disks"] == 0
 
 
 @pytest.mark.parametrize("leaf,tmin", [(32, 128), (32, 32), (16, 64), (8, 32), (16, 1000000)])

@@ -39,6 +39,49 @@ def test_exp_sin_is_harmonic():
     assert abs(lap) < 1e-6
 
 
+def test_eq46_solution_pins():
+    """u46 of the Poisson test (Eq. 46): its value at the origin (s = 1, w = 0), the odd symmetry
+    of its tanh part, and its gradient and Laplacian against central differences."""
+    u46 = problem.Operator.u46
+    assert abs(u46(0.0, 0.0)[0] - (3.0 + math.sin(1.0) / 3.0)) < 1e-15
+    rng = np.random.default_rng(46)
+    x, y = rng.uniform(-50, 50, 64), rng.uniform(-50, 50, 64)
+    u, ux, uy, lap = u46(x, y)
+    um = u46(-x, -y)[0]
+    # sin(s) is even in (x, y), tanh(w) odd: u(x) + u(-x) = 6 + 2 sin(s) / 3
+    s = np.sqrt(1.0 + x * x / 100.0 + y * y / 50.0)
+    assert np.abs(u + um - 6.0 - 2.0 * np.sin(s) / 3.0).max() < 1e-14
+    h = 1e-3
+    f = lambda a, b: u46(a, b)[0]
+    fx = (f(x + h, y) - f(x - h, y)) / (2 * h)
+    fy = (f(x, y + h) - f(x, y - h)) / (2 * h)
+    flap = (f(x + h, y) + f(x - h, y) + f(x, y + h) + f(x, y - h) - 4 * f(x, y)) / h ** 2
+    assert np.abs(fx - ux).max() < 1e-8
+    assert np.abs(fy - uy).max() < 1e-8
+    assert np.abs(flap - lap).max() < 1e-6
+    assert np.abs(lap).max() > 1e-2                  # the check above is not vacuous
+
+
+@pytest.mark.parametrize("b,c", [("zero", "zero"), ("sinx_cosy", "quadratic")])
+def test_eq46_source_solves_eq1(b, c):
+    """f = -(L u46 + c u46): (1/2) Lap u + b.grad u + c u + f = 0 by central differences; with
+    b = c = 0 this is the paper's Lap u = F with f = -F/2."""
+    dom = problem.Domain({"kind": "square", "p": [-50.0, -50.0, 50.0, 50.0]})
+    op = problem.Operator({"b": b, "c": c, "f": "eq46", "g": "eq46"}, dom)
+    rng = np.random.default_rng(47)
+    x, y = rng.uniform(-50, 50, 64), rng.uniform(-50, 50, 64)
+    h = 1e-3
+    u = lambda a, bb: problem.Operator.u46(a, bb)[0]
+    uxx = (u(x + h, y) - 2 * u(x, y) + u(x - h, y)) / h ** 2
+    uyy = (u(x, y + h) - 2 * u(x, y) + u(x, y - h)) / h ** 2
+    ux = (u(x + h, y) - u(x - h, y)) / (2 * h)
+    uy = (u(x, y + h) - u(x, y - h)) / (2 * h)
+    bx, by = op.b(x, y)
+    res = 0.5 * (uxx + uyy) + bx * ux + by * uy + op.c(x, y) * u(x, y) + op.f(x, y)
+    assert np.abs(res).max() < 1e-6 * max(1.0, np.abs(op.c(x, y)).max())
+    assert np.allclose(op.g(x, y), u(x, y), rtol=0, atol=0)
+
+
 @pytest.fixture(scope="module")
 def tiny_cover():
     return cover.full_cover(workloads.tiny())

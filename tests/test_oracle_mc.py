@@ -130,6 +130,24 @@ def test_boundary_shift_removes_the_exit_bias():
         assert np.abs(d - R).max() < 1e-12
 
 
+def test_feynman_kac_eq46_on_a_disk():
+    """Feynman-Kac (Eq. 25-27) for the Poisson test of Eq. 46 on a radius-9 disk at h = 0.015
+    with the boundary shift: E[u46(X_tau) + Z_tau] = u46(x0) within 4 SE + the O(h) bias.  This
+    ties the path simulator's source term to the exact solution; E[Z_tau] is far larger than
+    the tolerance, so a dropped or sign-flipped source fails."""
+    dom = problem.Domain({"kind": "square", "p": [-50.0, -50.0, 50.0, 50.0]})
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "eq46", "g": "eq46"}, dom)
+    cx, cy, R, h = 12.0, -7.0, 9.0, 0.015
+    shift = mc.boundary_shift({"h": h, "boundary_shift": True})
+    for (x0, y0) in ((cx, cy), (cx + 4.0, cy - 3.0)):
+        rec = mc.walk(op, cx, cy, R, x0, y0, 5, 2, h, 6000, shift=shift)
+        score = op.u46(rec.ex, rec.ey)[0] + rec.Z
+        est, se = score.mean(), score.std(ddof=1) / math.sqrt(score.size)
+        tol = 4 * se + 20 * h * 1e-2
+        assert abs(est - op.u46(x0, y0)[0]) < tol, (x0, y0, est, se)
+        assert abs(rec.Z.mean()) > 5 * tol
+
+
 def test_harmonic_measure_is_poisson_kernel():
     from oracle import spectral
     cfg, cov = _disk_cover()

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs for the five workloads of the circle-cover interfacial system.
+"""Seeded synthetic inputs for the six workloads of the circle-cover interfacial system.
 
 This module only describes problems: domains, cover lattices (or, for the
 adaptive cover, explicitly drawn centres and radii), coefficient families,
@@ -25,6 +25,13 @@ Workloads (the problem is Eq. 1 with L = 1/2 Laplacian + b.grad, sigma = I):
                    Monte Carlo knot, up to 10^5 where its standard error exceeds 2e-3.
 * ``grad``      -- ``tiny`` geometry; parameters are 64 RBF weights of c and 32
                    Fourier coefficients of g along the boundary arclength.
+* ``poisson46`` -- the paper's Poisson test (Sec. 5, Eq. 46) on [-50,50]^2: f and g from
+                   its exact solution u46, L = 1/2 Lap (so 1/2 Lap u = F/2 with
+                   F = Lap u46); 10x10 square lattice of circles of radius 9 (the
+                   paper's radii lie in [8.55, 9.43]; its layout figure is not
+                   available); 44 knots per circle; 22(r)x44(theta) disk grid (968
+                   nodes); 5,000 paths per Monte Carlo knot, h = 0.015, boundary
+                   shift on (Gobet-Menozzi); c^2 = 1.5.
 
 The random draws a workload needs (RBF centres and weights, adaptive radii,
 observation noise) are made here with numpy's seeded generators and passed to
@@ -41,8 +48,10 @@ import numpy as np
 # Coefficient-family vocabulary shared by both sides (names only).
 #   b:  "zero" | "sinx_cosy"                   b = (sin x, cos y)
 #   c:  "zero" | "quadratic" | "rbf"           c = -(1+x^2+y^2) | min(0, sum_p w_p psi_p(x))
-#   f:  "zero" | "one" | "manufactured"        manufactured from u = sin(pi x) cos(pi y)
-#   g:  "exp_sin" | "sin_cos" | "boundary_fourier" | "one" | "zero"
+#   f:  "zero" | "one" | "manufactured" | "eq46"
+#                                              manufactured from u = sin(pi x) cos(pi y) |
+#                                              from u46, the exact solution of Eq. 46
+#   g:  "exp_sin" | "sin_cos" | "boundary_fourier" | "one" | "zero" | "eq46"
 # --------------------------------------------------------------------------
 
 
@@ -242,5 +251,25 @@ def floating_only_disk(radius: float = 0.3, n_knots: int = 16, n_r: int = 16,
     }
 
 
+def poisson46(paths: int = 5000, h: float = 0.015, seed: int = 0, half_width: float = 50.0,
+              boundary_shift: bool = True) -> dict:
+    """Poisson's equation with the exact solution of Eq. 46 on [-L, L]^2, L = half_width.
+
+    Circles of radius 9 on a square lattice of pitch 10 (centres at -L + 5, ..., L - 5),
+    44 knots each, 22 x 44 pseudospectral nodes on the floating disks, as in Sec. 5.
+    """
+    n = int(round(2.0 * half_width / 10.0))
+    return {
+        "name": "poisson46",
+        "domain": _square(-half_width, -half_width, half_width, half_width),
+        "cover": {"kind": "square_lattice", "nx": n, "ny": n, "x_origin": -half_width + 5.0,
+                  "y_origin": -half_width + 5.0, "spacing": 10.0, "radius": 9.0},
+        "n_knots": 44, "n_r": 22, "n_theta": 44,
+        "op": {"b": "zero", "c": "zero", "f": "eq46", "g": "eq46"},
+        "mc": {"paths": paths, "h": h, "seed": seed, "boundary_shift": boundary_shift},
+        "imq_c2": 1.5,
+    }
+
+
 WORKLOADS = {"tiny": tiny, "varcoef": varcoef, "scaled": scaled, "adaptive": adaptive,
-             "grad": grad}
+             "grad": grad, "poisson46": poisson46}
