@@ -99,7 +99,17 @@ typedef struct {
     int n_explicit;                   /* PDD_COVER_EXPLICIT: number of circles       */
     const double *cx, *cy, *r;        /* host, n_explicit                           */
     const int *n_knots_per, *n_r_per, *n_theta_per;   /* host, n_explicit           */
+    int row_mode;                     /* PDD_ROWS_FARTHEST or PDD_ROWS_AVERAGED     */
 } pdd_cover_spec;
+
+/* Which subdomains a knot's row integrates in (Sec. 3.2):
+ *   FARTHEST: the one whose interface is farthest from the knot (Eq. 29-30);
+ *   AVERAGED: every subdomain whose open disk holds the knot, summed (Eq. 38-39):
+ *             C_ii = #Pi_i, C_ij = the subdomains' entries of their stencils,
+ *             r_i = the sum of their r's.  The k-th subdomain of a row draws its
+ *             paths with Philox counter word 3 = k.  RAS and the adjoint
+ *             gradient take FARTHEST covers only (PDD_EINVAL otherwise). */
+enum { PDD_ROWS_FARTHEST = 0, PDD_ROWS_AVERAGED = 1 };
 
 typedef struct pdd_cover pdd_cover;
 typedef struct pdd_system pdd_system;
@@ -114,7 +124,9 @@ typedef struct pdd_system pdd_system;
  *   (Dirichlet rows).  Knots are numbered circle by circle, each circle's
  *   knots by local angle from the midpoint of its largest outside arc.
  *   Each interior knot's row goes to the circle maximising r_m - |x_i - c_m|
- *   (Sec. 3.2, footnote 3), ties within 1e-12 r to the lowest index.
+ *   (Sec. 3.2, footnote 3), ties within 1e-12 r to the lowest index; with
+ *   row_mode PDD_ROWS_AVERAGED it goes to every circle m != owner with
+ *   r_m - |x_i - c_m| > 1e-12 r_owner (Eq. 38-39).
  *   Requires n_knots and n_theta even, n_r >= 1.  Checks Eq. 5 on a sample
  *   grid of pitch min(r)/4 (PDD_ECOVER_GAP).  Synchronises `stream`.
  */
@@ -237,8 +249,24 @@ pdd_status pdd_system_csr(const pdd_system *sys, const double **val, const doubl
                           const double **se, const double **se_b);
 
 /*
+ * pdd_cover_rows -- the subdomains each row integrates in (device, owned by
+ * the cover): Pi_i = pi_sub[pi_ptr[i] .. pi_ptr[i+1]) (int32, ascending); one
+ * entry per interior row for PDD_ROWS_FARTHEST, every circle holding the knot
+ * for PDD_ROWS_AVERAGED, none for Dirichlet rows.  n_pairs = pi_ptr[N].
+ */
+pdd_status pdd_cover_rows(const pdd_cover *cov, int *n_pairs, const int **pi_ptr, const int **pi_sub);
+
+/*
+ * pdd_system_mc_subs -- the subdomain (device int32, owned by the system) of
+ * each Monte Carlo slot of pdd_system_mc: slot k integrates knot rows[k] in
+ * circle subs[k].  With averaged rows a knot has one slot per subdomain.
+ */
+pdd_status pdd_system_mc_subs(const pdd_system *sys, const int **subs);
+
+/*
  * pdd_system_mc -- the raw Monte Carlo estimates (device, owned by the
- * system): for the k-th Monte Carlo row (row id rows[k]), moments
+ * system): for the k-th Monte Carlo slot (row id rows[k], subdomain
+ * pdd_system_mc_subs), moments
  * [mom_ptr[k], mom_ptr[k+1]) hold E[1_Gamma Y_tau phi_l(u_tau)] (IMQ basis) or
  * E[1_Gamma Y_tau H_j] (Fourier cardinals), and bmean[k] = E[1_dOmega g Y + Z].
  */

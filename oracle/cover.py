@@ -68,6 +68,9 @@ class Cover:
     kowner: np.ndarray = None
     kdir: np.ndarray = None       # bool: knot on dOmega (Dirichlet row)
     row_sub: np.ndarray = None    # int[N], -1 for Dirichlet rows
+    row_mode: str = "farthest"    # "farthest" (Sec. 3.2) or "averaged" (Eq. 38-39)
+    pi_ptr: np.ndarray = None     # int[N+1]: Pi_i = pi_sub[pi_ptr[i]:pi_ptr[i+1]], ascending
+    pi_sub: np.ndarray = None     # the subdomains whose rows include knot i
     rowptr: np.ndarray = None
     col: np.ndarray = None
     extra: dict = field(default_factory=dict)
@@ -80,8 +83,15 @@ class Cover:
     def N(self):
         return int(self.kx.size)
 
+    def pi(self, i):
+        """The subdomains integrated for row i: {row_sub[i]} (farthest interface), or every
+        subdomain containing x_i (averaged rows, Eq. 38-39); empty for Dirichlet rows."""
+        return self.pi_sub[self.pi_ptr[i]:self.pi_ptr[i + 1]]
+
     def sub_rows(self, m):
-        return np.nonzero(self.row_sub == m)[0]
+        """Rows that subdomain m contributes to, ascending."""
+        rows = np.repeat(np.arange(self.N), np.diff(self.pi_ptr))
+        return rows[self.pi_sub == m]
 
 
 # --------------------------------------------------------------------------
@@ -335,10 +345,18 @@ def duplicate_knots(cov: Cover, tol: float = 1e-12):
 # a4: row assignment (Sec. 3.2 and its footnote)
 # --------------------------------------------------------------------------
 
-def assign_rows(cov: Cover, chunk: int = 2048) -> Cover:
-    """m(i) = argmax_{m != owner, x_i in O_m} (r_m - |x_i - c_m|); -1 for Dirichlet rows."""
+def assign_rows(cov: Cover, chunk: int = 2048, mode: str = "farthest") -> Cover:
+    """m(i) = argmax_{m != owner, x_i in O_m} (r_m - |x_i - c_m|); -1 for Dirichlet rows.
+
+    Pi_i: {m(i)} (Sec. 3.2), or with mode "averaged" every subdomain whose open disk holds x_i
+    (Eq. 38-39: Pi_i = {Omega_k : x_i in Omega_k}), ascending.  "Holds" is the same test as the
+    candidates of m(i): r_m - |x_i - c_m| > 1e-12 r_owner.
+    """
+    if mode not in ("farthest", "averaged"):
+        raise CoverError("EINVAL", f"unknown row mode {mode}")
     N = cov.N
     row_sub = np.full(N, -1, np.int64)
+    pis = [np.zeros(0, np.int64)] * N
     for a in range(0, N, chunk):
         sl = slice(a, min(N, a + chunk))
         dx = cov.kx[sl, None] - cov.cx[None, :]
@@ -359,7 +377,11 @@ def assign_rows(cov: Cover, chunk: int = 2048) -> Cover:
                 raise CoverError("EKNOT_UNCOVERED", f"knot {i} is inside no other circle")
             cand = np.nonzero(s[q] >= best[q] - eps[q])[0]
             row_sub[i] = int(cand.min())
+            pis[i] = np.nonzero(inside[q])[0] if mode == "averaged" else np.array([row_sub[i]])
     cov.row_sub = row_sub
+    cov.row_mode = mode
+    cov.pi_ptr = np.concatenate([[0], np.cumsum([p.size for p in pis])]).astype(np.int64)
+    cov.pi_sub = np.concatenate(pis).astype(np.int64) if N else np.zeros(0, np.int64)
     return cov
 
 
@@ -368,16 +390,14 @@ def assign_rows(cov: Cover, chunk: int = 2048) -> Cover:
 # --------------------------------------------------------------------------
 
 def csr_pattern(cov: Cover) -> Cover:
+    """Row i: the diagonal and the stencils Xi_m of every m in Pi_i, columns sorted."""
     rowptr = [0]
     cols = []
     for i in range(cov.N):
-        m = cov.row_sub[i]
-        if m < 0:
-            cols.append(i)
-        else:
-            c = list(range(int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])))
-            c.append(i)
-            cols.extend(sorted(c))
+        c = [i]
+        for m in cov.pi(i):
+            c.extend(range(int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])))
+        cols.extend(sorted(c))
         rowptr.append(len(cols))
     cov.rowptr = np.array(rowptr, np.int64)
     cov.col = np.array(cols, np.int64)
@@ -395,6 +415,6 @@ def full_cover(cfg: dict, check_coverage: bool = True) -> Cover:
     build_knots(cov)
     if duplicate_knots(cov):
         raise CoverError("EINVAL", "two knots coincide")
-    assign_rows(cov)
+    assign_rows(cov, mode=cfg["cover"].get("rows", "farthest"))
     csr_pattern(cov)
     return cov

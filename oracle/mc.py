@@ -61,7 +61,7 @@ class _Problem(ctypes.Structure):
 class _Walk(ctypes.Structure):
     _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("knot", ctypes.c_uint32),
-                ("seed", ctypes.c_uint64), ("h", ctypes.c_double), ("n_paths", ctypes.c_int),
+                ("sub", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("h", ctypes.c_double), ("n_paths", ctypes.c_int),
                 ("max_steps", ctypes.c_int), ("shift", ctypes.c_double)]
 
 
@@ -94,10 +94,10 @@ def philox(ctr, key):
     return [int(v) for v in o]
 
 
-def normals(seed, knot, step, path):
+def normals(seed, knot, step, path, sub=0):
     xi = (ctypes.c_double * 2)()
-    lib().oracle_normals(ctypes.c_uint64(seed), ctypes.c_uint32(knot), ctypes.c_uint32(step),
-                         ctypes.c_uint32(path), xi)
+    lib().oracle_normals(ctypes.c_uint64(seed), ctypes.c_uint32(knot), ctypes.c_uint32(sub),
+                         ctypes.c_uint32(step), ctypes.c_uint32(path), xi)
     return xi[0], xi[1]
 
 
@@ -128,7 +128,7 @@ def max_steps_for(r, h):
 
 
 def walk(op: Operator, cx, cy, r, x0, y0, knot, seed, h, n_paths, with_grad=False,
-         max_steps=None, shift=0.0) -> PathRecords:
+         max_steps=None, shift=0.0, sub=0) -> PathRecords:
     dom = op.domain
     nr = op.rbf_w.size if with_grad else 0
     rec = PathRecords(n_paths, nr)
@@ -138,7 +138,7 @@ def walk(op: Operator, cx, cy, r, x0, y0, knot, seed, h, n_paths, with_grad=Fals
                     int(op.rbf_w.size), _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]),
                     op.rbf_sigma)
     ms = max_steps_for(r, h) if max_steps is None else int(max_steps)
-    w = _Walk(cx, cy, r, x0, y0, int(knot), int(seed), h, int(n_paths), ms, float(shift))
+    w = _Walk(cx, cy, r, x0, y0, int(knot), int(sub), int(seed), h, int(n_paths), ms, float(shift))
     got = lib().oracle_walk_knot(ctypes.byref(prob), ctypes.byref(w), _ptr(rec.side),
                                  _ptr(rec.edge), _ptr(rec.ex), _ptr(rec.ey), _ptr(rec.etheta),
                                  _ptr(rec.Y), _ptr(rec.Z), _ptr(rec.steps), _ptr(rec.dY),
@@ -207,10 +207,20 @@ def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = 
     return row
 
 
+def _sub_index(cov, i, m):
+    """Position of m in Pi_i (the Philox counter word that keeps the paths of a row's
+    subdomains independent when the row averages several, Eq. 38-39); 0 otherwise."""
+    if getattr(cov, "pi_ptr", None) is None:
+        return 0
+    hit = np.nonzero(cov.pi(i) == m)[0]
+    return int(hit[0]) if hit.size else 0
+
+
 def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis, with_grad, Kinv, P) -> McRow:
     cx, cy, r = float(cov.cx[m]), float(cov.cy[m]), float(cov.r[m])
     rec = walk(op, cx, cy, r, float(cov.kx[i]), float(cov.ky[i]), i, int(mc["seed"]),
-               float(mc["h"]), P, with_grad=with_grad, shift=boundary_shift(mc))
+               float(mc["h"]), P, with_grad=with_grad, shift=boundary_shift(mc),
+               sub=_sub_index(cov, i, m))
     if rec.capped:
         raise RuntimeError(f"EPATH_CAP: {rec.capped} paths of knot {i} hit the step cap")
     a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
@@ -251,28 +261,34 @@ def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis,
 
 def mc_rows(cov, op: Operator, rows, mc: dict, c2: float, threads: int = 1, basis=None,
             with_grad=False):
-    """Monte Carlo rows for a list of knots (each with its own subdomain)."""
+    """Monte Carlo rows for a list of knots i (integrated in their subdomain row_sub[i], keyed
+    by i) or of pairs (i, m) (knot i integrated in subdomain m, keyed by (i, m))."""
     Kcache = {}
 
-    def one(i):
-        m = int(cov.row_sub[i])
+    def pair(item):
+        if isinstance(item, tuple):
+            return int(item[0]), int(item[1]), item
+        return int(item), int(cov.row_sub[item]), int(item)
+
+    def kinv(m):
+        if m not in Kcache:
+            a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
+            Kcache[m] = imq.inverse(cov.ku[a:b], c2) if b > a else np.zeros((0, 0))
+        return Kcache[m]
+
+    def one(item):
+        i, m, key = pair(item)
         bas = basis or ("fourier" if cov.floating[m] else "imq")
-        Kinv = None
-        if bas == "imq":
-            if m not in Kcache:
-                a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
-                Kcache[m] = imq.inverse(cov.ku[a:b], c2) if b > a else np.zeros((0, 0))
-            Kinv = Kcache[m]
-        return int(i), mc_row(cov, op, int(i), m, mc, c2, bas, with_grad, Kinv)
+        Kinv = kinv(m) if bas == "imq" else None
+        return key, mc_row(cov, op, i, m, mc, c2, bas, with_grad, Kinv)
 
     lib()
     if threads <= 1:
-        return dict(one(i) for i in rows)
+        return dict(one(item) for item in rows)
     # build the IMQ inverses first so the worker threads only read the cache
-    for i in rows:
-        m = int(cov.row_sub[i])
-        if not cov.floating[m] and m not in Kcache:
-            a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
-            Kcache[m] = imq.inverse(cov.ku[a:b], c2) if b > a else np.zeros((0, 0))
+    for item in rows:
+        i, m, _ = pair(item)
+        if not cov.floating[m] and (basis or "imq") == "imq":
+            kinv(m)
     with ThreadPoolExecutor(threads) as ex:
         return dict(ex.map(one, rows))

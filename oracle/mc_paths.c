@@ -26,7 +26,8 @@
  * the true boundary (radial for circles, onto the edge for the square).
  *
  * Normals: Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo32, knot) and
- * counter (step, path, 0, 0).  The four 32-bit words (a, b, c, d) give two
+ * counter (step, path, 0, k), k = the position of the subdomain in the row's
+ * list Pi_i (0 unless the row averages several subdomains, Eq. 38-39).  The four 32-bit words (a, b, c, d) give two
  * 53-bit uniforms u1 = ((a << 21) ^ (b >> 11) + 0.5) 2^-53 and likewise u2
  * from (c, d); Box-Muller gives xi = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
  *
@@ -54,6 +55,7 @@ typedef struct {
     double cx, cy, r;        /* the subdomain's circle */
     double x0, y0;           /* the knot */
     uint32_t knot;
+    uint32_t sub;            /* position of the subdomain in Pi_i (Philox counter word 3) */
     uint64_t seed;
     double h;
     int n_paths;
@@ -90,9 +92,9 @@ static double uniform53(uint32_t a, uint32_t b)
     return ((double)m + 0.5) * 1.1102230246251565e-16;   /* 2^-53 */
 }
 
-void oracle_normals(uint64_t seed, uint32_t knot, uint32_t step, uint32_t path, double *xi)
+void oracle_normals(uint64_t seed, uint32_t knot, uint32_t sub, uint32_t step, uint32_t path, double *xi)
 {
-    uint32_t ctr[4] = {step, path, 0u, 0u};
+    uint32_t ctr[4] = {step, path, 0u, sub};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), knot};
     uint32_t w[4];
     philox4x32_10(ctr, key, w);
@@ -225,7 +227,7 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
                 break;
             }
             double xi[2];
-            oracle_normals(w->seed, w->knot, (uint32_t)k, (uint32_t)path, xi);
+            oracle_normals(w->seed, w->knot, w->sub, (uint32_t)k, (uint32_t)path, xi);
             double bx, by;
             drift(p, x, y, &bx, &by);
             double cv = killing(p, x, y);

@@ -64,7 +64,11 @@ class _CoverSpec(ctypes.Structure):
                 ("n_knots", ctypes.c_int), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
                 ("n_explicit", ctypes.c_int), ("cx", ctypes.c_void_p), ("cy", ctypes.c_void_p),
                 ("r", ctypes.c_void_p), ("n_knots_per", ctypes.c_void_p),
-                ("n_r_per", ctypes.c_void_p), ("n_theta_per", ctypes.c_void_p)]
+                ("n_r_per", ctypes.c_void_p), ("n_theta_per", ctypes.c_void_p),
+                ("row_mode", ctypes.c_int)]
+
+
+ROW_MODE = {"farthest": 0, "averaged": 1}
 
 
 class _AssemblyOpts(ctypes.Structure):
@@ -106,6 +110,7 @@ EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
            "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
            "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_grad", "pdd_ras_apply",
+           "pdd_cover_rows", "pdd_system_mc_subs",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
 _lib = None
@@ -230,12 +235,13 @@ def cover_struct(cfg: dict):
         nt = np.ascontiguousarray(c["n_theta"], np.int32)
         keep = [cx, cy, r, nk, nr, nt]
         s = _CoverSpec(2, 0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, cx.size, cx.ctypes.data, cy.ctypes.data,
-                       r.ctypes.data, nk.ctypes.data, nr.ctypes.data, nt.ctypes.data)
+                       r.ctypes.data, nk.ctypes.data, nr.ctypes.data, nt.ctypes.data,
+                       ROW_MODE[c.get("rows", "farthest")])
     else:
         s = _CoverSpec(_COVER[c["kind"]], int(c["nx"]), int(c["ny"]), float(c["x_origin"]),
                        float(c["y_origin"]), float(c["spacing"]), float(c["radius"]),
                        int(cfg["n_knots"]), int(cfg["n_r"]), int(cfg["n_theta"]), 0, None, None, None,
-                       None, None, None)
+                       None, None, None, ROW_MODE[c.get("rows", "farthest")])
     return s, keep
 
 
@@ -287,8 +293,14 @@ class Cover:
                  ("kx", N, torch.float64), ("ky", N, torch.float64), ("ku", N, torch.float64),
                  ("kowner", N, torch.int32), ("kdir", N, torch.uint8), ("row_sub", N, torch.int32),
                  ("rowptr", N + 1, torch.int32), ("col", nnz, torch.int32)]
+        npairs = ctypes.c_int()
+        pp = [ctypes.c_void_p() for _ in range(2)]
+        _check(load().pdd_cover_rows(self._h, ctypes.byref(npairs), *[ctypes.byref(p) for p in pp]))
         torch.cuda.synchronize()
-        return {nm: _to_tensor(p.value, n, dt) for (nm, n, dt), p in zip(names, ps)}
+        out = {nm: _to_tensor(p.value, n, dt) for (nm, n, dt), p in zip(names, ps)}
+        out["pi_ptr"] = _to_tensor(pp[0].value, N + 1, torch.int32)
+        out["pi_sub"] = _to_tensor(pp[1].value, npairs.value, torch.int32)
+        return out
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -335,7 +347,10 @@ class System:
         rows = _to_tensor(ps[0].value, k, torch.int32)
         mp = _to_tensor(ps[1].value, k + 1, torch.int32)
         nm = int(mp[-1].item()) if k else 0
-        return {"rows": rows, "mom_ptr": mp, "moments": _to_tensor(ps[2].value, nm, torch.float64),
+        sp = ctypes.c_void_p()
+        _check(load().pdd_system_mc_subs(self._h, ctypes.byref(sp)))
+        return {"rows": rows, "subs": _to_tensor(sp.value, k, torch.int32), "mom_ptr": mp,
+                "moments": _to_tensor(ps[2].value, nm, torch.float64),
                 "bmean": _to_tensor(ps[3].value, k, torch.float64)}
 
     def stats(self) -> dict:

@@ -68,16 +68,20 @@ void ProblemHolder::set(const pdd_domain &dom, const pdd_operator &op, cudaStrea
                                                   : 2.0 * PDD_PI * dom.p[2];
 }
 
-// diagonal ones (Eq. 29) and Dirichlet rows C_ii = 1, r_i = g(x_i)
-__global__ void k_diag_dirichlet(Problem P, int N, const int *row_sub, const int *knot_ptr, const int *rowptr,
-                                 const double *kx, const double *ky, double *val, double *b) {
+// the diagonal, C_ii = #Pi_i (1 for one subdomain, Eq. 29; Eq. 38 for averaged rows), and
+// Dirichlet rows C_ii = 1, r_i = g(x_i); the diagonal sits after the stencils below i
+__global__ void k_diag_dirichlet(Problem P, int N, const int *pi_ptr, const int *pi_sub, const int *knot_ptr,
+                                 const int *rowptr, const double *kx, const double *ky, double *val, double *b) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int m = row_sub[i];
+    const int e0 = pi_ptr[i], e1 = pi_ptr[i + 1];
     int pos = rowptr[i];
-    if (m >= 0 && i > knot_ptr[m]) pos += knot_ptr[m + 1] - knot_ptr[m];
-    val[pos] = 1.0;
-    if (m < 0) {
+    for (int e = e0; e < e1; ++e) {
+        const int m = pi_sub[e];
+        if (knot_ptr[m] < i) pos += knot_ptr[m + 1] - knot_ptr[m];
+    }
+    val[pos] = e1 > e0 ? (double)(e1 - e0) : 1.0;
+    if (e1 == e0) {
         const double x = kx[i], y = ky[i];
         double s = 0.0;
         if (P.g_kind == PDD_G_BOUNDARY_FOURIER) s = boundary_s(P, x, y, nearest_edge(P, x, y));
@@ -86,8 +90,26 @@ __global__ void k_diag_dirichlet(Problem P, int N, const int *row_sub, const int
 }
 
 void assemble_dirichlet(const pdd_cover &cov, const Problem &P, pdd_system &sys, cudaStream_t st) {
-    PDD_LAUNCH(k_diag_dirichlet, cdiv(cov.N, 256), 256, 0, st, P, cov.N, cov.row_sub.p, cov.knot_ptr.p,
-               cov.rowptr.p, cov.kx.p, cov.ky.p, sys.val.p, sys.b.p);
+    PDD_LAUNCH(k_diag_dirichlet, cdiv(cov.N, 256), 256, 0, st, P, cov.N, cov.pi_ptr.p, cov.pi_sub.p,
+               cov.knot_ptr.p, cov.rowptr.p, cov.kx.p, cov.ky.p, sys.val.p, sys.b.p);
+}
+
+// r_i = the sum of its subdomains' r's in the order of Pi_i (Eq. 30; Eq. 39), and the root sum
+// of squares of their standard errors (independent paths)
+__global__ void k_gather_rows(int N, const int *pi_ptr, const int *pair_spos, const double *bs,
+                              const double *se_bs, double *b, double *se_b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int e0 = pi_ptr[i], e1 = pi_ptr[i + 1];
+    if (e1 == e0) return;                          // Dirichlet row
+    double s = 0.0, v = 0.0;
+    for (int e = e0; e < e1; ++e) {
+        const int p = pair_spos[e];
+        s += bs[p];
+        v += se_bs[p] * se_bs[p];
+    }
+    b[i] = s;
+    se_b[i] = sqrt(v);
 }
 
 static void check_domain(const pdd_domain *d) {
@@ -123,6 +145,7 @@ static void check_spec(const pdd_cover_spec *s) {
     } else {
         fail(PDD_EINVAL, "unknown cover kind");
     }
+    if (s->row_mode != PDD_ROWS_FARTHEST && s->row_mode != PDD_ROWS_AVERAGED) fail(PDD_EINVAL, "unknown row mode");
 }
 
 static void check_op(const pdd_operator *op) {
@@ -237,6 +260,11 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         s->precision = opts->precision;
         s->val.alloc(cov->nnz);
         s->b.alloc(cov->N);
+        const int nsub = std::max(cov->h_sub_ptr.empty() ? 0 : cov->h_sub_ptr.back(), 1);
+        s->bs.alloc(nsub);
+        s->se_bs.alloc(nsub);
+        PDD_CUDA(cudaMemsetAsync(s->bs.p, 0, sizeof(double) * nsub, st));
+        PDD_CUDA(cudaMemsetAsync(s->se_bs.p, 0, sizeof(double) * nsub, st));
         s->se.alloc(cov->nnz);
         s->se_b.alloc(cov->N);
         PDD_CUDA(cudaMemsetAsync(s->val.p, 0, sizeof(double) * cov->nnz, st));
@@ -263,6 +291,8 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         cudaEventDestroy(e1);
         cudaEventDestroy(e2);
         McStats ms = assemble_mc(*cov, ph.P, *opts, *s, st);
+        PDD_LAUNCH(k_gather_rows, cdiv(cov->N, 256), 256, 0, st, cov->N, cov->pi_ptr.p, cov->pair_spos.p, s->bs.p,
+                   s->se_bs.p, s->b.p, s->se_b.p);
         PDD_CUDA(cudaStreamSynchronize(st));
         pdd_assembly_stats &S = s->stats;
         S.floating_disks = ds.disks;
@@ -320,6 +350,22 @@ pdd_status pdd_system_mc(const pdd_system *sys, int *n_rows, const int **rows, c
     if (mom_ptr) *mom_ptr = sys->mom_ptr.p;
     if (moments) *moments = sys->moments.p;
     if (bmean) *bmean = sys->bmean.p;
+    API_END
+}
+
+pdd_status pdd_cover_rows(const pdd_cover *cov, int *n_pairs, const int **pi_ptr, const int **pi_sub) {
+    API_BEGIN
+    if (!cov) fail(PDD_EINVAL, "null cover");
+    if (n_pairs) *n_pairs = cov->npairs;
+    if (pi_ptr) *pi_ptr = cov->pi_ptr.p;
+    if (pi_sub) *pi_sub = cov->pi_sub.p;
+    API_END
+}
+
+pdd_status pdd_system_mc_subs(const pdd_system *sys, const int **subs) {
+    API_BEGIN
+    if (!sys) fail(PDD_EINVAL, "null system");
+    if (subs) *subs = sys->mc_subs.p;
     API_END
 }
 
@@ -381,6 +427,7 @@ pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *
     check_solve_opts(opts);
     if (opts->transpose) fail(PDD_EINVAL, "the preconditioned solve takes C itself (transpose = 0)");
     if (!u) fail(PDD_EINVAL, "null u");
+    if (sys->cov->averaged) fail(PDD_EINVAL, "the RAS subsets need one subdomain per row (a farthest-interface cover)");
     cudaStream_t st = (cudaStream_t)stream;
     RasPrecond M;
     M.build(*sys->cov, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, st);
@@ -397,6 +444,7 @@ pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *
 pdd_status pdd_ras_apply(const pdd_system *sys, const double *v, double *y, void *stream) {
     API_BEGIN
     if (!sys || !v || !y) fail(PDD_EINVAL, "null argument");
+    if (sys->cov->averaged) fail(PDD_EINVAL, "the RAS subsets need one subdomain per row (a farthest-interface cover)");
     cudaStream_t st = (cudaStream_t)stream;
     RasPrecond M;
     M.build(*sys->cov, sys->cov->rowptr.p, sys->cov->col.p, sys->val.p, st);
@@ -431,6 +479,7 @@ pdd_status pdd_grad(const pdd_cover *cov, const pdd_operator *op, const pdd_asse
     API_BEGIN
     if (!cov || !sys || !u || !dJdu || !grad) fail(PDD_EINVAL, "null argument");
     if (sys->cov != cov) fail(PDD_EINVAL, "system was not assembled on this cover");
+    if (cov->averaged) fail(PDD_EINVAL, "the adjoint gradient needs one subdomain per row (a farthest-interface cover)");
     check_op(op);
     check_opts(opts);
     cudaStream_t st = (cudaStream_t)stream;

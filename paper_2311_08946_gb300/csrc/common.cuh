@@ -286,9 +286,11 @@ __device__ __forceinline__ double uniform53(uint32_t a, uint32_t b) {
     return ((double)m + 0.5) * 1.1102230246251565e-16;
 }
 
-__device__ __forceinline__ void normals64(uint64_t seed, uint32_t knot, uint32_t step, uint32_t path,
+// key (seed_lo32, knot), counter (step, path, 0, sub): sub is the position of the subdomain in the
+// row's list Pi_i (0 unless the row averages several subdomains)
+__device__ __forceinline__ void normals64(uint64_t seed, uint32_t knot, uint32_t sub, uint32_t step, uint32_t path,
                                           double &xi0, double &xi1) {
-    U4 w = philox10(step, path, 0u, 0u, (uint32_t)(seed & 0xffffffffu), knot);
+    U4 w = philox10(step, path, 0u, sub, (uint32_t)(seed & 0xffffffffu), knot);
     double u1 = uniform53(w.x, w.y);
     double u2 = uniform53(w.z, w.w);
     double rr = sqrt(-2.0 * log(u1));
@@ -327,9 +329,9 @@ __device__ __forceinline__ float uniform23(uint32_t w) {
     return (__uint_as_float(0x3f800000u | (w >> 9)) - 1.0f) + 0x1p-24f;
 }
 
-__device__ __forceinline__ void normals32(uint64_t seed, uint32_t knot, uint32_t step, uint32_t path,
+__device__ __forceinline__ void normals32(uint64_t seed, uint32_t knot, uint32_t sub, uint32_t step, uint32_t path,
                                           float &xi0, float &xi1) {
-    U4 w = philox10(step, path, 0u, 0u, (uint32_t)(seed & 0xffffffffu), knot);
+    U4 w = philox10(step, path, 0u, sub, (uint32_t)(seed & 0xffffffffu), knot);
     const float u1 = uniform23(w.x);
     const float u2 = uniform23(w.z);
     const float rr = sqrtf(-2.0f * __logf(u1));

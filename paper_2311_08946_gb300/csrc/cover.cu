@@ -456,41 +456,143 @@ __global__ void k_dup_knots(Grid G, int N, const double *kx, const double *ky, c
 }
 
 // ---------------------------------------------------------------------------
-// a5: CSR pattern and rows grouped by subdomain
+// Pi_i: the subdomains a row integrates in.  One (the farthest interface, Sec.
+// 3.2) or, for averaged rows (Eq. 38-39), every subdomain whose open disk holds
+// the knot -- the same "inside" test as the candidates of k_assign_rows --
+// listed in ascending order.
 // ---------------------------------------------------------------------------
-__global__ void k_row_len(int N, const int *row_sub, const int *knot_ptr, int *len, int *sub_cnt) {
+__global__ void k_pi_count(Grid G, int N, int averaged, const double *kx, const double *ky, const int *kowner,
+                           const int *row_sub, const int *cptr, const int *citems, const double *cx,
+                           const double *cy, const double *r, int *cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int m = row_sub[i];
-    if (m < 0) {
-        len[i] = 1;
-    } else {
-        len[i] = 1 + knot_ptr[m + 1] - knot_ptr[m];
-        atomicAdd(&sub_cnt[m], 1);
-    }
-}
-
-__global__ void k_csr_cols(int N, const int *row_sub, const int *knot_ptr, const int *rowptr, int *col) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int m = row_sub[i], p = rowptr[i];
-    if (m < 0) {
-        col[p] = i;
+    if (row_sub[i] < 0) {
+        cnt[i] = 0;
         return;
     }
-    int a = knot_ptr[m], b = knot_ptr[m + 1];
-    if (i < a) col[p++] = i;
-    for (int j = a; j < b; ++j) col[p++] = j;
-    if (i >= b) col[p] = i;
+    if (!averaged) {
+        cnt[i] = 1;
+        return;
+    }
+    const double x = kx[i], y = ky[i];
+    const int own = kowner[i];
+    const double eps = kScoreEps * r[own];
+    int c = G.cell_of(x, y), ix = c % G.gx, iy = c / G.gx, n = 0;
+    for (int b = max(0, iy - 1); b <= min(G.gy - 1, iy + 1); ++b)
+        for (int a = max(0, ix - 1); a <= min(G.gx - 1, ix + 1); ++a) {
+            int cc = b * G.gx + a;
+            for (int q = cptr[cc]; q < cptr[cc + 1]; ++q) {
+                int m = citems[q];
+                if (m == own) continue;
+                double dx = x - cx[m], dy = y - cy[m];
+                if (r[m] - sqrt(dx * dx + dy * dy) > eps) ++n;
+            }
+        }
+    cnt[i] = n;
 }
 
-__global__ void k_sub_fill(int N, const int *row_sub, const int *sub_ptr, int *cursor, int *sub_rows) {
+__global__ void k_pi_fill(Grid G, int N, int averaged, const double *kx, const double *ky, const int *kowner,
+                          const int *row_sub, const int *cptr, const int *citems, const double *cx,
+                          const double *cy, const double *r, const int *pi_ptr, int *pi_sub) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || row_sub[i] < 0) return;
+    int *out = pi_sub + pi_ptr[i];
+    if (!averaged) {
+        out[0] = row_sub[i];
+        return;
+    }
+    const double x = kx[i], y = ky[i];
+    const int own = kowner[i];
+    const double eps = kScoreEps * r[own];
+    int c = G.cell_of(x, y), ix = c % G.gx, iy = c / G.gx, n = 0;
+    for (int b = max(0, iy - 1); b <= min(G.gy - 1, iy + 1); ++b)
+        for (int a = max(0, ix - 1); a <= min(G.gx - 1, ix + 1); ++a) {
+            int cc = b * G.gx + a;
+            for (int q = cptr[cc]; q < cptr[cc + 1]; ++q) {
+                int m = citems[q];
+                if (m == own) continue;
+                double dx = x - cx[m], dy = y - cy[m];
+                if (!(r[m] - sqrt(dx * dx + dy * dy) > eps)) continue;
+                int k = n++;                               // insertion into the ascending list
+                while (k > 0 && out[k - 1] > m) {
+                    out[k] = out[k - 1];
+                    --k;
+                }
+                out[k] = m;
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// a5: CSR pattern (Eq. 29; Eq. 38 for averaged rows) and rows grouped by
+// subdomain.  Row i holds the diagonal and the stencils Xi_m of every m in
+// Pi_i; the stencils are disjoint knot ranges in the order of m, and i lies in
+// none of them (a knot is on its own circle, not inside it).
+// ---------------------------------------------------------------------------
+__global__ void k_row_len(int N, const int *pi_ptr, const int *pi_sub, const int *knot_ptr, int *len,
+                          int *sub_cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int m = row_sub[i];
-    if (m < 0) return;
-    int p = atomicAdd(&cursor[m], 1);
-    sub_rows[sub_ptr[m] + p] = i;
+    int n = 1;
+    for (int e = pi_ptr[i]; e < pi_ptr[i + 1]; ++e) {
+        const int m = pi_sub[e];
+        n += knot_ptr[m + 1] - knot_ptr[m];
+        atomicAdd(&sub_cnt[m], 1);
+    }
+    len[i] = n;
+}
+
+__global__ void k_csr_cols(int N, const int *pi_ptr, const int *pi_sub, const int *knot_ptr, const int *rowptr,
+                           int *col) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int p = rowptr[i];
+    bool diag = false;
+    for (int e = pi_ptr[i]; e < pi_ptr[i + 1]; ++e) {
+        const int m = pi_sub[e], a = knot_ptr[m], b = knot_ptr[m + 1];
+        if (!diag && i < a) {
+            col[p++] = i;
+            diag = true;
+        }
+        for (int j = a; j < b; ++j) col[p++] = j;
+    }
+    if (!diag) col[p] = i;
+}
+
+__global__ void k_sub_fill(int N, const int *pi_ptr, const int *pi_sub, const int *sub_ptr, int *cursor,
+                           int *sub_rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int e = pi_ptr[i]; e < pi_ptr[i + 1]; ++e) {
+        const int m = pi_sub[e];
+        int p = atomicAdd(&cursor[m], 1);
+        sub_rows[sub_ptr[m] + p] = i;
+    }
+}
+
+// per entry p of sub_rows (subdomain m, row i): the position k of m in Pi_i, the offset of
+// Xi_m's first column in row i, and the inverse map pair_spos[pi_ptr[i] + k] = p
+__global__ void k_sub_meta(int M, const int *sub_ptr, const int *sub_rows, const int *pi_ptr, const int *pi_sub,
+                           const int *knot_ptr, int *sub_m, int *sub_k, int *sub_off, int *pair_spos) {
+    const int m = blockIdx.x;
+    if (m >= M) return;
+    const int a = knot_ptr[m];
+    for (int p = sub_ptr[m] + threadIdx.x; p < sub_ptr[m + 1]; p += blockDim.x) {
+        const int i = sub_rows[p];
+        int off = (i < a) ? 1 : 0, k = 0;
+        for (int e = pi_ptr[i]; e < pi_ptr[i + 1]; ++e) {
+            const int q = pi_sub[e];
+            if (q == m) {
+                k = e - pi_ptr[i];
+                break;
+            }
+            off += knot_ptr[q + 1] - knot_ptr[q];
+        }
+        sub_m[p] = m;
+        sub_k[p] = k;
+        sub_off[p] = off;
+        pair_spos[pi_ptr[i] + k] = p;
+    }
 }
 
 __global__ void k_sub_sort(int M, const int *sub_ptr, int *sub_rows) {
@@ -524,6 +626,7 @@ void build_cover_impl(const pdd_domain &dom, const pdd_cover_spec &spec, pdd_cov
     P.dom_kind = dom.kind;
     for (int k = 0; k < 4; ++k) P.dom[k] = dom.p[k];
     cov.domain = dom;
+    cov.averaged = spec.row_mode == PDD_ROWS_AVERAGED ? 1 : 0;
 
     LatticeArgs L{};
     L.kind = spec.kind;
@@ -684,6 +787,18 @@ void build_cover_impl(const pdd_domain &dom, const pdd_cover_spec &spec, pdd_cov
     if (herr[2]) fail(PDD_EDUPLICATE_KNOT, "two knots coincide");
     if (herr[1]) fail(PDD_EKNOT_UNCOVERED, std::to_string(herr[1]) + " knots lie inside no other circle");
 
+    // Pi_i (one subdomain, or all that hold the knot for averaged rows)
+    DevBuf<int> picnt;
+    picnt.alloc(N + 1);
+    PDD_LAUNCH(k_pi_count, cdiv(N, 256), 256, 0, st, G, N, cov.averaged, cov.kx.p, cov.ky.p, cov.kowner.p,
+               cov.row_sub.p, cov.cell_ptr.p, cov.cell_items.p, cov.cx.p, cov.cy.p, cov.r.p, picnt.p);
+    cov.pi_ptr.alloc(N + 1);
+    cov.npairs = (int)exclusive_scan(picnt.p, cov.pi_ptr.p, N, st);
+    cov.pi_sub.alloc(std::max(cov.npairs, 1));
+    PDD_LAUNCH(k_pi_fill, cdiv(N, 256), 256, 0, st, G, N, cov.averaged, cov.kx.p, cov.ky.p, cov.kowner.p,
+               cov.row_sub.p, cov.cell_ptr.p, cov.cell_items.p, cov.cx.p, cov.cy.p, cov.r.p, cov.pi_ptr.p,
+               cov.pi_sub.p);
+
     // a5: CSR pattern + rows by subdomain
     DevBuf<int> len, sub_cnt, cursor;
     len.alloc(N + 1);
@@ -691,18 +806,27 @@ void build_cover_impl(const pdd_domain &dom, const pdd_cover_spec &spec, pdd_cov
     cursor.alloc(M + 1);
     PDD_CUDA(cudaMemsetAsync(sub_cnt.p, 0, sizeof(int) * (M + 1), st));
     PDD_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (M + 1), st));
-    PDD_LAUNCH(k_row_len, cdiv(N, 256), 256, 0, st, N, cov.row_sub.p, cov.knot_ptr.p, len.p, sub_cnt.p);
+    PDD_LAUNCH(k_row_len, cdiv(N, 256), 256, 0, st, N, cov.pi_ptr.p, cov.pi_sub.p, cov.knot_ptr.p, len.p,
+               sub_cnt.p);
     cov.rowptr.alloc(N + 1);
     cov.nnz = exclusive_scan(len.p, cov.rowptr.p, N, st);
     cov.col.alloc(cov.nnz);
-    PDD_LAUNCH(k_csr_cols, cdiv(N, 256), 256, 0, st, N, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p,
-               cov.col.p);
+    PDD_LAUNCH(k_csr_cols, cdiv(N, 256), 256, 0, st, N, cov.pi_ptr.p, cov.pi_sub.p, cov.knot_ptr.p,
+               cov.rowptr.p, cov.col.p);
     cov.sub_ptr.alloc(M + 1);
     int nsub = (int)exclusive_scan(sub_cnt.p, cov.sub_ptr.p, M, st);
     cov.sub_rows.alloc(std::max(nsub, 1));
-    PDD_LAUNCH(k_sub_fill, cdiv(N, 256), 256, 0, st, N, cov.row_sub.p, cov.sub_ptr.p, cursor.p,
+    PDD_LAUNCH(k_sub_fill, cdiv(N, 256), 256, 0, st, N, cov.pi_ptr.p, cov.pi_sub.p, cov.sub_ptr.p, cursor.p,
                cov.sub_rows.p);
     PDD_LAUNCH(k_sub_sort, cdiv(M, 128), 128, 0, st, M, cov.sub_ptr.p, cov.sub_rows.p);
+    const int np1 = std::max(nsub, 1);
+    cov.sub_m.alloc(np1);
+    cov.sub_k.alloc(np1);
+    cov.sub_off.alloc(np1);
+    cov.pair_spos.alloc(np1);
+    if (M > 0)
+        PDD_LAUNCH(k_sub_meta, M, 128, 0, st, M, cov.sub_ptr.p, cov.sub_rows.p, cov.pi_ptr.p, cov.pi_sub.p,
+                   cov.knot_ptr.p, cov.sub_m.p, cov.sub_k.p, cov.sub_off.p, cov.pair_spos.p);
     cov.h_knot_ptr = to_host(cov.knot_ptr, M + 1, st);
     cov.h_sub_ptr = to_host(cov.sub_ptr, M + 1, st);
     cov.max_stencil = 0;

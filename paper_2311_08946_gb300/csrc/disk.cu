@@ -1093,11 +1093,13 @@ __global__ void __launch_bounds__(256) k_residual_df(Shape S, const NodeCoef *co
 // ---------------------------------------------------------------------------
 // a9: evaluate at the disk's knots and scatter into C and r
 // ---------------------------------------------------------------------------
+// Entry p of sub_rows (row i, this disk) writes Xi_m's block of row i at rowptr[i] + sub_off[p] and
+// its part of r_i to bs[p] (rows that average several subdomains sum the parts afterwards).
 __global__ void __launch_bounds__(256) k_disk_eval(Shape S, const DiskDesc *disks, const int *sub_rows,
-                                                   const double *kx, const double *ky,
+                                                   const int *sub_off, const double *kx, const double *ky,
                                                    const int *rowptr, const double *Xall,
                                                    long strideR, int group, int per, double *val,
-                                                   double *b) {
+                                                   double *bs) {
     extern __shared__ double esm[];                 // per rows x (n + nt) evaluation weights
     __shared__ double lr[8][130];                   // radial barycentric weights, l = 0..nc
     __shared__ double sa[8][130];                   // angular cardinals at the grid angles
@@ -1158,10 +1160,9 @@ __global__ void __launch_bounds__(256) k_disk_eval(Shape S, const DiskDesc *disk
                 if (col < S.nk) {
                     // boundary ring: G_j = -H_j on the circle
                     for (int a = 0; a < S.nt; ++a) acc -= E[S.n + a] * S.Hg[a * S.nk + col];
-                    const int off = (i < dd.knot_base) ? 1 : 0;
-                    val[rowptr[i] + off + col] = acc;
+                    val[rowptr[i] + sub_off[row] + col] = acc;
                 } else {
-                    b[i] = acc;
+                    bs[row] = acc;
                 }
             }
         }
@@ -1181,9 +1182,9 @@ __global__ void k_split_x(long count, const double *X, float2 *Xhl) {
 }
 
 __global__ void __launch_bounds__(256) k_disk_eval_df(Shape S, const DiskDesc *disks, const int *sub_rows,
-                                                      const double *kx, const double *ky, const int *rowptr,
-                                                      const float2 *Xhl, long strideR, int kper, double *val,
-                                                      double *b) {
+                                                      const int *sub_off, const double *kx, const double *ky,
+                                                      const int *rowptr, const float2 *Xhl, long strideR, int kper,
+                                                      double *val, double *bs) {
     extern __shared__ float2 edf[];                 // kper (<= kEvalKnots) x (n + nt) weights
     __shared__ double lr[kEvalKnots][130];          // radial barycentric weights, l = 0..nc
     __shared__ double sa[kEvalKnots][130];          // angular cardinals at the grid angles
@@ -1256,10 +1257,9 @@ __global__ void __launch_bounds__(256) k_disk_eval_df(Shape S, const DiskDesc *d
                     const float2 hg = S.Hghl[a * S.nk + col];
                     df_acc(sh, sl, E[S.n + a], make_float2(-hg.x, -hg.y));
                 }
-                const int off = (i < dd.knot_base) ? 1 : 0;
-                val[rowptr[i] + off + col] = (double)sh + (double)sl;
+                val[rowptr[i] + sub_off[r0 + g] + col] = (double)sh + (double)sl;
             } else {
-                b[i] = (double)sh + (double)sl;
+                bs[r0 + g] = (double)sh + (double)sl;
             }
         }
         __syncthreads();
@@ -1552,8 +1552,8 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             if (kper < 1) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
             const size_t esm = kper * rowdf;
             PDD_CUDA(cudaFuncSetAttribute(k_disk_eval_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-            PDD_LAUNCH(k_disk_eval_df, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p, cov.rowptr.p,
-                       Dhl.p, sR, kper, sys.val.p, sys.b.p);
+            PDD_LAUNCH(k_disk_eval_df, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.sub_off.p, cov.kx.p, cov.ky.p,
+                       cov.rowptr.p, Dhl.p, sR, kper, sys.val.p, sys.bs.p);
         } else {
             const int group = (S.nrhs <= 32) ? 32 : ((S.nrhs <= 64) ? 64 : 128);
             const size_t rowb = (size_t)(S.n + S.nt) * sizeof(double);
@@ -1561,8 +1561,8 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             if (per < 1) fail(PDD_EINVAL, "disk grid too large for the evaluation kernel");
             const size_t esm = per * rowb;
             PDD_CUDA(cudaFuncSetAttribute(k_disk_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-            PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p,
-                       cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.b.p);
+            PDD_LAUNCH(k_disk_eval, nd, 256, esm, st, S, dd.p, cov.sub_rows.p, cov.sub_off.p, cov.kx.p, cov.ky.p,
+                       cov.rowptr.p, X.p, sR, group, per, sys.val.p, sys.bs.p);
         }
         tm.mark(4);
         std::vector<int> hinfo(nd);

@@ -21,8 +21,14 @@ struct pdd_cover {
     pdd::DevBuf<double> kx, ky, ku;
     pdd::DevBuf<int> kowner, row_sub;
     pdd::DevBuf<uint8_t> kdir;
-    // rows grouped by subdomain: rows of circle m are sub_rows[sub_ptr[m] .. sub_ptr[m+1])
-    pdd::DevBuf<int> sub_ptr, sub_rows;
+    // Pi_i, the subdomains row i integrates in (ascending): pi_sub[pi_ptr[i] .. pi_ptr[i+1]);
+    // one per interior row, or all that hold the knot for averaged rows (Eq. 38-39)
+    int averaged = 0, npairs = 0;
+    pdd::DevBuf<int> pi_ptr, pi_sub;
+    // rows grouped by subdomain: rows of circle m are sub_rows[sub_ptr[m] .. sub_ptr[m+1]); per
+    // entry p: its subdomain sub_m, the position sub_k of that subdomain in Pi_i, the offset
+    // sub_off of Xi_m's first column in the CSR row; pair_spos[pi_ptr[i] + k] = p
+    pdd::DevBuf<int> sub_ptr, sub_rows, sub_m, sub_k, sub_off, pair_spos;
     // CSR pattern
     pdd::DevBuf<int> rowptr, col;
     // spatial hash of circles (uniform grid of pitch max_r)
@@ -39,9 +45,11 @@ struct pdd_system {
     int64_t nnz = 0;
     const pdd_cover *cov = nullptr;
     pdd::DevBuf<double> val, b, se, se_b;
+    pdd::DevBuf<double> bs, se_bs;         // r and its SE per (row, subdomain) entry of sub_rows
     // Monte Carlo raw estimates
     int n_mc = 0;
-    pdd::DevBuf<int> mc_rows, mom_ptr;
+    // per Monte Carlo slot: row, subdomain, entry of sub_rows, position of the subdomain in Pi_i
+    pdd::DevBuf<int> mc_rows, mc_subs, mc_spos, mc_kword, mom_ptr;
     pdd::DevBuf<double> moments, bmean;
     pdd::DevBuf<int> mc_np;                // paths run for each Monte Carlo row
     pdd_assembly_stats stats{};

@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const i
 // a11
 // ---------------------------------------------------------------------------
 struct PathArgs {
-    const int *rows, *row_sub;
+    // per slot: the row (knot) i; per global slot gs: its subdomain and the position of that
+    // subdomain in Pi_i (Philox counter word 3; null: 0)
+    const int *rows, *subs, *kword;
     const double *kx, *ky, *ccx, *ccy, *cr, *theta_s;
     int paths;                       // paths per row when npaths is null
     double h;
@@ -98,6 +100,7 @@ struct PathArgs {
     const long *rec_off;             // per-row record offsets, or null (slot * paths)
     float2 *ez;                      // mixed form: the unfolded FP32 increments (e, z) of each record
     double shift;                    // Gobet-Menozzi boundary shift c0 sqrt(h), or 0 (plain exit)
+    const int *gslot;                // global slot of each launched slot, or null (slot)
 };
 
 // c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi shift in units of |sigma^T n| sqrt(h) (sigma = I)
@@ -132,8 +135,8 @@ template <typename R>
 struct Num;
 template <>
 struct Num<double> {
-    __device__ static void normals(uint64_t s, uint32_t k, uint32_t st, uint32_t p, double &a, double &b) {
-        normals64(s, k, st, p, a, b);
+    __device__ static void normals(uint64_t s, uint32_t k, uint32_t q, uint32_t st, uint32_t p, double &a, double &b) {
+        normals64(s, k, q, st, p, a, b);
     }
     __device__ static void drift(const Problem &P, double x, double y, double &bx, double &by) {
         pdd::drift(P, x, y, bx, by);
@@ -142,8 +145,8 @@ struct Num<double> {
 };
 template <>
 struct Num<float> {
-    __device__ static void normals(uint64_t s, uint32_t k, uint32_t st, uint32_t p, float &a, float &b) {
-        normals32(s, k, st, p, a, b);
+    __device__ static void normals(uint64_t s, uint32_t k, uint32_t q, uint32_t st, uint32_t p, float &a, float &b) {
+        normals32(s, k, q, st, p, a, b);
     }
     __device__ static void drift(const Problem &P, float x, float y, float &bx, float &by) {
         if (P.b_kind == PDD_B_SINX_COSY) {
@@ -201,7 +204,9 @@ template <typename R, bool KILL, bool SRC>
 __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     __shared__ int next_path;
     const int slot = blockIdx.x;
-    const int i = A.rows[slot], m = A.row_sub[i];
+    const int gsl = A.gslot ? A.gslot[slot] : slot;
+    const int i = A.rows[slot], m = A.subs[gsl];
+    const uint32_t kw = A.kword ? (uint32_t)A.kword[gsl] : 0u;
     const double rad = A.cr[m], ts = A.theta_s[m];
     // exit tests against the disk and the domain shrunk by the boundary shift (0: the true ones), in
     // the position type; computed once into shared memory so that the loop reads them instead of
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
             done = true;
         } else {
             R xi0, xi1;
-            Num<R>::normals(A.seed, (uint32_t)i, (uint32_t)k, (uint32_t)p, xi0, xi1);
+            Num<R>::normals(A.seed, (uint32_t)i, kw, (uint32_t)k, (uint32_t)p, xi0, xi1);
             R bx, by;
             Num<R>::drift(P, x, y, bx, by);
             double Yn = Yv, Zn = Zv;
@@ -427,7 +432,9 @@ __device__ __forceinline__ float gdata32(const Problem &P, float x, float y, flo
 }
 
 struct FinalArgs {
-    const int *rows, *row_sub, *knot_ptr, *rowptr;
+    // per slot: the row i; per global slot gs: its subdomain and its entry p of sub_rows, whose
+    // stencil block starts at rowptr[i] + sub_off[p] and whose part of r_i goes to bs[p]
+    const int *rows, *subs, *spos, *sub_off, *knot_ptr, *rowptr;
     const uint8_t *floating;
     const double *ku;
     const long *kinv_off;     // per circle (-1 when not IMQ)
@@ -441,7 +448,7 @@ struct FinalArgs {
     const double *su, *Y, *Z;
     const float2 *ez;                // mixed form: unfolded increments, Y (1 + e) and Z + Y z
     const int *mom_ptr;
-    double *moments, *bmean, *val, *se, *b, *se_b;
+    double *moments, *bmean, *val, *se, *bs, *se_bs;
 };
 
 __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
@@ -449,14 +456,14 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
     __shared__ double bsum[kBatches];
     __shared__ int bcnt[kBatches];
     const int slot = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = F.rows[slot], m = F.row_sub[i];
+    const int gs = F.gslot ? F.gslot[slot] : slot;
+    const int i = F.rows[slot], m = F.subs[gs], pe = F.spos[gs];
     const int a = F.knot_ptr[m], ns = F.knot_ptr[m + 1] - a;
     const bool imq = !F.floating[m];
     double *Mb = fsm;                                 // kBatches x ns
     double *Cb = fsm + kBatches * ns;                 // kBatches x ns
     const int npath = F.npaths ? F.npaths[slot] : F.paths;
     const long base = F.rec_off ? F.rec_off[slot] : (long)slot * F.paths;
-    const int gs = F.gslot ? F.gslot[slot] : slot;
     // this lane's stencil angles (IMQ) or knot angles (Fourier cardinals)
     double uk[kMaxStencil / 32];
     float ukf[kMaxStencil / 32];
@@ -586,7 +593,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         int ntot = 0;
         for (int w = 0; w < kBatches; ++w) ntot += bcnt[w];
         const double inv = ntot ? 1.0 / ntot : 0.0;
-        const int off = (i < a) ? 1 : 0;
+        const int off = F.sub_off[pe];
         const long rp = F.rowptr[i];
         for (int j = lane; j < ns; j += 32) {
             double mean = 0.0, msum = 0.0;
@@ -616,27 +623,30 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                 var += f * f * d * d;
             }
             var *= (double)kBatches / (kBatches - 1);
-            F.b[i] = bm;
+            F.bs[pe] = bm;
             F.bmean[gs] = bm;
-            F.se_b[i] = sqrt(var);
+            F.se_bs[pe] = sqrt(var);
         }
     }
 }
 
-// rows integrated by Monte Carlo: flag + compaction
-__global__ void k_mc_flag(int N, const int *row_sub, const uint8_t *floating, int mc_floating, int *flag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int m = row_sub[i];
-    flag[i] = (m >= 0 && (!floating[m] || mc_floating)) ? 1 : 0;
+// (row, subdomain) entries integrated by Monte Carlo: flag + compaction over sub_rows
+__global__ void k_mc_flag(int nsub, const int *sub_m, const uint8_t *floating, int mc_floating, int *flag) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nsub) return;
+    flag[p] = (!floating[sub_m[p]] || mc_floating) ? 1 : 0;
 }
 
-__global__ void k_mc_compact(int N, const int *flag, const int *pos, const int *row_sub,
-                             const int *knot_ptr, int *rows, int *ns) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || !flag[i]) return;
-    int s = pos[i], m = row_sub[i];
-    rows[s] = i;
+__global__ void k_mc_compact(int nsub, const int *flag, const int *pos, const int *sub_rows, const int *sub_m,
+                             const int *sub_k, const int *knot_ptr, int *rows, int *subs, int *spos, int *kword,
+                             int *ns) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nsub || !flag[p]) return;
+    int s = pos[p], m = sub_m[p];
+    rows[s] = sub_rows[p];
+    subs[s] = m;
+    spos[s] = p;
+    kword[s] = sub_k[p];
     ns[s] = knot_ptr[m + 1] - knot_ptr[m];
 }
 
@@ -680,13 +690,14 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
 }
 
 // adaptive path count of each row from its pilot standard errors
-__global__ void k_need(int nmc, const int *rows, const int *row_sub, const int *knot_ptr, const int *rowptr,
-                       const double *se, const double *se_b, int P0, int Pmax, double target, int *need) {
+__global__ void k_need(int nmc, const int *rows, const int *subs, const int *spos, const int *sub_off,
+                       const int *knot_ptr, const int *rowptr, const double *se, const double *se_bs, int P0,
+                       int Pmax, double target, int *need) {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= nmc) return;
-    const int i = rows[slot], m = row_sub[i];
-    const int a = knot_ptr[m], ns = knot_ptr[m + 1] - a, off = (i < a) ? 1 : 0;
-    double mx = se_b[i];
+    const int i = rows[slot], m = subs[slot], pe = spos[slot];
+    const int a = knot_ptr[m], ns = knot_ptr[m + 1] - a, off = sub_off[pe];
+    double mx = se_bs[pe];
     for (int j = 0; j < ns; ++j) mx = fmax(mx, se[rowptr[i] + off + j]);
     const double r = mx / target;
     double want = ceil(P0 * r * r);
@@ -710,20 +721,25 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     McStats ms;
     const int N = cov.N;
     const int mcf = o.floating_method == PDD_FLOATING_MONTE_CARLO ? 1 : 0;
+    const int nsub = cov.h_sub_ptr.empty() ? 0 : cov.h_sub_ptr.back();
+    (void)N;
     DevBuf<int> flag, pos;
-    flag.alloc(N + 1);
-    pos.alloc(N + 1);
-    PDD_LAUNCH(k_mc_flag, cdiv(N, 256), 256, 0, st, N, cov.row_sub.p, cov.floating.p, mcf, flag.p);
-    const int nmc = (int)exclusive_scan(flag.p, pos.p, N, st);
+    flag.alloc(nsub + 1);
+    pos.alloc(nsub + 1);
+    if (nsub > 0) PDD_LAUNCH(k_mc_flag, cdiv(nsub, 256), 256, 0, st, nsub, cov.sub_m.p, cov.floating.p, mcf, flag.p);
+    const int nmc = nsub > 0 ? (int)exclusive_scan(flag.p, pos.p, nsub, st) : 0;
     sys.n_mc = nmc;
     ms.rows = nmc;
     if (nmc == 0) return ms;
     sys.mc_rows.alloc(nmc);
+    sys.mc_subs.alloc(nmc);
+    sys.mc_spos.alloc(nmc);
+    sys.mc_kword.alloc(nmc);
     DevBuf<int> ns;
     ns.alloc(nmc + 1);
     sys.mom_ptr.alloc(nmc + 1);
-    PDD_LAUNCH(k_mc_compact, cdiv(N, 256), 256, 0, st, N, flag.p, pos.p, cov.row_sub.p, cov.knot_ptr.p,
-               sys.mc_rows.p, ns.p);
+    PDD_LAUNCH(k_mc_compact, cdiv(nsub, 256), 256, 0, st, nsub, flag.p, pos.p, cov.sub_rows.p, cov.sub_m.p,
+               cov.sub_k.p, cov.knot_ptr.p, sys.mc_rows.p, sys.mc_subs.p, sys.mc_spos.p, sys.mc_kword.p, ns.p);
     const int nmom = (int)exclusive_scan(ns.p, sys.mom_ptr.p, nmc, st);
     sys.moments.alloc(std::max(nmom, 1));
     sys.bmean.alloc(nmc);
@@ -760,18 +776,21 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     float tp = 0, tf = 0;
     const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
     PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    // per-slot arrays (subs, spos, kword, momp, bmean) are indexed like the global slot gs: offset to
+    // the wave's first slot when gsl is null, or the whole arrays with gsl
     auto run_wave = [&](const int *rows, int nr, const int *np, const long *roff, const int *gsl, const int *momp,
-                        double *bmean) {
-        PathArgs A{rows, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p, o.paths,
-                   o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p,
-                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0};
+                        double *bmean, size_t w0) {
+        const int *subs = sys.mc_subs.p + w0, *spos = sys.mc_spos.p + w0, *kword = sys.mc_kword.p + w0;
+        PathArgs A{rows, subs, kword, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
+                   cov.theta_s.p, o.paths, o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p,
+                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, gsl};
         PDD_CUDA(cudaEventRecord(e0, st));
         if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
         PDD_CUDA(cudaEventRecord(e1, st));
-        FinalArgs F{rows, cov.row_sub.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p,
-                    o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p, ez.p, momp, sys.moments.p, bmean,
-                    sys.val.p, sys.se.p, sys.b.p, sys.se_b.p};
+        FinalArgs F{rows, subs, spos, cov.sub_off.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p,
+                    cov.ku.p, koff_m.p, kinv.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p,
+                    ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p};
         PDD_LAUNCH(k_mc_finalize, nr, 512, fsm, st, P, F);
         PDD_CUDA(cudaEventRecord(e2, st));
         PDD_CUDA(cudaEventSynchronize(e2));
@@ -783,7 +802,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     };
     for (int w0 = 0; w0 < nmc; w0 += wave) {
         const int nr = std::min(wave, nmc - w0);
-        run_wave(sys.mc_rows.p + w0, nr, nullptr, nullptr, nullptr, sys.mom_ptr.p + w0, sys.bmean.p + w0);
+        run_wave(sys.mc_rows.p + w0, nr, nullptr, nullptr, nullptr, sys.mom_ptr.p + w0, sys.bmean.p + w0, w0);
     }
     ms.paths_total = (int64_t)nmc * P_;
     sys.mc_np.alloc(nmc);
@@ -793,8 +812,9 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     if (o.paths_max > o.paths && o.se_target > 0.0) {
         DevBuf<int> dneed;
         dneed.alloc(nmc);
-        PDD_LAUNCH(k_need, cdiv(nmc, 256), 256, 0, st, nmc, sys.mc_rows.p, cov.row_sub.p, cov.knot_ptr.p,
-                   cov.rowptr.p, sys.se.p, sys.se_b.p, o.paths, o.paths_max, o.se_target, dneed.p);
+        PDD_LAUNCH(k_need, cdiv(nmc, 256), 256, 0, st, nmc, sys.mc_rows.p, sys.mc_subs.p, sys.mc_spos.p,
+                   cov.sub_off.p, cov.knot_ptr.p, cov.rowptr.p, sys.se.p, sys.se_bs.p, o.paths, o.paths_max,
+                   o.se_target, dneed.p);
         PDD_CUDA(cudaMemcpyAsync(need.data(), dneed.p, nmc * sizeof(int), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));
         std::vector<int> ext_slot, ext_row_host;
@@ -838,7 +858,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
                 Z.alloc(off);
                 if (mixed) ez.alloc(off);
             }
-            run_wave(drows.p, (int)rows.size(), dnp.p, droff.p, dgsl.p, sys.mom_ptr.p, sys.bmean.p);
+            run_wave(drows.p, (int)rows.size(), dnp.p, droff.p, dgsl.p, sys.mom_ptr.p, sys.bmean.p, 0);
         }
     }
     PDD_CUDA(cudaMemcpyAsync(sys.mc_np.p, need.data(), nmc * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -892,7 +912,9 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     double *Gw = dZ + (size_t)nw * T;            // [nw][T]
     double *Gg = Gw + (size_t)nw * T;            // [ng][T]
     const int slot = blockIdx.x;
-    const int i = A.rows[slot], m = A.row_sub[i];
+    const int gsl = A.gslot ? A.gslot[slot] : slot;
+    const int i = A.rows[slot], m = A.subs[gsl];
+    const uint32_t kw = A.kword ? (uint32_t)A.kword[gsl] : 0u;
     const int a = G.knot_ptr[m], ns = G.knot_ptr[m + 1] - a;
     const bool imq = !G.floating[m];
     // u_hat(u) = sum_l alpha_l phi_l(u) (IMQ) or sum_j u_j H_j(theta) (Fourier cardinals)
@@ -939,7 +961,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
         for (;;) {
             if (k >= max_steps) break;
             R xi0, xi1;
-            Num<R>::normals(A.seed, (uint32_t)i, (uint32_t)k, (uint32_t)p, xi0, xi1);
+            Num<R>::normals(A.seed, (uint32_t)i, kw, (uint32_t)k, (uint32_t)p, xi0, xi1);
             R bx, by;
             Num<R>::drift(P, x, y, bx, by);
             const double xd = (double)x, yd = (double)y;
@@ -1085,9 +1107,9 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     DevBuf<int> capped;
     steps.alloc(1);
     capped.alloc(1);
-    PathArgs A{sys.mc_rows.p, cov.row_sub.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p, cov.theta_s.p,
-               o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p, sys.mc_np.p, nullptr,
-               nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0};
+    PathArgs A{sys.mc_rows.p, sys.mc_subs.p, sys.mc_kword.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
+               cov.theta_s.p, o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p,
+               sys.mc_np.p, nullptr, nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, nullptr};
     GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
     const int T = 64;
     const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);

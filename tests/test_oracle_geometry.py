@@ -196,6 +196,31 @@ def test_csr_structure(tiny_cover):
             assert set(cols.tolist()) == want
 
 
+def test_averaged_rows_brute_force():
+    """Eq. 38-39: Pi_i = every subdomain (other than the knot's own circle) whose open disk holds
+    x_i, by brute force over all circles; row i of C holds the diagonal and the union of their
+    stencils; the farthest-interface choice of Sec. 3.2 is one of them."""
+    cfg = workloads.tiny()
+    cfg["cover"]["rows"] = "averaged"
+    c = cover.full_cover(cfg)
+    multi = 0
+    for i in range(c.N):
+        got = c.pi(i).tolist()
+        if c.kdir[i]:
+            assert got == [] and c.row_sub[i] == -1
+            continue
+        own = c.kowner[i]
+        want = [m for m in range(c.M) if m != own and
+                c.r[m] - math.hypot(c.kx[i] - c.cx[m], c.ky[i] - c.cy[m]) > 1e-12 * c.r[own]]
+        assert got == want, i
+        assert c.row_sub[i] in got
+        multi += len(got) > 1
+        cols = c.col[c.rowptr[i]:c.rowptr[i + 1]]
+        stencil = {i} | {k for m in got for k in range(c.knot_ptr[m], c.knot_ptr[m + 1])}
+        assert cols.tolist() == sorted(stencil)
+    assert multi > c.N // 4            # the lattice overlaps: many knots lie in two or more disks
+
+
 def test_hex_workload_cover_is_valid():
     cfg = workloads.varcoef()
     c = cover.full_cover(cfg)

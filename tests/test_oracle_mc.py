@@ -181,6 +181,45 @@ def test_constant_data_rows():
         assert abs(lhs - row.b) <= err1 + 1e-12, (i, m, lhs, row.b)
 
 
+def test_averaged_rows_special_cases():
+    """Eq. 38-39 on the 4x4 lattice.  (a) Rows whose every subdomain is floating: each
+    subdomain's row reproduces the harmonic e^x sin y from its knot values, so the averaged row
+    does too, (C u*)_i = r_i, with C_ii = #Pi_i.  (b) Constant data on Monte Carlo pairs: each
+    subdomain's part satisfies 1 + sum_j C^m_ij = r^m_i up to the IMQ interpolation error of 1.
+    (c) A row's subdomains use independent streams: only the first shares the paths of the
+    single-subdomain row."""
+    cfg = workloads.tiny(paths=200)
+    cfg["cover"]["rows"] = "averaged"
+    cov = cover.full_cover(cfg)
+    fl = [i for i in range(cov.N) if cov.pi(i).size >= 2 and all(cov.floating[m] for m in cov.pi(i))]
+    assert fl
+    S = system.assemble(cfg, cov, rows=fl)
+    C = S.csr()
+    ustar = np.exp(cov.kx) * np.sin(cov.ky)
+    res = C @ ustar - S.b
+    for i in fl:
+        assert C[i, i] == cov.pi(i).size
+        assert abs(res[i]) < 1e-9, (i, res[i])
+    # a dropped subdomain or a diagonal of 1 would break the identity by O(1)
+    assert np.abs(ustar[fl]).max() > 0.1
+    # (b) constant data
+    cfg1 = workloads.tiny(paths=200)
+    cfg1["cover"]["rows"] = "averaged"
+    cfg1["op"] = {"b": "zero", "c": "zero", "f": "zero", "g": "one"}
+    cov1 = cover.full_cover(cfg1)
+    pairs = [(i, int(m)) for i in range(cov1.N) for m in cov1.pi(i)
+             if cov1.pi(i).size >= 2 and not cov1.floating[m]][:8]
+    assert pairs
+    rows = mc.mc_rows(cov1, problem.Operator(cfg1["op"], cov1.domain), pairs, cfg1["mc"], 1.5)
+    for (i, m), row in rows.items():
+        t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, 1.5, row.Kinv).sum(1) - 1).max()
+        assert abs(1.0 + row.vals.sum() - row.b) <= err1 + 1e-12, (i, m)
+    # (c) streams: the k-th subdomain of a row draws with Philox counter word 3 = k
+    assert mc.normals(0, 5, 3, 7) == mc.normals(0, 5, 3, 7, sub=0)
+    assert mc.normals(0, 5, 3, 7) != mc.normals(0, 5, 3, 7, sub=1)
+
+
 def test_direct_and_gmres_solves():
     cfg = workloads.tiny(paths=100)
     S = system.assemble(cfg)
