@@ -141,7 +141,7 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
              cudaStream_t st);
 // K^-1 of every perimeter stencil (offsets per circle, -1 when none)
 void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, DevBuf<long> &koff_m,
-                        cudaStream_t st);
+                        DevBuf<double> &kcond, cudaStream_t st);
 
 void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
                const pdd_system &sys, const double *u, const double *dJdu, double *grad,

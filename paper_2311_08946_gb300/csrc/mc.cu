@@ -27,14 +27,37 @@ namespace pdd {
 
 static constexpr int kBatches = 32;
 static constexpr int kMaxStencil = 96;
+static constexpr double kFastKappa = 1e5;      // largest kappa_1(K) summed in FP32 (mixed form)
 
 // ---------------------------------------------------------------------------
 // a10
 // ---------------------------------------------------------------------------
+// largest column sum of |A| (n x n in shared memory), by the block
+__device__ double norm1_block(const double *A, int n, double *red) {
+    double mx = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double s = 0.0;
+        for (int l = 0; l < n; ++l) s += fabs(A[l * n + c]);
+        mx = fmax(mx, s);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int t = 0; t < blockDim.x; ++t) v = fmax(v, red[t]);
+        red[0] = v;
+    }
+    __syncthreads();
+    const double v = red[0];
+    __syncthreads();
+    return v;
+}
+
 __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const int *knot_ptr,
                                                      const double *ku, const long *kinv_off,
-                                                     double c2, double *kinv, int *bad) {
+                                                     double c2, double *kinv, double *kcond, int *bad) {
     extern __shared__ double sm[];                    // K (n x n), then L in place
+    __shared__ double red[128];
     const int m = circles[blockIdx.x];
     const int a = knot_ptr[m], n = knot_ptr[m + 1] - a;
     double *K = sm;
@@ -46,6 +69,7 @@ __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const i
         K[idx] = 1.0 / sqrt(d * d + c2);
     }
     __syncthreads();
+    const double nK = norm1_block(K, n, red);
     // right-looking Cholesky, lower triangle
     for (int j = 0; j < n; ++j) {
         if (tid == 0) {
@@ -77,6 +101,8 @@ __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const i
         }
     }
     __syncthreads();
+    const double nZ = norm1_block(Z, n, red);
+    if (tid == 0) kcond[m] = nK * nZ;                 // kappa_1(K)
     double *out = kinv + kinv_off[blockIdx.x];
     for (int idx = tid; idx < n * n; idx += blockDim.x) out[idx] = Z[idx];
 }
@@ -431,6 +457,22 @@ __device__ __forceinline__ float gdata32(const Problem &P, float x, float y, flo
     }
 }
 
+// Fourier cardinal of a knot (Eq. 18) at angular distance t, closed form; out of line (Monte Carlo
+// rows of floating circles only) for the same reason as boundary_score
+__device__ __noinline__ double fourier_cardinal_at(double t, int n) {
+    const double x = remainder(t, PDD_TWO_PI);
+    return (x == 0.0) ? 1.0 : sin(0.5 * n * x) * cos(0.5 * x) / (sin(0.5 * x) * n);
+}
+
+// g at the boundary point of arclength s (FP32 data in the mixed form); kept out of line so that
+// the data families do not add to the register pressure of the finalize loop (taken only for
+// paths that exit through dOmega)
+__device__ __noinline__ double boundary_score(const Problem &P, double s, int mixed) {
+    double ex, ey;
+    boundary_point(P, s, ex, ey);
+    return mixed ? (double)gdata32(P, (float)ex, (float)ey, (float)s) : gdata(P, ex, ey, s);
+}
+
 struct FinalArgs {
     // per slot: the row i; per global slot gs: its subdomain and its entry p of sub_rows, whose
     // stencil block starts at rowptr[i] + sub_off[p] and whose part of r_i goes to bs[p]
@@ -439,6 +481,7 @@ struct FinalArgs {
     const double *ku;
     const long *kinv_off;     // per circle (-1 when not IMQ)
     const double *kinv;
+    const double *kcond;      // per circle: kappa_1(K) (0 when not IMQ)
     double c2;
     int paths, mc_floating, mixed;
     const int *npaths;               // per-row path counts, or null (paths)
@@ -474,7 +517,11 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         ukf[q] = (float)uk[q];
     }
     const float c2f = (float)F.c2;
-    const bool fast = F.mixed && imq;
+    // mixed form: FP32 basis sums where K is well conditioned.  C = -K^-T M amplifies the
+    // rounding of the moments by up to kappa(K); FP32 sums of FP32 phi are off by ~5e-11 kappa
+    // in C (measured: 0.03 at kappa 5.6e8), so stencils with kappa_1(K) > kFastKappa sum in FP64
+    const bool fast = F.mixed && imq && F.kcond[m] <= kFastKappa;
+    const int nq = (ns + 31) >> 5;                     // register slices holding stencil knots (block-uniform)
     for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each (p mod 32)
         double acc[kMaxStencil / 32];
         float accf[kMaxStencil / 32];                      // mixed form: FP32 sums of 16 paths
@@ -505,10 +552,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             if (sd != 2) {                                 // this lane's own contribution to r_i
                 ++cnt;
                 if (sd == 1) {
-                    double ex, ey;
-                    boundary_point(P, su, ex, ey);
-                    const double g = F.mixed ? (double)gdata32(P, (float)ex, (float)ey, (float)su) : gdata(P, ex, ey, su);
-                    bs += g * yv + zv;
+                    bs += boundary_score(P, su, F.mixed) * yv + zv;
                 } else {
                     bs += zv;
                 }
@@ -524,12 +568,14 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                     if (s_sd != 0) continue;
 #pragma unroll
                     for (int q = 0; q < kMaxStencil / 32; ++q) {
+                        if (q >= nq) break;                // slices past the stencil hold no knot
                         const float df = s_suf - ukf[q];
                         accf[q] = fmaf(s_yf, rsqrtf(df * df + c2f), accf[q]);
                     }
                     if (++pend == 16) {
 #pragma unroll
                         for (int q = 0; q < kMaxStencil / 32; ++q) {
+                            if (q >= nq) break;
                             acc[q] += (double)accf[q];
                             accf[q] = 0.f;
                         }
@@ -549,11 +595,9 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                         double phi;
                         if (imq) {
                             const double d = s_su - uk[q];
-                            phi = 1.0 / sqrt(d * d + F.c2);
+                            phi = F.mixed ? rsqrt(d * d + F.c2) : 1.0 / sqrt(d * d + F.c2);
                         } else {
-                            // Fourier cardinal of knot l (Eq. 18), closed form
-                            const double x = remainder(s_su - uk[q], PDD_TWO_PI);
-                            phi = (x == 0.0) ? 1.0 : sin(0.5 * ns * x) * cos(0.5 * x) / (sin(0.5 * x) * ns);
+                            phi = fourier_cardinal_at(s_su - uk[q], ns);
                         }
                         acc[q] += s_y * phi;
                     }
@@ -651,7 +695,7 @@ __global__ void k_mc_compact(int nsub, const int *flag, const int *pos, const in
 }
 
 void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, DevBuf<long> &koff_m,
-                        cudaStream_t st) {
+                        DevBuf<double> &kcond, cudaStream_t st) {
     if (cov.max_stencil > kMaxStencil) fail(PDD_EINVAL, "stencil larger than the Monte Carlo kernels support");
     std::vector<int> per;
     std::vector<long> off(cov.M, -1);
@@ -668,6 +712,8 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
     DevBuf<int> circ, bad;
     kinv.alloc(std::max<long>(tot, 1));
     koff_m.alloc(cov.M);
+    kcond.alloc(std::max(cov.M, 1));
+    PDD_CUDA(cudaMemsetAsync(kcond.p, 0, sizeof(double) * std::max(cov.M, 1), st));
     bad.alloc(1);
     PDD_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     PDD_CUDA(cudaMemcpyAsync(koff_m.p, off.data(), cov.M * sizeof(long), cudaMemcpyHostToDevice, st));
@@ -681,7 +727,7 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
         const size_t smem = (size_t)2 * cov.max_stencil * cov.max_stencil * sizeof(double);
         PDD_CUDA(cudaFuncSetAttribute(k_imq_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, koff_c.p, c2,
-                   kinv.p, bad.p);
+                   kinv.p, kcond.p, bad.p);
     }
     int hb = 0;
     PDD_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -745,9 +791,9 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     sys.bmean.alloc(nmc);
 
     // a10: IMQ inverses for every perimeter circle with a stencil
-    DevBuf<double> kinv;
+    DevBuf<double> kinv, kcond;
     DevBuf<long> koff_m;
-    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, st);
+    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, kcond, st);
 
     // a11: paths into the record scratch, in waves that bound the scratch size
     const long P_ = o.paths;
@@ -789,7 +835,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
         else launch_paths<double>(P, A, nr, st);
         PDD_CUDA(cudaEventRecord(e1, st));
         FinalArgs F{rows, subs, spos, cov.sub_off.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p,
-                    cov.ku.p, koff_m.p, kinv.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p, Y.p, Z.p,
+                    cov.ku.p, koff_m.p, kinv.p, kcond.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p,
+                    Y.p, Z.p,
                     ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p};
         PDD_LAUNCH(k_mc_finalize, nr, 512, fsm, st, P, F);
         PDD_CUDA(cudaEventRecord(e2, st));
@@ -1097,9 +1144,9 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
     const int ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
     if (nmc == 0 || nw + ng == 0) return;
-    DevBuf<double> kinv;
+    DevBuf<double> kinv, kcond;
     DevBuf<long> koff_m;
-    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, st);
+    build_imq_inverses(cov, o.imq_c2, kinv, koff_m, kcond, st);
     const int n_par = P.n_rbf + P.n_gcoef;
     partial.alloc((size_t)nmc * n_par);
     PDD_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double) * nmc * n_par, st));
