@@ -256,6 +256,49 @@ __device__ __forceinline__ int nearest_edge(const Problem &P, double x, double y
 }
 
 // ---------------------------------------------------------------------------
+// double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (Dekker 1971; Knuth's two-sum).  Products use __fmul_rn so that the
+// compiler cannot contract them into the following addition.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
+// (sh, sl) += w x, the accumulator left unnormalised
+__device__ __forceinline__ void df_acc(float &sh, float &sl, float2 w, float2 x) {
+    const float p = __fmul_rn(w.x, x.x);
+    float e = fmaf(w.x, x.x, -p);
+    e = fmaf(w.x, x.y, fmaf(w.y, x.x, e));
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl += t + e;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------
 struct U4 {

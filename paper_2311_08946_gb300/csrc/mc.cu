@@ -28,6 +28,7 @@ namespace pdd {
 static constexpr int kBatches = 32;
 static constexpr int kMaxStencil = 96;
 static constexpr double kFastKappa = 1e5;      // largest kappa_1(K) summed in FP32 (mixed form)
+static constexpr double kDfKappa = 1e10;       // largest kappa_1(K) summed in double-float (mixed form)
 
 // ---------------------------------------------------------------------------
 // a10
@@ -494,6 +495,30 @@ struct FinalArgs {
     double *moments, *bmean, *val, *se, *bs, *se_bs;
 };
 
+// 1 / sqrt(q) for q = qh + ql in double-float: one Newton step from rsqrtf, whose residual
+// t = 1 - q r0^2 is formed without rounding error in its leading part (r0^2 and q r0^2 by FMA
+// splits; 1 - h is exact because h is within 2^-22 of 1); relative error below 1e-13
+__device__ __forceinline__ float2 df_rsqrt(float qh, float ql) {
+    const float r0 = rsqrtf(qh);
+    const float a = __fmul_rn(r0, r0);
+    const float ae = fmaf(r0, r0, -a);
+    const float h = __fmul_rn(qh, a);
+    float he = fmaf(qh, a, -h);
+    he = fmaf(qh, ae, he);
+    he = fmaf(ql, a, he);
+    const float t = __fsub_rn(__fsub_rn(1.0f, h), he);
+    return make_float2(r0, __fmul_rn(__fmul_rn(0.5f, r0), t));
+}
+
+// Per-row finalize.  NQ = register slices of 32 stencil knots (the launch's largest stencil).
+// Basis sums of the mixed form (sum mode, per stencil):
+//   0: FP32 phi and FP32 sums of 16 paths (kappa_1(K) <= kFastKappa);
+//   1: double-float phi and sums (kappa_1(K) <= kDfKappa);
+//   2: FP64 (the FP64 form, Fourier cardinals, and larger kappa).
+// C = -K^-T M amplifies the rounding of the moments by up to kappa(K): FP32 sums of FP32 phi
+// were measured off by ~5e-11 kappa in C (0.03 at kappa 5.6e8); double-float phi is within
+// 1e-13 relative (an emulation over 2e4 random angles), FP64 within 2^-52.
+template <int NQ>
 __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
     extern __shared__ double fsm[];                   // [32 batches][ns] moments, then per-batch C
     __shared__ double bsum[kBatches];
@@ -507,28 +532,27 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
     double *Cb = fsm + kBatches * ns;                 // kBatches x ns
     const int npath = F.npaths ? F.npaths[slot] : F.paths;
     const long base = F.rec_off ? F.rec_off[slot] : (long)slot * F.paths;
-    // this lane's stencil angles (IMQ) or knot angles (Fourier cardinals)
-    double uk[kMaxStencil / 32];
-    float ukf[kMaxStencil / 32];
+    // this lane's stencil angles (IMQ) or knot angles (Fourier cardinals), also as hi + lo FP32
+    double uk[NQ];
+    float ukf[NQ], ukl[NQ];
 #pragma unroll
-    for (int q = 0; q < kMaxStencil / 32; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         const int l = lane + 32 * q;
         uk[q] = (l < ns) ? (imq ? F.ku[a + l] : PDD_TWO_PI * l / ns) : 0.0;
         ukf[q] = (float)uk[q];
+        ukl[q] = (float)(uk[q] - (double)ukf[q]);
     }
-    const float c2f = (float)F.c2;
-    // mixed form: FP32 basis sums where K is well conditioned.  C = -K^-T M amplifies the
-    // rounding of the moments by up to kappa(K); FP32 sums of FP32 phi are off by ~5e-11 kappa
-    // in C (measured: 0.03 at kappa 5.6e8), so stencils with kappa_1(K) > kFastKappa sum in FP64
-    const bool fast = F.mixed && imq && F.kcond[m] <= kFastKappa;
-    const int nq = (ns + 31) >> 5;                     // register slices holding stencil knots (block-uniform)
+    const float c2f = (float)F.c2, c2l = (float)(F.c2 - (double)c2f);
+    const int mode = (F.mixed && imq) ? (F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2)) : 2;
+    const int nq = (ns + 31) >> 5;                     // slices holding stencil knots (block-uniform)
     for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each (p mod 32)
-        double acc[kMaxStencil / 32];
-        float accf[kMaxStencil / 32];                      // mixed form: FP32 sums of 16 paths
+        double acc[NQ];
+        float accf[NQ], accl[NQ];                          // FP32 or double-float sums of 16 paths
 #pragma unroll
-        for (int q = 0; q < kMaxStencil / 32; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             acc[q] = 0.0;
             accf[q] = 0.f;
+            accl[q] = 0.f;
         }
         int pend = 0;
         double bs = 0.0;
@@ -558,8 +582,8 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                 }
             }
             // the chunk's interface exits, in path order, into every lane's basis sums
-            if (fast) {
-                // mixed form: each lane converts its own record once; FP32 values are shuffled
+            if (mode == 0) {
+                // each lane converts its own record once; FP32 values are shuffled
                 const float yf = (float)yv, suf = (float)su;
                 for (int src = 0; src < 32; ++src) {
                     const int s_sd = __shfl_sync(0xffffffffu, sd, src);
@@ -567,17 +591,61 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                     const float s_suf = __shfl_sync(0xffffffffu, suf, src);
                     if (s_sd != 0) continue;
 #pragma unroll
-                    for (int q = 0; q < kMaxStencil / 32; ++q) {
+                    for (int q = 0; q < NQ; ++q) {
                         if (q >= nq) break;                // slices past the stencil hold no knot
                         const float df = s_suf - ukf[q];
                         accf[q] = fmaf(s_yf, rsqrtf(df * df + c2f), accf[q]);
                     }
                     if (++pend == 16) {
 #pragma unroll
-                        for (int q = 0; q < kMaxStencil / 32; ++q) {
-                            if (q >= nq) break;
+                        for (int q = 0; q < NQ; ++q) {
                             acc[q] += (double)accf[q];
                             accf[q] = 0.f;
+                        }
+                        pend = 0;
+                    }
+                }
+            } else if (mode == 1) {
+                // double-float: the record's Y and angle split once per lane, then shuffled
+                const float yh = (float)yv, yl = (float)(yv - (double)yh);
+                const float sh = (float)su, sl = (float)(su - (double)sh);
+                for (int src = 0; src < 32; ++src) {
+                    const int s_sd = __shfl_sync(0xffffffffu, sd, src);
+                    const float s_yh = __shfl_sync(0xffffffffu, yh, src);
+                    const float s_yl = __shfl_sync(0xffffffffu, yl, src);
+                    const float s_sh = __shfl_sync(0xffffffffu, sh, src);
+                    const float s_sl = __shfl_sync(0xffffffffu, sl, src);
+                    if (s_sd != 0) continue;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        if (q >= nq) break;
+                        // d = u - u_l, then q = d^2 + c^2, both in double-float
+                        float dh, dl;
+                        two_sum(s_sh, -ukf[q], dh, dl);
+                        dl = __fadd_rn(dl, __fsub_rn(s_sl, ukl[q]));
+                        const float p = __fmul_rn(dh, dh);
+                        float pe2 = fmaf(dh, dh, -p);
+                        pe2 = fmaf(__fmul_rn(2.0f, dh), dl, pe2);
+                        float qh, ql;
+                        two_sum(p, c2f, qh, ql);
+                        ql = __fadd_rn(ql, __fadd_rn(pe2, c2l));
+                        const float2 phi = df_rsqrt(qh, ql);
+                        // (accf, accl) += Y phi
+                        const float mh = __fmul_rn(s_yh, phi.x);
+                        float me = fmaf(s_yh, phi.x, -mh);
+                        me = fmaf(s_yh, phi.y, me);
+                        me = fmaf(s_yl, phi.x, me);
+                        float sh2, se2;
+                        two_sum(accf[q], mh, sh2, se2);
+                        accf[q] = sh2;
+                        accl[q] = __fadd_rn(accl[q], __fadd_rn(se2, me));
+                    }
+                    if (++pend == 16) {
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            acc[q] += (double)accf[q] + (double)accl[q];
+                            accf[q] = 0.f;
+                            accl[q] = 0.f;
                         }
                         pend = 0;
                     }
@@ -589,7 +657,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                     const double s_su = __shfl_sync(0xffffffffu, su, src);
                     if (s_sd != 0) continue;
 #pragma unroll
-                    for (int q = 0; q < kMaxStencil / 32; ++q) {
+                    for (int q = 0; q < NQ; ++q) {
                         const int l = lane + 32 * q;
                         if (l >= ns) continue;
                         double phi;
@@ -605,11 +673,11 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             }
         }
 #pragma unroll
-        for (int q = 0; q < kMaxStencil / 32; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int l = lane + 32 * q;
-            if (l < ns) Mb[bt * ns + l] = acc[q] + (double)accf[q];
+            if (l < ns) Mb[bt * ns + l] = acc[q] + (double)accf[q] + (double)accl[q];
         }
-        for (int o = 16; o; o >>= 1) {
+    for (int o = 16; o; o >>= 1) {
             bs += __shfl_xor_sync(0xffffffffu, bs, o);
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         }
@@ -633,20 +701,24 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             Cb[bt * ns + j] = nb ? v / nb : 0.0;
         }
     __syncthreads();
+    // (the batch loops below stay partly rolled: fully unrolled they spilled)
     if (warp == 0) {
         int ntot = 0;
+#pragma unroll 4
         for (int w = 0; w < kBatches; ++w) ntot += bcnt[w];
         const double inv = ntot ? 1.0 / ntot : 0.0;
         const int off = F.sub_off[pe];
         const long rp = F.rowptr[i];
         for (int j = lane; j < ns; j += 32) {
             double mean = 0.0, msum = 0.0;
+#pragma unroll 4
             for (int w = 0; w < kBatches; ++w) {
                 mean += bcnt[w] * Cb[w * ns + j];
                 msum += Mb[w * ns + j];
             }
             mean *= inv;
             double var = 0.0;
+#pragma unroll 4
             for (int w = 0; w < kBatches; ++w) {
                 double f = bcnt[w] * inv, d = Cb[w * ns + j] - mean;
                 var += f * f * d * d;
@@ -821,7 +893,10 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     PDD_CUDA(cudaEventCreate(&e2));
     float tp = 0, tf = 0;
     const size_t fsm = (size_t)2 * kBatches * cov.max_stencil * sizeof(double);
-    PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    const int nq_launch = std::max(1, (cov.max_stencil + 31) / 32);
+    PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    PDD_CUDA(cudaFuncSetAttribute(k_mc_finalize<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
     // per-slot arrays (subs, spos, kword, momp, bmean) are indexed like the global slot gs: offset to
     // the wave's first slot when gsl is null, or the whole arrays with gsl
     auto run_wave = [&](const int *rows, int nr, const int *np, const long *roff, const int *gsl, const int *momp,
@@ -838,7 +913,9 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
                     cov.ku.p, koff_m.p, kinv.p, kcond.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p,
                     Y.p, Z.p,
                     ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p};
-        PDD_LAUNCH(k_mc_finalize, nr, 512, fsm, st, P, F);
+        if (nq_launch == 1) PDD_LAUNCH(k_mc_finalize<1>, nr, 512, fsm, st, P, F);
+        else if (nq_launch == 2) PDD_LAUNCH(k_mc_finalize<2>, nr, 512, fsm, st, P, F);
+        else PDD_LAUNCH(k_mc_finalize<3>, nr, 512, fsm, st, P, F);
         PDD_CUDA(cudaEventRecord(e2, st));
         PDD_CUDA(cudaEventSynchronize(e2));
         float ta = 0, tb = 0;
