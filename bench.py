@@ -279,7 +279,7 @@ def run_ours(args, rank, world):
 # Thread-instructions per Euler-Maruyama step of k_paths<float,1,1> on this workload, from
 # ncu (smsp__thread_inst_executed.sum / path-steps of the variable-coefficient case at 4096 paths
 # per knot, profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
-PATHS_THREAD_INST_PER_STEP = 243.0
+PATHS_THREAD_INST_PER_STEP = 236.0
 # DRAM bytes (read + write) of one launch from the same captures, or None: the first sweep of
 # k_lu_solve_rl<36> on the 864 disks of the workload (profiles/k_lu_solve_rl_varcoef_mixed.md).
 TRISOLVE_DRAM_BYTES_PER_LAUNCH = 4.209e9 + 0.209e9
