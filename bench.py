@@ -79,9 +79,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job units per second: every rank processed units_per_rank (replicas, weak
+    scaling) and the job took the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 def peaks():
@@ -212,7 +219,7 @@ def run_ours(args, rank, world):
     timed_solve_ms = statistics.mean(SOLVE_MS[-args.steps:])
     ms = statistics.mean(times)
     ms_max = max_over_ranks(ms, world)
-    value = world * N / (ms_max / 1e3)
+    value = job_throughput(N, world, ms_max)
     st = stats[-1]
     path_steps = st["path_steps"]
     mc_rate = path_steps / (statistics.mean(s["ms_paths"] for s in stats) / 1e3)
@@ -231,7 +238,7 @@ def run_ours(args, rank, world):
         del cov, S, u
     e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
     h2d = 36 + 112 + 72 + 48        # domain, cover spec, operator and option structs
-    e2e = {"value": world * N / e2e_s, "unit": "knots/s", "h2d_bytes_per_step": h2d,
+    e2e = {"value": job_throughput(N, world, 1e3 * e2e_s), "unit": "knots/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": N * 8}
 
     out = {"metric": METRIC, "value": value, "unit": "knots/s", "n_gpus": world, "steps": args.steps,
@@ -586,8 +593,8 @@ def run_reference(args, rank, world):
         return None
     import workloads
     cfg = workloads.varcoef()
-    for _ in range(max(3, args.warmup) if args.warmup > 0 else 0):
-        pass
+    if args.warmup > 0:
+        cpu_baseline(cfg, budget_s=2.0)     # builds the C path simulator and warms the caches
     vals = []
     bl = None
     for _ in range(max(1, args.steps)):

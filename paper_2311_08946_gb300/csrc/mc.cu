@@ -837,10 +837,8 @@ static void launch_paths(const Problem &P, const PathArgs &A, int nrows, cudaStr
 McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o, pdd_system &sys,
                     cudaStream_t st) {
     McStats ms;
-    const int N = cov.N;
     const int mcf = o.floating_method == PDD_FLOATING_MONTE_CARLO ? 1 : 0;
     const int nsub = cov.h_sub_ptr.empty() ? 0 : cov.h_sub_ptr.back();
-    (void)N;
     DevBuf<int> flag, pos;
     flag.alloc(nsub + 1);
     pos.alloc(nsub + 1);
