@@ -790,6 +790,40 @@ __global__ void __launch_bounds__(256) k_transpose_f32(const float *Aall, float 
     }
 }
 
+// the same transpose in 64 x 64 tiles with 16-byte loads and stores (n a multiple of 4): each
+// thread has four loads in flight, and the disk's tiles are a quarter as many blocks
+__global__ void __launch_bounds__(256) k_transpose_f32_v4(const float *Aall, float *ATall, int n, long strideA) {
+    __shared__ float t[64][65];
+    const int disk = blockIdx.z, bx = blockIdx.x * 64, by = blockIdx.y * 64;   // rows by.., columns bx..
+    const float *A = Aall + disk * strideA;
+    float *AT = ATall + disk * strideA;
+    const int c4 = threadIdx.x & 15, rr = threadIdx.x >> 4;                    // 16 float4 per tile row
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int gr = by + rr + 16 * k, gc = bx + 4 * c4;
+        v[k] = (gr < n && gc < n) ? *reinterpret_cast<const float4 *>(A + (long)gr * n + gc)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float *row = &t[rr + 16 * k][4 * c4];
+        row[0] = v[k].x;
+        row[1] = v[k].y;
+        row[2] = v[k].z;
+        row[3] = v[k].w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = rr + 16 * k;                       // row bx + o of AT = column bx + o of A
+        const int gr = bx + o, gc = by + 4 * c4;
+        if (gr < n && gc < n)
+            *reinterpret_cast<float4 *>(AT + (long)gr * n + gc) =
+                make_float4(t[4 * c4][o], t[4 * c4 + 1][o], t[4 * c4 + 2][o], t[4 * c4 + 3][o]);
+    }
+}
+
 // per disk: count the sweep and stop refining once the correction just applied, or the next one
 // predicted from the contraction of the last two (|W_s|^2 / |W_{s-1}|, when they contract), is at
 // most tol max|X|
@@ -1422,8 +1456,12 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             const long items = (long)nd * nblk * 2;
             PDD_LAUNCH(k_diag_inv, (int)((items + 3) / 4), 128, 0, st, reinterpret_cast<const float *>(A.p), S.n, sA,
                        nd, dinv.p);
-            PDD_LAUNCH(k_transpose_f32, dim3(cdiv(S.n, 32), cdiv(S.n, 32), nd), 256, 0, st,
-                       reinterpret_cast<const float *>(A.p), AT.p, S.n, sA);
+            if ((S.n & 3) == 0)       // rows and disks start on 16-byte boundaries (cudaMalloc'd buffers)
+                PDD_LAUNCH(k_transpose_f32_v4, dim3(cdiv(S.n, 64), cdiv(S.n, 64), nd), 256, 0, st,
+                           reinterpret_cast<const float *>(A.p), AT.p, S.n, sA);
+            else
+                PDD_LAUNCH(k_transpose_f32, dim3(cdiv(S.n, 32), cdiv(S.n, 32), nd), 256, 0, st,
+                           reinterpret_cast<const float *>(A.p), AT.p, S.n, sA);
         }
         tm.mark(2);
         if (!mixed) {
