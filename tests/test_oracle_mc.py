@@ -306,3 +306,37 @@ def test_adjoint_against_central_differences():
         assert abs(fd4 - g[idx]) <= 1e-6 * max(1e-2, abs(fd4)), (param, idx, fd4, g[idx])
         fd6 = _fd(param, idx, 1e-6, u_obs, cov)
         assert abs(fd6 - g[idx]) <= 2e-5 * max(1e-2, abs(fd6)), (param, idx, fd6, g[idx])
+
+
+def _table1():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_poisson46.txt")
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def test_poisson46_statistics_against_table1():
+    """The oracle's C for the Poisson test of Eq. 46 against the [-50,50]^2 column of Table 1.
+    The circle layout is ours (the paper's figure of it is missing; radius 9 on a pitch-10
+    lattice), so the statistics are compared loosely: 100 subdomains exactly, rho(C - I) within
+    0.03 (an M-matrix-like C with spectral radius just below one), kappa_2(C) within a factor
+    of 2, and the solution within the Monte Carlo error of 64 paths per knot (the paper's RMS
+    comes from 5000 paths with variance reduction)."""
+    t1 = _table1()
+    cfg = workloads.poisson46(paths=64)
+    cov = cover.full_cover(cfg)
+    S = system.assemble(cfg, cov, threads=8)
+    C = S.csr().toarray()
+    assert cov.M == t1["subdomains"]
+    assert abs(cov.N - t1["N"]) < 0.1 * t1["N"]
+    rho = np.abs(np.linalg.eigvals(C - np.eye(cov.N))).max()
+    sv = np.linalg.svd(C, compute_uv=False)
+    assert abs(rho - t1["rho_C_minus_I"]) < 0.03 and rho < 1.0, rho
+    assert 0.5 * t1["kappa2_C"] < sv[0] / sv[-1] < 2.0 * t1["kappa2_C"], sv[0] / sv[-1]
+    u = np.linalg.solve(C, S.b)
+    rms = np.sqrt(np.mean((u - problem.Operator.u46(cov.kx, cov.ky)[0]) ** 2))
+    assert rms < 0.05, rms
