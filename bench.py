@@ -376,7 +376,7 @@ def fp64_form(pdd, cfg, stream, flush):
     return res
 
 
-# The [-50,50]^2 column of the paper's Table 1 (Sec. 5): 1152 A64FX cores, 96 MPI processes,
+# The [-50,50]^2 column of the paper's Table 1 (Sec. 4): 1152 A64FX cores, 96 MPI processes,
 # METIS + MUMPS RAS, Gobet-Menozzi paths with pathwise variance reduction.
 TABLE1_50 = {"subdomains": 100, "N": 3636, "sparsity": 0.02066, "rho_C_minus_I": 0.9558,
              "max_offdiag_C": 0.0445, "kappa2_C": 84.0, "rms_error": 3.72e-5, "gmres_iters": 19,
@@ -384,7 +384,7 @@ TABLE1_50 = {"subdomains": 100, "N": 3636, "sparsity": 0.02066, "rho_C_minus_I":
 
 
 def poisson46_leg(pdd, stream, flush, steps=3):
-    """The paper's Poisson test (Eq. 46) on [-50,50]^2 at its Sec. 5 parameters (5,000 paths per
+    """The paper's Poisson test (Eq. 46) on [-50,50]^2 at its Sec. 4 parameters (5,000 paths per
     Monte Carlo knot, h = 0.015, boundary shift, 44 knots, 22 x 44 disk nodes, c^2 = 1.5):
     throughput of the same step, and the statistics of Table 1 computed from the GPU's C, r and u
     (rho(C - I), max off-diagonal C_ij, kappa_2(C) on the host in FP64)."""

@@ -188,7 +188,7 @@ typedef struct {
                                  exceeds it rerun with paths (se/se_target)^2 paths,
                                  capped at paths_max (rounded up to 32); path ids
                                  continue the pilot's Philox streams                 */
-    int boundary_shift;       /* 1: Gobet-Menozzi stopped Euler scheme (Sec. 5: the
+    int boundary_shift;       /* 1: Gobet-Menozzi stopped Euler scheme (Sec. 4: the
                                  paper's perimeter subdomains): exit tests against
                                  the disk and the domain shrunk by c0 sqrt(h),
                                  c0 = -zeta(1/2)/sqrt(2 pi) = 0.5826 (sigma = I), and

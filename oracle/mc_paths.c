@@ -18,7 +18,7 @@
  * a tie goes to dOmega).  The weights are the ones after the exit step.
  *
  * Boundary shift (the Gobet-Menozzi stopped-diffusion correction, Stoch.
- * Proc. Appl. 120 (2010); the paper's perimeter subdomains use it, Sec. 5):
+ * Proc. Appl. 120 (2010); the paper's perimeter subdomains use it, Sec. 4):
  * with shift = c0 |sigma^T n| sqrt(h) > 0 (sigma = I; c0 = -zeta(1/2)/sqrt(2 pi)
  * = 0.5826) the exit test uses the disk and the domain shrunk by `shift`, the
  * piece left first is chosen as above on the shrunk boundaries, and the path

@@ -131,7 +131,7 @@ def test_floating_rows_varcoef_sampled(pdd, precision, factor):
 def test_floating_rows_poisson46_sampled(pdd, precision, factor):
     """The paper's Poisson test (Eq. 46) on [-50,50]^2: 968-node disks (22 x 44, not a multiple
     of the LU panel width), 44 knots; 4 disks recomputed by the oracle.  The collocation matrix
-    has kappa ~ 1e5 (Sec. 5), so rows agree to ~kappa u, inside 1e-9."""
+    has kappa ~ 1e5 (Sec. 4), so rows agree to ~kappa u, inside 1e-9."""
     cfg = workloads.poisson46(paths=16)
     oc = _oracle_cover("poisson46", cfg)
     S = pdd.System(pdd.Cover(cfg), cfg, precision, factor=factor)
@@ -173,7 +173,7 @@ def test_mc_rows_identical_streams_poisson46_sampled(pdd):
 def test_solution_poisson46_against_oracle(pdd):
     """Whole path on the Eq. 46 workload (32 paths per knot, FP64 form, identical streams).
 
-    With 44 knots per arc and c^2 = 1.5 in the angle (Sec. 5), the IMQ matrices K of the perimeter
+    With 44 knots per arc and c^2 = 1.5 in the angle (Sec. 4), the IMQ matrices K of the perimeter
     circles have kappa(K) up to ~7e11, so their rows of C are fixed by FP64 only to ~16 kappa(K) u
     (~1e-3 relative); the moments are not affected.  Checks: every entry of C and r within its own
     bound (floating rows 1e-9), and u within the perturbation bound
@@ -214,7 +214,7 @@ def test_solution_poisson46_against_oracle(pdd):
 
 
 def test_poisson46_full_size_accuracy(pdd):
-    """Sec. 5 parameters (5,000 paths per knot, h = 0.015, boundary shift), mixed form with RAS:
+    """Sec. 4 parameters (5,000 paths per knot, h = 0.015, boundary shift), mixed form with RAS:
     the interfacial solution against u46 at the knots.  Without the paper's pathwise variance
     reduction the error is the Monte Carlo one: 32 paths give RMS ~2e-2 on the oracle, so 5,000
     give ~2e-3; the bound leaves a factor 2.5."""

@@ -106,7 +106,7 @@ def test_manufactured_variable_coefficients():
 
 
 def test_eq46_disk_reproduces_the_exact_solution():
-    """Sec. 5's floating disk: radius 9, 44 knots, 22 x 44 nodes, Poisson data of Eq. 46.  The
+    """Sec. 4's floating disk: radius 9, 44 knots, 22 x 44 nodes, Poisson data of Eq. 46.  The
     paper reports a maximum interior error of order 1e-12 for this solver; the row identity
     u(x_i) = -sum_j C_ij u_j + r_i holds to the knot interpolation error."""
     cfg = workloads.poisson46()

@@ -25,7 +25,7 @@ Workloads (the problem is Eq. 1 with L = 1/2 Laplacian + b.grad, sigma = I):
                    Monte Carlo knot, up to 10^5 where its standard error exceeds 2e-3.
 * ``grad``      -- ``tiny`` geometry; parameters are 64 RBF weights of c and 32
                    Fourier coefficients of g along the boundary arclength.
-* ``poisson46`` -- the paper's Poisson test (Sec. 5, Eq. 46) on [-50,50]^2: f and g from
+* ``poisson46`` -- the paper's Poisson test (Sec. 4, Eq. 46) on [-50,50]^2: f and g from
                    its exact solution u46, L = 1/2 Lap (so 1/2 Lap u = F/2 with
                    F = Lap u46); 10x10 square lattice of circles of radius 9 (the
                    paper's radii lie in [8.55, 9.43]; its layout figure is not
@@ -256,7 +256,7 @@ def poisson46(paths: int = 5000, h: float = 0.015, seed: int = 0, half_width: fl
     """Poisson's equation with the exact solution of Eq. 46 on [-L, L]^2, L = half_width.
 
     Circles of radius 9 on a square lattice of pitch 10 (centres at -L + 5, ..., L - 5),
-    44 knots each, 22 x 44 pseudospectral nodes on the floating disks, as in Sec. 5.
+    44 knots each, 22 x 44 pseudospectral nodes on the floating disks, as in Sec. 4.
     """
     n = int(round(2.0 * half_width / 10.0))
     return {
