@@ -63,3 +63,21 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     so = pkg._SolveOpts(0, 10, 1e-10, 0)
     st = pkg._lib.pdd_solve_csr(4, None, None, None, None, None, ctypes.byref(so), None, None)
     assert st == 1
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu(lib):
+    """The row mode, the Eq. 46 families and the new accessors are validated on the host."""
+    import paper_2311_08946_gb300 as pkg
+    pkg.load()
+    h = ctypes.c_void_p()
+    dom = pkg._Domain(0, (ctypes.c_double * 4)(0, 0, 1, 1))
+    spec = pkg._CoverSpec(0, 4, 4, 0.125, 0.125, 0.25, 0.2, 16, 16, 16, 0, None, None, None, None, None, None, 7)
+    st = pkg._lib.pdd_build_cover(ctypes.byref(dom), ctypes.byref(spec), ctypes.byref(h), None)
+    assert st == 1 and b"row mode" in pkg._lib.pdd_last_error()
+    n = ctypes.c_int()
+    pp = ctypes.c_void_p()
+    assert pkg._lib.pdd_cover_rows(None, ctypes.byref(n), ctypes.byref(pp), ctypes.byref(pp)) == 1
+    assert pkg._lib.pdd_system_mc_subs(None, ctypes.byref(pp)) == 1
+    assert pkg.ROW_MODE == {"farthest": 0, "averaged": 1}
+    assert pkg._F["eq46"] == 3 and pkg._G["eq46"] == 5
+
