@@ -2,22 +2,23 @@
 // 56 and sigma = I), IMQ cardinals on perimeter arcs (Eq. 19-22).
 //
 //   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c^2)^-1/2 per perimeter stencil,
-//       Cholesky factor and K^-1 in FP64 (one CTA per circle).
+//       Cholesky factor and K^-1 in FP64 (one CTA per circle), and kappa_1(K).
 //   a11 k_paths: Euler-Maruyama paths of dX = b dt + dW, dY = c Y dt,
 //       dZ = f Y dt from the knot, stopped at the first step whose end point
-//       leaves the open disk or the open domain.  One CTA per row; each thread
-//       runs paths p = tid, tid + blockDim, ... (a lane takes its next path as
-//       soon as one exits).  Exit point: the first crossing of the segment
-//       with the circle or dOmega (ties to dOmega).  Normals: Philox4x32-10,
-//       key (seed, knot), counter (step, path, 0, 0).  FP64 form: every
-//       quantity in FP64.  Mixed form: position, drift and normals in FP32,
-//       weights Y, Z and all scores in FP64.  Per-path exit records (side,
-//       angle or arclength, Y, Z) go to a device scratch buffer.
-//   a12 k_mc_finalize: one CTA of 32 warps per row; warp b owns batch b
-//       (paths p = b mod 32) and its lanes own basis functions.  The row's
+//       leaves the open disk or the open domain (optionally both shrunk by the
+//       Gobet-Menozzi shift).  One CTA per (row, subdomain) slot; a lane takes
+//       the row's next path id as soon as its path exits.  Exit point: the
+//       first crossing of the segment with the circle or dOmega (ties to
+//       dOmega).  Normals: Philox4x32-10, key (seed, knot), counter (step,
+//       path, 0, k) with k the subdomain's position in the row's list.  FP64
+//       form: every quantity in FP64.  Mixed form: position, drift and normals
+//       in FP32, weights Y, Z and all scores in FP64.  Per-path exit records
+//       (side, angle or arclength, Y, Z) go to a device scratch buffer.
+//   a12 k_mc_finalize: one CTA of 16 warps per slot; warp w owns batches w and
+//       w + 16 (paths p = b mod 32) and its lanes own basis functions.  The
 //       moments M_l = E[1_Gamma Y phi_l(u)], C_ij = -sum_l (K^-1)_lj M_l (IMQ)
-//       or -M_j (Fourier cardinals), r_i = E[1_dOmega g Y + Z]; standard errors
-//       by batch means over the 32 batches.
+//       or -M_j (Fourier cardinals), the slot's part of r_i = E[1_dOmega g Y +
+//       Z]; standard errors by batch means over the 32 batches.
 #include <algorithm>
 #include <vector>
 
