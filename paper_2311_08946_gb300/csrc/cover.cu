@@ -16,7 +16,8 @@
 //     outside Omega (first such arc in angle order when lengths agree to 1e-9);
 //   * row i goes to the circle with the largest r_m - |x_i - c_m| among those
 //     (other than its owner) whose score exceeds 1e-12 r_owner; scores within
-//     1e-12 r_owner of the best tie to the lowest circle index.
+//     1e-12 r_owner of the best tie to the lowest circle index;
+//   * averaged rows (Eq. 38-39): row i goes to every such circle, ascending.
 #include <algorithm>
 
 #include "handles.cuh"

@@ -4,15 +4,19 @@
 //   a6  k_node_coef + k_fill_operator: per-node FP64 coefficients and row
 //       scales (one thread per node), the right-hand sides [A_IB H, -f], then
 //       the rows of the row-equilibrated collocation matrix of L + c.
-//   a7  k_lu: right-looking blocked LU with partial pivoting, one CTA per
-//       disk, panel in shared memory.  The paper factors by QR (Eq. 41);
-//       LU solves the same systems.
-//   a8  k_lu_solve (+ k_residual): multi-RHS forward/back substitution; in
-//       the mixed form the factors are FP32 and FP64 iterative refinement
-//       with a matrix-free FP64 residual recovers the FP64 solution.
-//   a9  k_disk_eval: tensor interpolation (barycentric Chebyshev in r over all
-//       2 n_r + 2 points, the Fourier cardinal in theta) at the disk's knots,
-//       scattered into the CSR values of C and into r.
+//   a7  FP64 form: k_lu, right-looking blocked LU with partial pivoting, one
+//       CTA per disk, panel in shared memory.  Mixed form: the recursive FP32
+//       LU of lu_rec.cu (tensor-core Schur updates) or the blocked one, chosen
+//       by tune_lu.  The paper factors by QR (Eq. 41); LU solves the same
+//       systems.
+//   a8  FP64 form: k_lu_solve.  Mixed form: k_lu_solve_rl on the transposed
+//       FP32 factors, refined in FP64 (first residual k_residual in FP64,
+//       later ones k_residual_df in double-float delta form) until the
+//       predicted next correction is below the tolerance.
+//   a9  k_disk_eval / k_disk_eval_df: tensor interpolation (barycentric
+//       Chebyshev in r over all 2 n_r + 2 points, the Fourier cardinal in
+//       theta) at the knots of every row the disk contributes to, written into
+//       the CSR values of C and the row's part of r.
 //
 // Grid: N_c = 2 n_r + 1 Chebyshev points x_k = cos(k pi / N_c); unknowns at
 // radius x_k (k = 1..n_r) and angle t_j = 2 pi j / n_theta, index
