@@ -496,6 +496,25 @@ struct FinalArgs {
     double *moments, *bmean, *val, *se, *bs, *se_bs;
 };
 
+// v = hi + lo with hi = v truncated to 24 significant bits and lo the rest rounded to FP32, built
+// from the bit fields by integer operations (the FP64 pipe of this part is 1/64 of the FP32 rate).
+// |v| < 2^-126 gives (0, 0) and |v| < 2^-74 drops lo (relative error up to 2^-23 there); above
+// that the split is within 2^-47 relative (an emulation over 2e4 values per decade); the Monte Carlo
+// weights and exit angles are far from either.
+__device__ __forceinline__ float2 split_df_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int eh = e - 896;                                 // FP32 biased exponent of hi
+    if (eh >= 255) return make_float2((float)v, 0.f);       // beyond FP32 range (not reached)
+    if (eh <= 0) return make_float2(__uint_as_float(sign), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned)eh << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+    const int el = e - 948;                                 // FP32 biased exponent of 2^(e - 1075)
+    float lo = 0.f;
+    if (el > 0) lo = __fmul_rn(__uint2float_rn((unsigned)(b & 0x1FFFFFFFull)), __uint_as_float((unsigned)el << 23));
+    return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
 // 1 / sqrt(q) for q = qh + ql in double-float: one Newton step from rsqrtf, whose residual
 // t = 1 - q r0^2 is formed without rounding error in its leading part (r0^2 and q r0^2 by FMA
 // splits; 1 - h is exact because h is within 2^-22 of 1); relative error below 1e-13
@@ -563,17 +582,23 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             const int pl = bt + kBatches * (t0 + lane);
             int sd = 2;
             double yv = 0.0, zv = 0.0, su = 0.0;
+            double yraw = 0.0;
+            float ey = 0.f;                                // mixed form: the unfolded increment of Y
             if (pl < npath) {
                 sd = F.side[base + pl];
-                yv = F.Y[base + pl];
+                yraw = F.Y[base + pl];
                 zv = F.Z[base + pl];
                 su = F.su[base + pl];
                 if (F.mixed) {
                     const float2 q = F.ez[base + pl];
-                    zv = fma(yv, (double)q.y, zv);
-                    yv = fma(yv, (double)q.x, yv);
+                    zv = fma(yraw, (double)q.y, zv);
+                    ey = q.x;
                 }
             }
+            // Y (1 + e) in FP64 where it is used in FP64: always, except for the double-float basis
+            // sums, which need it only for a boundary score
+            yv = yraw;
+            if (F.mixed && ey != 0.f && (mode != 1 || sd == 1)) yv = fma(yraw, (double)ey, yraw);
             if (sd != 2) {                                 // this lane's own contribution to r_i
                 ++cnt;
                 if (sd == 1) {
@@ -607,9 +632,17 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                     }
                 }
             } else if (mode == 1) {
-                // double-float: the record's Y and angle split once per lane, then shuffled
-                const float yh = (float)yv, yl = (float)(yv - (double)yh);
-                const float sh = (float)su, sl = (float)(su - (double)sh);
+                // double-float: the record's Y and angle split once per lane by integer operations
+                // (no FP64 instruction), Y (1 + e) formed in double-float, then shuffled
+                float2 y2 = split_df_bits(yraw);
+                if (ey != 0.f) {
+                    const float p = __fmul_rn(y2.x, ey);
+                    float pe = fmaf(y2.x, ey, -p);
+                    pe = fmaf(y2.y, ey, pe);
+                    y2 = df_add(y2, make_float2(p, pe));
+                }
+                const float2 s2 = split_df_bits(su);
+                const float yh = y2.x, yl = y2.y, sh = s2.x, sl = s2.y;
                 for (int src = 0; src < 32; ++src) {
                     const int s_sd = __shfl_sync(0xffffffffu, sd, src);
                     const float s_yh = __shfl_sync(0xffffffffu, yh, src);
@@ -641,15 +674,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                         accf[q] = sh2;
                         accl[q] = __fadd_rn(accl[q], __fadd_rn(se2, me));
                     }
-                    if (++pend == 16) {
-#pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            acc[q] += (double)accf[q] + (double)accl[q];
-                            accf[q] = 0.f;
-                            accl[q] = 0.f;
-                        }
-                        pend = 0;
-                    }
+                    // (no periodic fold: a double-float sum of a batch's paths stays within ~1e-13)
                 }
             } else {
                 for (int src = 0; src < 32; ++src) {
