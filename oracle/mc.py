@@ -13,8 +13,12 @@ sqrt(paths).
 
 Pins (tests): the generator against an independent Philox4x32-10
 implementation; exit statistics of Brownian motion from a disk (mean exit
-time (R^2 - |x|^2)/2, harmonic measure = Poisson kernel); constant data give
-unit rows up to the interpolation error.  Test infrastructure only.
+time (R^2 - |x|^2)/2, harmonic measure = Poisson kernel); the boundary shift
+against optional stopping of a harmonic function on circles cut by one and by
+two edges of the square (exits on their edges); the batch-means standard error
+against its chi-square law on normal samples; the adaptive path counts by
+hand; constant data give unit rows up to the interpolation error.  Test
+infrastructure only.
 """
 from __future__ import annotations
 
@@ -181,8 +185,12 @@ def batch_mean_se(per_path, bsamp, batches=32):
 
 
 def adaptive_paths(P0, Pmax, se, target):
-    """Path count of the adaptive rule: P0 (se/target)^2 within [P0, Pmax], rounded up to 32."""
-    want = min(max(math.ceil(P0 * (se / target) ** 2), P0), Pmax)
+    """Path count of the adaptive rule: a row whose largest standard error se is at most the
+    target keeps its P0 pilot paths; otherwise ceil(P0 (se/target)^2) rounded up to a
+    multiple of 32, capped at Pmax."""
+    if not se > target:
+        return P0
+    want = math.ceil(P0 * (se / target) ** 2)
     want = ((want + 31) // 32) * 32
     return min(want, Pmax)
 

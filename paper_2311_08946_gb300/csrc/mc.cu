@@ -843,9 +843,14 @@ __global__ void k_need(int nmc, const int *rows, const int *subs, const int *spo
     const int a = knot_ptr[m], ns = knot_ptr[m + 1] - a, off = sub_off[pe];
     double mx = se_bs[pe];
     for (int j = 0; j < ns; ++j) mx = fmax(mx, se[rowptr[i] + off + j]);
+    // rows at or below the target keep the pilot; the others rerun with ceil(P0 (se/target)^2)
+    // paths rounded up to a multiple of 32, capped at Pmax
+    if (!(mx > target)) {
+        need[slot] = P0;
+        return;
+    }
     const double r = mx / target;
-    double want = ceil(P0 * r * r);
-    want = fmin(fmax(want, (double)P0), (double)Pmax);
+    const double want = fmin(ceil(P0 * r * r), (double)Pmax);
     int w = (int)want;
     w = ((w + 31) / 32) * 32;
     need[slot] = w > Pmax ? Pmax : w;

@@ -130,6 +130,92 @@ def test_boundary_shift_removes_the_exit_bias():
         assert np.abs(d - R).max() < 1e-12
 
 
+def test_boundary_shift_on_the_square_edges():
+    """Gobet-Menozzi projection onto the domain's edges (the paths of a perimeter circle that
+    leave through dOmega): with L = Laplacian/2, f = c = 0 and the harmonic u = e^x sin y,
+    optional stopping gives E[u(X_tau)] = u(x0) for the exact exit law.  On a circle cut by one
+    edge and on a corner circle cut by two, at sqrt(h) = r/10, the shifted scheme scored at its
+    projected exit points is within 4 SE + h of u(x0), while the plain scheme shows its
+    O(sqrt h) bias (> 5 SE).  Every exit through dOmega lies exactly on the edge it records,
+    inside the closed square, and every interface exit lies on the circle."""
+    dom = problem.Domain({"kind": "square", "p": [0.0, 0.0, 1.0, 1.0]})
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"}, dom)
+    edge_value = {0: ("y", 0.0), 1: ("x", 1.0), 2: ("y", 1.0), 3: ("x", 0.0)}
+    # (circle, start): one cut by the bottom edge, one cut by the left and bottom edges
+    for (cx, cy, r), (x0, y0), want_edges in (((0.5, 0.1, 0.3), (0.45, 0.12), {0}),
+                                              ((0.1, 0.1, 0.3), (0.12, 0.15), {0, 3})):
+        h = (0.1 * r) ** 2
+        shift = mc.boundary_shift({"h": h, "boundary_shift": True})
+        u0 = math.exp(x0) * math.sin(y0)
+        plain = mc.walk(op, cx, cy, r, x0, y0, 7, 3, h, 100000)
+        shifted = mc.walk(op, cx, cy, r, x0, y0, 7, 3, h, 100000, shift=shift)
+        us = np.exp(shifted.ex) * np.sin(shifted.ey)
+        up = np.exp(plain.ex) * np.sin(plain.ey)
+        se = us.std(ddof=1) / math.sqrt(us.size)
+        assert abs(us.mean() - u0) < 4 * se + h, (cx, cy, us.mean(), u0, se)
+        assert up.mean() - u0 > 5 * se, (cx, cy, up.mean(), u0, se)
+        side1 = shifted.side == 1
+        assert 0.2 < side1.mean() < 0.8
+        assert set(np.unique(shifted.edge[side1]).tolist()) == want_edges
+        for e, (axis, v) in edge_value.items():
+            sel = side1 & (shifted.edge == e)
+            coord = shifted.ey if axis == "y" else shifted.ex
+            assert np.all(coord[sel] == v), e
+        assert np.all((shifted.ex[side1] >= 0.0) & (shifted.ex[side1] <= 1.0))
+        assert np.all((shifted.ey[side1] >= 0.0) & (shifted.ey[side1] <= 1.0))
+        side0 = shifted.side == 0
+        d = np.hypot(shifted.ex[side0] - cx, shifted.ey[side0] - cy)
+        assert np.abs(d - r).max() < 1e-12
+
+
+def test_batch_mean_standard_error():
+    """The batch-means standard error (path p in batch p mod 32) on i.i.d. N(mu, s^2) samples:
+    with equal batches, 31 (SE / (s / sqrt(P)))^2 is chi-square with 31 degrees of freedom.
+    Every replicate lies inside its 1e-6 quantiles, and the mean of (SE / (s / sqrt(P)))^2
+    over 4000 replicates is 1 within 5 of its standard deviations (a wrong degrees-of-freedom
+    factor, 32/31, is 6 of them).  The estimator reports the largest SE over the row's
+    columns and its right-hand side."""
+    from scipy.stats import chi2
+    rng = np.random.default_rng(11)
+    P, s = 32 * 40, 2.5
+    lo, hi = chi2.ppf(1e-6, 31) / 31, chi2.ppf(1 - 1e-6, 31) / 31
+    ratios = []
+    for _ in range(4000):
+        x = 3.0 + s * rng.standard_normal(P)
+        se = mc.batch_mean_se(np.zeros((P, 0)), x)
+        ratios.append((se / (s / math.sqrt(P))) ** 2)
+    ratios = np.array(ratios)
+    assert np.all((ratios > lo) & (ratios < hi)), (ratios.min(), ratios.max())
+    sd = math.sqrt(2.0 / 31.0) / math.sqrt(ratios.size)
+    assert abs(ratios.mean() - 1.0) < 5 * sd, ratios.mean()
+    # the largest over the columns and the right-hand side
+    a = rng.standard_normal(P)
+    cols = np.stack([0.01 * a, 10.0 * a], 1)
+    assert mc.batch_mean_se(cols, 0.1 * a) == pytest.approx(mc.batch_mean_se(np.zeros((P, 0)), 10.0 * a), rel=1e-12)
+    # a constant sample has zero standard error; batch membership is p mod 32
+    assert mc.batch_mean_se(np.zeros((P, 1)), np.full(P, 4.0)) == 0.0
+    y = np.where(np.arange(P) % 32 == 5, 1.0, 0.0)
+    bm = np.zeros(32)
+    bm[5] = 1.0
+    want = math.sqrt(np.sum((bm - bm.mean()) ** 2) / 31.0 / 32.0)
+    assert mc.batch_mean_se(np.zeros((P, 0)), y) == pytest.approx(want, rel=1e-12)
+
+
+def test_adaptive_path_counts_by_hand():
+    """The adaptive rule: a row whose largest standard error se exceeds the target reruns with
+    ceil(P0 (se/target)^2) paths rounded up to a multiple of 32 and capped at paths_max; a row at
+    or below the target keeps its pilot."""
+    assert mc.adaptive_paths(1000, 100000, 2.0e-3, 2.0e-3) == 1000
+    assert mc.adaptive_paths(1000, 100000, 1.0e-3, 2.0e-3) == 1000
+    assert mc.adaptive_paths(1000, 100000, 4.0e-3, 2.0e-3) == 4000        # 1000 * 4
+    assert mc.adaptive_paths(1000, 100000, 3.0e-3, 2.0e-3) == 2272        # 2250 -> 71 * 32
+    assert mc.adaptive_paths(1000, 100000, 2.002e-3, 2.0e-3) == 1024      # 1002.001 -> 1003 -> 32 * 32
+    assert mc.adaptive_paths(1000, 100000, 1.0, 2.0e-3) == 100000         # capped
+    assert mc.adaptive_paths(1000, 5000, 1.0, 2.0e-3) == 5000
+    assert mc.adaptive_paths(1000, 5010, 1.0, 2.0e-3) == 5010             # the cap itself, not rounded past it
+    assert mc.adaptive_paths(64, 1000, 5.0, 1.0) == 1000                  # 64 * 25 = 1600 -> cap
+
+
 def test_feynman_kac_eq46_on_a_disk():
     """Feynman-Kac (Eq. 25-27) for the Poisson test of Eq. 46 on a radius-9 disk at h = 0.015
     with the boundary shift: E[u46(X_tau) + Z_tau] = u46(x0) within 4 SE + the O(h) bias.  This
