@@ -171,13 +171,32 @@ enum { PDD_FACTOR_RECURSIVE_TC = 0,      /* recursive LU, Schur updates on tcgen
 enum { PDD_FLOATING_PSEUDOSPECTRAL = 0,   /* Sec. 3.3 (default)                      */
        PDD_FLOATING_MONTE_CARLO = 1 };    /* integrate floating rows by paths too     */
 
+/* Per-stage overrides of `precision`: the floating disks (a6-a9) and the Monte
+ * Carlo paths (a11) may take different forms, e.g. mixed disks with FP64 paths
+ * on the oracle's Philox streams. */
+enum { PDD_STAGE_DEFAULT = 0,   /* as `precision`                                    */
+       PDD_STAGE_FP64 = 1,
+       PDD_STAGE_MIXED = 2 };
+
+/* Summation of the IMQ basis moments M_l of mixed-form paths (a12).  C = -K^-T M
+ * amplifies their rounding by up to kappa(K). */
+enum { PDD_SUMS_AUTO = 0,          /* by kappa_1(K): FP32 up to 1e5, double-float up to
+                                      1e10, FP64 beyond                              */
+       PDD_SUMS_FP32 = 1,          /* FP32 values of phi, FP32 sums of 16 paths       */
+       PDD_SUMS_DOUBLE_FLOAT = 2,  /* double-float phi and sums (~1e-13 relative)     */
+       PDD_SUMS_FP64 = 3 };
+
 typedef struct {
     int precision;            /* PDD_PREC_*                                          */
     int floating_method;      /* PDD_FLOATING_*                                      */
     int paths;                /* Monte Carlo paths per knot (> 0)                    */
     double h;                 /* Euler-Maruyama time step (> 0)                      */
     uint64_t seed;            /* Philox key word 0 (low 32 bits used)                */
-    double imq_c2;            /* IMQ shape c^2 of Eq. 19 (1.5 in the paper)          */
+    double imq_c2;            /* IMQ shape c^2 of Eq. 19 in squared length units:
+                                 theta is measured along the interface (arclength
+                                 r_m u for the local angle u), so a circle's
+                                 cardinals are those of u with c^2 / r_m^2 (1.5 on
+                                 the paper's radius-9 circles, Sec. 4)               */
     int max_refine;           /* refinement sweeps cap (mixed form), e.g. 12         */
     double refine_tol;        /* stop when |dx|_inf <= tol |x|_inf per column        */
     int factor;               /* mixed form's LU: PDD_FACTOR_*                        */
@@ -195,6 +214,14 @@ typedef struct {
                                  the path scored at the projection of its first
                                  point outside onto that piece of the true boundary;
                                  0: plain exit at the first crossing of the segment */
+    int max_steps;            /* Euler-Maruyama steps allowed per path; 0 = 50 r^2/h
+                                 (about 100 mean exit times).  A path that reaches
+                                 the cap is not scored: the call returns
+                                 PDD_EPATH_CAP (the system is still created only
+                                 when no path was capped)                            */
+    int disk_precision;       /* PDD_STAGE_*: form of the floating disks (a6-a9)     */
+    int path_precision;       /* PDD_STAGE_*: form of the Monte Carlo paths (a11)    */
+    int moment_sums;          /* PDD_SUMS_*: basis sums of mixed-form paths (a12)    */
 } pdd_assembly_opts;
 
 typedef struct {
@@ -322,6 +349,13 @@ pdd_status pdd_solve(const pdd_system *sys, const pdd_solve_opts *opts, double *
 pdd_status pdd_ras_apply(const pdd_system *sys, const double *v_dev, double *y_dev, void *stream);
 
 /*
+ * Failure injection (tests): with PDD_INJECT_BARRIER_TIMEOUT=1 in the environment, every grid
+ * barrier of the solver's fused Arnoldi kernel waits for one block more than the grid holds,
+ * with a short poll limit; the blocks give up, record the error and return, and the solve
+ * returns PDD_ECUDA ("grid barrier timed out").  The device context stays usable.
+ */
+
+/*
  * pdd_solve_csr -- the same solver on any square CSR matrix in device memory
  * (rowptr [n+1], col [nnz] int32 sorted per row; val [nnz], b [n], u [n]
  * double).  u is overwritten (the initial guess is 0).  Workspace is
@@ -346,7 +380,8 @@ pdd_status pdd_solve_csr(int n, const int *rowptr_dev, const int *col_dev, const
  *   the sizes in pdd_last_error() and touch nothing.
  *   The first call on a device looks up the array's device address once
  *   (with that device current); make that first call before any stream
- *   capture on the device.
+ *   capture on the device.  The address is kept for the process: do not
+ *   reset the device (cudaDeviceReset) between calls.
  *   Every call uses the same array, which keeps the previous call's contents
  *   (the solver clears what must start at zero).  Calls that overlap on the
  *   GPU -- on different streams, or from different host threads, on the same

@@ -113,7 +113,8 @@ def gradient(cfg, system, u, dJdu):
             H = spectral.fourier_cardinal(rec.etheta, tk, n)
         else:
             ut = np.array([unwrap(t, float(cov.theta_s[m])) for t in rec.etheta])
-            H = imq.imq(ut, row.u_stencil, c2) @ row.Kinv if row.cols.size else np.zeros((P, 0))
+            ca = imq.angle_c2(c2, cov.r[m])
+            H = imq.imq(ut, row.u_stencil, ca) @ row.Kinv if row.cols.size else np.zeros((P, 0))
         uhat = np.where(gam, H @ uX if row.cols.size else 0.0, 0.0)
         gv = np.zeros(P)
         if np.any(bnd):

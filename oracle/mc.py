@@ -197,7 +197,7 @@ def adaptive_paths(P0, Pmax, se, target):
 
 def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = "imq",
            with_grad=False, Kinv=None) -> McRow:
-    """a11 + a12 for knot i integrated in subdomain m.
+    """a11 + a12 for knot i integrated in subdomain m (c2: c^2 of Eq. 19 in squared length).
 
     With mc["paths_max"] > mc["paths"] and mc["se_target"] > 0 the pilot of
     mc["paths"] paths is followed, when the row's largest batch-means standard
@@ -227,8 +227,8 @@ def _sub_index(cov, i, m):
 def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis, with_grad, Kinv, P) -> McRow:
     cx, cy, r = float(cov.cx[m]), float(cov.cy[m]), float(cov.r[m])
     rec = walk(op, cx, cy, r, float(cov.kx[i]), float(cov.ky[i]), i, int(mc["seed"]),
-               float(mc["h"]), P, with_grad=with_grad, shift=boundary_shift(mc),
-               sub=_sub_index(cov, i, m))
+               float(mc["h"]), P, with_grad=with_grad, max_steps=mc.get("max_steps") or None,
+               shift=boundary_shift(mc), sub=_sub_index(cov, i, m))
     if rec.capped:
         raise RuntimeError(f"EPATH_CAP: {rec.capped} paths of knot {i} hit the step cap")
     a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
@@ -241,10 +241,11 @@ def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis,
         gvals[bnd] = op.g(rec.ex[bnd], rec.ey[bnd], rec.edge[bnd].astype(np.int64))
     bsamp = np.where(bnd, gvals * rec.Y, 0.0) + rec.Z
     if basis == "imq":
+        ca = imq.angle_c2(c2, r)
         if Kinv is None and us.size:
-            Kinv = imq.inverse(us, c2)
+            Kinv = imq.inverse(us, ca)
         ut = np.array([unwrap(t, float(cov.theta_s[m])) for t in rec.etheta])
-        phi = imq.imq(ut, us, c2) if us.size else np.zeros((P, 0))
+        phi = imq.imq(ut, us, ca) if us.size else np.zeros((P, 0))
         phi = np.where(gam[:, None], phi, 0.0)
         moments = (phi * rec.Y[:, None]).sum(0) / P
         vals = -(Kinv.T @ moments) if us.size else np.zeros(0)
@@ -281,7 +282,7 @@ def mc_rows(cov, op: Operator, rows, mc: dict, c2: float, threads: int = 1, basi
     def kinv(m):
         if m not in Kcache:
             a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
-            Kcache[m] = imq.inverse(cov.ku[a:b], c2) if b > a else np.zeros((0, 0))
+            Kcache[m] = imq.inverse(cov.ku[a:b], imq.angle_c2(c2, cov.r[m])) if b > a else np.zeros((0, 0))
         return Kcache[m]
 
     def one(item):

@@ -77,7 +77,13 @@ class _AssemblyOpts(ctypes.Structure):
                 ("imq_c2", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("factor", ctypes.c_int),
                 ("lu_leaf_width", ctypes.c_int), ("lu_tensor_min", ctypes.c_int),
-                ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double), ("boundary_shift", ctypes.c_int)]
+                ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double), ("boundary_shift", ctypes.c_int),
+                ("max_steps", ctypes.c_int), ("disk_precision", ctypes.c_int), ("path_precision", ctypes.c_int),
+                ("moment_sums", ctypes.c_int)]
+
+
+STAGE = {None: 0, "fp64": 1, "mixed": 2}
+SUMS = {"auto": 0, "fp32": 1, "double_float": 2, "fp64": 3}
 
 
 class _AssemblyStats(ctypes.Structure):
@@ -250,13 +256,17 @@ FACTOR = {"recursive_tc": 0, "blocked": 1}
 
 def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps",
                   max_refine: int = 12, refine_tol: float = 1e-14, factor: str = "recursive_tc",
-                  lu_leaf_width: int = 0, lu_tensor_min: int = 0) -> _AssemblyOpts:
+                  lu_leaf_width: int = 0, lu_tensor_min: int = 0, disk_precision: str | None = None,
+                  path_precision: str | None = None, moment_sums: str = "auto") -> _AssemblyOpts:
+    """pdd_assembly_opts from a workload; disk_precision / path_precision ("fp64" or "mixed")
+    override `precision` for one stage, moment_sums picks the mixed paths' basis sums."""
     mc = cfg["mc"]
     return _AssemblyOpts(PREC[precision], 0 if floating_method == "ps" else 1, int(mc["paths"]),
                          float(mc["h"]), int(mc["seed"]), float(cfg.get("imq_c2", 1.5)),
                          int(max_refine), float(refine_tol), FACTOR[factor], int(lu_leaf_width),
                          int(lu_tensor_min), int(mc.get("paths_max", 0)), float(mc.get("se_target", 0.0)),
-                         1 if mc.get("boundary_shift", False) else 0)
+                         1 if mc.get("boundary_shift", False) else 0, int(mc.get("max_steps", 0)),
+                         STAGE[disk_precision], STAGE[path_precision], SUMS[moment_sums])
 
 
 # ---------------------------------------------------------------------------
@@ -314,7 +324,8 @@ class System:
     def __init__(self, cov: Cover, cfg: dict | None = None, precision: str = "fp64",
                  floating_method: str = "ps", stream=None, max_refine: int = 12,
                  refine_tol: float = 1e-14, factor: str = "recursive_tc", lu_leaf_width: int = 0,
-                 lu_tensor_min: int = 0):
+                 lu_tensor_min: int = 0, disk_precision: str | None = None, path_precision: str | None = None,
+                 moment_sums: str = "auto"):
         lib = load()
         self.cov = cov
         self.cfg = cfg or cov.cfg
@@ -322,7 +333,7 @@ class System:
         self.floating_method = floating_method
         self._op, self._keep = operator_struct(self.cfg["op"])
         self._opts = assembly_opts(self.cfg, precision, floating_method, max_refine, refine_tol, factor,
-                                   lu_leaf_width, lu_tensor_min)
+                                   lu_leaf_width, lu_tensor_min, disk_precision, path_precision, moment_sums)
         h = ctypes.c_void_p()
         _check(lib.pdd_assemble_G(cov.handle, ctypes.byref(self._op), ctypes.byref(self._opts),
                                   ctypes.byref(h), _stream(stream)))

@@ -165,6 +165,11 @@ static void check_opts(const pdd_assembly_opts *o) {
     if (o->lu_tensor_min < 0) fail(PDD_EINVAL, "lu_tensor_min must be >= 0");
     if (o->paths_max > 0 && o->paths_max > (1 << 28)) fail(PDD_EINVAL, "paths_max too large");
     if (o->paths <= 1 || !(o->h > 0) || !(o->imq_c2 > 0)) fail(PDD_EINVAL, "paths > 1, h > 0 and c^2 > 0 required");
+    if (o->max_steps < 0) fail(PDD_EINVAL, "max_steps must be >= 0 (0: 50 r^2/h)");
+    if (o->disk_precision < PDD_STAGE_DEFAULT || o->disk_precision > PDD_STAGE_MIXED ||
+        o->path_precision < PDD_STAGE_DEFAULT || o->path_precision > PDD_STAGE_MIXED)
+        fail(PDD_EINVAL, "unknown stage precision");
+    if (o->moment_sums < PDD_SUMS_AUTO || o->moment_sums > PDD_SUMS_FP64) fail(PDD_EINVAL, "unknown moment summation");
 }
 
 }  // namespace pdd
@@ -257,7 +262,7 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         s->N = cov->N;
         s->nnz = cov->nnz;
         s->cov = cov;
-        s->precision = opts->precision;
+        s->precision = disk_mixed(*opts) || path_mixed(*opts) ? PDD_PREC_MIXED : PDD_PREC_FP64;
         s->val.alloc(cov->nnz);
         s->b.alloc(cov->N);
         const int nsub = std::max(cov->h_sub_ptr.empty() ? 0 : cov->h_sub_ptr.back(), 1);

@@ -1598,7 +1598,7 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
     for (auto &kv : groups) {
         ShapeTables tab;
         tab.build(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), st);
-        DiskStats d = (o.precision == PDD_PREC_MIXED)
+        DiskStats d = disk_mixed(o)
                           ? run_group<float>(cov, P, o, sys, tab, kv.second, st)
                           : run_group<double>(cov, P, o, sys, tab, kv.second, st);
         all.disks += d.disks;

@@ -58,6 +58,14 @@ struct pdd_system {
 
 namespace pdd {
 
+// the form each stage runs in: `precision`, unless the stage's own override is set
+inline bool disk_mixed(const pdd_assembly_opts &o) {
+    return o.disk_precision != PDD_STAGE_DEFAULT ? o.disk_precision == PDD_STAGE_MIXED : o.precision == PDD_PREC_MIXED;
+}
+inline bool path_mixed(const pdd_assembly_opts &o) {
+    return o.path_precision != PDD_STAGE_DEFAULT ? o.path_precision == PDD_STAGE_MIXED : o.precision == PDD_PREC_MIXED;
+}
+
 // device problem description (uploads the operator's host arrays)
 struct ProblemHolder {
     Problem P{};

@@ -9,6 +9,7 @@
 // cooperative kernel (k_arnoldi_fused); the Hessenberg matrix, Givens
 // rotations and the residual estimate live on the device, and the host
 // synchronises once per restart cycle to read the true residual.
+#include <cstdlib>
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -171,6 +172,8 @@ struct FusedArnoldi {
     int *err;
     double rtol;
     int max_iters;
+    unsigned bar_extra;          // arrivals a barrier waits for beyond the grid (0; 1 = never completes)
+    long long bar_limit;         // polls before a barrier wait gives up
     // right preconditioner (Eq. 44-45); ras_P = 0: none
     int ras_P, ras_NP;
     const int *ras_wptr, *ras_widx, *ras_p1, *ras_l1, *ras_p2, *ras_l2;
@@ -189,14 +192,14 @@ __device__ __forceinline__ bool grid_barrier(const FusedArnoldi &F) {
         volatile unsigned *gen = F.bar + 1;
         const unsigned g0 = *gen;
         __threadfence();
-        if (atomicAdd(F.bar, 1u) == gridDim.x - 1) {
+        if (atomicAdd(F.bar, 1u) == gridDim.x - 1 + F.bar_extra) {
             atomicExch(F.bar, 0u);
             __threadfence();
             atomicAdd(F.bar + 1, 1u);
         } else {
             long long it = 0;
             while (*gen == g0) {
-                if (++it > kBarrierLimit) {
+                if (++it > F.bar_limit) {
                     atomicExch(F.err, 1);
                     break;
                 }
@@ -418,18 +421,32 @@ struct GmresBufs {
     int *err;
 };
 
+// SM count of the current device (the occupancy check once per device: devices may differ)
 static int fused_grid(int n) {
-    static int per_sm = 0, sms = 0;
+    static constexpr int kDevs = 64;
+    static int sms_of[kDevs] = {0};
     static std::mutex mu;
+    int dev = 0;
+    PDD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kDevs) fail(PDD_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(mu);
-    if (!per_sm) {
-        int dev = 0;
-        PDD_CUDA(cudaGetDevice(&dev));
+    if (!sms_of[dev]) {
+        int sms = 0, per_sm = 0;
         PDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         PDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_fused, kFusedThreads, 0));
         if (per_sm < 1) fail(PDD_ECUDA, "the fused Arnoldi kernel does not fit on an SM");
+        sms_of[dev] = sms;
     }
-    return std::max(1, std::min(sms, cdiv(n, 64)));     // one block per SM: co-resident, cheap barriers
+    return std::max(1, std::min(sms_of[dev], cdiv(n, 64)));     // one block per SM: co-resident, cheap barriers
+}
+
+// Failure injection on the host (tests): PDD_INJECT_BARRIER_TIMEOUT=1 makes every grid barrier
+// of the fused Arnoldi kernel wait for one arrival more than the grid has, with a short poll
+// limit; each block gives up after that limit, records the error and returns, and the solve
+// reports PDD_ECUDA.  The device context stays usable.
+static bool inject_barrier_timeout() {
+    const char *v = std::getenv("PDD_INJECT_BARRIER_TIMEOUT");
+    return v && v[0] == '1';
 }
 
 static SolveResult gmres_run(int n, const int *rowptr, const int *col, const double *val, const double *b, double *u,
@@ -444,8 +461,10 @@ static SolveResult gmres_run(int n, const int *rowptr, const int *col, const dou
     const int vb = std::min(cdiv(n, 256), 2048);
     const int max_iters = std::max(1, o.max_iters);
     const int Gf = fused_grid(n);
+    const bool inject = inject_barrier_timeout();
     FusedArnoldi F{n, m, rowptr, col, val, B.V, B.w, B.fpart, B.H, B.cs, B.sn, B.g, B.gs, B.bar, B.err, o.rtol,
-                   max_iters, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                   max_iters, inject ? 1u : 0u, inject ? (1LL << 14) : kBarrierLimit, 0, 0, nullptr, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (Mr) {
         F.ras_P = Mr->P;
         F.ras_NP = Mr->NP;

@@ -1,8 +1,12 @@
 // a10-a12: Monte Carlo rows (Eq. 25-30 with the representation of Eq. 53,
 // 56 and sigma = I), IMQ cardinals on perimeter arcs (Eq. 19-22).
 //
-//   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c^2)^-1/2 per perimeter stencil,
+//   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c_m^2)^-1/2 per perimeter stencil,
 //       Cholesky factor and K^-1 in FP64 (one CTA per circle), and kappa_1(K).
+//       Eq. 19 measures theta along the interface (arclength r_m u, c in the
+//       length units of Omega); the cardinal functions of Eq. 22 are unchanged
+//       when the basis is scaled, so the kernels work in the local angle u with
+//       c_m^2 = c^2 / r_m^2.
 //   a11 k_paths: Euler-Maruyama paths of dX = b dt + dW, dY = c Y dt,
 //       dZ = f Y dt from the knot, stopped at the first step whose end point
 //       leaves the open disk or the open domain (optionally both shrunk by the
@@ -56,19 +60,20 @@ __device__ double norm1_block(const double *A, int n, double *red) {
 }
 
 __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const int *knot_ptr,
-                                                     const double *ku, const long *kinv_off,
+                                                     const double *ku, const double *cr, const long *kinv_off,
                                                      double c2, double *kinv, double *kcond, int *bad) {
     extern __shared__ double sm[];                    // K (n x n), then L in place
     __shared__ double red[128];
     const int m = circles[blockIdx.x];
     const int a = knot_ptr[m], n = knot_ptr[m + 1] - a;
+    const double c2m = c2 / (cr[m] * cr[m]);          // c^2 of Eq. 19 in the local angle
     double *K = sm;
     double *Z = sm + n * n;                           // n x n work for the inverse
     const int tid = threadIdx.x;
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
         int l = idx / n, k = idx % n;
         double d = ku[a + l] - ku[a + k];
-        K[idx] = 1.0 / sqrt(d * d + c2);
+        K[idx] = 1.0 / sqrt(d * d + c2m);
     }
     __syncthreads();
     const double nK = norm1_block(K, n, red);
@@ -129,6 +134,7 @@ struct PathArgs {
     float2 *ez;                      // mixed form: the unfolded FP32 increments (e, z) of each record
     double shift;                    // Gobet-Menozzi boundary shift c0 sqrt(h), or 0 (plain exit)
     const int *gslot;                // global slot of each launched slot, or null (slot)
+    int max_steps;                   // step cap per path (0: 50 r^2 / h)
 };
 
 // c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi shift in units of |sigma^T n| sqrt(h) (sigma = I)
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     }
     __syncthreads();
     const R rcx = kc[0], rcy = kc[1], r2 = kc[2];
-    const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
+    const int max_steps = A.max_steps > 0 ? A.max_steps : (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = kc[11], sh = kc[12];
     const float hf = (float)kc[11];
     const bool sq_dom = P.dom_kind == 0;
@@ -494,6 +500,8 @@ struct FinalArgs {
     const float2 *ez;                // mixed form: unfolded increments, Y (1 + e) and Z + Y z
     const int *mom_ptr;
     double *moments, *bmean, *val, *se, *bs, *se_bs;
+    const double *cr;                // circle radii (c^2 of Eq. 19 is in squared length)
+    int sums;                        // PDD_SUMS_* of the mixed form (AUTO: by kappa_1(K))
 };
 
 // v = hi + lo with hi = v truncated to 24 significant bits and lo the rest rounded to FP32, built
@@ -562,8 +570,11 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         ukf[q] = (float)uk[q];
         ukl[q] = (float)(uk[q] - (double)ukf[q]);
     }
-    const float c2f = (float)F.c2, c2l = (float)(F.c2 - (double)c2f);
-    const int mode = (F.mixed && imq) ? (F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2)) : 2;
+    const double c2m = F.c2 / (F.cr[m] * F.cr[m]);     // c^2 of Eq. 19 in the local angle
+    const float c2f = (float)c2m, c2l = (float)(c2m - (double)c2f);
+    const int mode = (F.mixed && imq) ? (F.sums != PDD_SUMS_AUTO ? F.sums - 1
+                                                                 : (F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2)))
+                                      : 2;
     const int nq = (ns + 31) >> 5;                     // slices holding stencil knots (block-uniform)
     for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each (p mod 32)
         double acc[NQ];
@@ -574,7 +585,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             accf[q] = 0.f;
             accl[q] = 0.f;
         }
-        int pend = 0;
+        int pend = 0;                                      // mode 0: paths in the FP32 sums since the last fold
         double bs = 0.0;
         int cnt = 0;
         // chunks of 32 paths of this batch: lane l loads path bt + 32 (t0 + l)
@@ -689,7 +700,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                         double phi;
                         if (imq) {
                             const double d = s_su - uk[q];
-                            phi = F.mixed ? rsqrt(d * d + F.c2) : 1.0 / sqrt(d * d + F.c2);
+                            phi = F.mixed ? rsqrt(d * d + c2m) : 1.0 / sqrt(d * d + c2m);
                         } else {
                             phi = fourier_cardinal_at(s_su - uk[q], ns);
                         }
@@ -703,7 +714,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
             const int l = lane + 32 * q;
             if (l < ns) Mb[bt * ns + l] = acc[q] + (double)accf[q] + (double)accl[q];
         }
-    for (int o = 16; o; o >>= 1) {
+        for (int o = 16; o; o >>= 1) {
             bs += __shfl_xor_sync(0xffffffffu, bs, o);
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         }
@@ -824,7 +835,7 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
         PDD_CUDA(cudaMemcpyAsync(koff_c.p, offc.data(), per.size() * sizeof(long), cudaMemcpyHostToDevice, st));
         const size_t smem = (size_t)2 * cov.max_stencil * cov.max_stencil * sizeof(double);
         PDD_CUDA(cudaFuncSetAttribute(k_imq_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, koff_c.p, c2,
+        PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, cov.r.p, koff_c.p, c2,
                    kinv.p, kcond.p, bad.p);
     }
     int hb = 0;
@@ -898,7 +909,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
 
     // a11: paths into the record scratch, in waves that bound the scratch size
     const long P_ = o.paths;
-    const int mixed = o.precision == PDD_PREC_MIXED ? 1 : 0;
+    const int mixed = path_mixed(o) ? 1 : 0;
     const size_t rec_bytes = 1 + 3 * sizeof(double) + (mixed ? sizeof(float2) : 0);
     const size_t per_row = (size_t)P_ * rec_bytes;
     const int wave = (int)std::max<size_t>(1, std::min<size_t>(nmc, ((size_t)8 << 30) / per_row));
@@ -933,7 +944,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
         const int *subs = sys.mc_subs.p + w0, *spos = sys.mc_spos.p + w0, *kword = sys.mc_kword.p + w0;
         PathArgs A{rows, subs, kword, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
                    cov.theta_s.p, o.paths, o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p,
-                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, gsl};
+                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, gsl, o.max_steps};
         PDD_CUDA(cudaEventRecord(e0, st));
         if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
@@ -941,7 +952,8 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
         FinalArgs F{rows, subs, spos, cov.sub_off.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p,
                     cov.ku.p, koff_m.p, kinv.p, kcond.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p,
                     Y.p, Z.p,
-                    ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p};
+                    ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p, cov.r.p,
+                    o.moment_sums};
         if (nq_launch == 1) PDD_LAUNCH(k_mc_finalize<1>, nr, 512, fsm, st, P, F);
         else if (nq_launch == 2) PDD_LAUNCH(k_mc_finalize<2>, nr, 512, fsm, st, P, F);
         else PDD_LAUNCH(k_mc_finalize<3>, nr, 512, fsm, st, P, F);
@@ -1052,6 +1064,7 @@ struct GradArgs {
     double c2;
     int n_par;
     double *partial;          // [slot][n_rbf + n_gcoef]
+    const double *cr;         // circle radii (c^2 of Eq. 19 is in squared length)
 };
 
 template <typename R, bool SRC>
@@ -1097,7 +1110,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     } else {
         Ps.dom[2] -= A.shift;
     }
-    const int max_steps = (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
+    const int max_steps = A.max_steps > 0 ? A.max_steps : (int)fmin(2147483647.0, ceil(50.0 * rad * rad / A.h));
     const R h = (R)A.h, sh = Num<R>::sq((R)A.h);
     const double inv2s = nw ? 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma) : 0.0;
     const int npath = A.npaths ? A.npaths[slot] : A.paths;
@@ -1223,7 +1236,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
                 double ph;
                 if (imq) {
                     const double d = su - G.ku[a + l];
-                    ph = 1.0 / sqrt(d * d + G.c2);
+                    ph = 1.0 / sqrt(d * d + G.c2 / (G.cr[m] * G.cr[m]));
                 } else {
                     double xx = remainder(su - PDD_TWO_PI * l / ns, PDD_TWO_PI);
                     ph = (xx == 0.0) ? 1.0 : sin(0.5 * ns * xx) * cos(0.5 * xx) / (sin(0.5 * xx) * ns);
@@ -1262,8 +1275,9 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     capped.alloc(1);
     PathArgs A{sys.mc_rows.p, sys.mc_subs.p, sys.mc_kword.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
                cov.theta_s.p, o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p,
-               sys.mc_np.p, nullptr, nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, nullptr};
-    GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
+               sys.mc_np.p, nullptr, nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, nullptr, o.max_steps};
+    GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p,
+               cov.r.p};
     const int T = 64;
     const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);
     if (smem > 220 * 1024) fail(PDD_EINVAL, "too many gradient parameters for the replay kernel");
@@ -1274,7 +1288,7 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
                                       (int)smem));                                                       \
         PDD_LAUNCH((k_paths_grad<R, SRCV>), nmc, T, smem, st, P, A, G);                                   \
     } while (0)
-    if (o.precision == PDD_PREC_MIXED) {
+    if (path_mixed(o)) {
         if (src) PDD_GRAD_LAUNCH(float, true); else PDD_GRAD_LAUNCH(float, false);
     } else {
         if (src) PDD_GRAD_LAUNCH(double, true); else PDD_GRAD_LAUNCH(double, false);

@@ -262,7 +262,8 @@ def test_constant_data_rows():
         m = cov.row_sub[i]
         # worst interpolation error of the constant 1 over the sampled exit angles
         t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
-        err1 = np.abs(imq.cardinal(t, row.u_stencil, 1.5, row.Kinv).sum(1) - 1).max()
+        ca = imq.angle_c2(cfg["imq_c2"], cov.r[m])
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, ca, row.Kinv).sum(1) - 1).max()
         lhs = 1.0 + row.vals.sum()
         assert abs(lhs - row.b) <= err1 + 1e-12, (i, m, lhs, row.b)
 
@@ -299,7 +300,8 @@ def test_averaged_rows_special_cases():
     rows = mc.mc_rows(cov1, problem.Operator(cfg1["op"], cov1.domain), pairs, cfg1["mc"], 1.5)
     for (i, m), row in rows.items():
         t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
-        err1 = np.abs(imq.cardinal(t, row.u_stencil, 1.5, row.Kinv).sum(1) - 1).max()
+        ca = imq.angle_c2(cfg["imq_c2"], cov.r[m])
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, ca, row.Kinv).sum(1) - 1).max()
         assert abs(1.0 + row.vals.sum() - row.b) <= err1 + 1e-12, (i, m)
     # (c) streams: the k-th subdomain of a row draws with Philox counter word 3 = k
     assert mc.normals(0, 5, 3, 7) == mc.normals(0, 5, 3, 7, sub=0)

@@ -47,7 +47,9 @@ def _call(fn, n, rp, ci, va, b, u, restart=30, rtol=1e-13, transpose=0):
 
 def test_noalloc_matches_allocating_solve_twice(lib):
     rel_tol = 1e-10          # the solver tolerance of the other parity tests
-    for seed, n in ((3, 3001), (5, 20011)):
+    # small, large, then small again: leftovers of a larger solve in the shared array must not
+    # reach a smaller one
+    for seed, n in ((3, 3001), (5, 20011), (7, 3001)):
         A, rp, ci, va, b = _csr(n, seed)
         ref = torch.empty(n, dtype=torch.float64, device="cuda")
         st, info = _call(lib.pdd_solve_csr, n, rp, ci, va, b, ref)
@@ -72,3 +74,20 @@ def test_noalloc_rejects_oversized_and_transposed(lib):
     assert st == 1 and b"exceeds" in lib.pdd_last_error()
     st, _ = _call(lib.pdd_solve_csr_noalloc, 64, rp, ci, va, b, u, transpose=1)
     assert st == 1
+
+
+def test_noalloc_allocates_no_device_memory(lib):
+    """After one warm-up call, further calls leave the device's free memory unchanged."""
+    n = 20011
+    A, rp, ci, va, b = _csr(n, 9)
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, info = _call(lib.pdd_solve_csr_noalloc, n, rp, ci, va, b, u)
+    assert st == 0 and info.converged
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        st, info = _call(lib.pdd_solve_csr_noalloc, n, rp, ci, va, b, u)
+        assert st == 0 and info.converged
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)

@@ -55,6 +55,17 @@ import numpy as np
 # --------------------------------------------------------------------------
 
 
+# IMQ shape parameter of Eq. 19, with theta measured as arclength (c in the length units of
+# Omega): the paper's c^2 = 1.5 on radius-9 circles with 44 knots (Sec. 4) puts c at 0.953 knot
+# spacings.  Workloads for which no c^2 is given keep that ratio of c to the knot spacing.
+PAPER_C_PER_SPACING = math.sqrt(1.5) / (9.0 * 2.0 * math.pi / 44.0)
+
+
+def imq_c2_for(radius: float, n_knots: int) -> float:
+    """c^2 that puts c at the paper's 0.953 knot spacings on circles of this radius."""
+    return (PAPER_C_PER_SPACING * 2.0 * math.pi * radius / n_knots) ** 2
+
+
 def _square(x0, y0, x1, y1):
     return {"kind": "square", "p": [float(x0), float(y0), float(x1), float(y1)]}
 
@@ -73,7 +84,7 @@ def tiny(paths: int = 1000, h: float = 1e-4, seed: int = 0) -> dict:
         "n_knots": 16, "n_r": 16, "n_theta": 16,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": 1.5,
+        "imq_c2": imq_c2_for(0.2, 16),
     }
 
 
@@ -90,7 +101,7 @@ def varcoef(paths: int = 10000, h: float = 1e-5, seed: int = 0) -> dict:
         "n_knots": 32, "n_r": 32, "n_theta": 32,
         "op": {"b": "sinx_cosy", "c": "quadratic", "f": "manufactured", "g": "sin_cos"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": 1.5,
+        "imq_c2": imq_c2_for(0.05, 32),
     }
 
 
@@ -105,7 +116,7 @@ def scaled(paths: int = 1000, h: float = 1e-5, seed: int = 0) -> dict:
         "n_knots": 16, "n_r": 48, "n_theta": 64,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": 1.5,
+        "imq_c2": imq_c2_for(0.8 * s, 16),
     }
 
 
@@ -176,7 +187,7 @@ def adaptive(paths: int = 1000, h: float = 1e-5, seed: int = 0, cells: int = 16,
         # pilot of `paths` per Monte Carlo knot, then up to paths_max where the largest
         # standard error of the row exceeds se_target
         "mc": {"paths": paths, "h": h, "seed": seed, "paths_max": paths_max, "se_target": se_target},
-        "imq_c2": 1.5,
+        "imq_c2": imq_c2_for(0.025, 16),
     }
 
 
@@ -247,7 +258,7 @@ def floating_only_disk(radius: float = 0.3, n_knots: int = 16, n_r: int = 16,
         "n_knots": 0, "n_r": 0, "n_theta": 0,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": 1000, "h": 1e-4, "seed": 0},
-        "imq_c2": 1.5,
+        "imq_c2": imq_c2_for(radius, n_knots),
     }
 
 
