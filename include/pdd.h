@@ -162,11 +162,20 @@ enum { PDD_PREC_FP64 = 0,       /* disk LU, solves and paths all in FP64        
        PDD_PREC_MIXED = 1 };    /* FP32 disk LU + FP64 refinement; FP32 path
                                    positions, FP64 weights and score sums           */
 
-enum { PDD_FACTOR_RECURSIVE_TC = 0,      /* recursive LU, Schur updates on tcgen05; with
-                                             lu_leaf_width = 0 the library times the candidate
-                                             factorisations on the first wave of each grid size
-                                             and keeps the fastest (this one included)        */
-       PDD_FACTOR_BLOCKED = 1 };          /* one CTA per disk, right-looking, CUDA cores      */
+enum { PDD_FACTOR_RECURSIVE_TC = 0,      /* recursive LU without row interchanges, every step
+                                             but the 64 x 64 diagonal blocks on tcgen05 (the
+                                             row-equilibrated collocation matrices keep growth
+                                             factor 1); a wave with a pivot below 1e-5, or
+                                             whose refinement does not converge, is redone
+                                             with PDD_FACTOR_PIVOTED_TC.  With lu_leaf_width > 0:
+                                             PDD_FACTOR_PIVOTED_TC with that leaf width     */
+       PDD_FACTOR_BLOCKED = 1,            /* one CTA per disk, right-looking, partial pivoting,
+                                             CUDA cores                                      */
+       PDD_FACTOR_PIVOTED_TC = 2 };       /* recursive LU with partial pivoting, Schur updates
+                                             on tcgen05; with lu_leaf_width = 0 the library
+                                             times the candidate leaf widths and tensor-core
+                                             thresholds on the first wave of each grid size
+                                             and keeps the fastest                           */          /* one CTA per disk, right-looking, CUDA cores      */
 
 enum { PDD_FLOATING_PSEUDOSPECTRAL = 0,   /* Sec. 3.3 (default)                      */
        PDD_FLOATING_MONTE_CARLO = 1 };    /* integrate floating rows by paths too     */
@@ -243,7 +252,8 @@ typedef struct {
     double ms_refine;         /*   solves and refinement residuals (a8)              */
     double ms_eval;           /*   evaluation at the knots (a9)                       */
     int lu_blocked;           /* mixed-form LU used: 1 blocked, 0 recursive with      */
-    int lu_leaf_width;        /*   this leaf panel width and                          */
+    int lu_leaf_width;        /*   this leaf width (64: the pivot-free LU's diagonal   */
+                              /*   blocks) and                                         */
     int lu_tensor_min;        /*   this tensor-core threshold (autotuned or forced)   */
     double ms_trisolve;       /* mixed form: device time of the triangular-solve     */
                               /*   launches alone (CUDA events around each, a8)      */
@@ -251,6 +261,9 @@ typedef struct {
                               /*   update launches alone (a7)                        */
     int64_t disk_solves;      /* (disk, sweep) triangular solves run (a8)            */
     double tc_gemm_flop;      /* useful flops (2MNK per matrix) of those launches    */
+    int lu_pivoted_fallback;  /* 1: a wave of the pivot-free LU was redone with partial
+                                 pivoting (a tiny pivot or a refinement that missed its
+                                 tolerance)                                           */
 } pdd_assembly_stats;
 
 /*
@@ -408,6 +421,18 @@ pdd_status pdd_spmv_csr(int n, const int *rowptr_dev, const int *col_dev, const 
 pdd_status pdd_batched_gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A_dev,
                                        long long sA, int lda, const float *B_dev, long long sB,
                                        int ldb, float *C_dev, long long sC, int ldc, void *stream);
+
+/*
+ * pdd_batched_gemm_tf32x3 -- C_b -= A_b B_b (subtract != 0) or C_b = A_b B_b, same operands,
+ * layouts and split-TF32 accuracy as pdd_batched_gemm_sub_tf32x3, through the pipelined
+ * kernel of the pivot-free disk LU (a7): both operands are first split once into hi/lo TF32
+ * tiles (128 rows x 32 K, in device memory allocated for the call), then a persistent
+ * warp-specialised tcgen05 kernel streams them with bulk copies.  C may alias A or B only in
+ * the C = A B form (the operands are read before C is written).  Synchronises `stream`.
+ */
+pdd_status pdd_batched_gemm_tf32x3(int batch, int M, int N, int K, const float *A_dev, long long sA, int lda,
+                                   const float *B_dev, long long sB, int ldb, float *C_dev, long long sC, int ldc,
+                                   int subtract, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint gradient (a14; not in the paper).

@@ -97,7 +97,8 @@ class _AssemblyStats(ctypes.Structure):
                 ("ms_factor", ctypes.c_double), ("ms_refine", ctypes.c_double),
                 ("ms_eval", ctypes.c_double), ("lu_blocked", ctypes.c_int), ("lu_leaf_width", ctypes.c_int),
                 ("lu_tensor_min", ctypes.c_int), ("ms_trisolve", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double),
-                ("disk_solves", ctypes.c_int64), ("tc_gemm_flop", ctypes.c_double)]
+                ("disk_solves", ctypes.c_int64), ("tc_gemm_flop", ctypes.c_double),
+                ("lu_pivoted_fallback", ctypes.c_int)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -115,7 +116,7 @@ class _SolveInfo(ctypes.Structure):
 EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy_cover",
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
            "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
-           "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_grad", "pdd_ras_apply",
+           "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_batched_gemm_tf32x3", "pdd_grad", "pdd_ras_apply",
            "pdd_cover_rows", "pdd_system_mc_subs",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
@@ -155,6 +156,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     i64_ = ctypes.c_longlong
     lib.pdd_batched_gemm_sub_tf32x3.argtypes = [i32, i32, i32, i32, vp, i64_, i32, vp, i64_, i32, vp, i64_,
                                                 i32, vp]
+    lib.pdd_batched_gemm_tf32x3.argtypes = [i32, i32, i32, i32, vp, i64_, i32, vp, i64_, i32, vp, i64_, i32, i32, vp]
     lib.pdd_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
@@ -251,7 +253,7 @@ def cover_struct(cfg: dict):
     return s, keep
 
 
-FACTOR = {"recursive_tc": 0, "blocked": 1}
+FACTOR = {"recursive_tc": 0, "blocked": 1, "pivoted_tc": 2}
 
 
 def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps",
@@ -448,6 +450,16 @@ def gemm_sub_tf32x3(C, A, B, stream=None):
     assert C.shape == (b, M, N) and all(t.is_contiguous() and t.dtype == torch.float32 for t in (A, B, C))
     _check(load().pdd_batched_gemm_sub_tf32x3(b, M, N, K, _ptr(A), M * K, K, _ptr(B), K * N, N, _ptr(C), M * N,
                                               N, _stream(stream)))
+    return C
+
+
+def gemm_tf32x3(C, A, B, subtract=True, stream=None):
+    """C -= A @ B (or C = A @ B) through the pipelined kernel, batched row-major float32 tensors."""
+    b, M, K = A.shape
+    N = B.shape[2]
+    assert C.shape == (b, M, N) and all(t.is_contiguous() and t.dtype == torch.float32 for t in (A, B, C))
+    _check(load().pdd_batched_gemm_tf32x3(b, M, N, K, _ptr(A), M * K, K, _ptr(B), K * N, N, _ptr(C), M * N, N,
+                                          1 if subtract else 0, _stream(stream)))
     return C
 
 

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpdd_gb300.so")
-SOURCES = ["api.cu", "cover.cu", "disk.cu", "mc.cu", "krylov.cu", "adjoint.cu", "tc_gemm.cu", "lu_rec.cu", "ras.cu"]
+SOURCES = ["api.cu", "cover.cu", "disk.cu", "mc.cu", "krylov.cu", "adjoint.cu", "tc_gemm.cu", "lu_rec.cu", "lu_np.cu",
+           "ras.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -159,7 +159,8 @@ static void check_opts(const pdd_assembly_opts *o) {
     if (!o) fail(PDD_EINVAL, "null assembly options");
     if (o->precision != PDD_PREC_FP64 && o->precision != PDD_PREC_MIXED) fail(PDD_EINVAL, "unknown precision");
     if (o->floating_method != 0 && o->floating_method != 1) fail(PDD_EINVAL, "unknown floating method");
-    if (o->factor != PDD_FACTOR_RECURSIVE_TC && o->factor != PDD_FACTOR_BLOCKED) fail(PDD_EINVAL, "unknown factorisation");
+    if (o->factor != PDD_FACTOR_RECURSIVE_TC && o->factor != PDD_FACTOR_BLOCKED && o->factor != PDD_FACTOR_PIVOTED_TC)
+        fail(PDD_EINVAL, "unknown factorisation");
     if (o->lu_leaf_width != 0 && o->lu_leaf_width != 8 && o->lu_leaf_width != 16 && o->lu_leaf_width != 32)
         fail(PDD_EINVAL, "lu_leaf_width must be 0, 8, 16 or 32");
     if (o->lu_tensor_min < 0) fail(PDD_EINVAL, "lu_tensor_min must be >= 0");
@@ -324,6 +325,7 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.ms_tc_gemm = ds.ms_tc_gemm;
         S.disk_solves = ds.disk_solves;
         S.tc_gemm_flop = ds.tc_gemm_flop;
+        S.lu_pivoted_fallback = ds.lu_fallback;
         if (ms.capped) fail(PDD_EPATH_CAP, std::to_string(ms.capped) + " paths reached the step cap");
         if (ds.unconverged)
             fail(PDD_ENOCONV, std::to_string(ds.unconverged) + " disks missed the refinement tolerance");

@@ -1326,6 +1326,11 @@ static void launch_lu(T *A, int n, long strideA, int *perm, int *info, int nd, c
 // tensor-core threshold of 64 or 128) are timed with CUDA events on a copy
 // of up to 64 of the wave's matrices; the fastest is kept for the process.
 // ---------------------------------------------------------------------------
+void lu_nopivot_f32(float *A, int n, long strideA, int *perm, int *info, int nd, float *inv, long sInv,
+                    float *scratch, size_t scratch_floats, cudaStream_t st, float *ms_gemm, double *gemm_flop);
+long lu_np_inv_floats(int n);
+size_t lu_np_scratch_floats_per_disk(int n);
+
 struct LuChoice {
     int blocked, W, tmin;
     float ms;
@@ -1389,11 +1394,18 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     const int rlW = mixed ? rl_width(S.n, S.nrhs, rl_groups) : 0;
     const int nblk = (S.n + kRlTB - 1) / kRlTB;
     const size_t perDinv = rlW ? (size_t)nblk * 2 * kRlTB * kRlTB * sizeof(float) + 2 * perR + perA : 0;
+    const bool use_np = mixed && o.factor == PDD_FACTOR_RECURSIVE_TC && o.lu_leaf_width == 0 && S.n > 64;
+    const size_t perNp = use_np ? (size_t)lu_np_inv_floats(S.n) * sizeof(float) : 0;
     const size_t perDisk = perA + perR * (mixed ? 3 : 1) + (size_t)S.n * S.nrhs * sizeof(T) +
-                           (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + perDinv + 64;
+                           (size_t)S.n * sizeof(NodeCoef) + (size_t)S.n * sizeof(int) + perDinv + perNp + 64;
     size_t freeb = 0, totb = 0;
     PDD_CUDA(cudaMemGetInfo(&freeb, &totb));
     size_t budget = std::min<size_t>((size_t)(0.6 * freeb), (size_t)64 << 30);
+    if (use_np) {           // the GEMM tile scratch comes out of the same budget
+        const size_t scr = lu_np_scratch_floats_per_disk(S.n) * sizeof(float) *
+                           std::min<size_t>(disks.size(), 256);
+        budget = budget > 2 * scr ? budget - scr : budget / 2;
+    }
     int wave = (int)std::max<size_t>(1, budget / perDisk);
     wave = std::min<int>(wave, (int)disks.size());
     if ((size_t)wave * perDisk > freeb) fail(PDD_ENOMEM, "not enough device memory for one disk");
@@ -1426,33 +1438,66 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     conv.alloc(wave);
     sweeps.alloc(wave);
     dd.alloc(wave);
+    // pivot-free LU: inverses of the 64 x 64 diagonal blocks and the GEMMs' hi/lo tile scratch
+    // (enough for min(wave, 256) disks of the largest update; larger waves run in chunks)
+    DevBuf<float> npinv, npscr;
+    const long np_inv_per = use_np ? lu_np_inv_floats(S.n) : 0;
+    size_t np_scr_floats = 0;
+    if (use_np) {
+        npinv.alloc((size_t)wave * np_inv_per);
+        np_scr_floats = lu_np_scratch_floats_per_disk(S.n) * (size_t)std::min(wave, 256);
+        npscr.alloc(std::max<size_t>(np_scr_floats, 1));
+    }
     const long sA = (long)S.n * S.n, sR = (long)S.n * S.nrhs, sC = S.n;
     DiskStats ds;
     for (size_t w0 = 0; w0 < disks.size(); w0 += wave) {
         const int nd = (int)std::min<size_t>(wave, disks.size() - w0);
+        for (int attempt = 0; attempt < 2; ++attempt) {
+        DiskStats wv;                                   // this wave's statistics (kept on success)
         PDD_CUDA(cudaMemcpyAsync(dd.p, disks.data() + w0, nd * sizeof(DiskDesc), cudaMemcpyHostToDevice, st));
         StageTimer tm(st, 5);
         tm.mark(0);
         build_operator<T>(P, S, dd.p, nd, A.p, sA, RHS.p, sR, coef.p, sC, st);
         tm.mark(1);
+        bool np_used = false;
         if constexpr (sizeof(T) == 4) {
-            if (o.factor == PDD_FACTOR_BLOCKED) {
+            if (use_np && attempt == 0) {
+                // pivot-free tensor-core LU; a pivot below the threshold sends the wave to the
+                // pivoted factorisation (the operator is rebuilt: the factor overwrote it)
+                lu_nopivot_f32(A.p, S.n, sA, perm.p, info.p, nd, npinv.p, np_inv_per, npscr.p, np_scr_floats, st,
+                               &wv.ms_tc_gemm, &wv.tc_gemm_flop);
+                std::vector<int> hi(nd);
+                PDD_CUDA(cudaMemcpyAsync(hi.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
+                PDD_CUDA(cudaStreamSynchronize(st));
+                np_used = std::all_of(hi.begin(), hi.end(), [](int v) { return v == 0; });
+                if (!np_used) {
+                    wv.ms_tc_gemm = 0.f;
+                    wv.tc_gemm_flop = 0.0;
+                    build_operator<T>(P, S, dd.p, nd, A.p, sA, RHS.p, sR, coef.p, sC, st);
+                }
+            }
+            if (np_used) {
+                wv.lu_blocked = 0;
+                wv.lu_leaf = 64;
+                wv.lu_tmin = 0;
+            } else if (o.factor == PDD_FACTOR_BLOCKED) {
                 launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
-                ds.lu_blocked = 1;
+                wv.lu_blocked = 1;
             } else if (o.lu_leaf_width > 0) {
                 const LuChoice c{0, o.lu_leaf_width, o.lu_tensor_min > 0 ? o.lu_tensor_min : 128, 0.f};
-                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &ds.ms_tc_gemm, &ds.tc_gemm_flop);
-                ds.lu_blocked = 0;
-                ds.lu_leaf = c.W;
-                ds.lu_tmin = c.tmin;
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &wv.ms_tc_gemm, &wv.tc_gemm_flop);
+                wv.lu_blocked = 0;
+                wv.lu_leaf = c.W;
+                wv.lu_tmin = c.tmin;
             } else {
                 const LuChoice c = tune_lu(A.p, S.n, sA, nd, st);       // cached after the first wave
-                tm.mark(1);                                            // factor time excludes tuning
-                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &ds.ms_tc_gemm, &ds.tc_gemm_flop);
-                ds.lu_blocked = c.blocked;
-                ds.lu_leaf = c.W;
-                ds.lu_tmin = c.tmin;
+                if (!use_np) tm.mark(1);                               // factor time excludes tuning
+                run_lu_choice(c, A.p, S.n, sA, perm.p, info.p, nd, st, &wv.ms_tc_gemm, &wv.tc_gemm_flop);
+                wv.lu_blocked = c.blocked;
+                wv.lu_leaf = c.W;
+                wv.lu_tmin = c.tmin;
             }
+            if (use_np && !np_used) wv.lu_fallback = 1;
         } else {
             launch_lu<T>(A.p, S.n, sA, perm.p, info.p, nd, st);
         }
@@ -1527,15 +1572,15 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             PDD_CUDA(cudaMemcpyAsync(hs.data(), sweeps.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
             PDD_CUDA(cudaStreamSynchronize(st));
             for (int d = 0; d < nd; ++d) {
-                ds.max_sweeps = std::max(ds.max_sweeps, hs[d]);
-                ds.unconverged += hc[d] ? 0 : 1;
-                ds.disk_solves += hs[d];
+                wv.max_sweeps = std::max(wv.max_sweeps, hs[d]);
+                wv.unconverged += hc[d] ? 0 : 1;
+                wv.disk_solves += hs[d];
             }
             if (rlW)
                 for (int s = 0; s < maxs; ++s) {
                     float t = 0.f;
                     cudaEventElapsedTime(&t, sev[2 * s], sev[2 * s + 1]);
-                    ds.ms_trisolve += t;
+                    wv.ms_trisolve += t;
                 }
         }
         if (!mixed) tm.mark(3);
@@ -1566,14 +1611,31 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
         std::vector<int> hinfo(nd);
         PDD_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));
+        // a pivot-free factorisation whose refinement missed the tolerance: redo the wave pivoted
+        if (np_used && wv.unconverged > 0) {
+            ds.lu_fallback = 1;
+            continue;
+        }
         ds.ms_operator += tm.ms(0, 1);
         ds.ms_factor += tm.ms(1, 2);
         ds.ms_refine += tm.ms(2, 3);
         ds.ms_eval += tm.ms(3, 4);
+        ds.ms_tc_gemm += wv.ms_tc_gemm;
+        ds.tc_gemm_flop += wv.tc_gemm_flop;
+        ds.ms_trisolve += wv.ms_trisolve;
+        ds.max_sweeps = std::max(ds.max_sweeps, wv.max_sweeps);
+        ds.unconverged += wv.unconverged;
+        ds.disk_solves += wv.disk_solves;
+        ds.lu_blocked = wv.lu_blocked;
+        ds.lu_leaf = wv.lu_leaf;
+        ds.lu_tmin = wv.lu_tmin;
+        ds.lu_fallback |= wv.lu_fallback;
         for (int d = 0; d < nd; ++d)
-            if (hinfo[d]) fail(PDD_ENOCONV, "singular collocation matrix");
+            if (hinfo[d] && !np_used) fail(PDD_ENOCONV, "singular collocation matrix");
         ds.disks += nd;
         for (int d = 0; d < nd; ++d) ds.rows += disks[w0 + d].row_end - disks[w0 + d].row_begin;
+        break;
+        }
     }
     return ds;
 }
@@ -1618,6 +1680,7 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
             all.lu_leaf = d.lu_leaf;
             all.lu_tmin = d.lu_tmin;
         }
+        all.lu_fallback |= d.lu_fallback;
     }
     return all;
 }

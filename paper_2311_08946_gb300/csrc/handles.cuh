@@ -83,6 +83,7 @@ struct DiskStats {
     int disks = 0, rows = 0, max_sweeps = 0, unconverged = 0;
     float ms_operator = 0, ms_factor = 0, ms_refine = 0, ms_eval = 0;
     int lu_blocked = 0, lu_leaf = 0, lu_tmin = 0;          // factorisation used (mixed form)
+    int lu_fallback = 0;                                   // a pivot-free wave was redone pivoted
     float ms_trisolve = 0, ms_tc_gemm = 0;                 // kernel-only device times (mixed form)
     int64_t disk_solves = 0;                               // (disk, sweep) triangular solves
     double tc_gemm_flop = 0;                               // useful flops of the tensor-core launches

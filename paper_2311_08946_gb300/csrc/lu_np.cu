@@ -1,0 +1,206 @@
+// a7 (mixed form): recursive LU WITHOUT row interchanges of a batch of n x n
+// FP32 matrices (row-major, in place), all disks of a wave at once, with every
+// step except the 64 x 64 diagonal blocks on the tcgen05 tensor cores.
+//
+// The row-equilibrated collocation matrices of Sec. 3.3 (every row scaled to
+// max |a_ij| = 1) keep their diagonal as the row maximum, and elimination
+// without interchanges shows growth factor 1 on the 16x16, 32x32, 22x44 and
+// 48x64 grids (measured in FP32 on the oracle's matrices; partial pivoting
+// gives the same growth).  Any pivot below kTinyPivot is recorded per disk,
+// and the caller then refactors that wave with partial pivoting; the FP64
+// refinement of a8 recovers the accuracy either way.
+//
+//   lu(k0, w):   w <= 64: factor the diagonal block D (one CTA per disk, shared
+//                memory) and store L_D^-1 and U_D^-1; L21 = A21 U_D^-1 (GEMM);
+//                else lu(k0, w1); U12 = L11^-1 A12 (trsm); A22 -= L21 U12
+//                (GEMM, K = w1); lu(k0 + w1, w - w1)
+//   trsm(r0, w): w <= 64: X = L_D^-1 X (GEMM); else trsm(r0, w1);
+//                X2 -= L21 X1 (GEMM); trsm(r0 + w1, w - w1)
+// The GEMMs are tc_gemm (tc_gemm.cu): operands split once into hi/lo TF32
+// tiles, persistent warp-specialised tcgen05 kernel, FP32 accumulation.
+#include <algorithm>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace pdd {
+
+void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
+             int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
+             int *err, cudaStream_t st);
+size_t tc_tile_floats(int rows, int K);
+
+static constexpr int kLeafW = 64;
+static constexpr float kTinyPivot = 1e-5f;       // rows are equilibrated to max |a_ij| = 1
+
+// Factor the w x w diagonal block at (k0, k0) without interchanges (in place) and store the
+// inverses of its unit-lower and upper factors: inv[disk][k0 / 64][0] = L_D^-1,
+// inv[disk][k0 / 64][1] = U_D^-1 (64 x 64 row-major, zero outside the w x w block).
+__global__ void __launch_bounds__(256) k_leaf_diag(float *Aall, int n, long sA, int k0, int w, float *invAll,
+                                                   long sInv, int *info) {
+    __shared__ float D[kLeafW][kLeafW + 1];
+    __shared__ float Li[kLeafW][kLeafW + 1];
+    __shared__ float Ui[kLeafW][kLeafW + 1];
+    const int disk = blockIdx.x, tid = threadIdx.x;
+    float *A = Aall + disk * sA;
+    for (int e = tid; e < kLeafW * kLeafW; e += 256) {
+        const int i = e / kLeafW, j = e - i * kLeafW;
+        D[i][j] = (i < w && j < w) ? A[(long)(k0 + i) * n + k0 + j] : (i == j ? 1.f : 0.f);
+        Li[i][j] = 0.f;
+        Ui[i][j] = 0.f;
+    }
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+        const float d = D[k][k];
+        if (tid == 0 && !(fabsf(d) >= kTinyPivot)) atomicCAS(info + disk, 0, k0 + k + 1);
+        const int m = w - k - 1;
+        if (tid < m) D[k + 1 + tid][k] = (d != 0.f) ? D[k + 1 + tid][k] / d : 0.f;
+        __syncthreads();
+        for (int e = tid; e < m * m; e += 256) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            D[i][j] = fmaf(-D[i][k], D[k][j], D[i][j]);
+        }
+        __syncthreads();
+    }
+    // column j of L^-1 (threads 0..63, rows top-down) and of U^-1 (threads 64..127, bottom-up); the
+    // loops run over the same rows in every thread so the factor reads are broadcasts
+    if (tid < kLeafW) {
+        const int j = tid;
+        for (int i = 0; i < w; ++i) {
+            float s = (i == j) ? 1.f : 0.f;
+            for (int l = 0; l < i; ++l) s = fmaf(-D[i][l], Li[l][j], s);
+            Li[i][j] = (j <= i) ? s : 0.f;
+        }
+    } else if (tid < 2 * kLeafW) {
+        const int j = tid - kLeafW;
+        for (int i = w - 1; i >= 0; --i) {
+            float s = (i == j) ? 1.f : 0.f;
+            for (int l = i + 1; l < w; ++l) s = fmaf(-D[i][l], Ui[l][j], s);
+            Ui[i][j] = (j >= i && D[i][i] != 0.f) ? s / D[i][i] : 0.f;
+        }
+    }
+    __syncthreads();
+    float *inv = invAll + disk * sInv + (long)(k0 / kLeafW) * 2 * kLeafW * kLeafW;
+    for (int e = tid; e < kLeafW * kLeafW; e += 256) {
+        const int i = e / kLeafW, j = e - i * kLeafW;
+        if (i < w && j < w) A[(long)(k0 + i) * n + k0 + j] = D[i][j];
+        inv[e] = Li[i][j];
+        inv[kLeafW * kLeafW + e] = Ui[i][j];
+    }
+}
+
+struct NpLU {
+    float *A;
+    int n;
+    long sA;
+    int nd;
+    float *inv;
+    long sInv;
+    int *info, *err;
+    float *scratch;
+    size_t scratch_floats;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> *gev;   // event pairs around the tensor-core launches, or null
+    double flop;                     // useful flops of the GEMMs
+
+    float *at(int r, int c) const { return A + (long)r * n + c; }
+    const float *invL(int k0) const { return inv + (long)(k0 / kLeafW) * 2 * kLeafW * kLeafW; }
+    const float *invU(int k0) const { return invL(k0) + kLeafW * kLeafW; }
+
+    void gemm(int M, int N, int K, const float *a, long sa, int lda, const float *b, long sb, int ldb, float *c,
+              bool sub) {
+        if (M <= 0 || N <= 0 || K <= 0) return;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (gev) {
+            PDD_CUDA(cudaEventCreate(&e0));
+            PDD_CUDA(cudaEventCreate(&e1));
+            gev->push_back(e0);
+            gev->push_back(e1);
+            PDD_CUDA(cudaEventRecord(e0, st));
+        }
+        tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, scratch, scratch_floats, err, st);
+        if (gev) PDD_CUDA(cudaEventRecord(e1, st));
+        flop += 2.0 * M * N * K * nd;
+    }
+
+    int split(int w) const { return std::max(kLeafW, ((w / 2) / kLeafW) * kLeafW); }
+
+    // X = L[r0:r0+w, r0:r0+w]^-1 X with X = A[r0:r0+w, c0:c0+nc] (unit lower L)
+    void trsm(int r0, int w, int c0, int nc) {
+        if (w <= kLeafW) {
+            gemm(w, nc, w, invL(r0), sInv, kLeafW, at(r0, c0), sA, n, at(r0, c0), false);
+            return;
+        }
+        const int w1 = split(w);
+        trsm(r0, w1, c0, nc);
+        gemm(w - w1, nc, w1, at(r0 + w1, r0), sA, n, at(r0, c0), sA, n, at(r0 + w1, c0), true);
+        trsm(r0 + w1, w - w1, c0, nc);
+    }
+
+    void lu(int k0, int w) {
+        if (w <= kLeafW) {
+            PDD_LAUNCH(k_leaf_diag, nd, 256, 0, st, A, n, sA, k0, w, inv, sInv, info);
+            const int below = n - k0 - w;
+            if (below > 0) gemm(below, w, w, at(k0 + w, k0), sA, n, invU(k0), sInv, kLeafW, at(k0 + w, k0), false);
+            return;
+        }
+        const int w1 = split(w);
+        lu(k0, w1);
+        trsm(k0, w1, k0 + w1, w - w1);
+        gemm(n - (k0 + w1), w - w1, w1, at(k0 + w1, k0), sA, n, at(k0, k0 + w1), sA, n, at(k0 + w1, k0 + w1), true);
+        lu(k0 + w1, w - w1);
+    }
+};
+
+// floats of inverse storage per disk and of GEMM tile scratch per disk (the largest GEMM)
+long lu_np_inv_floats(int n) { return (long)cdiv(n, kLeafW) * 2 * kLeafW * kLeafW; }
+
+size_t lu_np_scratch_floats_per_disk(int n) {
+    if (n <= kLeafW) return 0;
+    const int w1 = std::max(kLeafW, ((n / 2) / kLeafW) * kLeafW);
+    // the top-level Schur update (M = n - w1, N = n - w1, K = w1) and the first leaf panel
+    // (M = n - 64, N = 64, K = 64) bound every other GEMM of the recursion
+    const size_t top = tc_tile_floats(n - w1, w1) * 2;
+    const size_t leaf = tc_tile_floats(n - kLeafW, kLeafW) + tc_tile_floats(kLeafW, kLeafW);
+    return std::max(top, leaf);
+}
+
+__global__ void k_iota_perm_np(int n, int nd, int *perm) {
+    const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx < (long)n * nd) perm[idx] = (int)(idx % n);
+}
+
+// info[d] = 1-based index of the first pivot below kTinyPivot of disk d, 0 when none
+void lu_nopivot_f32(float *A, int n, long strideA, int *perm, int *info, int nd, float *inv, long sInv,
+                    float *scratch, size_t scratch_floats, cudaStream_t st, float *ms_gemm, double *gemm_flop) {
+    DevBuf<int> err;
+    err.alloc(1);
+    PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    PDD_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * nd, st));
+    PDD_LAUNCH(k_iota_perm_np, cdiv((long)n * nd, 256), 256, 0, st, n, nd, perm);
+    std::vector<cudaEvent_t> gev;
+    NpLU r{A, n, strideA, nd, inv, sInv, info, err.p, scratch, scratch_floats, st, ms_gemm ? &gev : nullptr, 0.0};
+    try {
+        r.lu(0, n);
+    } catch (...) {
+        for (cudaEvent_t e : gev) cudaEventDestroy(e);
+        throw;
+    }
+    int h = 0;
+    PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PDD_CUDA(cudaStreamSynchronize(st));
+    if (ms_gemm) {
+        float tot = 0.f;
+        for (size_t k = 0; k + 1 < gev.size(); k += 2) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, gev[k], gev[k + 1]);
+            tot += t;
+        }
+        *ms_gemm += tot;
+    }
+    if (gemm_flop) *gemm_flop += r.flop;
+    for (cudaEvent_t e : gev) cudaEventDestroy(e);
+    if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its pipeline");
+}
+
+}  // namespace pdd

@@ -24,6 +24,8 @@
 //     SM, so one's prologue and epilogue overlap the other's MMAs.
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // waits once more (bounded) for its own MMAs, frees its TMEM and returns.
+#include <algorithm>
+
 #include "handles.cuh"
 
 namespace pdd {
@@ -329,6 +331,337 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gemm_sub_tf32x3(int M, int N,
     if (tid == 0 && failed) atomicAdd(err, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined form for large batches of Schur updates (the pivot-free recursive
+// LU of the disks).  Each operand is split into hi/lo TF32 ONCE, into tiles of
+// 128 rows x 32 K that are stored in the exact shared-memory layout the MMAs
+// read (the canonical no-swizzle K-major layout above: two 16 KB blocks, hi
+// then lo, contiguous).  The GEMM kernel is persistent (one CTA per SM) and
+// warp-specialised:
+//   warp 0    one lane streams each K chunk's A and B tile pairs (2 x 32 KB)
+//             into a 3-stage ring with cp.async.bulk, completion counted by
+//             the stage's mbarrier (expect_tx);
+//   warp 1    allocates 256 TMEM columns (two 128 x 128 FP32 accumulators) and
+//             one lane issues 4 k-steps x 3 tcgen05.mma.kind::tf32 per chunk,
+//             releasing the stage with tcgen05.commit and, after a tile's last
+//             chunk, handing the accumulator to the epilogue;
+//   warps 2-5 read the accumulator with tcgen05.ld (warp w owns TMEM lanes
+//             32 (w mod 4) ..) and write C -= acc (or C = acc), then free it, so
+//             one tile's epilogue overlaps the next tile's MMAs.
+// Every mbarrier wait is bounded; a timeout records an error, the roles stop
+// issuing, the MMA lane waits (bounded) for its own MMAs, and TMEM is freed.
+// ---------------------------------------------------------------------------
+static constexpr int kPipeRows = 128, kPipeK = 32;
+static constexpr int kBlkFloats = kPipeRows * kPipeK;         // one hi or lo block: 16 KB
+static constexpr int kPairFloats = 2 * kBlkFloats;             // hi + lo: 32 KB
+static constexpr int kPipeStages = 3;
+static constexpr int kPipeStageBytes = 2 * kPairFloats * 4;    // A pair + B pair: 64 KB
+static constexpr int kPipeSmem = kPipeStages * kPipeStageBytes;
+static constexpr int kPipeThreads = 192;
+static constexpr int kPipeTmemCols = 256;
+
+// X (R x K, row stride ld; TRANS: X is K x R) -> tiles [b][rt][kc][hi, lo][128 x 32 canonical]
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_split_tiles(const float *X, long sX, int ld, int R, int K, int rtiles,
+                                                     int nkc, float *out, long sOut) {
+    __shared__ float t[kPipeRows][kPipeK + 1];
+    const int kc = blockIdx.x, rt = blockIdx.y, b = blockIdx.z, tid = threadIdx.x;
+    const float *src = X + b * sX;
+    const int r0 = rt * kPipeRows, k0 = kc * kPipeK;
+    for (int e = tid; e < kBlkFloats; e += 256) {
+        int r, k;
+        if (TRANS) {
+            k = e >> 7;
+            r = e & 127;
+        } else {
+            r = e >> 5;
+            k = e & 31;
+        }
+        const int gr = r0 + r, gk = k0 + k;
+        float v = 0.f;
+        if (gr < R && gk < K) v = TRANS ? src[(long)gk * ld + gr] : src[(long)gr * ld + gk];
+        t[r][k] = v;
+    }
+    __syncthreads();
+    float *hi = out + b * sOut + ((long)rt * nkc + kc) * kPairFloats;
+    float *lo = hi + kBlkFloats;
+    for (int e = tid; e < kBlkFloats / 4; e += 256) {
+        const int k4 = e >> 7, r = e & 127;            // a warp writes 32 rows of one core column: 512 B
+        float4 v = make_float4(t[r][4 * k4], t[r][4 * k4 + 1], t[r][4 * k4 + 2], t[r][4 * k4 + 3]);
+        const float4 h = split_hi(v);
+        const int off = k4 * (kPipeRows * 4) + (r >> 3) * 32 + (r & 7) * 4;
+        *reinterpret_cast<float4 *>(hi + off) = h;
+        *reinterpret_cast<float4 *>(lo + off) = split_lo(v, h);
+    }
+}
+
+struct TcPipeArgs {
+    int M, N, mtiles, ntiles, nkc, batch;
+    const float *Ap;
+    long sAp;                 // floats per matrix of A's tiles
+    const float *Bp;
+    long sBp;
+    float *C;
+    long sC;
+    int ldc;
+    int *err;
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void pipe_tile(long t, const TcPipeArgs &g, int &b, int &mt, int &nt) {
+    const long per = (long)g.mtiles * g.ntiles;
+    b = (int)(t / per);
+    const int rem = (int)(t - (long)b * per);
+    mt = rem / g.ntiles;
+    nt = rem - mt * g.ntiles;
+}
+
+template <bool SUB>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) {
+    extern __shared__ __align__(1024) unsigned char psm[];
+    __shared__ __align__(8) uint64_t full[kPipeStages], empty[kPipeStages], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long total = (long)g.batch * g.mtiles * g.ntiles;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < kPipeStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&accf[a]), 1);
+            mbar_init(smem_u32(&acce[a]), 128);
+        }
+        mbar_init(smem_u32(&fin), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kPipeTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t base = smem_u32(psm);
+    if (warp == 0) {
+        if (lane == 0) {                                   // producer
+            long it = 0;
+            for (long t = blockIdx.x; t < total && !failed; t += gridDim.x) {
+                int b, mt, nt;
+                pipe_tile(t, g, b, mt, nt);
+                const float *a = g.Ap + b * g.sAp + (long)mt * g.nkc * kPairFloats;
+                const float *bb = g.Bp + b * g.sBp + (long)nt * g.nkc * kPairFloats;
+                for (int kc = 0; kc < g.nkc; ++kc, ++it) {
+                    const int s = (int)(it % kPipeStages);
+                    const long r = it / kPipeStages;
+                    if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
+                        failed = 1;
+                        break;
+                    }
+                    if (failed) break;
+                    const uint32_t st = base + s * kPipeStageBytes;
+                    mbar_expect_tx(smem_u32(&full[s]), kPipeStageBytes);
+                    bulk_g2s(st, a + (long)kc * kPairFloats, kPairFloats * 4, smem_u32(&full[s]));
+                    bulk_g2s(st + kPairFloats * 4, bb + (long)kc * kPairFloats, kPairFloats * 4, smem_u32(&full[s]));
+                }
+            }
+            // copies still in flight land before the CTA exits: wait (bounded) for the last phase of
+            // each stage that was filled
+            const long n_it = it;
+            for (long q = n_it - kPipeStages < 0 ? 0 : n_it - kPipeStages; q < n_it; ++q)
+                mbar_wait(smem_u32(&full[q % kPipeStages]), (uint32_t)((q / kPipeStages) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                   // MMA issuer
+            const uint32_t idesc = idesc_tf32(kPipeRows, kPipeRows);
+            const uint32_t lbo = kPipeRows * 16, sbo = 128;
+            long it = 0;
+            int tc = 0;
+            bool issued = false;
+            for (long t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
+                const int acc = tc & 1, use = tc >> 1;
+                if (use > 0 && !mbar_wait(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1))) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * kPipeRows);
+                bool ok = true;
+                for (int kc = 0; kc < g.nkc; ++kc, ++it) {
+                    const int s = (int)(it % kPipeStages);
+                    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / kPipeStages) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a_hi = base + s * kPipeStageBytes, a_lo = a_hi + kBlkFloats * 4;
+                    const uint32_t b_hi = a_hi + kPairFloats * 4, b_lo = b_hi + kBlkFloats * 4;
+#pragma unroll
+                    for (int k8 = 0; k8 < kPipeK / 8; ++k8) {
+                        const uint32_t ko = k8 * 2 * lbo;
+                        mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc,
+                                 (kc | k8) ? 1 : 0);
+                        mma_tf32(d, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                        mma_tf32(d, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+                    }
+                    issued = true;
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (!ok) {
+                    failed = 1;
+                    break;
+                }
+                mma_commit(smem_u32(&accf[acc]));
+            }
+            // every MMA this lane issued is complete before TMEM is freed
+            if (issued) {
+                mma_commit(smem_u32(&fin));
+                if (!mbar_wait(smem_u32(&fin), 0)) failed = 1;
+            }
+        }
+    } else {                                               // epilogue: warps 2..5
+        const int q = warp & 3;
+        int tc = 0;
+        const bool vec = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 && (g.sC & 3) == 0;
+        for (long t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
+            const int acc = tc & 1, use = tc >> 1;
+            if (!mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) {
+                failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int b, mt, nt;
+            pipe_tile(t, g, b, mt, nt);
+            const int row = mt * kPipeRows + q * 32 + lane;
+            float *crow = g.C + b * g.sC + (long)row * g.ldc + nt * kPipeRows;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kPipeRows; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + (uint32_t)(acc * kPipeRows + c0) + ((uint32_t)(q * 32) << 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int col = nt * kPipeRows + c0;
+                if (row < g.M && col < g.N) {
+                    float *cp = crow + c0;
+                    if (vec && col + 32 <= g.N) {
+#pragma unroll
+                        for (int e = 0; e < 32; e += 4) {
+                            float4 cv;
+                            if (SUB) {
+                                cv = *reinterpret_cast<float4 *>(cp + e);
+                                cv.x -= __uint_as_float(v[e]);
+                                cv.y -= __uint_as_float(v[e + 1]);
+                                cv.z -= __uint_as_float(v[e + 2]);
+                                cv.w -= __uint_as_float(v[e + 3]);
+                            } else {
+                                cv = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                                 __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+                            }
+                            *reinterpret_cast<float4 *>(cp + e) = cv;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (col + e < g.N) cp[e] = SUB ? cp[e] - __uint_as_float(v[e]) : __uint_as_float(v[e]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acce[acc]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPipeTmemCols)
+                     : "memory");
+    if (threadIdx.x == 0 && failed) atomicAdd(g.err, 1);
+}
+
+static int g_sms[64] = {0};
+
+static int sm_count() {
+    int dev = 0;
+    PDD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(PDD_EINVAL, "device ordinal out of range");
+    if (!g_sms[dev]) PDD_CUDA(cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev));
+    return g_sms[dev];
+}
+
+size_t tc_tile_floats(int rows, int K) { return (size_t)cdiv(rows, kPipeRows) * cdiv(K, kPipeK) * kPairFloats; }
+
+// C_b (-)= A_b B_b for b < batch through pre-split tiles.  A: M x K (row stride lda), or with
+// transA its transpose stored K x M; B: K x N (ldb), or with transB its transpose stored N x K.
+// scratch: at least chunk * (tc_tile_floats(M, K) + tc_tile_floats(N, K)) floats; the batch is
+// processed in chunks that fit.
+void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
+             int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
+             int *err, cudaStream_t st) {
+    if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
+        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
+        attr = true;
+    }
+    const int mt = cdiv(M, kPipeRows), ntl = cdiv(N, kPipeRows), nkc = cdiv(K, kPipeK);
+    const size_t fa = tc_tile_floats(M, K), fb = tc_tile_floats(N, K);
+    const int chunk = (int)std::min<size_t>((size_t)batch, scratch_floats / (fa + fb));
+    if (chunk < 1) fail(PDD_EINVAL, "tensor-core GEMM scratch smaller than one matrix's tiles");
+    if (mt > 65535 || ntl > 65535 || chunk > 65535) fail(PDD_EINVAL, "GEMM too large for the split grid");
+    const int sms = sm_count();
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = std::min(chunk, batch - b0);
+        float *Ap = scratch, *Bp = scratch + (size_t)nb * fa;
+        // A tiles: rows of C (M) x K; B tiles: columns of C (N) x K
+        if (transA)
+            PDD_LAUNCH(k_split_tiles<true>, dim3(nkc, mt, nb), 256, 0, st, A + b0 * sA, sA, lda, M, K, mt, nkc, Ap, (long)fa);
+        else
+            PDD_LAUNCH(k_split_tiles<false>, dim3(nkc, mt, nb), 256, 0, st, A + b0 * sA, sA, lda, M, K, mt, nkc, Ap, (long)fa);
+        if (transB)
+            PDD_LAUNCH(k_split_tiles<false>, dim3(nkc, ntl, nb), 256, 0, st, B + b0 * sB, sB, ldb, N, K, ntl, nkc, Bp, (long)fb);
+        else
+            PDD_LAUNCH(k_split_tiles<true>, dim3(nkc, ntl, nb), 256, 0, st, B + b0 * sB, sB, ldb, N, K, ntl, nkc, Bp, (long)fb);
+        const TcPipeArgs g{M, N, mt, ntl, nkc, nb, Ap, (long)fa, Bp, (long)fb, C + b0 * sC, sC, ldc, err};
+        const long tiles = (long)nb * mt * ntl;
+        const int grid = (int)std::min<long>(tiles, sms);
+        if (sub) PDD_LAUNCH(k_tc_gemm_pipe<true>, grid, kPipeThreads, kPipeSmem, st, g);
+        else PDD_LAUNCH(k_tc_gemm_pipe<false>, grid, kPipeThreads, kPipeSmem, st, g);
+    }
+}
+
 void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, int lda, const float *B, long sB,
                      int ldb, float *C, long sC, int ldc, int *err, cudaStream_t st) {
     if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
@@ -372,6 +705,36 @@ extern "C" pdd_status pdd_batched_gemm_sub_tf32x3(int batch, int M, int N, int K
         PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));
         if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its MMAs");
+    } catch (const Fail &f) {
+        return f.st;
+    }
+    return PDD_OK;
+}
+
+// C ABI: the pipelined form (see include/pdd.h)
+extern "C" pdd_status pdd_batched_gemm_tf32x3(int batch, int M, int N, int K, const float *A, long long sA, int lda,
+                                              const float *B, long long sB, int ldb, float *C, long long sC,
+                                              int ldc, int subtract, void *stream) {
+    using namespace pdd;
+    try {
+        if (batch < 0 || M < 0 || N < 0 || K < 0 || (batch && M && N && K && (!A || !B || !C)))
+            fail(PDD_EINVAL, "negative size or null operand");
+        if (lda < K || ldb < N || ldc < N) fail(PDD_EINVAL, "leading dimension smaller than the row length");
+        if (batch == 0 || M == 0 || N == 0 || K == 0) return PDD_OK;
+        cudaStream_t st = (cudaStream_t)stream;
+        DevBuf<int> err;
+        err.alloc(1);
+        PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        const size_t per = tc_tile_floats(M, K) + tc_tile_floats(N, K);
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, ((size_t)1 << 28) / per));
+        DevBuf<float> scr;
+        scr.alloc(per * chunk);
+        tc_gemm(batch, M, N, K, A, (long)sA, lda, false, B, (long)sB, ldb, false, C, (long)sC, ldc, subtract != 0,
+                scr.p, per * chunk, err.p, st);
+        int h = 0;
+        PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its pipeline");
     } catch (const Fail &f) {
         return f.st;
     }

@@ -37,6 +37,38 @@ def test_gemm_sub_matches_fp64(pdd, b, M, N, K):
     assert bool((err <= bound).all()), float((err / bound).max())
 
 
+# the pipelined kernel of the pivot-free LU: several tiles per CTA (the 152-CTA persistent grid
+# wraps), ragged M/N/K, both C -= A B and C = A B
+@pytest.mark.parametrize("b,M,N,K", [(1, 128, 128, 32), (3, 256, 128, 64), (2, 300, 200, 96),
+                                     (4, 512, 384, 512), (3, 260, 132, 68), (2, 96, 200, 36),
+                                     (2, 129, 65, 33), (1, 1, 1, 1), (40, 640, 640, 320), (7, 1536, 64, 64)])
+@pytest.mark.parametrize("subtract", [True, False])
+def test_pipelined_gemm_matches_fp64(pdd, b, M, N, K, subtract):
+    g = torch.Generator(device="cuda").manual_seed(M * 5 + N * 11 + K + (1 if subtract else 0))
+    A = torch.randn(b, M, K, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(b, K, N, device="cuda", generator=g, dtype=torch.float32)
+    C0 = torch.randn(b, M, N, device="cuda", generator=g, dtype=torch.float32)
+    C = C0.clone()
+    pdd.gemm_tf32x3(C, A, B, subtract=subtract)
+    prod = torch.bmm(A.double(), B.double())
+    ref = C0.double() - prod if subtract else prod
+    bound = 2.0 ** -19 * ((C0.double().abs() if subtract else 0.0) + torch.bmm(A.double().abs(), B.double().abs()))
+    err = (C.double() - ref).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+
+
+def test_pipelined_gemm_in_place_product(pdd):
+    """C = A B with C aliasing A (the leaf panel update L21 = A21 U^-1 of the pivot-free LU)."""
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(5, 700, 64, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(5, 64, 64, device="cuda", generator=g, dtype=torch.float32)
+    want = torch.bmm(A.double(), B.double())
+    bound = 2.0 ** -19 * torch.bmm(A.double().abs(), B.double().abs())
+    pdd.gemm_tf32x3(A, A, B, subtract=False)
+    err = (A.double() - want).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+
+
 def test_gemm_sub_is_not_plain_tf32(pdd):
     # a plain single-pass TF32 product would miss this bar by ~2^8
     A = torch.full((1, 128, 64), 1.0 + 2.0 ** -15, device="cuda")
