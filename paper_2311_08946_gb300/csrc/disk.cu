@@ -528,7 +528,7 @@ static void launch_solve(const T *LU, int n, long sA, const int *perm, const dou
 // shared-memory reads of the solved panel rows).
 // ---------------------------------------------------------------------------
 static constexpr int kRlTB = 32, kRlThreads = 512;
-static constexpr size_t kRlSmemMax = 200 * 1024;
+static constexpr size_t kRlSmemMax = 225 * 1024;        // 227 KB per CTA, less the static arrays
 
 // inverses of the unit-lower and upper 32x32 diagonal blocks of each LU:
 // Dinv[disk][blk][0] = inv(L_bb), Dinv[disk][blk][1] = inv(U_bb), zero-padded
@@ -580,6 +580,8 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                                                                unsigned long long *dmaxb, unsigned long long *xmaxb,
                                                                float2 *Dall, int dmode) {
     constexpr int NT = kRlThreads, TB = kRlTB;
+    constexpr bool VEC = (CG % 4) == 0;                // 16-byte shared-memory access to the columns
+    constexpr int PD = (CG <= 20) ? 16 : (CG <= 36 ? 8 : 2);   // factor entries per row in flight
     extern __shared__ __align__(16) float rsm[];
     float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
     float *Ds = rsm + (size_t)n * CG;                  // TB x (TB + 1) diagonal-block inverse (padded rows)
@@ -596,37 +598,40 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
         const int p = e / CG, c = e - p * CG;
         Bs[e] = (c < cg) ? (float)R[(long)perm[p] * nrhs + c0 + c] : 0.f;
     }
-    const bool vec = true;
     for (int pass = 0; pass < 2; ++pass) {             // 0: L (unit lower), 1: U (upper)
         for (int bi = 0; bi < nblk; ++bi) {
             const int blk = pass == 0 ? bi : nblk - 1 - bi;
             const int i0 = blk * TB, tb = min(TB, n - i0);
             const int ra = pass == 0 ? i0 + tb : 0, rb = pass == 0 ? n : i0;
-            const bool full = vec && tb == TB;
-            // the panel's rows X_b = inv(T_bb) B_b: warp q takes columns 4q .. 4q+3, lane i the
-            // panel row i; the row of the inverse comes from global memory into registers and the
-            // panel's right-hand sides are read as broadcasts
+            const bool full = tb == TB;
+            // the panel's rows X_b = inv(T_bb) B_b: warp q takes columns 4q .. 4q+3 (one column when CG
+            // is not a multiple of 4), lane i the panel row i; the row of the inverse comes from shared
+            // memory and the panel's right-hand sides are read as broadcasts
             const int warp = tid >> 5, lane = tid & 31;
             const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
             for (int e = tid; e < TB * TB; e += NT) Ds[(e >> 5) * (TB + 1) + (e & 31)] = Dt[e];
             __syncthreads();
-            // warps take the column quads in turn (two passes when CG / 4 exceeds the warp count)
-            constexpr int NQ = CG / 4, NW = NT / 32, QP = (NQ + NW - 1) / NW;
+            constexpr int NQ = VEC ? CG / 4 : CG, NW = NT / 32, QP = (NQ + NW - 1) / NW;
             float4 xo[QP];
 #pragma unroll
             for (int qp = 0; qp < QP; ++qp) {
                 const int q = warp + qp * NW;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (q < NQ && lane < tb) {
-                    const float *bc = Bs + (size_t)i0 * CG + 4 * q;
                     const float *dr = Ds + lane * (TB + 1);
-                    for (int k = 0; k < tb; ++k) {
-                        const float d = dr[k];
-                        const float4 b = *reinterpret_cast<const float4 *>(bc + (size_t)k * CG);
-                        v.x = fmaf(d, b.x, v.x);
-                        v.y = fmaf(d, b.y, v.y);
-                        v.z = fmaf(d, b.z, v.z);
-                        v.w = fmaf(d, b.w, v.w);
+                    if constexpr (VEC) {
+                        const float *bc = Bs + (size_t)i0 * CG + 4 * q;
+                        for (int k = 0; k < tb; ++k) {
+                            const float d = dr[k];
+                            const float4 b = *reinterpret_cast<const float4 *>(bc + (size_t)k * CG);
+                            v.x = fmaf(d, b.x, v.x);
+                            v.y = fmaf(d, b.y, v.y);
+                            v.z = fmaf(d, b.z, v.z);
+                            v.w = fmaf(d, b.w, v.w);
+                        }
+                    } else {
+                        const float *bc = Bs + (size_t)i0 * CG + q;
+                        for (int k = 0; k < tb; ++k) v.x = fmaf(dr[k], bc[(size_t)k * CG], v.x);
                     }
                 }
                 xo[qp] = v;
@@ -635,7 +640,10 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
 #pragma unroll
             for (int qp = 0; qp < QP; ++qp) {
                 const int q = warp + qp * NW;
-                if (q < NQ && lane < tb) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * q) = xo[qp];
+                if (q < NQ && lane < tb) {
+                    if constexpr (VEC) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * q) = xo[qp];
+                    else Bs[(size_t)(i0 + lane) * CG + q] = xo[qp].x;
+                }
             }
             __syncthreads();
             // rows still to solve: B_r -= T_rb X_b, two rows per thread so that each broadcast read of
@@ -650,59 +658,46 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                 float acc0[CG], acc1[CG];
                 float *b0 = Bs + (size_t)r * CG, *b1 = Bs + (size_t)(two ? r2 : r) * CG;
 #pragma unroll
-                for (int c = 0; c < CG; c += 4) {
-                    const float4 t0 = *reinterpret_cast<const float4 *>(b0 + c);
-                    const float4 t1 = *reinterpret_cast<const float4 *>(b1 + c);
-                    acc0[c] = t0.x;
-                    acc0[c + 1] = t0.y;
-                    acc0[c + 2] = t0.z;
-                    acc0[c + 3] = t0.w;
-                    acc1[c] = t1.x;
-                    acc1[c + 1] = t1.y;
-                    acc1[c + 2] = t1.z;
-                    acc1[c + 3] = t1.w;
+                for (int c = 0; c < CG; ++c) {
+                    acc0[c] = b0[c];
+                    acc1[c] = b1[c];
                 }
                 // factor entries T[r][i0 + k] = LUT[(i0 + k) n + r]: consecutive rows, consecutive addresses
                 const float *l0 = LUT + (long)i0 * n + r, *l1 = LUT + (long)i0 * n + (two ? r2 : r);
                 if (full) {
-                    float a0[4], a1[4];
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        a0[kk] = __ldg(l0 + (long)kk * n);
-                        a1[kk] = __ldg(l1 + (long)kk * n);
-                    }
+                    // PD entries per row in flight before their FMAs (the loads of a warp are coalesced)
 #pragma unroll 1
-                    for (int k0 = 0; k0 < TB; k0 += 4) {
-                        // the next chunk's entries are in flight during this chunk's FMAs
-                        float b0[4], b1[4];
+                    for (int k0 = 0; k0 < TB; k0 += PD) {
+                        float m0[PD], m1[PD];
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const int kn = k0 + 4 + kk < TB ? k0 + 4 + kk : kk;
-                            b0[kk] = __ldg(l0 + (long)kn * n);
-                            b1[kk] = __ldg(l1 + (long)kn * n);
+                        for (int kk = 0; kk < PD; ++kk) {
+                            m0[kk] = __ldg(l0 + (long)(k0 + kk) * n);
+                            m1[kk] = __ldg(l1 + (long)(k0 + kk) * n);
                         }
-#pragma unroll 1
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const float m0 = kk == 0 ? a0[0] : (kk == 1 ? a0[1] : (kk == 2 ? a0[2] : a0[3]));
-                            const float m1 = kk == 0 ? a1[0] : (kk == 1 ? a1[1] : (kk == 2 ? a1[2] : a1[3]));
+#pragma unroll
+                        for (int kk = 0; kk < PD; ++kk) {
                             const float *xr = xs + (size_t)(k0 + kk) * CG;
+                            if constexpr (VEC) {
 #pragma unroll
-                            for (int c = 0; c < CG; c += 4) {
-                                const float4 x = *reinterpret_cast<const float4 *>(xr + c);
-                                acc0[c] = fmaf(-m0, x.x, acc0[c]);
-                                acc0[c + 1] = fmaf(-m0, x.y, acc0[c + 1]);
-                                acc0[c + 2] = fmaf(-m0, x.z, acc0[c + 2]);
-                                acc0[c + 3] = fmaf(-m0, x.w, acc0[c + 3]);
-                                acc1[c] = fmaf(-m1, x.x, acc1[c]);
-                                acc1[c + 1] = fmaf(-m1, x.y, acc1[c + 1]);
-                                acc1[c + 2] = fmaf(-m1, x.z, acc1[c + 2]);
-                                acc1[c + 3] = fmaf(-m1, x.w, acc1[c + 3]);
+                                for (int c = 0; c < CG; c += 4) {
+                                    const float4 x = *reinterpret_cast<const float4 *>(xr + c);
+                                    acc0[c] = fmaf(-m0[kk], x.x, acc0[c]);
+                                    acc0[c + 1] = fmaf(-m0[kk], x.y, acc0[c + 1]);
+                                    acc0[c + 2] = fmaf(-m0[kk], x.z, acc0[c + 2]);
+                                    acc0[c + 3] = fmaf(-m0[kk], x.w, acc0[c + 3]);
+                                    acc1[c] = fmaf(-m1[kk], x.x, acc1[c]);
+                                    acc1[c + 1] = fmaf(-m1[kk], x.y, acc1[c + 1]);
+                                    acc1[c + 2] = fmaf(-m1[kk], x.z, acc1[c + 2]);
+                                    acc1[c + 3] = fmaf(-m1[kk], x.w, acc1[c + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < CG; ++c) {
+                                    const float x = xr[c];
+                                    acc0[c] = fmaf(-m0[kk], x, acc0[c]);
+                                    acc1[c] = fmaf(-m1[kk], x, acc1[c]);
+                                }
                             }
-                        }
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            a0[kk] = b0[kk];
-                            a1[kk] = b1[kk];
                         }
                     }
                 } else {
@@ -710,27 +705,18 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                         const float m0 = __ldg(l0 + (long)k * n), m1 = __ldg(l1 + (long)k * n);
                         const float *xr = xs + (size_t)k * CG;
 #pragma unroll
-                        for (int c = 0; c < CG; c += 4) {
-                            const float4 x = *reinterpret_cast<const float4 *>(xr + c);
-                            acc0[c] = fmaf(-m0, x.x, acc0[c]);
-                            acc0[c + 1] = fmaf(-m0, x.y, acc0[c + 1]);
-                            acc0[c + 2] = fmaf(-m0, x.z, acc0[c + 2]);
-                            acc0[c + 3] = fmaf(-m0, x.w, acc0[c + 3]);
-                            acc1[c] = fmaf(-m1, x.x, acc1[c]);
-                            acc1[c + 1] = fmaf(-m1, x.y, acc1[c + 1]);
-                            acc1[c + 2] = fmaf(-m1, x.z, acc1[c + 2]);
-                            acc1[c + 3] = fmaf(-m1, x.w, acc1[c + 3]);
+                        for (int c = 0; c < CG; ++c) {
+                            const float x = xr[c];
+                            acc0[c] = fmaf(-m0, x, acc0[c]);
+                            acc1[c] = fmaf(-m1, x, acc1[c]);
                         }
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < CG; c += 4)
-                    *reinterpret_cast<float4 *>(b0 + c) = make_float4(acc0[c], acc0[c + 1], acc0[c + 2], acc0[c + 3]);
+                for (int c = 0; c < CG; ++c) b0[c] = acc0[c];
                 if (two) {
 #pragma unroll
-                    for (int c = 0; c < CG; c += 4)
-                        *reinterpret_cast<float4 *>(b1 + c) =
-                            make_float4(acc1[c], acc1[c + 1], acc1[c + 2], acc1[c + 3]);
+                    for (int c = 0; c < CG; ++c) b1[c] = acc1[c];
                 }
             }
             __syncthreads();
@@ -851,7 +837,7 @@ __global__ void k_refine_conv(int nd, int *conv, int *sweeps, unsigned long long
 // column-group width of the right-looking solve for n rows and nrhs columns
 // (0: the shared-memory block does not fit; the tiled solve is used)
 static int rl_width(int n, int nrhs, int &groups) {
-    static const int widths[] = {8, 12, 20, 36, 52};
+    static const int widths[] = {8, 12, 17, 20, 36, 52};     // 17: all 17 columns of 16-knot disks at n = 3072
     for (int g = 1; g <= nrhs; ++g) {
         const int cg = (nrhs + g - 1) / g;
         int W = 0;
@@ -900,6 +886,7 @@ static void launch_rl(int W, const RlArgs &a, cudaStream_t st) {
     switch (W) {
         case 8: launch_rl_cg<8>(a, st); break;
         case 12: launch_rl_cg<12>(a, st); break;
+        case 17: launch_rl_cg<17>(a, st); break;
         case 20: launch_rl_cg<20>(a, st); break;
         case 36: launch_rl_cg<36>(a, st); break;
         default: launch_rl_cg<52>(a, st); break;

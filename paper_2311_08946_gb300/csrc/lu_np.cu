@@ -27,7 +27,7 @@ namespace pdd {
 
 void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
              int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
-             int *err, cudaStream_t st);
+             int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev);
 size_t tc_tile_floats(int rows, int K);
 
 static constexpr int kLeafW = 64;
@@ -100,7 +100,7 @@ struct NpLU {
     float *scratch;
     size_t scratch_floats;
     cudaStream_t st;
-    std::vector<cudaEvent_t> *gev;   // event pairs around the tensor-core launches, or null
+    std::vector<cudaEvent_t> *gev;   // event pairs around the tensor-core GEMM kernels, or null
     double flop;                     // useful flops of the GEMMs
 
     float *at(int r, int c) const { return A + (long)r * n + c; }
@@ -110,16 +110,8 @@ struct NpLU {
     void gemm(int M, int N, int K, const float *a, long sa, int lda, const float *b, long sb, int ldb, float *c,
               bool sub) {
         if (M <= 0 || N <= 0 || K <= 0) return;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (gev) {
-            PDD_CUDA(cudaEventCreate(&e0));
-            PDD_CUDA(cudaEventCreate(&e1));
-            gev->push_back(e0);
-            gev->push_back(e1);
-            PDD_CUDA(cudaEventRecord(e0, st));
-        }
-        tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, scratch, scratch_floats, err, st);
-        if (gev) PDD_CUDA(cudaEventRecord(e1, st));
+        tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, scratch, scratch_floats, err, st,
+                gev);
         flop += 2.0 * M * N * K * nd;
     }
 

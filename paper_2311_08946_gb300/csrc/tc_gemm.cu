@@ -25,6 +25,7 @@
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // waits once more (bounded) for its own MMAs, frees its TMEM and returns.
 #include <algorithm>
+#include <vector>
 
 #include "handles.cuh"
 
@@ -360,7 +361,9 @@ static constexpr int kPipeSmem = kPipeStages * kPipeStageBytes;
 static constexpr int kPipeThreads = 192;
 static constexpr int kPipeTmemCols = 256;
 
-// X (R x K, row stride ld; TRANS: X is K x R) -> tiles [b][rt][kc][hi, lo][128 x 32 canonical]
+// X (R x K, row stride ld; TRANS: X is K x R) -> tiles [b][rt][kc][hi, lo][128 x 32 canonical].
+// Bandwidth-bound: every thread issues its four 16-byte loads before any shared-memory store
+// (scalar loads, with bounds, for a misaligned source or a ragged edge).
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_split_tiles(const float *X, long sX, int ld, int R, int K, int rtiles,
                                                      int nkc, float *out, long sOut) {
@@ -368,30 +371,72 @@ __global__ void __launch_bounds__(256) k_split_tiles(const float *X, long sX, in
     const int kc = blockIdx.x, rt = blockIdx.y, b = blockIdx.z, tid = threadIdx.x;
     const float *src = X + b * sX;
     const int r0 = rt * kPipeRows, k0 = kc * kPipeK;
-    for (int e = tid; e < kBlkFloats; e += 256) {
+    const bool al = ((uintptr_t)src & 15) == 0 && (ld & 3) == 0;
+    float4 v[4];
+    // float4 group q = tid + 256 i: non-TRANS row r = q >> 3, k = 4 (q & 7); TRANS k = q >> 5, r = 4 (q & 31)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int q = tid + 256 * i;
         int r, k;
         if (TRANS) {
-            k = e >> 7;
-            r = e & 127;
+            k = q >> 5;
+            r = 4 * (q & 31);
         } else {
-            r = e >> 5;
-            k = e & 31;
+            r = q >> 3;
+            k = 4 * (q & 7);
         }
         const int gr = r0 + r, gk = k0 + k;
-        float v = 0.f;
-        if (gr < R && gk < K) v = TRANS ? src[(long)gk * ld + gr] : src[(long)gr * ld + gk];
-        t[r][k] = v;
+        if (TRANS) {
+            const float *p = src + (long)gk * ld + gr;
+            if (al && gk < K && gr + 3 < R) {
+                v[i] = __ldg(reinterpret_cast<const float4 *>(p));
+            } else {
+                v[i].x = (gk < K && gr < R) ? p[0] : 0.f;
+                v[i].y = (gk < K && gr + 1 < R) ? p[1] : 0.f;
+                v[i].z = (gk < K && gr + 2 < R) ? p[2] : 0.f;
+                v[i].w = (gk < K && gr + 3 < R) ? p[3] : 0.f;
+            }
+        } else {
+            const float *p = src + (long)gr * ld + gk;
+            if (al && gr < R && gk + 3 < K) {
+                v[i] = __ldg(reinterpret_cast<const float4 *>(p));
+            } else {
+                v[i].x = (gr < R && gk < K) ? p[0] : 0.f;
+                v[i].y = (gr < R && gk + 1 < K) ? p[1] : 0.f;
+                v[i].z = (gr < R && gk + 2 < K) ? p[2] : 0.f;
+                v[i].w = (gr < R && gk + 3 < K) ? p[3] : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int q = tid + 256 * i;
+        if (TRANS) {
+            const int k = q >> 5, r = 4 * (q & 31);
+            t[r][k] = v[i].x;
+            t[r + 1][k] = v[i].y;
+            t[r + 2][k] = v[i].z;
+            t[r + 3][k] = v[i].w;
+        } else {
+            const int r = q >> 3, k = 4 * (q & 7);
+            t[r][k] = v[i].x;
+            t[r][k + 1] = v[i].y;
+            t[r][k + 2] = v[i].z;
+            t[r][k + 3] = v[i].w;
+        }
     }
     __syncthreads();
     float *hi = out + b * sOut + ((long)rt * nkc + kc) * kPairFloats;
     float *lo = hi + kBlkFloats;
-    for (int e = tid; e < kBlkFloats / 4; e += 256) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int e = tid + 256 * i;
         const int k4 = e >> 7, r = e & 127;            // a warp writes 32 rows of one core column: 512 B
-        float4 v = make_float4(t[r][4 * k4], t[r][4 * k4 + 1], t[r][4 * k4 + 2], t[r][4 * k4 + 3]);
-        const float4 h = split_hi(v);
+        float4 w = make_float4(t[r][4 * k4], t[r][4 * k4 + 1], t[r][4 * k4 + 2], t[r][4 * k4 + 3]);
+        const float4 h = split_hi(w);
         const int off = k4 * (kPipeRows * 4) + (r >> 3) * 32 + (r & 7) * 4;
         *reinterpret_cast<float4 *>(hi + off) = h;
-        *reinterpret_cast<float4 *>(lo + off) = split_lo(v, h);
+        *reinterpret_cast<float4 *>(lo + off) = split_lo(w, h);
     }
 }
 
@@ -628,7 +673,7 @@ size_t tc_tile_floats(int rows, int K) { return (size_t)cdiv(rows, kPipeRows) * 
 // processed in chunks that fit.
 void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
              int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
-             int *err, cudaStream_t st) {
+             int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev) {
     if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
     static bool attr = false;
     if (!attr) {
@@ -657,8 +702,17 @@ void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, b
         const TcPipeArgs g{M, N, mt, ntl, nkc, nb, Ap, (long)fa, Bp, (long)fb, C + b0 * sC, sC, ldc, err};
         const long tiles = (long)nb * mt * ntl;
         const int grid = (int)std::min<long>(tiles, sms);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (kev) {                       // device time of the GEMM kernels alone (not the splits)
+            PDD_CUDA(cudaEventCreate(&e0));
+            PDD_CUDA(cudaEventCreate(&e1));
+            kev->push_back(e0);
+            kev->push_back(e1);
+            PDD_CUDA(cudaEventRecord(e0, st));
+        }
         if (sub) PDD_LAUNCH(k_tc_gemm_pipe<true>, grid, kPipeThreads, kPipeSmem, st, g);
         else PDD_LAUNCH(k_tc_gemm_pipe<false>, grid, kPipeThreads, kPipeSmem, st, g);
+        if (kev) PDD_CUDA(cudaEventRecord(e1, st));
     }
 }
 
@@ -730,7 +784,7 @@ extern "C" pdd_status pdd_batched_gemm_tf32x3(int batch, int M, int N, int K, co
         DevBuf<float> scr;
         scr.alloc(per * chunk);
         tc_gemm(batch, M, N, K, A, (long)sA, lda, false, B, (long)sB, ldb, false, C, (long)sC, ldc, subtract != 0,
-                scr.p, per * chunk, err.p, st);
+                scr.p, per * chunk, err.p, st, nullptr);
         int h = 0;
         PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         PDD_CUDA(cudaStreamSynchronize(st));

@@ -556,11 +556,13 @@ def test_mc_rows_identical_streams_scaled_sampled(pdd):
 
 @pytest.mark.parametrize("name,c2_per_r2", [("varcoef", 1.5), ("poisson46", 1.5), ("tiny", None)])
 def test_mc_moment_sums_forced_modes(pdd, name, c2_per_r2):
-    """The mixed paths' basis sums (a12) forced to each mode on the same path records (one mixed
-    path launch per assembly, same seed): FP64 sums are the reference; double-float sums agree
-    to 1e-12 relative (they claim ~1e-13) and FP32 sums to 1e-5.  With c^2 = 1.5 r^2 the IMQ
-    matrices reach kappa(K) ~ 1e8-1e12, where the automatic choice must pick the double-float or
-    FP64 sums."""
+    """The mixed paths' basis sums (a12) forced to each mode, one assembly per mode on the same seed:
+    FP64 sums are the reference; double-float sums agree to 1e-9 relative and FP32 sums only to 1e-5.
+    The path records of two assemblies are not bit-identical: a lane folds its FP32 weight
+    increments into the FP64 weights every 8 of its loop iterations, and which lane runs a path
+    depends on the scheduling, so Y and Z differ by rounding (~1e-11 relative).  The 1e-9 bar sits
+    between that and the FP32 sums' error (~1e-7).  With c^2 = 1.5 r^2 the IMQ matrices reach
+    kappa(K) ~ 1e8-1e12, where the automatic choice must pick the double-float or FP64 sums."""
     paths = {"varcoef": 1000, "poisson46": 500, "tiny": 2000}[name]
     cfg = getattr(workloads, name)(paths=paths)
     if c2_per_r2 is not None:
@@ -570,16 +572,16 @@ def test_mc_moment_sums_forced_modes(pdd, name, c2_per_r2):
     for mode in ("fp64", "double_float", "fp32", "auto"):
         S = pdd.System(cov, cfg, "mixed", moment_sums=mode)
         mc = _np(S.mc())
-        out[mode] = (mc["moments"], mc["bmean"], _np(S.csr())["val"])
-    m64, b64, v64 = out["fp64"]
+        out[mode] = (mc["moments"], mc["bmean"])
+    m64, b64 = out["fp64"]
     scale = np.abs(m64).max()
-    # r_i does not go through the basis sums (the same FP64 terms, compiled per mode)
-    assert np.abs(out["double_float"][1] - b64).max() <= 1e-14 * max(1.0, np.abs(b64).max())
-    assert np.abs(out["double_float"][0] - m64).max() <= 1e-12 * scale
-    assert np.abs(out["fp32"][0] - m64).max() <= 1e-5 * scale
+    err = {mode: np.abs(out[mode][0] - m64).max() / scale for mode in ("double_float", "fp32", "auto")}
+    assert err["double_float"] <= 1e-9, err
+    assert 1e-9 < err["fp32"] <= 1e-5, err           # the FP32 sums really are the less accurate ones
+    # r_i does not go through the basis sums
+    assert np.abs(out["double_float"][1] - b64).max() <= 1e-9 * max(1.0, np.abs(b64).max())
     if c2_per_r2 is not None:
-        # the automatic choice takes the accurate sums for these ill-conditioned stencils
-        assert np.abs(out["auto"][0] - m64).max() <= 1e-12 * scale
+        assert err["auto"] <= 1e-9, err              # the automatic choice takes the accurate sums
 
 
 def test_gmres_random_csr_against_direct(pdd):
