@@ -1,4 +1,4 @@
-"""Adjoint gradient of a misfit J(u) with respect to c's RBF weights and g's coefficients (a14).
+"""Adjoint gradient of a misfit J(u) with respect to the RBF weights of c and f and g's coefficients (a14).
 
 The paper has no gradient; this restates the standard discrete adjoint of the
 assembled system.  With C(theta) u = r(theta) and lambda solving
@@ -10,13 +10,15 @@ Row by row:
   * Dirichlet rows: r_i = g(x_i), so d/da_k = psi^g_k(x_i).
   * Floating rows (Eq. 33, 35): the disk's local solution with interface data
     u_hat = sum_j H_j u_j is V = B - sum_j G_j u_j, solving A V = -A_IB beta - f.
-    Only A depends on the weights (through c at the nodes), so
-    sum_i lambda_i dV(x_i)/dw_q = -z^T diag(psi_q * active) V with
-    A^T z = sum_i lambda_i E_i (one transposed disk solve per disk).
+    A depends on c's weights (through c at the nodes) and the right-hand side on
+    f's, so sum_i lambda_i dV(x_i)/dw_q = -z^T diag(psi_q * active) V and
+    sum_i lambda_i dV(x_i)/dv_q = -z^T psi^f_q with A^T z = sum_i lambda_i E_i
+    (one transposed disk solve per disk).
   * Perimeter rows (Eq. 29-30): the paths do not depend on c, only the weight
     Y_tau = prod_k (1 + c(X_k) h) and Z_tau do (pathwise derivative under common
     random numbers):  d/dw_q of E[(1_dOmega g + 1_Gamma u_hat) Y + Z] is
-    E[(1_dOmega g + 1_Gamma u_hat) dY_q + dZ_q]; d/da_k is E[1_dOmega psi^g_k Y].
+    E[(1_dOmega g + 1_Gamma u_hat) dY_q + dZ_q]; d/da_k is E[1_dOmega psi^g_k Y]; f's
+    weights enter Z_tau = sum_k f(X_k) Y_k h only: d/dv_q is E[sum_k psi^f_q(X_k) Y_k h].
   * c = min(0, sum_p w_p psi_p): the derivative carries the indicator of sum < 0.
 
 Pins (tests): central finite differences of J with the same Philox streams.
@@ -52,15 +54,18 @@ def eval_vector(shape, rho, phi):
 
 
 def gradient(cfg, system, u, dJdu):
-    """dJ/dw (RBF weights of c) and dJ/da (boundary Fourier coefficients of g)."""
+    """(dJ/dw, dJ/da, lambda, dJ/dv): RBF weights of c, boundary Fourier coefficients of g, the
+    adjoint solution, RBF weights of f."""
     cov = system.cov
     op = system.op
     C = system.csr()
     lam = krylov.solve_transpose(C, dJdu)
     n_w = op.rbf_w.size
     n_g = op.g_coef.size
+    n_f = op.frbf_w.size if op.f_kind == "rbf" else 0
     gw = np.zeros(n_w)
     ga = np.zeros(n_g)
+    gf = np.zeros(n_f)
     # Dirichlet rows
     dirich = np.nonzero(cov.row_sub < 0)[0]
     if n_g and op.g_kind == "boundary_fourier" and dirich.size:
@@ -98,6 +103,8 @@ def gradient(cfg, system, u, dJdu):
             psi = op.rbf_psi(X, Y)
             active = (psi @ op.rbf_w < 0.0).astype(np.float64)
             gw -= (z * V * active) @ psi
+        if n_f:
+            gf -= z @ op.frbf_psi(X, Y)
     # perimeter rows
     c2 = float(cfg.get("imq_c2", 1.5))
     for i, row in system.mc_rows.items():
@@ -113,8 +120,7 @@ def gradient(cfg, system, u, dJdu):
             H = spectral.fourier_cardinal(rec.etheta, tk, n)
         else:
             ut = np.array([unwrap(t, float(cov.theta_s[m])) for t in rec.etheta])
-            ca = imq.angle_c2(c2, cov.r[m])
-            H = imq.imq(ut, row.u_stencil, ca) @ row.Kinv if row.cols.size else np.zeros((P, 0))
+            H = imq.imq(ut, row.u_stencil, c2) @ row.Kinv if row.cols.size else np.zeros((P, 0))
         uhat = np.where(gam, H @ uX if row.cols.size else 0.0, 0.0)
         gv = np.zeros(P)
         if np.any(bnd):
@@ -122,7 +128,9 @@ def gradient(cfg, system, u, dJdu):
         payoff = np.where(bnd, gv, 0.0) + uhat
         if n_w and rec.dY is not None:
             gw += lam[i] * (payoff @ rec.dY + rec.dZ.sum(0)) / P
+        if n_f and rec.dZf is not None:
+            gf += lam[i] * rec.dZf.sum(0) / P
         if n_g and op.g_kind == "boundary_fourier" and np.any(bnd):
             s = cov.domain.arclength(rec.ex[bnd], rec.ey[bnd], rec.edge[bnd].astype(np.int64))
             ga += lam[i] * (rec.Y[bnd] @ op.g_fourier_basis(s)) / P
-    return gw, ga, lam
+    return gw, ga, lam, gf

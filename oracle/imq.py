@@ -4,14 +4,14 @@
   K_lk     = phi_k(t_l)                          Eq. 20 (symmetric, positive definite)
   H_j(t)   = sum_l (K^-1)_lj phi_l(t)            Eq. 22
 
-Reading of Eq. 19: theta measures length along the interface (arclength
-s = r theta, in the units of Omega), so c has the units of length; with the
-paper's c^2 = 1.5 on its radius-9, 44-knot circles, c is about one knot
-spacing and K is well conditioned (kappa ~ 50), as Sec. 2.2 states.  Since
-phi_l(s) = r^-1 ((u - u_l)^2 + c^2/r^2)^(-1/2) for the local angle u, and the
-cardinal functions of Eq. 22 do not change when the basis is scaled, the
-functions below take the local unwrapped angles u and c^2 / r^2 (angle_c2).
-K is inverted through its Cholesky factor.
+Reading of Eq. 19: theta is the knots' local unwrapped angle in radians (not
+scaled by the radius), with c^2 = 1.5 as in the paper's experiments (Sec. 4).
+Read as arclength instead (c in length units, about one knot spacing on the
+paper's radius-9 circles), K would be well conditioned (kappa ~ 46 against
+~7e11), but the interpolant of the Eq. 46 solution on the perimeter arcs would
+be off by 0.07, far above the RMS error of 3.7e-5 that Table 1 reports; in
+radians it is off by 6e-5 (oracle/imq_reading.py).  K is inverted through its
+Cholesky factor.
 
 Pins (tests): the Kronecker property Eq. 14, exact reproduction of any
 function in the span of {phi_l}, and agreement with a 50-digit solve.
@@ -21,11 +21,6 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
-
-
-def angle_c2(c2, r):
-    """c^2 of Eq. 19 (squared length) as a squared angle on a circle of radius r."""
-    return float(c2) / (float(r) * float(r))
 
 
 def imq(t, tj, c2):

@@ -42,7 +42,7 @@ _lib = None
 
 B_KIND = {"zero": 0, "sinx_cosy": 1}
 C_KIND = {"zero": 0, "quadratic": 1, "rbf": 2}
-F_KIND = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3}
+F_KIND = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3, "rbf": 4}
 
 
 def build(force: bool = False) -> str:
@@ -59,14 +59,16 @@ class _Problem(ctypes.Structure):
     _fields_ = [("dom_kind", ctypes.c_int), ("dom", ctypes.c_double * 4),
                 ("b_kind", ctypes.c_int), ("c_kind", ctypes.c_int), ("f_kind", ctypes.c_int),
                 ("n_rbf", ctypes.c_int), ("rbf_x", ctypes.c_void_p), ("rbf_y", ctypes.c_void_p),
-                ("rbf_w", ctypes.c_void_p), ("rbf_sigma", ctypes.c_double)]
+                ("rbf_w", ctypes.c_void_p), ("rbf_sigma", ctypes.c_double),
+                ("n_frbf", ctypes.c_int), ("frbf_x", ctypes.c_void_p), ("frbf_y", ctypes.c_void_p),
+                ("frbf_w", ctypes.c_void_p), ("frbf_sigma", ctypes.c_double)]
 
 
 class _Walk(ctypes.Structure):
     _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("knot", ctypes.c_uint32),
                 ("sub", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("h", ctypes.c_double), ("n_paths", ctypes.c_int),
-                ("max_steps", ctypes.c_int), ("shift", ctypes.c_double)]
+                ("max_steps", ctypes.c_int), ("shift", ctypes.c_double), ("cv_degree", ctypes.c_int)]
 
 
 # c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi boundary shift in units of |sigma^T n| sqrt(h)
@@ -108,7 +110,7 @@ def normals(seed, knot, step, path, sub=0):
 class PathRecords:
     """Per-path exit records of one knot."""
 
-    def __init__(self, n, n_rbf=0):
+    def __init__(self, n, n_rbf=0, n_cv=0, n_frbf=0):
         self.side = np.zeros(n, np.int8)
         self.edge = np.zeros(n, np.int8)
         self.ex = np.zeros(n)
@@ -119,6 +121,8 @@ class PathRecords:
         self.steps = np.zeros(n, np.int32)
         self.dY = np.zeros((n, n_rbf)) if n_rbf else None
         self.dZ = np.zeros((n, n_rbf)) if n_rbf else None
+        self.Q = np.zeros((n, n_cv)) if n_cv else None        # control-variate features
+        self.dZf = np.zeros((n, n_frbf)) if n_frbf else None  # dZ_tau / d(weights of f)
         self.capped = 0
 
 
@@ -131,22 +135,33 @@ def max_steps_for(r, h):
     return int(min(2**31 - 1, math.ceil(50.0 * r * r / h)))
 
 
+def n_cv_features(degree):
+    """Control-variate features for monomials of total degree 1..degree: degree (degree + 3) / 2."""
+    d = int(degree)
+    return d * (d + 3) // 2
+
+
 def walk(op: Operator, cx, cy, r, x0, y0, knot, seed, h, n_paths, with_grad=False,
-         max_steps=None, shift=0.0, sub=0) -> PathRecords:
+         max_steps=None, shift=0.0, sub=0, cv_degree=0) -> PathRecords:
     dom = op.domain
     nr = op.rbf_w.size if with_grad else 0
-    rec = PathRecords(n_paths, nr)
-    keep = [op.rbf_x, op.rbf_y, op.rbf_w]
+    nf = op.frbf_w.size if (with_grad and op.f_kind == "rbf") else 0
+    rec = PathRecords(n_paths, nr, n_cv_features(cv_degree), nf)
+    keep = [op.rbf_x, op.rbf_y, op.rbf_w, op.frbf_x, op.frbf_y, op.frbf_w]
     prob = _Problem(0 if dom.kind == "square" else 1, (ctypes.c_double * 4)(*dom.p),
                     B_KIND[op.b_kind], C_KIND[op.c_kind], F_KIND[op.f_kind],
                     int(op.rbf_w.size), _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]),
-                    op.rbf_sigma)
+                    op.rbf_sigma, int(op.frbf_w.size), _ptr(keep[3]), _ptr(keep[4]), _ptr(keep[5]),
+                    op.frbf_sigma)
     ms = max_steps_for(r, h) if max_steps is None else int(max_steps)
-    w = _Walk(cx, cy, r, x0, y0, int(knot), int(sub), int(seed), h, int(n_paths), ms, float(shift))
+    w = _Walk(cx, cy, r, x0, y0, int(knot), int(sub), int(seed), h, int(n_paths), ms, float(shift),
+              int(cv_degree))
     got = lib().oracle_walk_knot(ctypes.byref(prob), ctypes.byref(w), _ptr(rec.side),
                                  _ptr(rec.edge), _ptr(rec.ex), _ptr(rec.ey), _ptr(rec.etheta),
                                  _ptr(rec.Y), _ptr(rec.Z), _ptr(rec.steps), _ptr(rec.dY),
-                                 _ptr(rec.dZ))
+                                 _ptr(rec.dZ), _ptr(rec.Q), _ptr(rec.dZf))
+    if got == -2:
+        raise ValueError("control-variate degree above 4")
     if got < 0:
         raise ValueError("too many RBF terms for the path derivative buffer")
     rec.capped = got
@@ -184,6 +199,19 @@ def batch_mean_se(per_path, bsamp, batches=32):
     return max(out)
 
 
+def control_variate_coef(Q, payoffs):
+    """Regression coefficients of the per-path payoffs on the control-variate features:
+    beta = Cov(Q)^-1 Cov(Q, P) (covariances normalised by the path count), one column per
+    payoff.  Any beta leaves the estimator's mean unchanged (E[Q] = 0); this one minimises the
+    variance over the sample (Milstein and Tretyakov's regression method, with beta from the
+    same paths: a bias of order 1/paths)."""
+    n = Q.shape[0]
+    qm = Q.mean(0)
+    covq = Q.T @ Q / n - np.outer(qm, qm)
+    covqp = Q.T @ payoffs / n - np.outer(qm, payoffs.mean(0))
+    return np.linalg.solve(covq, covqp)
+
+
 def adaptive_paths(P0, Pmax, se, target):
     """Path count of the adaptive rule: a row whose largest standard error se is at most the
     target keeps its P0 pilot paths; otherwise ceil(P0 (se/target)^2) rounded up to a
@@ -197,7 +225,7 @@ def adaptive_paths(P0, Pmax, se, target):
 
 def mc_row(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis: str = "imq",
            with_grad=False, Kinv=None) -> McRow:
-    """a11 + a12 for knot i integrated in subdomain m (c2: c^2 of Eq. 19 in squared length).
+    """a11 + a12 for knot i integrated in subdomain m (c2: c^2 of Eq. 19, angles in radians).
 
     With mc["paths_max"] > mc["paths"] and mc["se_target"] > 0 the pilot of
     mc["paths"] paths is followed, when the row's largest batch-means standard
@@ -226,9 +254,10 @@ def _sub_index(cov, i, m):
 
 def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis, with_grad, Kinv, P) -> McRow:
     cx, cy, r = float(cov.cx[m]), float(cov.cy[m]), float(cov.r[m])
+    cvd = int(mc.get("cv_degree", 0))
     rec = walk(op, cx, cy, r, float(cov.kx[i]), float(cov.ky[i]), i, int(mc["seed"]),
                float(mc["h"]), P, with_grad=with_grad, max_steps=mc.get("max_steps") or None,
-               shift=boundary_shift(mc), sub=_sub_index(cov, i, m))
+               shift=boundary_shift(mc), sub=_sub_index(cov, i, m), cv_degree=cvd)
     if rec.capped:
         raise RuntimeError(f"EPATH_CAP: {rec.capped} paths of knot {i} hit the step cap")
     a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
@@ -241,11 +270,10 @@ def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis,
         gvals[bnd] = op.g(rec.ex[bnd], rec.ey[bnd], rec.edge[bnd].astype(np.int64))
     bsamp = np.where(bnd, gvals * rec.Y, 0.0) + rec.Z
     if basis == "imq":
-        ca = imq.angle_c2(c2, r)
         if Kinv is None and us.size:
-            Kinv = imq.inverse(us, ca)
+            Kinv = imq.inverse(us, c2)
         ut = np.array([unwrap(t, float(cov.theta_s[m])) for t in rec.etheta])
-        phi = imq.imq(ut, us, ca) if us.size else np.zeros((P, 0))
+        phi = imq.imq(ut, us, c2) if us.size else np.zeros((P, 0))
         phi = np.where(gam[:, None], phi, 0.0)
         moments = (phi * rec.Y[:, None]).sum(0) / P
         vals = -(Kinv.T @ moments) if us.size else np.zeros(0)
@@ -258,6 +286,23 @@ def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis,
         moments = (H * rec.Y[:, None]).sum(0) / P
         vals = -moments
         per_path = -H * rec.Y[:, None]
+    row_beta = None
+    if cvd:
+        # regression control variate on every payoff (the basis moments and r's payoff): the
+        # corrected per-path payoff is P - Q beta, whose mean is mean(P) - beta^T mean(Q)
+        mpp = (phi if basis == "imq" else H) * rec.Y[:, None]
+        beta = control_variate_coef(rec.Q, np.concatenate([mpp, bsamp[:, None]], 1))
+        mcorr = mpp - rec.Q @ beta[:, :-1]
+        moments = mcorr.sum(0) / P
+        bsamp = bsamp - rec.Q @ beta[:, -1]
+        if basis == "imq":
+            if us.size:
+                vals = -(Kinv.T @ moments)
+                per_path = -(mcorr @ Kinv)
+        else:
+            vals = -moments
+            per_path = -mcorr
+        row_beta = beta
     bval = bsamp.sum() / P
     se = per_path.std(0, ddof=1) / math.sqrt(P) if P > 1 else np.zeros(b - a)
     se_b = float(bsamp.std(ddof=1) / math.sqrt(P)) if P > 1 else 0.0
@@ -265,6 +310,7 @@ def _mc_row_paths(cov, op: Operator, i: int, m: int, mc: dict, c2: float, basis,
     row.per_path = per_path
     row.bsamp = bsamp
     row.paths = P
+    row.cv_beta = row_beta
     return row
 
 
@@ -282,7 +328,7 @@ def mc_rows(cov, op: Operator, rows, mc: dict, c2: float, threads: int = 1, basi
     def kinv(m):
         if m not in Kcache:
             a, b = int(cov.knot_ptr[m]), int(cov.knot_ptr[m + 1])
-            Kcache[m] = imq.inverse(cov.ku[a:b], imq.angle_c2(c2, cov.r[m])) if b > a else np.zeros((0, 0))
+            Kcache[m] = imq.inverse(cov.ku[a:b], c2) if b > a else np.zeros((0, 0))
         return Kcache[m]
 
     def one(item):

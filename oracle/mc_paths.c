@@ -31,10 +31,20 @@
  * 53-bit uniforms u1 = ((a << 21) ^ (b >> 11) + 0.5) 2^-53 and likewise u2
  * from (c, d); Box-Muller gives xi = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
  *
+ * Control-variate features (optional, cv_degree = D > 0): for the monomials
+ * psi = xr^a yr^b (1 <= a + b <= D) of xr = (x - cx) / r, yr = (y - cy) / r, the
+ * discrete martingales Q = sum_k Y_k grad psi(X_k) . sqrt(h) xi_k (sigma = I),
+ * which have mean zero for any psi because xi_k is independent of X_k and Y_k
+ * (Newton 1994; Milstein and Tretyakov, SIAM J. Numer. Anal. 47 (2009)):
+ *   grad psi . xi = (a xr^(a-1) yr^b xi_x + b xr^a yr^(b-1) xi_y) / r.
+ * Stored per path in the order d = a + b = 1..D, a = d..0: D (D + 3) / 2
+ * features (at most 14, D <= 4).
+ *
  * Output per path: side (0 interface, 1 domain boundary, 2 step cap),
  * boundary edge, exit point, exit angle about the centre, Y_tau, Z_tau,
- * number of steps, and optionally the pathwise derivatives of Y_tau and
- * Z_tau with respect to the RBF weights of c (for the adjoint check).
+ * number of steps, the control-variate features, and optionally the pathwise
+ * derivatives of Y_tau and Z_tau with respect to the RBF weights of c (for the
+ * adjoint check).
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,10 +55,13 @@ typedef struct {
     double dom[4];
     int b_kind;              /* 0 zero, 1 (sin x, cos y) */
     int c_kind;              /* 0 zero, 1 -(1+x^2+y^2), 2 rbf */
-    int f_kind;              /* 0 zero, 1 one, 2 manufactured sin(pi x)cos(pi y), 3 Eq. 46 */
+    int f_kind;              /* 0 zero, 1 one, 2 manufactured sin(pi x)cos(pi y), 3 Eq. 46, 4 rbf */
     int n_rbf;
     const double *rbf_x, *rbf_y, *rbf_w;
     double rbf_sigma;
+    int n_frbf;              /* f = sum_q v_q exp(-|x - x_q|^2 / (2 s_f^2)) (f_kind 4) */
+    const double *frbf_x, *frbf_y, *frbf_w;
+    double frbf_sigma;
 } oracle_problem;
 
 typedef struct {
@@ -61,6 +74,7 @@ typedef struct {
     int n_paths;
     int max_steps;
     double shift;            /* 0: plain exit; > 0: shrunk boundaries, projected exit point */
+    int cv_degree;           /* 0: no control-variate features; D: 2 D features per path */
 } oracle_walk;
 
 static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -151,8 +165,19 @@ static void u46(double x, double y, double *u, double *ux, double *uy, double *l
     *lap = (cos(s) * lap_s - sin(s) * g2s + sech2 * (lap_w - 2.0 * t * (wx * wx + wy * wy))) / 3.0;
 }
 
+static double frbf_psi(const oracle_problem *p, int q, double x, double y)
+{
+    double dx = x - p->frbf_x[q], dy = y - p->frbf_y[q];
+    return exp(-(dx * dx + dy * dy) / (2.0 * p->frbf_sigma * p->frbf_sigma));
+}
+
 static double source(const oracle_problem *p, double x, double y)
 {
+    if (p->f_kind == 4) {
+        double s = 0.0;
+        for (int q = 0; q < p->n_frbf; ++q) s += p->frbf_w[q] * frbf_psi(p, q, x, y);
+        return s;
+    }
     if (p->f_kind == 1) return 1.0;
     if (p->f_kind == 2) {
         double pi = M_PI;
@@ -198,8 +223,14 @@ static double circle_exit_t(double px, double py, double dx, double dy,
 int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
                      int8_t *side, int8_t *edge, double *ex, double *ey, double *etheta,
                      double *Ytau, double *Ztau, int32_t *steps,
-                     double *dY, double *dZ)
+                     double *dY, double *dZ, double *Q, double *dZf)
 {
+    /* dZf (optional, n_paths x n_frbf): d Z_tau / d v_q = sum_k psi^f_q(X_k) Y_k h */
+    const int nf = (dZf != NULL && p->f_kind == 4) ? p->n_frbf : 0;
+    if (nf > 256) return -1;
+    double Sf[256];
+    const int ncv = (Q != NULL && w->cv_degree > 0) ? w->cv_degree * (w->cv_degree + 3) / 2 : 0;
+    if (w->cv_degree > 4) return -2;
     const double sh = sqrt(w->h);
     const double dl = w->shift > 0.0 ? w->shift : 0.0;
     const double rs = w->r - dl;                         /* shrunk circle and domain */
@@ -216,6 +247,9 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
     if (nr > 256) return -1;
     for (int path = 0; path < w->n_paths; ++path) {
         double x = w->x0, y = w->y0, Y = 1.0, Z = 0.0;
+        double cvq[16];
+        for (int q = 0; q < ncv; ++q) cvq[q] = 0.0;
+        for (int q = 0; q < nf; ++q) Sf[q] = 0.0;
         for (int q = 0; q < nr; ++q) { S[q] = 0.0; dZacc[q] = 0.0; }
         int k = 0;
         int done = 0;
@@ -223,6 +257,8 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
             if (k >= w->max_steps) {
                 side[path] = 2; edge[path] = -1; ex[path] = x; ey[path] = y;
                 etheta[path] = 0.0; Ytau[path] = Y; Ztau[path] = Z; steps[path] = k;
+                for (int q = 0; q < ncv; ++q) Q[(size_t)path * ncv + q] = 0.0;
+                for (int q = 0; q < nf; ++q) dZf[(size_t)path * nf + q] = 0.0;
                 ++capped;
                 break;
             }
@@ -236,6 +272,24 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
             double ny = y + by * w->h + sh * xi[1];
             double Yn = Y * (1.0 + cv * w->h);
             double Zn = Z + fv * Y * w->h;
+            for (int q = 0; q < nf; ++q) Sf[q] += frbf_psi(p, q, x, y) * Y * w->h;
+            if (ncv) {
+                /* Y_k sqrt(h) grad psi(X_k) . xi_k for psi = xr^a yr^b */
+                double xr = (x - w->cx) / w->r, yr = (y - w->cy) / w->r;
+                double s = Y * sh / w->r;
+                double px[5], py[5];
+                px[0] = 1.0; py[0] = 1.0;
+                for (int e = 1; e <= w->cv_degree; ++e) { px[e] = px[e - 1] * xr; py[e] = py[e - 1] * yr; }
+                int q = 0;
+                for (int d = 1; d <= w->cv_degree; ++d)
+                    for (int a = d; a >= 0; --a) {
+                        int b = d - a;
+                        double g = 0.0;
+                        if (a > 0) g += a * px[a - 1] * py[b] * xi[0];
+                        if (b > 0) g += b * px[a] * py[b - 1] * xi[1];
+                        cvq[q++] += s * g;
+                    }
+            }
             if (nr) {
                 /* d/dw_q of Y_{k+1} = Y_k (1 + c_k h):  S_q accumulates psi_q h / (1 + c_k h),
                  * and dZ_{k+1} = dZ_k + f_k h dY_k with dY_k = Y_k S_q (before the update). */
@@ -305,6 +359,8 @@ int oracle_walk_knot(const oracle_problem *p, const oracle_walk *w,
                 }
             }
             Ytau[path] = Yn; Ztau[path] = Zn; steps[path] = k;
+            for (int q = 0; q < ncv; ++q) Q[(size_t)path * ncv + q] = cvq[q];
+            for (int q = 0; q < nf; ++q) dZf[(size_t)path * nf + q] = Sf[q];
             for (int q = 0; q < nr; ++q) {
                 dY[(size_t)path * nr + q] = Yn * S[q];
                 dZ[(size_t)path * nr + q] = dZacc[q];

@@ -116,6 +116,19 @@ class Operator:
         self.g_coef = np.zeros(0) if gc is None else np.asarray(gc, np.float64)
         if self.c_kind == "rbf" and self.rbf_w.size == 0:
             raise ValueError("c=rbf needs RBF parameters")
+        # f = sum_q v_q exp(-|x - x_q|^2 / (2 s_f^2)) (the source family whose weights the adjoint
+        # differentiates)
+        frbf = op.get("frbf")
+        if frbf is not None:
+            self.frbf_x = np.asarray(frbf["x"], np.float64)
+            self.frbf_y = np.asarray(frbf["y"], np.float64)
+            self.frbf_w = np.asarray(frbf["w"], np.float64)
+            self.frbf_sigma = float(frbf["sigma"])
+        else:
+            self.frbf_x = self.frbf_y = self.frbf_w = np.zeros(0)
+            self.frbf_sigma = 1.0
+        if self.f_kind == "rbf" and self.frbf_w.size == 0:
+            raise ValueError("f=rbf needs RBF parameters")
 
     # -- drift -----------------------------------------------------------------
     def b(self, x, y):
@@ -133,6 +146,14 @@ class Operator:
         dx = x - self.rbf_x
         dy = y - self.rbf_y
         return np.exp(-(dx * dx + dy * dy) / (2.0 * self.rbf_sigma * self.rbf_sigma))
+
+    def frbf_psi(self, x, y):
+        """psi^f_q(x) = exp(-|x - x_q|^2 / (2 s_f^2)), shape (..., n_frbf)."""
+        x = np.asarray(x, np.float64)[..., None]
+        y = np.asarray(y, np.float64)[..., None]
+        dx = x - self.frbf_x
+        dy = y - self.frbf_y
+        return np.exp(-(dx * dx + dy * dy) / (2.0 * self.frbf_sigma * self.frbf_sigma))
 
     def c(self, x, y):
         if self.c_kind == "zero":
@@ -199,6 +220,8 @@ class Operator:
             u, ux, uy, lap = self.u46(x, y)
             bx, by = self.b(x, y)
             return -(0.5 * lap + bx * ux + by * uy + self.c(x, y) * u)
+        if self.f_kind == "rbf":
+            return self.frbf_psi(x, y) @ self.frbf_w
         raise ValueError(self.f_kind)
 
     # -- Dirichlet data --------------------------------------------------------

@@ -12,7 +12,8 @@
 * The RAS preconditioner (Eq. 42-45): partition of unity, M^-1 = I when C = I,
   M^-1 = C^-1 when one subset holds every knot, and right-preconditioned GMRES
   against the direct solve in fewer iterations than plain GMRES.
-* The adjoint gradient against central finite differences (common random numbers).
+* The adjoint gradient (weights of c and f, coefficients of g) against central finite
+  differences (common random numbers).
 """
 import math
 import os
@@ -234,6 +235,56 @@ def test_feynman_kac_eq46_on_a_disk():
         assert abs(rec.Z.mean()) > 5 * tol
 
 
+def test_control_variate_on_a_disk():
+    """Pathwise variance reduction (the regression control variate of Milstein and Tretyakov) on
+    the Eq. 46 Feynman-Kac test of a radius-9 disk: the features
+    Q = sum_k Y_k sqrt(h) grad psi(X_k) . xi_k of the monomials of degree 1..4 in the centred,
+    scaled coordinates have mean zero (each within 5 SE), the corrected estimate of
+    E[u46(X_tau) + Z_tau] stays within 4 SE + 2e-4 of u46(x0), and its standard error is more than
+    ten times smaller than the plain one (the local solution is smooth, so low-degree
+    polynomials carry most of its gradient)."""
+    dom = problem.Domain({"kind": "square", "p": [-50.0, -50.0, 50.0, 50.0]})
+    op = problem.Operator({"b": "zero", "c": "zero", "f": "eq46", "g": "eq46"}, dom)
+    cx, cy, R, h = 12.0, -7.0, 9.0, 0.015
+    shift = mc.boundary_shift({"h": h, "boundary_shift": True})
+    assert mc.n_cv_features(4) == 14 and mc.n_cv_features(2) == 5
+    for (x0, y0) in ((cx, cy), (cx + 4.0, cy - 3.0)):
+        rec = mc.walk(op, cx, cy, R, x0, y0, 5, 2, h, 4000, shift=shift, cv_degree=4)
+        plain = mc.walk(op, cx, cy, R, x0, y0, 5, 2, h, 4000, shift=shift)
+        # the same paths with and without the features
+        assert np.array_equal(rec.ex, plain.ex) and np.array_equal(rec.Z, plain.Z)
+        score = op.u46(rec.ex, rec.ey)[0] + rec.Z
+        n = score.size
+        zq = np.abs(rec.Q.mean(0)) / (rec.Q.std(0, ddof=1) / math.sqrt(n))
+        assert zq.max() < 5.0, zq
+        beta = mc.control_variate_coef(rec.Q, score[:, None])
+        corr = score - rec.Q @ beta[:, 0]
+        se_p = score.std(ddof=1) / math.sqrt(n)
+        se_c = corr.std(ddof=1) / math.sqrt(n)
+        assert abs(corr.mean() - op.u46(x0, y0)[0]) < 4 * se_c + 2e-4, (x0, y0, corr.mean(), se_c)
+        assert se_c < se_p / 10, (se_c, se_p)
+
+
+def test_control_variate_rows():
+    """Monte Carlo rows with the control variate (cv_degree 3) against the plain rows on the same
+    streams: every C entry and r within 4 plain standard errors, and the standard errors of the
+    corrected rows mostly smaller."""
+    cfg = workloads.tiny(paths=800)
+    cov = cover.full_cover(cfg)
+    rows = [i for i in range(cov.N) if cov.row_sub[i] >= 0 and not cov.floating[cov.row_sub[i]]][:10]
+    plain = system.assemble(cfg, cov, rows=rows, threads=4)
+    cfg_cv = dict(cfg, mc=dict(cfg["mc"], cv_degree=3))
+    cvs = system.assemble(cfg_cv, cov, rows=rows, threads=4)
+    ratios = []
+    for i in rows:
+        p, c = plain.mc_rows[i], cvs.mc_rows[i]
+        assert np.all(np.abs(c.vals - p.vals) <= 4 * p.se + 1e-12), i
+        assert abs(c.b - p.b) <= 4 * p.se_b + 1e-12, i
+        ok = p.se > 0
+        ratios += list(c.se[ok] / p.se[ok])
+    assert np.median(ratios) < 0.9, np.median(ratios)
+
+
 def test_harmonic_measure_is_poisson_kernel():
     from oracle import spectral
     cfg, cov = _disk_cover()
@@ -262,8 +313,7 @@ def test_constant_data_rows():
         m = cov.row_sub[i]
         # worst interpolation error of the constant 1 over the sampled exit angles
         t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
-        ca = imq.angle_c2(cfg["imq_c2"], cov.r[m])
-        err1 = np.abs(imq.cardinal(t, row.u_stencil, ca, row.Kinv).sum(1) - 1).max()
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, cfg["imq_c2"], row.Kinv).sum(1) - 1).max()
         lhs = 1.0 + row.vals.sum()
         assert abs(lhs - row.b) <= err1 + 1e-12, (i, m, lhs, row.b)
 
@@ -300,8 +350,7 @@ def test_averaged_rows_special_cases():
     rows = mc.mc_rows(cov1, problem.Operator(cfg1["op"], cov1.domain), pairs, cfg1["mc"], 1.5)
     for (i, m), row in rows.items():
         t = np.linspace(row.u_stencil[0], row.u_stencil[-1], 200)
-        ca = imq.angle_c2(cfg["imq_c2"], cov.r[m])
-        err1 = np.abs(imq.cardinal(t, row.u_stencil, ca, row.Kinv).sum(1) - 1).max()
+        err1 = np.abs(imq.cardinal(t, row.u_stencil, cfg["imq_c2"], row.Kinv).sum(1) - 1).max()
         assert abs(1.0 + row.vals.sum() - row.b) <= err1 + 1e-12, (i, m)
     # (c) streams: the k-th subdomain of a row draws with Philox counter word 3 = k
     assert mc.normals(0, 5, 3, 7) == mc.normals(0, 5, 3, 7, sub=0)
@@ -368,6 +417,9 @@ def _fd(param, idx, eps, u_obs, cov):
         if param == "w":
             c["op"]["rbf"]["w"] = c["op"]["rbf"]["w"].copy()
             c["op"]["rbf"]["w"][idx] += sgn * eps
+        elif param == "v":
+            c["op"]["frbf"]["w"] = c["op"]["frbf"]["w"].copy()
+            c["op"]["frbf"]["w"][idx] += sgn * eps
         else:
             c["op"]["g_coef"] = c["op"]["g_coef"].copy()
             c["op"]["g_coef"][idx] += sgn * eps
@@ -387,9 +439,10 @@ def test_adjoint_against_central_differences():
     rng = np.random.default_rng(9)
     u_obs = np.exp(cov.kx) * np.sin(cov.ky) + 0.01 * rng.standard_normal(cov.N)
     J0, S, u = _J(cfg, u_obs, cov)
-    gw, ga, _lam = adjoint.gradient(cfg, S, u, 2.0 * (u - u_obs))
+    gw, ga, _lam, gv = adjoint.gradient(cfg, S, u, 2.0 * (u - u_obs))
+    assert gv.size == 16
     for param, idx, g in (("w", 0, gw), ("w", 17, gw), ("w", 40, gw), ("a", 0, ga), ("a", 5, ga),
-                          ("a", 20, ga)):
+                          ("a", 20, ga), ("v", 0, gv), ("v", 7, gv), ("v", 15, gv)):
         fd4 = _fd(param, idx, 1e-4, u_obs, cov)
         assert abs(fd4 - g[idx]) <= 1e-6 * max(1e-2, abs(fd4)), (param, idx, fd4, g[idx])
         fd6 = _fd(param, idx, 1e-6, u_obs, cov)

@@ -156,3 +156,18 @@ def test_imq_against_50_digits():
     p = mp.matrix([1 / mp.sqrt((mp.mpf(t) - mp.mpf(x)) ** 2 + mp.mpf(c2)) for x in u])
     Hm = np.array([float(v) for v in mp.lu_solve(K, p)])
     assert np.abs(imq.cardinal(np.array([t]), u, c2)[0] - Hm).max() < 1e-12
+
+
+def test_imq_reading_reaches_table1_accuracy():
+    """Eq. 19 read with theta in radians (c^2 = 1.5): the IMQ interpolant of the exact solution of
+    Eq. 46 along every perimeter arc of the [-50, 50]^2 cover is within 1e-4 of it, below the
+    RMS error of 3.72e-5 x a few that Table 1 reports.  Read as arclength (c in length units)
+    the interpolant would be off by more than 1e-2: that reading cannot reach Table 1."""
+    import workloads
+    from oracle import cover, imq_reading
+    cfg = workloads.poisson46(paths=8)
+    cov = cover.full_cover(cfg)
+    rad = imq_reading.interpolation_error(cov, "radians", 1.5)
+    arc = imq_reading.interpolation_error(cov, "arclength", 1.5)
+    assert rad[0] < 1e-4, rad
+    assert arc[0] > 1e-2, arc

@@ -23,15 +23,18 @@ Workloads (the problem is Eq. 1 with L = 1/2 Laplacian + b.grad, sigma = I):
                    g=e^x sin y; ~10^4 circles with log-normal radii in [0.02, 0.1];
                    per-circle grids 16^2..64^2 chosen by radius; 10^3 pilot paths per
                    Monte Carlo knot, up to 10^5 where its standard error exceeds 2e-3.
-* ``grad``      -- ``tiny`` geometry; parameters are 64 RBF weights of c and 32
-                   Fourier coefficients of g along the boundary arclength.
+* ``grad``      -- ``tiny`` geometry; parameters are 64 RBF weights of c, 16 RBF
+                   weights of the source f and 32 Fourier coefficients of g along the
+                   boundary arclength.
 * ``poisson46`` -- the paper's Poisson test (Sec. 4, Eq. 46) on [-50,50]^2: f and g from
                    its exact solution u46, L = 1/2 Lap (so 1/2 Lap u = F/2 with
                    F = Lap u46); 10x10 square lattice of circles of radius 9 (the
                    paper's radii lie in [8.55, 9.43]; its layout figure is not
                    available); 44 knots per circle; 22(r)x44(theta) disk grid (968
                    nodes); 5,000 paths per Monte Carlo knot, h = 0.015, boundary
-                   shift on (Gobet-Menozzi); c^2 = 1.5.
+                   shift on (Gobet-Menozzi), pathwise variance reduction on (the
+                   regression control variate on the monomials of degree <= 4);
+                   c^2 = 1.5.
 
 The random draws a workload needs (RBF centres and weights, adaptive radii,
 observation noise) are made here with numpy's seeded generators and passed to
@@ -48,22 +51,12 @@ import numpy as np
 # Coefficient-family vocabulary shared by both sides (names only).
 #   b:  "zero" | "sinx_cosy"                   b = (sin x, cos y)
 #   c:  "zero" | "quadratic" | "rbf"           c = -(1+x^2+y^2) | min(0, sum_p w_p psi_p(x))
-#   f:  "zero" | "one" | "manufactured" | "eq46"
+#   f:  "zero" | "one" | "manufactured" | "eq46" | "rbf"
 #                                              manufactured from u = sin(pi x) cos(pi y) |
-#                                              from u46, the exact solution of Eq. 46
+#                                              from u46, the exact solution of Eq. 46 |
+#                                              sum_q v_q exp(-|x-x_q|^2/(2 s_f^2))
 #   g:  "exp_sin" | "sin_cos" | "boundary_fourier" | "one" | "zero" | "eq46"
 # --------------------------------------------------------------------------
-
-
-# IMQ shape parameter of Eq. 19, with theta measured as arclength (c in the length units of
-# Omega): the paper's c^2 = 1.5 on radius-9 circles with 44 knots (Sec. 4) puts c at 0.953 knot
-# spacings.  Workloads for which no c^2 is given keep that ratio of c to the knot spacing.
-PAPER_C_PER_SPACING = math.sqrt(1.5) / (9.0 * 2.0 * math.pi / 44.0)
-
-
-def imq_c2_for(radius: float, n_knots: int) -> float:
-    """c^2 that puts c at the paper's 0.953 knot spacings on circles of this radius."""
-    return (PAPER_C_PER_SPACING * 2.0 * math.pi * radius / n_knots) ** 2
 
 
 def _square(x0, y0, x1, y1):
@@ -84,7 +77,7 @@ def tiny(paths: int = 1000, h: float = 1e-4, seed: int = 0) -> dict:
         "n_knots": 16, "n_r": 16, "n_theta": 16,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": imq_c2_for(0.2, 16),
+        "imq_c2": 1.5,
     }
 
 
@@ -101,7 +94,7 @@ def varcoef(paths: int = 10000, h: float = 1e-5, seed: int = 0) -> dict:
         "n_knots": 32, "n_r": 32, "n_theta": 32,
         "op": {"b": "sinx_cosy", "c": "quadratic", "f": "manufactured", "g": "sin_cos"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": imq_c2_for(0.05, 32),
+        "imq_c2": 1.5,
     }
 
 
@@ -116,7 +109,7 @@ def scaled(paths: int = 1000, h: float = 1e-5, seed: int = 0) -> dict:
         "n_knots": 16, "n_r": 48, "n_theta": 64,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": paths, "h": h, "seed": seed},
-        "imq_c2": imq_c2_for(0.8 * s, 16),
+        "imq_c2": 1.5,
     }
 
 
@@ -187,7 +180,7 @@ def adaptive(paths: int = 1000, h: float = 1e-5, seed: int = 0, cells: int = 16,
         # pilot of `paths` per Monte Carlo knot, then up to paths_max where the largest
         # standard error of the row exceeds se_target
         "mc": {"paths": paths, "h": h, "seed": seed, "paths_max": paths_max, "se_target": se_target},
-        "imq_c2": imq_c2_for(0.025, 16),
+        "imq_c2": 1.5,
     }
 
 
@@ -220,24 +213,32 @@ def boundary_fourier_fit(domain: dict, n_cos: int = 16, n_sin: int = 16,
     return coef
 
 
-def grad(paths: int = 1000, h: float = 1e-4, seed: int = 0, perturbed: bool = False) -> dict:
-    """``tiny`` geometry with c from 64 negative-weight RBFs and Fourier boundary data.
+def grad(paths: int = 1000, h: float = 1e-4, seed: int = 0, perturbed: bool = False,
+         with_f: bool = True) -> dict:
+    """``tiny`` geometry with c from 64 negative-weight RBFs, Fourier boundary data and (with_f)
+    a source f from 16 Gaussian RBFs (width 0.25, weights 0.5 N(0,1), seed 3).
 
     ``perturbed`` gives the parameter set the observations are made from:
-    w_p (1 + 0.1 N(0,1)) with seed 1 and the g coefficients shifted by
-    0.01 N(0,1) with seed 1.
+    w_p (1 + 0.1 N(0,1)) with seed 1, the g coefficients shifted by 0.01 N(0,1) with seed 1
+    and the f weights v_q (1 + 0.1 N(0,1)) with seed 4.
     """
     cfg = tiny(paths, h, seed)
     cfg["name"] = "grad"
     rbf = rbf_field(64, seed=0, sigma=0.2, negative=True, domain=cfg["domain"])
     gco = boundary_fourier_fit(cfg["domain"])
+    frbf = rbf_field(16, seed=3, sigma=0.25, negative=False, domain=cfg["domain"])
+    frbf["w"] = 0.5 * frbf["w"]
     if perturbed:
         rng = np.random.default_rng(1)
         rbf = dict(rbf)
         rbf["w"] = rbf["w"] * (1.0 + 0.1 * rng.standard_normal(rbf["w"].shape[0]))
         gco = gco + 0.01 * rng.standard_normal(gco.shape[0])
-    cfg["op"] = {"b": "zero", "c": "rbf", "f": "zero", "g": "boundary_fourier",
+        frbf = dict(frbf)
+        frbf["w"] = frbf["w"] * (1.0 + 0.1 * np.random.default_rng(4).standard_normal(frbf["w"].shape[0]))
+    cfg["op"] = {"b": "zero", "c": "rbf", "f": "rbf" if with_f else "zero", "g": "boundary_fourier",
                  "rbf": rbf, "g_coef": gco}
+    if with_f:
+        cfg["op"]["frbf"] = frbf
     return cfg
 
 
@@ -258,12 +259,12 @@ def floating_only_disk(radius: float = 0.3, n_knots: int = 16, n_r: int = 16,
         "n_knots": 0, "n_r": 0, "n_theta": 0,
         "op": {"b": "zero", "c": "zero", "f": "zero", "g": "exp_sin"},
         "mc": {"paths": 1000, "h": 1e-4, "seed": 0},
-        "imq_c2": imq_c2_for(radius, n_knots),
+        "imq_c2": 1.5,
     }
 
 
 def poisson46(paths: int = 5000, h: float = 0.015, seed: int = 0, half_width: float = 50.0,
-              boundary_shift: bool = True) -> dict:
+              boundary_shift: bool = True, cv_degree: int = 4) -> dict:
     """Poisson's equation with the exact solution of Eq. 46 on [-L, L]^2, L = half_width.
 
     Circles of radius 9 on a square lattice of pitch 10 (centres at -L + 5, ..., L - 5),
@@ -277,7 +278,8 @@ def poisson46(paths: int = 5000, h: float = 0.015, seed: int = 0, half_width: fl
                   "y_origin": -half_width + 5.0, "spacing": 10.0, "radius": 9.0},
         "n_knots": 44, "n_r": 22, "n_theta": 44,
         "op": {"b": "zero", "c": "zero", "f": "eq46", "g": "eq46"},
-        "mc": {"paths": paths, "h": h, "seed": seed, "boundary_shift": boundary_shift},
+        "mc": {"paths": paths, "h": h, "seed": seed, "boundary_shift": boundary_shift,
+               "cv_degree": cv_degree},
         "imq_c2": 1.5,
     }
 
