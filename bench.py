@@ -186,7 +186,7 @@ def step(pdd, cfg, precision, stream):
     return cov, S, u
 
 
-def _timed(pdd, cfg, precision, stream, flush, steps, **kw):
+def _timed(pdd, cfg, precision, stream, flush, steps, precond=None, **kw):
     """steps timed passes (cover + assembly + solve) after one warm-up; returns (ms list, last stats, N)."""
     import torch
     times, st, N = [], None, 0
@@ -197,7 +197,7 @@ def _timed(pdd, cfg, precision, stream, flush, steps, **kw):
         e0.record(stream)
         cov = pdd.Cover(cfg, stream=stream)
         S = pdd.System(cov, cfg, precision, stream=stream, **kw)
-        u = S.solve(rtol=1e-13, restart=64, stream=stream, precond=SOLVE["precond"])
+        u = S.solve(rtol=1e-13, restart=64, stream=stream, precond=precond or SOLVE["precond"])
         e1.record(stream)
         torch.cuda.synchronize()
         if rep:
@@ -456,7 +456,8 @@ def adaptive_leg(pdd, stream, flush, steps=2):
     grouped by shape, adaptive path counts (pilot 10^3, up to 10^5 per Monte Carlo knot)."""
     import workloads
     cfg = workloads.adaptive()
-    t, st, N = _timed(pdd, cfg, "mixed", stream, flush, steps)
+    # plain GMRES: the 64-knot circles' RAS subsets exceed the 128-knot limit of the FP32 inverses
+    t, st, N = _timed(pdd, cfg, "mixed", stream, flush, steps, precond="none")
     ms = statistics.mean(t)
     return {"workload": "adaptive: unit disk, c(x) from 64 Gaussian RBFs (clipped <= 0); adaptive cover of "
                         "log-normal radii in [0.02, 0.1] (grids 16^2..64^2 by radius); 10^3-10^5 paths/knot by "
@@ -466,7 +467,7 @@ def adaptive_leg(pdd, stream, flush, steps=2):
             "extended_rows": st["extended_rows"],
             "mc_path_steps_per_s": st["path_steps"] / (st["ms_paths"] / 1e3) if st["ms_paths"] else None,
             "stages_ms": {k: st[k] for k in ("ms_disks", "ms_factor", "ms_refine", "ms_paths", "ms_finalize")},
-            "gmres_iters": st["gmres_iters"]}
+            "gmres_iters": st["gmres_iters"], "precond": "none"}
 
 
 # The [-50,50]^2 column of the paper's Table 1 (Sec. 4): 1152 A64FX cores, 96 MPI processes,
@@ -687,7 +688,8 @@ def grad_bench(pdd, stream):
     g = S.grad(u, dJ, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    return {"workload": "grad: tiny geometry, 64 RBF weights of c + 32 boundary Fourier coefficients of g, "
+    return {"workload": "grad: tiny geometry, 64 RBF weights of c + 16 RBF weights of f + 32 boundary Fourier "
+                        "coefficients of g, "
                         "1000 paths/knot", "ms": e0.elapsed_time(e1), "n_params": int(g.numel()),
             "grad_norm": float(g.norm().item())}
 

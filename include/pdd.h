@@ -61,10 +61,11 @@ enum { PDD_C_ZERO = 0, PDD_C_QUADRATIC = 1,                    /* c = -(1+x^2+y^
        PDD_C_RBF = 2 };              /* c = min(0, sum_p w_p exp(-|x-x_p|^2/(2 s^2))) */
 enum { PDD_F_ZERO = 0, PDD_F_ONE = 1,
        PDD_F_MANUFACTURED = 2,       /* f = -(L u* + c u*), u* = sin(pi x) cos(pi y)  */
-       PDD_F_EQ46 = 3 };             /* f = -(L u46 + c u46), u46 = exact solution of
+       PDD_F_EQ46 = 3,               /* f = -(L u46 + c u46), u46 = exact solution of
                                         the Poisson test, Eq. 46:
                                         3 + sin(sqrt(1+x^2/100+y^2/50))/3
                                           + tanh(sin(3x/25+y/20) + sin(x/20-3y/25))/3 */
+       PDD_F_RBF = 4 };              /* f = sum_q v_q exp(-|x-x_q|^2/(2 s_f^2))       */
 enum { PDD_G_EXP_SIN = 0,            /* g = e^x sin y                                 */
        PDD_G_SIN_COS = 1,            /* g = sin(pi x) cos(pi y)                       */
        PDD_G_BOUNDARY_FOURIER = 2,   /* g(s) = sum_k a_k cos(2 pi k s/P) + b_k sin(.)  */
@@ -81,6 +82,10 @@ typedef struct {
     const double *g_coef;             /* host: a_0..a_{Kc-1}, b_1..b_{Ks}; Kc = ceil(n/2),
                                          s = arclength counter-clockwise from (x0,y0),
                                          P = perimeter of the square               */
+    int n_frbf;                       /* PDD_F_RBF: number of Gaussians of f        */
+    const double *frbf_x, *frbf_y;    /* host, n_frbf centres                       */
+    const double *frbf_w;             /* host, n_frbf weights v_q                   */
+    double frbf_sigma;                /* Gaussian width s_f                         */
 } pdd_operator;
 
 /* ---------------------------------------------------------------------------
@@ -201,11 +206,8 @@ typedef struct {
     int paths;                /* Monte Carlo paths per knot (> 0)                    */
     double h;                 /* Euler-Maruyama time step (> 0)                      */
     uint64_t seed;            /* Philox key word 0 (low 32 bits used)                */
-    double imq_c2;            /* IMQ shape c^2 of Eq. 19 in squared length units:
-                                 theta is measured along the interface (arclength
-                                 r_m u for the local angle u), so a circle's
-                                 cardinals are those of u with c^2 / r_m^2 (1.5 on
-                                 the paper's radius-9 circles, Sec. 4)               */
+    double imq_c2;            /* IMQ shape c^2 of Eq. 19, the knots' local angle in
+                                 radians (1.5 in the paper, Sec. 4)                  */
     int max_refine;           /* refinement sweeps cap (mixed form), e.g. 12         */
     double refine_tol;        /* stop when |dx|_inf <= tol |x|_inf per column        */
     int factor;               /* mixed form's LU: PDD_FACTOR_*                        */
@@ -231,6 +233,15 @@ typedef struct {
     int disk_precision;       /* PDD_STAGE_*: form of the floating disks (a6-a9)     */
     int path_precision;       /* PDD_STAGE_*: form of the Monte Carlo paths (a11)    */
     int moment_sums;          /* PDD_SUMS_*: basis sums of mixed-form paths (a12)    */
+    int cv_degree;            /* pathwise variance reduction (Sec. 4: the paper's
+                                 perimeter rows use one): 0 = off; D = 1..4: the
+                                 regression control variate of Milstein and Tretyakov
+                                 with the D (D + 3) / 2 martingales
+                                 sum_k Y_k sqrt(h) grad psi(X_k) . xi_k of the monomials
+                                 psi = ((x - c_x)/r)^a ((y - c_y)/r)^b, 1 <= a + b <= D
+                                 (mean zero for any psi); every payoff of a row (basis
+                                 moments, r) is regressed on them over the row's paths
+                                 and corrected.  pdd_grad takes cv_degree = 0 only     */
 } pdd_assembly_opts;
 
 typedef struct {
@@ -439,15 +450,18 @@ pdd_status pdd_batched_gemm_tf32x3(int batch, int M, int N, int K, const float *
  * ------------------------------------------------------------------------- */
 
 /*
- * pdd_grad -- dJ/dw (RBF weights of c, n_rbf values) and dJ/da (boundary
- * Fourier coefficients of g, n_gcoef values) of a misfit J(u), given u and
- * dJ/du.  lambda solves C^T lambda = dJ/du; floating disks contribute
- * -z^T diag(psi_q 1{c<0}) V with A^T z = sum_i lambda_i E_i (transposed
+ * pdd_grad -- dJ/dw (RBF weights of c, n_rbf values), dJ/dv (RBF weights of
+ * f, n_frbf values) and dJ/da (boundary Fourier coefficients of g, n_gcoef
+ * values) of a misfit J(u), given u and dJ/du.  lambda solves
+ * C^T lambda = dJ/du; floating disks contribute -z^T diag(psi_q 1{c<0}) V to
+ * dJ/dw and -z^T psi^f_q to dJ/dv, with A^T z = sum_i lambda_i E_i (transposed
  * disk solves, factors recomputed per disk) and V the disk solution for the
  * interface data of u; perimeter rows replay their Philox paths (common
- * random numbers) and accumulate the pathwise derivative of Y_tau and Z_tau.
+ * random numbers) and accumulate the pathwise derivatives of Y_tau and Z_tau
+ * (Z_tau = sum_k f(X_k) Y_k h, so dZ/dv_q = sum_k psi^f_q(X_k) Y_k h).
  * The operator and options must be those the system was assembled with.
- * grad_dev [n_rbf + n_gcoef] caller-owned device memory (weights first).
+ * grad_dev [n_rbf + n_frbf + n_gcoef] caller-owned device memory, in that
+ * order (a family the operator does not use has no entries).
  * lambda_dev [N] may be NULL.  Synchronises `stream`.
  */
 pdd_status pdd_grad(const pdd_cover *cov, const pdd_operator *op, const pdd_assembly_opts *opts,

@@ -30,7 +30,7 @@ PDD_STATUS = {0: "PDD_OK", 1: "PDD_EINVAL", 2: "PDD_ECOVER_GAP", 3: "PDD_ECIRCLE
 
 _B = {"zero": 0, "sinx_cosy": 1}
 _C = {"zero": 0, "quadratic": 1, "rbf": 2}
-_F = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3}
+_F = {"zero": 0, "one": 1, "manufactured": 2, "eq46": 3, "rbf": 4}
 _G = {"exp_sin": 0, "sin_cos": 1, "boundary_fourier": 2, "one": 3, "zero": 4, "eq46": 5}
 _COVER = {"square_lattice": 0, "hex_lattice": 1, "explicit": 2}
 PREC = {"fp64": 0, "mixed": 1}
@@ -54,7 +54,9 @@ class _Operator(ctypes.Structure):
     _fields_ = [("b_kind", ctypes.c_int), ("c_kind", ctypes.c_int), ("f_kind", ctypes.c_int),
                 ("g_kind", ctypes.c_int), ("n_rbf", ctypes.c_int), ("rbf_x", ctypes.c_void_p),
                 ("rbf_y", ctypes.c_void_p), ("rbf_w", ctypes.c_void_p), ("rbf_sigma", ctypes.c_double),
-                ("n_gcoef", ctypes.c_int), ("g_coef", ctypes.c_void_p)]
+                ("n_gcoef", ctypes.c_int), ("g_coef", ctypes.c_void_p), ("n_frbf", ctypes.c_int),
+                ("frbf_x", ctypes.c_void_p), ("frbf_y", ctypes.c_void_p), ("frbf_w", ctypes.c_void_p),
+                ("frbf_sigma", ctypes.c_double)]
 
 
 class _CoverSpec(ctypes.Structure):
@@ -79,7 +81,7 @@ class _AssemblyOpts(ctypes.Structure):
                 ("lu_leaf_width", ctypes.c_int), ("lu_tensor_min", ctypes.c_int),
                 ("paths_max", ctypes.c_int), ("se_target", ctypes.c_double), ("boundary_shift", ctypes.c_int),
                 ("max_steps", ctypes.c_int), ("disk_precision", ctypes.c_int), ("path_precision", ctypes.c_int),
-                ("moment_sums", ctypes.c_int)]
+                ("moment_sums", ctypes.c_int), ("cv_degree", ctypes.c_int)]
 
 
 STAGE = {None: 0, "fp64": 1, "mixed": 2}
@@ -224,12 +226,18 @@ def operator_struct(op: dict):
         gp = _f64(gco)
         keep.append(gp)
         n_g = gp.size
+    frbf = op.get("frbf")
+    n_f, fx, fy, fw, fsig = 0, None, None, None, 1.0
+    if frbf is not None and op["f"] == "rbf":
+        fx, fy, fw = _f64(frbf["x"]), _f64(frbf["y"]), _f64(frbf["w"])
+        keep += [fx, fy, fw]
+        n_f, fsig = fx.size, float(frbf["sigma"])
 
     def p(a):
         return a.ctypes.data if a is not None else None
 
     s = _Operator(_B[op["b"]], _C[op["c"]], _F[op["f"]], _G[op["g"]], n_rbf, p(rx), p(ry), p(rw), sig,
-                  n_g, p(gp))
+                  n_g, p(gp), n_f, p(fx), p(fy), p(fw), fsig)
     return s, keep
 
 
@@ -268,7 +276,8 @@ def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps
                          int(max_refine), float(refine_tol), FACTOR[factor], int(lu_leaf_width),
                          int(lu_tensor_min), int(mc.get("paths_max", 0)), float(mc.get("se_target", 0.0)),
                          1 if mc.get("boundary_shift", False) else 0, int(mc.get("max_steps", 0)),
-                         STAGE[disk_precision], STAGE[path_precision], SUMS[moment_sums])
+                         STAGE[disk_precision], STAGE[path_precision], SUMS[moment_sums],
+                         int(mc.get("cv_degree", 0)))
 
 
 # ---------------------------------------------------------------------------
@@ -390,17 +399,19 @@ class System:
         return y
 
     def grad(self, u: torch.Tensor, dJdu: torch.Tensor, stream=None, return_lambda=False):
-        """dJ/d(theta) = [RBF weights of c, boundary Fourier coefficients of g]."""
+        """dJ/d(theta) = [RBF weights of c, RBF weights of f, boundary Fourier coefficients of g]
+        (a family the operator does not use has no entries)."""
         op = self.cfg["op"]
         n_w = len(op["rbf"]["w"]) if (op["c"] == "rbf" and op.get("rbf") is not None) else 0
+        n_f = len(op["frbf"]["w"]) if (op["f"] == "rbf" and op.get("frbf") is not None) else 0
         n_g = len(op["g_coef"]) if (op["g"] == "boundary_fourier" and op.get("g_coef") is not None) else 0
-        g = torch.zeros(max(1, n_w + n_g), dtype=torch.float64, device="cuda")
+        g = torch.zeros(max(1, n_w + n_f + n_g), dtype=torch.float64, device="cuda")
         lam = torch.empty(self.cov.N, dtype=torch.float64, device="cuda")
         u = u.contiguous()
         dJdu = dJdu.contiguous()
         _check(load().pdd_grad(self.cov.handle, ctypes.byref(self._op), ctypes.byref(self._opts), self._h,
                                _ptr(u), _ptr(dJdu), _ptr(g), _ptr(lam), _stream(stream)))
-        g = g[:n_w + n_g]
+        g = g[:n_w + n_f + n_g]
         return (g, lam) if return_lambda else g
 
     def __del__(self):
@@ -468,30 +479,38 @@ def launch_count() -> int:
 
 
 class MisfitSolve(torch.autograd.Function):
-    """u(theta) with theta = (RBF weights of c, boundary Fourier coefficients of g).
+    """u(theta) with theta = (RBF weights of c, boundary Fourier coefficients of g, and -- when the
+    workload's f is "rbf" -- RBF weights of f).
 
     forward: assemble C, r at theta and solve; backward: the hand-written
     adjoint (pdd_grad).  ``cfg`` is the workload description (its c must be
-    "rbf" and its g "boundary_fourier").
+    "rbf" and its g "boundary_fourier").  ``v`` (f's weights) may be None.
     """
 
     @staticmethod
-    def forward(ctx, w, a, cfg, precision="fp64"):
+    def forward(ctx, w, a, cfg, precision="fp64", v=None):
         c = dict(cfg)
         c["op"] = dict(cfg["op"])
         c["op"]["rbf"] = dict(cfg["op"]["rbf"])
         c["op"]["rbf"]["w"] = w.detach().cpu().numpy()
         c["op"]["g_coef"] = a.detach().cpu().numpy()
+        if v is not None:
+            c["op"]["frbf"] = dict(cfg["op"]["frbf"])
+            c["op"]["frbf"]["w"] = v.detach().cpu().numpy()
         cov = Cover(c)
         sys_ = System(cov, c, precision)
         u = sys_.solve(rtol=1e-14)
         ctx.sys = sys_
         ctx.n_w = w.numel()
+        ctx.n_f = len(c["op"]["frbf"]["w"]) if c["op"]["f"] == "rbf" else 0
+        ctx.has_v = v is not None
         ctx.save_for_backward(u)
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
         (u,) = ctx.saved_tensors
-        g = ctx.sys.grad(u, grad_u.to(torch.float64))
-        return g[:ctx.n_w].to(grad_u.device), g[ctx.n_w:].to(grad_u.device), None, None
+        g = ctx.sys.grad(u, grad_u.to(torch.float64)).to(grad_u.device)
+        nw, nf = ctx.n_w, ctx.n_f
+        gv = g[nw:nw + nf] if ctx.has_v else None
+        return g[:nw], g[nw + nf:], None, None, gv

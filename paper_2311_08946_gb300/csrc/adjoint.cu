@@ -33,16 +33,18 @@ __global__ void __launch_bounds__(256) k_grad_dirichlet(Problem P, int N, const 
     }
 }
 
-// grad[q] = base[q] + sum_d partial_disk[d][q] (q < nw) + sum_s partial_mc[s][q]
-__global__ void k_sum_partials(int nw, int ng, const double *pd, int nd, const double *pm, int nm,
+// grad[q] = sum_d partial_disk[d][q] (q < nw + nf) + sum_s partial_mc[s][q] + dirichlet[q - nw - nf]
+// (q >= nw + nf), in the layout [c weights][f weights][g coefficients], each sum in a fixed order
+__global__ void k_sum_partials(int nw, int nf, int ng, const double *pd, int nd, const double *pm, int nm,
                                const double *pg, double *grad) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nw + ng) return;
+    const int np = nw + nf + ng;
+    if (q >= np) return;
     double s = 0.0;
-    if (q < nw)
-        for (int d = 0; d < nd; ++d) s += pd[(long)d * nw + q];
-    for (int r = 0; r < nm; ++r) s += pm[(long)r * (nw + ng) + q];
-    if (q >= nw && pg) s += pg[q - nw];
+    if (q < nw + nf)
+        for (int d = 0; d < nd; ++d) s += pd[(long)d * (nw + nf) + q];
+    for (int r = 0; r < nm; ++r) s += pm[(long)r * np + q];
+    if (q >= nw + nf && pg) s += pg[q - nw - nf];
     grad[q] = s;
 }
 
@@ -50,6 +52,7 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
                const double *u, const double *dJdu, double *grad, double *lambda_out, cudaStream_t st) {
     const int N = cov.N;
     const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
+    const int nf = (P.f_kind == PDD_F_RBF) ? P.n_frbf : 0;
     const int ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
     DevBuf<double> lam_own;
     double *lambda = lambda_out;
@@ -66,7 +69,7 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
         SolveResult r = gmres_csr(N, rt.p, ct.p, vt.p, dJdu, lambda, so, st);
         if (!r.converged) fail(PDD_ENOCONV, "adjoint GMRES did not converge");
     }
-    const int n_all = P.n_rbf + P.n_gcoef;
+    const int n_all = nw + nf + ng;
     if (n_all == 0) return;
     PDD_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * n_all, st));
     DevBuf<double> pg;
@@ -76,19 +79,12 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
     }
     DevBuf<double> pd, pm;
     int nd = 0, nm = 0;
-    if (nw && o.floating_method == PDD_FLOATING_PSEUDOSPECTRAL) grad_disks(cov, P, u, lambda, pd, nd, st);
+    if ((nw || nf) && o.floating_method == PDD_FLOATING_PSEUDOSPECTRAL) grad_disks(cov, P, u, lambda, pd, nd, st);
     grad_mc(cov, P, o, sys, u, lambda, pm, nm, st);
-    // parameters of kinds the operator does not use stay 0
-    if (nw + ng) {
-        DevBuf<double> tmp;
-        tmp.alloc(nw + ng);
-        PDD_LAUNCH(k_sum_partials, cdiv(nw + ng, 128), 128, 0, st, nw, ng, pd.p, nd, pm.p, nm, ng ? pg.p : nullptr,
-                   tmp.p);
-        // layout of grad: [n_rbf weights][n_gcoef coefficients]
-        if (nw) PDD_CUDA(cudaMemcpyAsync(grad, tmp.p, sizeof(double) * nw, cudaMemcpyDeviceToDevice, st));
-        if (ng)
-            PDD_CUDA(cudaMemcpyAsync(grad + P.n_rbf, tmp.p + nw, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st));
-    }
+    // layout of grad: [c weights][f weights][g coefficients] (families the operator does not use
+    // have no entries)
+    PDD_LAUNCH(k_sum_partials, cdiv(n_all, 128), 128, 0, st, nw, nf, ng, pd.p, nd, pm.p, nm, ng ? pg.p : nullptr,
+               grad);
     PDD_CUDA(cudaStreamSynchronize(st));
 }
 

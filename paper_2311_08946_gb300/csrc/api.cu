@@ -57,6 +57,33 @@ void ProblemHolder::set(const pdd_domain &dom, const pdd_operator &op, cudaStrea
         P.rbf32 = rbf32.p;
         P.rbf_inv2s2 = (float)(1.0 / (2.0 * op.rbf_sigma * op.rbf_sigma));
     }
+    if (op.f_kind == PDD_F_RBF) {
+        if (op.n_frbf <= 0 || op.n_frbf > 256 || !op.frbf_x || !op.frbf_y || !op.frbf_w || !(op.frbf_sigma > 0))
+            fail(PDD_EINVAL, "f = RBF needs 1..256 Gaussians, centres, weights and sigma > 0");
+        const int nq = op.n_frbf;
+        frbf_x.alloc(nq);
+        frbf_y.alloc(nq);
+        frbf_w.alloc(nq);
+        PDD_CUDA(cudaMemcpyAsync(frbf_x.p, op.frbf_x, nq * 8, cudaMemcpyHostToDevice, st));
+        PDD_CUDA(cudaMemcpyAsync(frbf_y.p, op.frbf_y, nq * 8, cudaMemcpyHostToDevice, st));
+        PDD_CUDA(cudaMemcpyAsync(frbf_w.p, op.frbf_w, nq * 8, cudaMemcpyHostToDevice, st));
+        std::vector<float> f32(3 * (size_t)nq);
+        for (int q = 0; q < nq; ++q) {
+            f32[q] = (float)op.frbf_x[q];
+            f32[nq + q] = (float)op.frbf_y[q];
+            f32[2 * nq + q] = (float)op.frbf_w[q];
+        }
+        frbf32.alloc(f32.size());
+        PDD_CUDA(cudaMemcpyAsync(frbf32.p, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        PDD_CUDA(cudaStreamSynchronize(st));
+        P.n_frbf = nq;
+        P.frbf_x = frbf_x.p;
+        P.frbf_y = frbf_y.p;
+        P.frbf_w = frbf_w.p;
+        P.frbf_sigma = op.frbf_sigma;
+        P.frbf32 = frbf32.p;
+        P.frbf_inv2s2 = (float)(1.0 / (2.0 * op.frbf_sigma * op.frbf_sigma));
+    }
     if (op.g_kind == PDD_G_BOUNDARY_FOURIER) {
         if (op.n_gcoef <= 0 || !op.g_coef) fail(PDD_EINVAL, "g = boundary Fourier needs coefficients");
         g_coef.alloc(op.n_gcoef);
@@ -150,7 +177,7 @@ static void check_spec(const pdd_cover_spec *s) {
 
 static void check_op(const pdd_operator *op) {
     if (!op) fail(PDD_EINVAL, "null operator");
-    if (op->b_kind < 0 || op->b_kind > 1 || op->c_kind < 0 || op->c_kind > 2 || op->f_kind < 0 || op->f_kind > 3 ||
+    if (op->b_kind < 0 || op->b_kind > 1 || op->c_kind < 0 || op->c_kind > 2 || op->f_kind < 0 || op->f_kind > 4 ||
         op->g_kind < 0 || op->g_kind > 5)
         fail(PDD_EINVAL, "unknown coefficient family");
 }
@@ -171,6 +198,7 @@ static void check_opts(const pdd_assembly_opts *o) {
         o->path_precision < PDD_STAGE_DEFAULT || o->path_precision > PDD_STAGE_MIXED)
         fail(PDD_EINVAL, "unknown stage precision");
     if (o->moment_sums < PDD_SUMS_AUTO || o->moment_sums > PDD_SUMS_FP64) fail(PDD_EINVAL, "unknown moment summation");
+    if (o->cv_degree < 0 || o->cv_degree > 4) fail(PDD_EINVAL, "cv_degree must be in [0, 4]");
 }
 
 }  // namespace pdd
@@ -489,6 +517,7 @@ pdd_status pdd_grad(const pdd_cover *cov, const pdd_operator *op, const pdd_asse
     if (cov->averaged) fail(PDD_EINVAL, "the adjoint gradient needs one subdomain per row (a farthest-interface cover)");
     check_op(op);
     check_opts(opts);
+    if (opts->cv_degree) fail(PDD_EINVAL, "the adjoint gradient differentiates the plain estimator (cv_degree = 0)");
     cudaStream_t st = (cudaStream_t)stream;
     ProblemHolder ph;
     ph.set(cov->domain, *op, st);

@@ -86,6 +86,11 @@ struct Problem {
     double perimeter;
     const float *rbf32;                    // device: the RBF centres and weights as FP32, x[n] y[n] w[n]
     float rbf_inv2s2;                      // 1 / (2 sigma^2) in FP32
+    int n_frbf;                            // f = sum_q v_q exp(-|x - x_q|^2 / (2 s_f^2)) (PDD_F_RBF)
+    const double *frbf_x, *frbf_y, *frbf_w;   // device
+    double frbf_sigma;
+    const float *frbf32;                   // device: FP32 x[n] y[n] v[n]
+    float frbf_inv2s2;
 };
 
 #define PDD_PI 3.141592653589793
@@ -161,6 +166,15 @@ __device__ __forceinline__ void u46_derivs(T x, T y, T &u, T &ux, T &uy, T &lap)
 }
 
 __device__ __forceinline__ double source(const Problem &P, double x, double y) {
+    if (P.f_kind == PDD_F_RBF) {
+        const double inv = 1.0 / (2.0 * P.frbf_sigma * P.frbf_sigma);
+        double s = 0.0;
+        for (int q = 0; q < P.n_frbf; ++q) {
+            const double dx = x - P.frbf_x[q], dy = y - P.frbf_y[q];
+            s += P.frbf_w[q] * exp(-(dx * dx + dy * dy) * inv);
+        }
+        return s;
+    }
     if (P.f_kind == PDD_F_ONE) return 1.0;
     if (P.f_kind == PDD_F_MANUFACTURED) {
         double spx, cpx, spy, cpy;

@@ -30,39 +30,107 @@ static constexpr double kJunctionGap = 0.25;
 static constexpr double kScoreEps = 1e-12;
 
 // ---------------------------------------------------------------------------
-// scan (one CTA of 1024 threads, each over a contiguous segment)
+// Device-wide exclusive scan of int32 counts by warp scans (reduce, scan of the
+// tile sums, scan within the tiles): a tile is 1024 threads x 4 counts; a warp
+// scans its threads' sums with shuffles, the block its 32 warp sums the same
+// way.  out[n] = the total.  64-bit partial sums; no host synchronisation
+// unless the caller needs the total (exclusive_scan).
 // ---------------------------------------------------------------------------
-__global__ void k_scan(const int *in, int *out, int n, long long *total) {
-    __shared__ long long s[1024];
-    const int t = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int a = min(n, t * per), b = min(n, a + per);
-    long long sum = 0;
-    for (int i = a; i < b; ++i) sum += in[i];
-    s[t] = sum;
+static constexpr int kScanThreads = 1024, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive prefix of v over the block (and the block total)
+__device__ __forceinline__ long long block_excl_scan(long long v, long long *total) {
+    __shared__ long long ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long inc = warp_incl_scan(v);
+    if (lane == 31) ws[warp] = inc;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        long long v = (t >= off) ? s[t - off] : 0;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const long long w = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+        ws[lane] = warp_incl_scan(w);
     }
-    long long base = s[t] - sum;
-    for (int i = a; i < b; ++i) {
-        int v = in[i];
-        out[i] = (int)base;
-        base += v;
+    __syncthreads();
+    const long long before = (warp > 0 ? ws[warp - 1] : 0) + inc - v;
+    if (total) *total = ws[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *in, int n, long long *tile_sum) {
+    const long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    long long tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// one block: exclusive offsets of the tile sums (in place), chunk by chunk
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(long long *tile_sum, int ntiles, int *out_last,
+                                                            long long *total) {
+    long long carry = 0;
+    for (int c0 = 0; c0 < ntiles; c0 += kScanThreads) {
+        const int i = c0 + threadIdx.x;
+        const long long v = i < ntiles ? tile_sum[i] : 0;
+        long long tot;
+        const long long ex = block_excl_scan(v, &tot);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        carry += tot;
     }
-    if (t == 1023) {
-        out[n] = (int)s[1023];
-        *total = s[1023];
+    if (threadIdx.x == 0) {
+        *out_last = (int)carry;
+        if (total) *total = carry;
     }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *in, int *out, int n,
+                                                            const long long *tile_off) {
+    const long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    long long run = tile_off[blockIdx.x] + block_excl_scan(s, nullptr);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) {
+            out[base + k] = (int)run;
+            run += v[k];
+        }
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total; queued on st (no synchronisation);
+// the total also goes to *total_dev when given
+void exclusive_scan_async(const int *in, int *out, int n, cudaStream_t st, long long *total_dev) {
+    const int ntiles = std::max(1, cdiv(n, kScanTile));
+    long long *ts = nullptr;                     // stream-ordered: freed after the launches that read it
+    PDD_CUDA(cudaMallocAsync((void **)&ts, sizeof(long long) * ntiles, st));
+    if (n > 0) PDD_LAUNCH(k_scan_reduce, ntiles, kScanThreads, 0, st, in, n, ts);
+    else PDD_CUDA(cudaMemsetAsync(ts, 0, sizeof(long long), st));
+    PDD_LAUNCH(k_scan_tiles, 1, kScanThreads, 0, st, ts, ntiles, out + n, total_dev);
+    if (n > 0) PDD_LAUNCH(k_scan_apply, ntiles, kScanThreads, 0, st, in, out, n, ts);
+    PDD_CUDA(cudaFreeAsync(ts, st));
 }
 
 int64_t exclusive_scan(const int *in, int *out, int n, cudaStream_t st) {
     DevBuf<long long> tot;
     tot.alloc(1);
-    PDD_LAUNCH(k_scan, 1, 1024, 0, st, in, out, n, tot.p);
+    exclusive_scan_async(in, out, n, st, tot.p);
     long long h = 0;
     PDD_CUDA(cudaMemcpyAsync(&h, tot.p, sizeof(long long), cudaMemcpyDeviceToHost, st));
     PDD_CUDA(cudaStreamSynchronize(st));
@@ -360,7 +428,7 @@ static void build_grid(Grid G, int n, const double *x, const double *y, DevBuf<i
     PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (ncell + 1), st));
     PDD_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (ncell + 1), st));
     if (n) PDD_LAUNCH(k_cell_count, cdiv(n, 256), 256, 0, st, G, n, x, y, cnt.p, cell.p);
-    exclusive_scan(cnt.p, ptr.p, ncell, st);
+    exclusive_scan_async(cnt.p, ptr.p, ncell, st, nullptr);
     if (n) PDD_LAUNCH(k_cell_fill, cdiv(n, 256), 256, 0, st, n, cell.p, ptr.p, cursor.p, items.p);
 }
 

@@ -1772,13 +1772,17 @@ __global__ void __launch_bounds__(256) k_lu_solve_T(const double *LUall, int n, 
     }
 }
 
+// per disk: the c-weight partials -sum_p z_p V_p 1{c<0} psi_q(x_p) and the f-weight partials
+// -sum_p z_p psi^f_q(x_p), in the layout [disk][c weights, f weights]
 __global__ void __launch_bounds__(256) k_adjoint_contract(Problem P, Shape S, const DiskDesc *disks,
                                                           const double *Vall, const double *Zall,
                                                           double *partial) {
-    extern __shared__ double csm[];             // per node: x, y, z V 1{c<0}
+    extern __shared__ double csm[];             // per node: x, y, z V 1{c<0}, z
     const int disk = blockIdx.x, tid = threadIdx.x;
     const DiskDesc dd = disks[disk];
-    double *nx = csm, *ny = csm + S.n, *tv = csm + 2 * S.n;
+    const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
+    const int nf = (P.f_kind == PDD_F_RBF) ? P.n_frbf : 0;
+    double *nx = csm, *ny = csm + S.n, *tv = csm + 2 * S.n, *zz = csm + 3 * S.n;
     for (int p = tid; p < S.n; p += 256) {
         const int k = p / S.nt + 1, j = p % S.nt;
         double st, ct;
@@ -1788,23 +1792,35 @@ __global__ void __launch_bounds__(256) k_adjoint_contract(Problem P, Shape S, co
         ny[p] = Y;
         const double act = (P.c_kind == PDD_C_RBF && rbf_sum(P, X, Y) < 0.0) ? 1.0 : 0.0;
         tv[p] = Zall[(long)disk * S.n + p] * Vall[(long)disk * S.n + p] * act;
+        zz[p] = Zall[(long)disk * S.n + p];
     }
     __syncthreads();
-    const double inv = 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma);
-    for (int q = tid; q < P.n_rbf; q += 256) {
+    const double inv = nw ? 1.0 / (2.0 * P.rbf_sigma * P.rbf_sigma) : 0.0;
+    const double invf = nf ? 1.0 / (2.0 * P.frbf_sigma * P.frbf_sigma) : 0.0;
+    for (int q = tid; q < nw + nf; q += 256) {
         double s = 0.0;
-        for (int p = 0; p < S.n; ++p) {
-            const double dx = nx[p] - P.rbf_x[q], dy = ny[p] - P.rbf_y[q];
-            s += tv[p] * exp(-(dx * dx + dy * dy) * inv);
+        if (q < nw) {
+            for (int p = 0; p < S.n; ++p) {
+                const double dx = nx[p] - P.rbf_x[q], dy = ny[p] - P.rbf_y[q];
+                s += tv[p] * exp(-(dx * dx + dy * dy) * inv);
+            }
+        } else {
+            const int qf = q - nw;
+            for (int p = 0; p < S.n; ++p) {
+                const double dx = nx[p] - P.frbf_x[qf], dy = ny[p] - P.frbf_y[qf];
+                s += zz[p] * exp(-(dx * dx + dy * dy) * invf);
+            }
         }
-        partial[(long)disk * P.n_rbf + q] = -s;
+        partial[(long)disk * (nw + nf) + q] = -s;
     }
 }
 
 void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const double *lambda,
                 DevBuf<double> &partial, int &n_part, cudaStream_t st) {
     n_part = 0;
-    if (P.c_kind != PDD_C_RBF || P.n_rbf == 0) return;
+    const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
+    const int nf = (P.f_kind == PDD_F_RBF) ? P.n_frbf : 0;
+    if (nw + nf == 0) return;
     std::map<std::tuple<int, int, int>, std::vector<DiskDesc>> groups;
     std::vector<double> hcx(cov.M), hcy(cov.M), hr(cov.M);
     PDD_CUDA(cudaMemcpyAsync(hcx.data(), cov.cx.p, cov.M * 8, cudaMemcpyDeviceToHost, st));
@@ -1821,7 +1837,7 @@ void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const d
         ++total;
     }
     if (!total) return;
-    partial.alloc((size_t)total * P.n_rbf);
+    partial.alloc((size_t)total * (nw + nf));
     int done = 0;
     for (auto &kv : groups) {
         ShapeTables tab;
@@ -1861,10 +1877,10 @@ void grad_disks(const pdd_cover &cov, const Problem &P, const double *u, const d
             PDD_LAUNCH(k_adjoint_vecs, nd, 256, 0, st, S, dd.p, cov.sub_rows.p, cov.kx.p, cov.ky.p, X.p, sR, u,
                        lambda, Vb.p, Eb.p);
             PDD_LAUNCH(k_lu_solve_T, nd, 256, 0, st, A.p, S.n, sA, perm.p, coef.p, sC, Eb.p, Wt.p, Zb.p);
-            const size_t csm = (size_t)3 * S.n * sizeof(double);
+            const size_t csm = (size_t)4 * S.n * sizeof(double);
             PDD_CUDA(cudaFuncSetAttribute(k_adjoint_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
             PDD_LAUNCH(k_adjoint_contract, nd, 256, csm, st, P, S, dd.p, Vb.p, Zb.p,
-                       partial.p + (size_t)(done + w0) * P.n_rbf);
+                       partial.p + (size_t)(done + w0) * (nw + nf));
         }
         PDD_CUDA(cudaStreamSynchronize(st));
         done += (int)disks.size();

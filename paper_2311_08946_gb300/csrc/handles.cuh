@@ -69,8 +69,8 @@ inline bool path_mixed(const pdd_assembly_opts &o) {
 // device problem description (uploads the operator's host arrays)
 struct ProblemHolder {
     Problem P{};
-    DevBuf<double> rbf_x, rbf_y, rbf_w, g_coef;
-    DevBuf<float> rbf32;
+    DevBuf<double> rbf_x, rbf_y, rbf_w, g_coef, frbf_x, frbf_y, frbf_w;
+    DevBuf<float> rbf32, frbf32;
     void set(const pdd_domain &dom, const pdd_operator &op, cudaStream_t st);
 };
 
@@ -161,7 +161,10 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
 void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st, int W,
                       int tensor_min, float *ms_gemm = nullptr, double *gemm_flop = nullptr);
 
-// device-wide exclusive scan of int32 counts (in place into out, returns the total)
+// device-wide exclusive scan of int32 counts by warp scans (out[n] = the total): the _async form
+// queues the work on st and returns at once (the total optionally to *total_dev); exclusive_scan
+// also returns the total to the host (one synchronisation)
+void exclusive_scan_async(const int *in, int *out, int n, cudaStream_t st, long long *total_dev);
 int64_t exclusive_scan(const int *in, int *out, int n, cudaStream_t st);
 
 }  // namespace pdd

@@ -596,7 +596,7 @@ void csr_transpose(int n, int64_t nnz, const int *rowptr, const int *col, const 
     PDD_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (n + 1), st));
     PDD_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (n + 1), st));
     PDD_LAUNCH(k_col_count, 1024, 256, 0, st, nnz, col, cnt.p);
-    exclusive_scan(cnt.p, rowptr_t.p, n, st);
+    exclusive_scan_async(cnt.p, rowptr_t.p, n, st, nullptr);
     PDD_LAUNCH(k_t_fill, cdiv(n, 256), 256, 0, st, n, rowptr, col, val, rowptr_t.p, cursor.p, col_t.p, val_t.p);
     PDD_LAUNCH(k_t_sort, cdiv(n, 256), 256, 0, st, n, rowptr_t.p, col_t.p, val_t.p);
 }

@@ -1,12 +1,9 @@
 // a10-a12: Monte Carlo rows (Eq. 25-30 with the representation of Eq. 53,
 // 56 and sigma = I), IMQ cardinals on perimeter arcs (Eq. 19-22).
 //
-//   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c_m^2)^-1/2 per perimeter stencil,
-//       Cholesky factor and K^-1 in FP64 (one CTA per circle), and kappa_1(K).
-//       Eq. 19 measures theta along the interface (arclength r_m u, c in the
-//       length units of Omega); the cardinal functions of Eq. 22 are unchanged
-//       when the basis is scaled, so the kernels work in the local angle u with
-//       c_m^2 = c^2 / r_m^2.
+//   a10 k_imq_inverse: K_lk = ((u_l - u_k)^2 + c^2)^-1/2 per perimeter stencil
+//       (u the knots' local angles in radians), Cholesky factor and K^-1 in FP64
+//       (one CTA per circle), and kappa_1(K).
 //   a11 k_paths: Euler-Maruyama paths of dX = b dt + dW, dY = c Y dt,
 //       dZ = f Y dt from the knot, stopped at the first step whose end point
 //       leaves the open disk or the open domain (optionally both shrunk by the
@@ -60,20 +57,19 @@ __device__ double norm1_block(const double *A, int n, double *red) {
 }
 
 __global__ void __launch_bounds__(128) k_imq_inverse(const int *circles, const int *knot_ptr,
-                                                     const double *ku, const double *cr, const long *kinv_off,
+                                                     const double *ku, const long *kinv_off,
                                                      double c2, double *kinv, double *kcond, int *bad) {
     extern __shared__ double sm[];                    // K (n x n), then L in place
     __shared__ double red[128];
     const int m = circles[blockIdx.x];
     const int a = knot_ptr[m], n = knot_ptr[m + 1] - a;
-    const double c2m = c2 / (cr[m] * cr[m]);          // c^2 of Eq. 19 in the local angle
     double *K = sm;
     double *Z = sm + n * n;                           // n x n work for the inverse
     const int tid = threadIdx.x;
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
         int l = idx / n, k = idx % n;
         double d = ku[a + l] - ku[a + k];
-        K[idx] = 1.0 / sqrt(d * d + c2m);
+        K[idx] = 1.0 / sqrt(d * d + c2);
     }
     __syncthreads();
     const double nK = norm1_block(K, n, red);
@@ -135,6 +131,8 @@ struct PathArgs {
     double shift;                    // Gobet-Menozzi boundary shift c0 sqrt(h), or 0 (plain exit)
     const int *gslot;                // global slot of each launched slot, or null (slot)
     int max_steps;                   // step cap per path (0: 50 r^2 / h)
+    int cvd, ncv;                    // control-variate monomial degree (0: none) and feature count
+    double *cvq;                     // per-path features [rec][ncv]
 };
 
 // c0 = -zeta(1/2) / sqrt(2 pi): the Gobet-Menozzi shift in units of |sigma^T n| sqrt(h) (sigma = I)
@@ -211,6 +209,16 @@ __device__ __forceinline__ float killing32(const Problem &P, float x, float y) {
 
 // f of the manufactured solution from already evaluated b and c (FP32)
 __device__ __forceinline__ float source32_given(const Problem &P, float x, float y, float bx, float by, float cv) {
+    if (P.f_kind == PDD_F_RBF) {
+        const int nq = P.n_frbf;
+        const float *fx = P.frbf32, *fy = P.frbf32 + nq, *fw = P.frbf32 + 2 * nq;
+        float s = 0.f;
+        for (int q = 0; q < nq; ++q) {
+            const float dx = x - fx[q], dy = y - fy[q];
+            s += fw[q] * __expf(-(dx * dx + dy * dy) * P.frbf_inv2s2);
+        }
+        return s;
+    }
     if (P.f_kind == PDD_F_ONE) return 1.0f;
     if (P.f_kind == PDD_F_MANUFACTURED) {
         float spx, cpx, spy, cpy;
@@ -234,7 +242,39 @@ __device__ __forceinline__ float source32(const Problem &P, float x, float y) {
     return source32_given(P, x, y, bx, by, killing32(P, x, y));
 }
 
-template <typename R, bool KILL, bool SRC>
+// Control-variate features (CV): for the monomials psi = xr^a yr^b (1 <= a + b <= D <= 4) of
+// xr = (x - cx) / r, yr = (y - cy) / r, the sums Q = sum_k Y_k sqrt(h) grad psi(X_k) . xi_k, which have
+// mean zero whatever psi (xi_k is independent of X_k and Y_k): the regression control variate of
+// Milstein and Tretyakov (features in the order d = a + b = 1..D, a = d..0).
+static constexpr int kMaxCv = 14;
+
+template <typename R>
+__device__ __forceinline__ void cv_accumulate(R (&cq)[kMaxCv], int D, R xr, R yr, R s, R xi0, R xi1) {
+    R px[5], py[5];
+    px[0] = (R)1;
+    py[0] = (R)1;
+#pragma unroll
+    for (int e = 1; e <= 4; ++e) {
+        px[e] = px[e - 1] * xr;
+        py[e] = py[e - 1] * yr;
+    }
+    int q = 0;
+#pragma unroll
+    for (int d = 1; d <= 4; ++d) {
+        if (d > D) break;
+#pragma unroll
+        for (int a = d; a >= 0; --a) {
+            const int b = d - a;
+            R g = (R)0;
+            if (a > 0) g += (R)a * px[a - 1] * py[b] * xi0;
+            if (b > 0) g += (R)b * px[a] * py[b - 1] * xi1;
+            cq[q] += s * g;
+            ++q;
+        }
+    }
+}
+
+template <typename R, bool KILL, bool SRC, bool CV>
 __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     __shared__ int next_path;
     const int slot = blockIdx.x;
@@ -285,6 +325,10 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
     // the same iteration, so the lanes of a warp stay converged whatever the path lengths.
     int p = threadIdx.x;
     R x = x_start, y = y_start;
+    R cq[kMaxCv];
+#pragma unroll
+    for (int q = 0; q < kMaxCv; ++q) cq[q] = (R)0;
+    const R crad = (R)rad;
     double Yv = 1.0, Zv = 0.0;
     float e = 0.f, z = 0.f;    // mixed form: Y = Yv (1 + e), Z = Zv + Yv z (FP32 block increments)
     int k = 0;
@@ -298,11 +342,18 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
             A.Y[rec] = 0.0;
             A.Z[rec] = 0.0;
             if constexpr (sizeof(R) == 4) A.ez[rec] = make_float2(0.f, 0.f);
+            if constexpr (CV)
+                for (int q = 0; q < A.ncv; ++q) A.cvq[rec * A.ncv + q] = 0.0;
             ++my_capped;
             done = true;
         } else {
             R xi0, xi1;
             Num<R>::normals(A.seed, (uint32_t)i, kw, (uint32_t)k, (uint32_t)p, xi0, xi1);
+            if constexpr (CV) {
+                // Y_k sqrt(h) grad psi(X_k) . xi_k / r, with Y_k the weight before this step
+                const R yk = sizeof(R) == 8 ? (R)Yv : (R)((float)Yv * (1.0f + e));
+                cv_accumulate<R>(cq, A.cvd, (x - rcx) / crad, (y - rcy) / crad, yk * sh / crad, xi0, xi1);
+            }
             R bx, by;
             Num<R>::drift(P, x, y, bx, by);
             double Yn = Yv, Zn = Zv;
@@ -400,6 +451,11 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
                 A.Y[rec] = Yn;
                 A.Z[rec] = Zn;
                 if constexpr (sizeof(R) == 4) A.ez[rec] = make_float2(en, zn);
+                if constexpr (CV) {
+#pragma unroll
+                    for (int q = 0; q < kMaxCv; ++q)
+                        if (q < A.ncv) A.cvq[rec * A.ncv + q] = (double)cq[q];
+                }
                 done = true;
             }
         }
@@ -413,6 +469,10 @@ __global__ void __launch_bounds__(256) k_paths(Problem P, PathArgs A) {
             e = 0.f;
             z = 0.f;
             k = 0;
+            if constexpr (CV) {
+#pragma unroll
+                for (int q = 0; q < kMaxCv; ++q) cq[q] = (R)0;
+            }
         }
     }
     // block totals
@@ -500,8 +560,11 @@ struct FinalArgs {
     const float2 *ez;                // mixed form: unfolded increments, Y (1 + e) and Z + Y z
     const int *mom_ptr;
     double *moments, *bmean, *val, *se, *bs, *se_bs;
-    const double *cr;                // circle radii (c^2 of Eq. 19 is in squared length)
     int sums;                        // PDD_SUMS_* of the mixed form (AUTO: by kappa_1(K))
+    // regression control variate (null: none): per launched slot, beta [ns_max + 1][ncv] (the basis
+    // moments' rows, then r's) and the per-batch feature sums [32][ncv]
+    const double *cv_beta, *cv_sq;
+    int ncv, cv_stride;              // features, beta rows per slot (the launch's largest stencil + 1)
 };
 
 // v = hi + lo with hi = v truncated to 24 significant bits and lo the rest rounded to FP32, built
@@ -570,8 +633,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         ukf[q] = (float)uk[q];
         ukl[q] = (float)(uk[q] - (double)ukf[q]);
     }
-    const double c2m = F.c2 / (F.cr[m] * F.cr[m]);     // c^2 of Eq. 19 in the local angle
-    const float c2f = (float)c2m, c2l = (float)(c2m - (double)c2f);
+    const float c2f = (float)F.c2, c2l = (float)(F.c2 - (double)c2f);
     const int mode = (F.mixed && imq) ? (F.sums != PDD_SUMS_AUTO ? F.sums - 1
                                                                  : (F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2)))
                                       : 2;
@@ -700,7 +762,7 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
                         double phi;
                         if (imq) {
                             const double d = s_su - uk[q];
-                            phi = F.mixed ? rsqrt(d * d + c2m) : 1.0 / sqrt(d * d + c2m);
+                            phi = F.mixed ? rsqrt(d * d + F.c2) : 1.0 / sqrt(d * d + F.c2);
                         } else {
                             phi = fourier_cardinal_at(s_su - uk[q], ns);
                         }
@@ -724,6 +786,20 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         }
     }
     __syncthreads();
+    // regression control variate: every batch sum of a payoff loses beta^T (the batch's feature sums)
+    if (F.cv_beta) {
+        const double *beta = F.cv_beta + (long)slot * F.cv_stride * F.ncv;
+        const double *sq = F.cv_sq + (long)slot * kBatches * F.ncv;
+        for (int e = threadIdx.x; e < kBatches * (ns + 1); e += blockDim.x) {
+            const int bt = e / (ns + 1), l = e - bt * (ns + 1);
+            const double *bl = beta + (long)(l < ns ? l : F.cv_stride - 1) * F.ncv;
+            double c = 0.0;
+            for (int q = 0; q < F.ncv; ++q) c += bl[q] * sq[bt * F.ncv + q];
+            if (l < ns) Mb[bt * ns + l] -= c;
+            else bsum[bt] -= c;
+        }
+        __syncthreads();
+    }
     // per-batch C estimates (batch means)
     const double *Ki = imq ? F.kinv + F.kinv_off[m] : nullptr;
     for (int bt = warp; bt < kBatches; bt += 16)
@@ -835,13 +911,210 @@ void build_imq_inverses(const pdd_cover &cov, double c2, DevBuf<double> &kinv, D
         PDD_CUDA(cudaMemcpyAsync(koff_c.p, offc.data(), per.size() * sizeof(long), cudaMemcpyHostToDevice, st));
         const size_t smem = (size_t)2 * cov.max_stencil * cov.max_stencil * sizeof(double);
         PDD_CUDA(cudaFuncSetAttribute(k_imq_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, cov.r.p, koff_c.p, c2,
+        PDD_LAUNCH(k_imq_inverse, (int)per.size(), 128, smem, st, circ.p, cov.knot_ptr.p, cov.ku.p, koff_c.p, c2,
                    kinv.p, kcond.p, bad.p);
     }
     int hb = 0;
     PDD_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PDD_CUDA(cudaStreamSynchronize(st));
     if (hb) fail(PDD_EINVAL, "IMQ matrix not positive definite (coincident stencil angles)");
+}
+
+// ---------------------------------------------------------------------------
+// Regression control variate (Milstein and Tretyakov): per slot, beta = Cov(Q)^-1 Cov(Q, P) for the
+// payoffs P = (1_Gamma Y phi_l(u), l < ns; the boundary payoff of r), covariances normalised by the
+// path count, and the per-batch sums of the features Q.  Any beta leaves the estimators unbiased
+// (E[Q] = 0); this one is the sample's least-squares choice.  FP64 throughout (the basis values
+// too, in both forms: beta only needs to be near the optimum).  One CTA per slot; paths go
+// through shared memory 256 at a time.
+// ---------------------------------------------------------------------------
+static constexpr int kCvThreads = 256;
+
+__global__ void __launch_bounds__(kCvThreads) k_cv_regress(Problem P, FinalArgs F, const double *cvq,
+                                                           double *beta_out, double *sq_out) {
+    const int M = F.ncv;
+    extern __shared__ double cvs[];
+    double *Qs = cvs;                                 // [256][M] this chunk's features
+    double *Ys = Qs + kCvThreads * M;                 // [256] Y at the exit (0: not an interface exit)
+    double *Us = Ys + kCvThreads;                     // [256] exit angle
+    double *QQ = Us + kCvThreads;                     // [M][M]
+    double *QP = QQ + M * M;                          // [ns + 1][M]
+    double *Pm = QP + (F.cv_stride) * M;              // [ns + 1] payoff sums
+    double *Qm = Pm + F.cv_stride;                    // [M] feature sums
+    double *SQ = Qm + M;                              // [32][M] per-batch feature sums
+    double *L = SQ + kBatches * M;                    // [M][M] Cholesky factor
+    __shared__ int s_cnt;
+    const int slot = blockIdx.x, tid = threadIdx.x;
+    const int gs = F.gslot ? F.gslot[slot] : slot;
+    const int m = F.subs[gs];
+    const int a = F.knot_ptr[m], ns = F.knot_ptr[m + 1] - a;
+    const bool imq = !F.floating[m];
+    const int npath = F.npaths ? F.npaths[slot] : F.paths;
+    const long base = F.rec_off ? F.rec_off[slot] : (long)slot * F.paths;
+    for (int e = tid; e < M * M + F.cv_stride * M + F.cv_stride + M + kBatches * M; e += kCvThreads) QQ[e] = 0.0;
+    __syncthreads();
+    // per-thread sums: the thread's paths are p = tid (mod 256), all in batch tid mod 32
+    double my_sq[kMaxCv], my_bq[kMaxCv], my_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < kMaxCv; ++q) {
+        my_sq[q] = 0.0;
+        my_bq[q] = 0.0;
+    }
+    int my_cnt = 0;
+    // QQ entry (i, j) per thread (M (M + 1) / 2 <= 105 < 256); QP rows per thread l = tid (mod ns + 1)
+    int qi = -1, qj = -1;
+    {
+        int e = tid;
+        for (int i = 0; i < M && qi < 0; ++i) {
+            if (e < M - i) {
+                qi = i;
+                qj = i + e;
+            } else {
+                e -= M - i;
+            }
+        }
+    }
+    double acc_qq = 0.0;
+    for (int c0 = 0; c0 < npath; c0 += kCvThreads) {
+        const int p = c0 + tid;
+        double yv = 0.0, ut = 0.0;
+        if (p < npath) {
+            const long rec = base + p;
+            const int sd = F.side[rec];
+            double y = F.Y[rec], z = F.Z[rec];
+            if (F.mixed) {
+                const float2 q = F.ez[rec];
+                z = fma(y, (double)q.y, z);
+                y = fma(y, (double)q.x, y);
+            }
+            for (int q = 0; q < M; ++q) Qs[tid * M + q] = (sd != 2) ? cvq[rec * M + q] : 0.0;
+            if (sd != 2) {
+                ++my_cnt;
+                const double bp = (sd == 1) ? boundary_score(P, F.su[rec], F.mixed) * y + z : z;
+                my_b += bp;
+                for (int q = 0; q < M; ++q) {
+                    const double qv = cvq[rec * M + q];
+                    my_sq[q] += qv;
+                    my_bq[q] += bp * qv;
+                }
+                if (sd == 0) {
+                    yv = y;
+                    ut = F.su[rec];
+                }
+            }
+        } else {
+            for (int q = 0; q < M; ++q) Qs[tid * M + q] = 0.0;
+        }
+        Ys[tid] = yv;
+        Us[tid] = ut;
+        __syncthreads();
+        if (qi >= 0)
+            for (int t = 0; t < kCvThreads; ++t) acc_qq += Qs[t * M + qi] * Qs[t * M + qj];
+        // basis payoffs: thread l < ns accumulates sum_p Y phi_l(u_p) Q_p and sum_p Y phi_l(u_p)
+        for (int l = tid; l < ns; l += kCvThreads) {
+            const double ul = imq ? F.ku[a + l] : PDD_TWO_PI * l / ns;
+            double acc[kMaxCv], ps = 0.0;
+#pragma unroll
+            for (int q = 0; q < kMaxCv; ++q) acc[q] = 0.0;
+            for (int t = 0; t < kCvThreads; ++t) {
+                if (Ys[t] == 0.0) continue;
+                const double d = Us[t] - ul;
+                const double phi = imq ? 1.0 / sqrt(d * d + F.c2) : fourier_cardinal_at(d, ns);
+                const double w = Ys[t] * phi;
+                ps += w;
+#pragma unroll
+                for (int q = 0; q < kMaxCv; ++q)
+                    if (q < M) acc[q] += w * Qs[t * M + q];
+            }
+            Pm[l] += ps;
+            for (int q = 0; q < M; ++q) QP[l * M + q] += acc[q];
+        }
+        __syncthreads();
+    }
+    if (qi >= 0) {
+        QQ[qi * M + qj] = acc_qq;
+        QQ[qj * M + qi] = acc_qq;
+    }
+    // the features' sums per batch (lane = batch; the 8 warps added in order), then over batches;
+    // the boundary payoff's sums by warp shuffles and the 8 warps in order (deterministic)
+    __shared__ double wb[8][kMaxCv + 1];
+    __shared__ int wc[8];
+    for (int q = 0; q < M; ++q) Qs[tid * M + q] = my_sq[q];
+#pragma unroll
+    for (int q = 0; q <= kMaxCv; ++q) {
+        double v = q < kMaxCv ? my_bq[q] : my_b;
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) wb[tid >> 5][q] = v;
+    }
+    for (int o = 16; o; o >>= 1) my_cnt += __shfl_xor_sync(0xffffffffu, my_cnt, o);
+    if ((tid & 31) == 0) wc[tid >> 5] = my_cnt;
+    __syncthreads();
+    for (int e = tid; e < kBatches * M; e += kCvThreads) {
+        const int bt = e / M, q = e - bt * M;
+        double v = 0.0;
+        for (int w = 0; w < kCvThreads / 32; ++w) v += Qs[(w * 32 + bt) * M + q];
+        SQ[e] = v;
+    }
+    if (tid <= M) {
+        double v = 0.0;
+        for (int w = 0; w < kCvThreads / 32; ++w) v += wb[w][tid < M ? tid : kMaxCv];
+        if (tid < M) QP[(F.cv_stride - 1) * M + tid] = v;
+        else Pm[F.cv_stride - 1] = v;
+    }
+    if (tid == 0) {
+        int c = 0;
+        for (int w = 0; w < kCvThreads / 32; ++w) c += wc[w];
+        s_cnt = c;
+    }
+    __syncthreads();
+    if (tid < M) {
+        double v = 0.0;
+        for (int bt = 0; bt < kBatches; ++bt) v += SQ[bt * M + tid];
+        Qm[tid] = v;
+    }
+    __syncthreads();
+    // Cov(Q) = QQ / n - qm qm^T, Cholesky in place (thread 0; M <= 14)
+    const double inv_n = s_cnt ? 1.0 / s_cnt : 0.0;
+    if (tid == 0) {
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) L[i * M + j] = QQ[i * M + j] * inv_n - Qm[i] * inv_n * Qm[j] * inv_n;
+        for (int j = 0; j < M; ++j) {
+            double dg = L[j * M + j];
+            for (int k = 0; k < j; ++k) dg -= L[j * M + k] * L[j * M + k];
+            dg = dg > 0.0 ? sqrt(dg) : 0.0;
+            L[j * M + j] = dg;
+            for (int i = j + 1; i < M; ++i) {
+                double v = L[i * M + j];
+                for (int k = 0; k < j; ++k) v -= L[i * M + k] * L[j * M + k];
+                L[i * M + j] = dg > 0.0 ? v / dg : 0.0;
+            }
+        }
+    }
+    __syncthreads();
+    // beta for each payoff row: rows l < ns (basis moments) and row cv_stride - 1 (r); zero when the
+    // covariance is singular (no paths, or a feature that never moved)
+    double *bo = beta_out + (long)slot * F.cv_stride * M;
+    for (int l = tid; l < F.cv_stride; l += kCvThreads) {
+        if (l >= ns && l != F.cv_stride - 1) {
+            for (int q = 0; q < M; ++q) bo[l * M + q] = 0.0;
+            continue;
+        }
+        double y[kMaxCv];
+        bool ok = s_cnt > 1;
+        for (int i = 0; i < M; ++i) {
+            double v = QP[l * M + i] * inv_n - Qm[i] * inv_n * Pm[l] * inv_n;
+            for (int k = 0; k < i; ++k) v -= L[i * M + k] * y[k];
+            ok = ok && L[i * M + i] > 0.0;
+            y[i] = ok ? v / L[i * M + i] : 0.0;
+        }
+        for (int i = M - 1; i >= 0; --i) {
+            double v = y[i];
+            for (int k = i + 1; k < M; ++k) v -= L[k * M + i] * y[k];
+            y[i] = ok ? v / L[i * M + i] : 0.0;
+        }
+        for (int q = 0; q < M; ++q) bo[l * M + q] = y[q];
+    }
+    for (int e = tid; e < kBatches * M; e += kCvThreads) sq_out[(long)slot * kBatches * M + e] = SQ[e];
 }
 
 // adaptive path count of each row from its pilot standard errors
@@ -867,13 +1140,19 @@ __global__ void k_need(int nmc, const int *rows, const int *subs, const int *spo
     need[slot] = w > Pmax ? Pmax : w;
 }
 
+template <typename R, bool CV>
+static void launch_paths_cv(const Problem &P, const PathArgs &A, int nrows, cudaStream_t st) {
+    const bool kill = P.c_kind != PDD_C_ZERO, src = P.f_kind != PDD_F_ZERO;
+    if (kill && src) PDD_LAUNCH((k_paths<R, true, true, CV>), nrows, 256, 0, st, P, A);
+    else if (kill) PDD_LAUNCH((k_paths<R, true, false, CV>), nrows, 256, 0, st, P, A);
+    else if (src) PDD_LAUNCH((k_paths<R, false, true, CV>), nrows, 256, 0, st, P, A);
+    else PDD_LAUNCH((k_paths<R, false, false, CV>), nrows, 256, 0, st, P, A);
+}
+
 template <typename R>
 static void launch_paths(const Problem &P, const PathArgs &A, int nrows, cudaStream_t st) {
-    const bool kill = P.c_kind != PDD_C_ZERO, src = P.f_kind != PDD_F_ZERO;
-    if (kill && src) PDD_LAUNCH((k_paths<R, true, true>), nrows, 256, 0, st, P, A);
-    else if (kill) PDD_LAUNCH((k_paths<R, true, false>), nrows, 256, 0, st, P, A);
-    else if (src) PDD_LAUNCH((k_paths<R, false, true>), nrows, 256, 0, st, P, A);
-    else PDD_LAUNCH((k_paths<R, false, false>), nrows, 256, 0, st, P, A);
+    if (A.cvd > 0) launch_paths_cv<R, true>(P, A, nrows, st);
+    else launch_paths_cv<R, false>(P, A, nrows, st);
 }
 
 McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o, pdd_system &sys,
@@ -910,7 +1189,9 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     // a11: paths into the record scratch, in waves that bound the scratch size
     const long P_ = o.paths;
     const int mixed = path_mixed(o) ? 1 : 0;
-    const size_t rec_bytes = 1 + 3 * sizeof(double) + (mixed ? sizeof(float2) : 0);
+    const int cvd = o.cv_degree, ncv = cvd * (cvd + 3) / 2;          // control-variate features per path
+    const int cv_stride = cov.max_stencil + 1;
+    const size_t rec_bytes = 1 + 3 * sizeof(double) + (mixed ? sizeof(float2) : 0) + (size_t)ncv * sizeof(double);
     const size_t per_row = (size_t)P_ * rec_bytes;
     const int wave = (int)std::max<size_t>(1, std::min<size_t>(nmc, ((size_t)8 << 30) / per_row));
     DevBuf<int8_t> side;
@@ -921,6 +1202,11 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
     Z.alloc((size_t)wave * P_);
     DevBuf<float2> ez;
     if (mixed) ez.alloc((size_t)wave * P_);
+    DevBuf<double> cvq, cvbeta, cvsq;
+    if (ncv) cvq.alloc((size_t)wave * P_ * ncv);
+    const size_t cv_smem = ((size_t)kCvThreads * ncv + 2 * kCvThreads + 2 * ncv * ncv + (size_t)cv_stride * ncv +
+                            cv_stride + ncv + (size_t)kBatches * ncv) * sizeof(double);
+    if (ncv) PDD_CUDA(cudaFuncSetAttribute(k_cv_regress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cv_smem));
     DevBuf<unsigned long long> steps;
     DevBuf<int> capped;
     steps.alloc(1);
@@ -944,7 +1230,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
         const int *subs = sys.mc_subs.p + w0, *spos = sys.mc_spos.p + w0, *kword = sys.mc_kword.p + w0;
         PathArgs A{rows, subs, kword, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
                    cov.theta_s.p, o.paths, o.h, o.seed, side.p, su.p, Y.p, Z.p, steps.p, capped.p, np, roff, ez.p,
-                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, gsl, o.max_steps};
+                   o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, gsl, o.max_steps, cvd, ncv, cvq.p};
         PDD_CUDA(cudaEventRecord(e0, st));
         if (mixed) launch_paths<float>(P, A, nr, st);
         else launch_paths<double>(P, A, nr, st);
@@ -952,8 +1238,15 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
         FinalArgs F{rows, subs, spos, cov.sub_off.p, cov.knot_ptr.p, cov.rowptr.p, cov.floating.p,
                     cov.ku.p, koff_m.p, kinv.p, kcond.p, o.imq_c2, o.paths, mcf, mixed, np, roff, gsl, side.p, su.p,
                     Y.p, Z.p,
-                    ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p, cov.r.p,
-                    o.moment_sums};
+                    ez.p, momp, sys.moments.p, bmean, sys.val.p, sys.se.p, sys.bs.p, sys.se_bs.p, o.moment_sums,
+                    nullptr, nullptr, ncv, cv_stride};
+        if (ncv) {
+            if (cvbeta.n < (size_t)nr * cv_stride * ncv) cvbeta.alloc((size_t)nr * cv_stride * ncv);
+            if (cvsq.n < (size_t)nr * kBatches * ncv) cvsq.alloc((size_t)nr * kBatches * ncv);
+            PDD_LAUNCH(k_cv_regress, nr, kCvThreads, cv_smem, st, P, F, cvq.p, cvbeta.p, cvsq.p);
+            F.cv_beta = cvbeta.p;
+            F.cv_sq = cvsq.p;
+        }
         if (nq_launch == 1) PDD_LAUNCH(k_mc_finalize<1>, nr, 512, fsm, st, P, F);
         else if (nq_launch == 2) PDD_LAUNCH(k_mc_finalize<2>, nr, 512, fsm, st, P, F);
         else PDD_LAUNCH(k_mc_finalize<3>, nr, 512, fsm, st, P, F);
@@ -1022,6 +1315,7 @@ McStats assemble_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_o
                 Y.alloc(off);
                 Z.alloc(off);
                 if (mixed) ez.alloc(off);
+                if (ncv) cvq.alloc((size_t)off * ncv);
             }
             run_wave(drows.p, (int)rows.size(), dnp.p, droff.p, dgsl.p, sys.mom_ptr.p, sys.bmean.p, 0);
         }
@@ -1064,7 +1358,6 @@ struct GradArgs {
     double c2;
     int n_par;
     double *partial;          // [slot][n_rbf + n_gcoef]
-    const double *cr;         // circle radii (c^2 of Eq. 19 is in squared length)
 };
 
 template <typename R, bool SRC>
@@ -1072,11 +1365,13 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     extern __shared__ double gsm[];
     const int T = blockDim.x, tid = threadIdx.x;
     const int nw = P.n_rbf, ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
+    const int nf = (P.f_kind == PDD_F_RBF) ? P.n_frbf : 0;
     double *alpha = gsm;                         // kMaxStencil
     double *S = alpha + kMaxStencil;             // [nw][T]
     double *dZ = S + (size_t)nw * T;             // [nw][T]
     double *Gw = dZ + (size_t)nw * T;            // [nw][T]
     double *Gg = Gw + (size_t)nw * T;            // [ng][T]
+    double *Gf = Gg + (size_t)ng * T;            // [nf][T]: sum over paths of dZ_tau / dv_q
     const int slot = blockIdx.x;
     const int gsl = A.gslot ? A.gslot[slot] : slot;
     const int i = A.rows[slot], m = A.subs[gsl];
@@ -1096,7 +1391,9 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
     }
     for (int q = 0; q < nw; ++q) Gw[q * T + tid] = 0.0;
     for (int k = 0; k < ng; ++k) Gg[k * T + tid] = 0.0;
+    for (int q = 0; q < nf; ++q) Gf[q * T + tid] = 0.0;
     __syncthreads();
+    const double inv2f = nf ? 1.0 / (2.0 * P.frbf_sigma * P.frbf_sigma) : 0.0;
     const double cx = A.ccx[m], cy = A.ccy[m], rad = A.cr[m];
     // the same exit rule as k_paths: disk and domain shrunk by the boundary shift (0: plain)
     const double rs = rad - A.shift;
@@ -1156,6 +1453,11 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
             }
             const double Yn = Yv * (1.0 + cv * A.h);
             const double Zn = Zv + fv * Yv * A.h;
+            // f's weights: dZ_{k+1} / dv_q = dZ_k / dv_q + psi^f_q(X_k) Y_k h (kept for the paths that exit)
+            for (int q = 0; q < nf; ++q) {
+                const double ddx = xd - P.frbf_x[q], ddy = yd - P.frbf_y[q];
+                Gf[q * T + tid] += exp(-(ddx * ddx + ddy * ddy) * inv2f) * Yv * A.h;
+            }
             const R nx = x + bx * h + sh * xi0;
             const R ny = y + by * h + sh * xi1;
             ++k;
@@ -1236,7 +1538,7 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
                 double ph;
                 if (imq) {
                     const double d = su - G.ku[a + l];
-                    ph = 1.0 / sqrt(d * d + G.c2 / (G.cr[m] * G.cr[m]));
+                    ph = 1.0 / sqrt(d * d + G.c2);
                 } else {
                     double xx = remainder(su - PDD_TWO_PI * l / ns, PDD_TWO_PI);
                     ph = (xx == 0.0) ? 1.0 : sin(0.5 * ns * xx) * cos(0.5 * xx) / (sin(0.5 * xx) * ns);
@@ -1247,9 +1549,11 @@ __global__ void __launch_bounds__(64) k_paths_grad(Problem P, PathArgs A, GradAr
         for (int q = 0; q < nw; ++q) Gw[q * T + tid] += payoff * Yv * S[q * T + tid] + dZ[q * T + tid];
     }
     __syncthreads();
+    // partial layout [c weights][f weights][g coefficients]
     const double scale = G.lambda[i] / npath;
-    for (int q = tid; q < nw + ng; q += T) {
-        const double *src = (q < nw) ? Gw + (size_t)q * T : Gg + (size_t)(q - nw) * T;
+    for (int q = tid; q < nw + nf + ng; q += T) {
+        const double *src = (q < nw) ? Gw + (size_t)q * T
+                                     : (q < nw + nf ? Gf + (size_t)(q - nw) * T : Gg + (size_t)(q - nw - nf) * T);
         double s = 0.0;
         for (int t = 0; t < T; ++t) s += src[t];
         G.partial[(long)slot * G.n_par + q] = scale * s;
@@ -1262,11 +1566,12 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     const int nmc = sys.n_mc;
     const int nw = (P.c_kind == PDD_C_RBF) ? P.n_rbf : 0;
     const int ng = (P.g_kind == PDD_G_BOUNDARY_FOURIER) ? P.n_gcoef : 0;
-    if (nmc == 0 || nw + ng == 0) return;
+    const int nf = (P.f_kind == PDD_F_RBF) ? P.n_frbf : 0;
+    if (nmc == 0 || nw + nf + ng == 0) return;
     DevBuf<double> kinv, kcond;
     DevBuf<long> koff_m;
     build_imq_inverses(cov, o.imq_c2, kinv, koff_m, kcond, st);
-    const int n_par = P.n_rbf + P.n_gcoef;
+    const int n_par = nw + nf + ng;
     partial.alloc((size_t)nmc * n_par);
     PDD_CUDA(cudaMemsetAsync(partial.p, 0, sizeof(double) * nmc * n_par, st));
     DevBuf<unsigned long long> steps;
@@ -1275,11 +1580,11 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
     capped.alloc(1);
     PathArgs A{sys.mc_rows.p, sys.mc_subs.p, sys.mc_kword.p, cov.kx.p, cov.ky.p, cov.cx.p, cov.cy.p, cov.r.p,
                cov.theta_s.p, o.paths, o.h, o.seed, nullptr, nullptr, nullptr, nullptr, steps.p, capped.p,
-               sys.mc_np.p, nullptr, nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, nullptr, o.max_steps};
-    GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p,
-               cov.r.p};
+               sys.mc_np.p, nullptr, nullptr, o.boundary_shift ? kGmC0 * sqrt(o.h) : 0.0, nullptr, o.max_steps, 0, 0,
+               nullptr};
+    GradArgs G{u, lambda, cov.knot_ptr.p, cov.floating.p, cov.ku.p, koff_m.p, kinv.p, o.imq_c2, n_par, partial.p};
     const int T = 64;
-    const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng) * T) * sizeof(double);
+    const size_t smem = (size_t)(kMaxStencil + (3 * nw + ng + nf) * T) * sizeof(double);
     if (smem > 220 * 1024) fail(PDD_EINVAL, "too many gradient parameters for the replay kernel");
     const bool src = P.f_kind != PDD_F_ZERO;
 #define PDD_GRAD_LAUNCH(R, SRCV)                                                                          \
