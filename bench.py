@@ -318,8 +318,9 @@ def run_ours(args, rank, world):
 PATHS_THREAD_INST_PER_STEP = 236.0
 # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch of k_tc_gemm_pipe from ncu on the 25 x 1536^3 Schur update
-# (profiles/k_tc_gemm_pipe_scaled_mixed.md), per useful flop; None until captured for this kernel
+# DRAM bytes (read + write) per useful flop of k_tc_gemm_fused from ncu on the top-level Schur update
+# of the scaled workload's disks (profiles/k_tc_gemm_fused_scaled_mixed.md); None until captured for
+# the current kernel
 GEMM_DRAM_BYTES_PER_FLOP = None
 
 
@@ -345,7 +346,8 @@ def roofline(stats, cfg, N, ms_solve):
                         "solve": ms_solve}}
     # a7: split-TF32 GEMMs of the pivot-free LU on tcgen05 (useful 2MNK flop; three TF32 products each)
     gflop = st["tc_gemm_flop"]
-    gem = {"kernel": "k_tc_gemm_pipe (a7 Schur updates, panels, TRSM leaves)", "bound": "tensor",
+    gem = {"kernel": "k_tc_gemm_fused (a7 Schur updates, panels, TRSM leaves; operands split in the kernel)",
+           "bound": "tensor",
            "ms": mean("ms_tc_gemm"), "unit": "TFLOP/s",
            "achieved": gflop / (mean("ms_tc_gemm") / 1e3) / 1e12 if mean("ms_tc_gemm") else None,
            "peak": tf32 / 3.0,

@@ -192,8 +192,9 @@ enum { PDD_STAGE_DEFAULT = 0,   /* as `precision`                               
        PDD_STAGE_FP64 = 1,
        PDD_STAGE_MIXED = 2 };
 
-/* Summation of the IMQ basis moments M_l of mixed-form paths (a12).  C = -K^-T M
- * amplifies their rounding by up to kappa(K). */
+/* Summation of the IMQ basis moments M_l (a12).  C = -K^-T M amplifies their
+ * rounding by up to kappa(K).  AUTO chooses by kappa_1(K) for mixed-form paths and
+ * takes FP64 for FP64 paths; a forced choice applies to either path form. */
 enum { PDD_SUMS_AUTO = 0,          /* by kappa_1(K): FP32 up to 1e5, double-float up to
                                       1e10, FP64 beyond                              */
        PDD_SUMS_FP32 = 1,          /* FP32 values of phi, FP32 sums of 16 paths       */
@@ -209,7 +210,10 @@ typedef struct {
     double imq_c2;            /* IMQ shape c^2 of Eq. 19, the knots' local angle in
                                  radians (1.5 in the paper, Sec. 4)                  */
     int max_refine;           /* refinement sweeps cap (mixed form), e.g. 12         */
-    double refine_tol;        /* stop when |dx|_inf <= tol |x|_inf per column        */
+    double refine_tol;        /* stop once the correction just applied, or the next
+                                 one predicted from the last two, is <= tol |x|_inf
+                                 per disk (0 = 1e-12: the refined entries then agree
+                                 with FP64 to ~1e-12, against a 1e-10 requirement)  */
     int factor;               /* mixed form's LU: PDD_FACTOR_*                        */
     int lu_leaf_width;        /* recursive LU leaf panel width 8/16/32; 0 = autotune */
     int lu_tensor_min;        /* smallest GEMM side sent to tcgen05; 0 = autotune    */
@@ -232,7 +236,7 @@ typedef struct {
                                  when no path was capped)                            */
     int disk_precision;       /* PDD_STAGE_*: form of the floating disks (a6-a9)     */
     int path_precision;       /* PDD_STAGE_*: form of the Monte Carlo paths (a11)    */
-    int moment_sums;          /* PDD_SUMS_*: basis sums of mixed-form paths (a12)    */
+    int moment_sums;          /* PDD_SUMS_*: basis sums of the IMQ moments (a12)     */
     int cv_degree;            /* pathwise variance reduction (Sec. 4: the paper's
                                  perimeter rows use one): 0 = off; D = 1..4: the
                                  regression control variate of Milstein and Tretyakov
@@ -471,6 +475,18 @@ pdd_status pdd_grad(const pdd_cover *cov, const pdd_operator *op, const pdd_asse
 /* ---------------------------------------------------------------------------
  * Diagnostics.
  * ------------------------------------------------------------------------- */
+
+/*
+ * pdd_split_df -- the double-float split that the double-float moment sums (a12,
+ * PDD_SUMS_DOUBLE_FLOAT) apply to each path record's weight and exit angle, built
+ * from the FP64 bit fields by integer operations: hi = v truncated to 24
+ * significant bits, lo = the remaining bits rounded to FP32, so |hi + lo - v| <=
+ * 2^-47 |v| for 2^-74 <= |v| < 2^128; 2^-126 <= |v| < 2^-74 gives lo = 0 (error
+ * below 2^-23 |v|) and |v| < 2^-126 gives hi = lo = 0 with v's sign.
+ * v_dev [n] FP64 in, hilo_dev [n][2] FP32 out (hi, lo), both caller-owned device
+ * memory, hilo_dev 8-byte aligned.  Synchronises `stream`.
+ */
+pdd_status pdd_split_df(const double *v_dev, float *hilo_dev, long long n, void *stream);
 
 const char *pdd_last_error(void);
 

@@ -119,7 +119,7 @@ EXPORTS = ["pdd_build_cover", "pdd_cover_info", "pdd_cover_arrays", "pdd_destroy
            "pdd_assemble_G", "pdd_system_csr", "pdd_system_mc", "pdd_system_stats",
            "pdd_destroy_system", "pdd_solve", "pdd_solve_csr", "pdd_solve_csr_noalloc",
            "pdd_spmv_csr", "pdd_batched_gemm_sub_tf32x3", "pdd_batched_gemm_tf32x3", "pdd_grad", "pdd_ras_apply",
-           "pdd_cover_rows", "pdd_system_mc_subs",
+           "pdd_cover_rows", "pdd_system_mc_subs", "pdd_split_df",
            "pdd_last_error", "pdd_launch_count", "pdd_version"]
 
 _lib = None
@@ -155,6 +155,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdd_solve_csr.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pdd_solve_csr_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pdd_spmv_csr.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp]
+    lib.pdd_split_df.argtypes = [vp, vp, i64, vp]
     i64_ = ctypes.c_longlong
     lib.pdd_batched_gemm_sub_tf32x3.argtypes = [i32, i32, i32, i32, vp, i64_, i32, vp, i64_, i32, vp, i64_,
                                                 i32, vp]
@@ -265,7 +266,7 @@ FACTOR = {"recursive_tc": 0, "blocked": 1, "pivoted_tc": 2}
 
 
 def assembly_opts(cfg: dict, precision: str = "fp64", floating_method: str = "ps",
-                  max_refine: int = 12, refine_tol: float = 1e-14, factor: str = "recursive_tc",
+                  max_refine: int = 12, refine_tol: float = 1e-12, factor: str = "recursive_tc",
                   lu_leaf_width: int = 0, lu_tensor_min: int = 0, disk_precision: str | None = None,
                   path_precision: str | None = None, moment_sums: str = "auto") -> _AssemblyOpts:
     """pdd_assembly_opts from a workload; disk_precision / path_precision ("fp64" or "mixed")
@@ -334,7 +335,7 @@ class System:
 
     def __init__(self, cov: Cover, cfg: dict | None = None, precision: str = "fp64",
                  floating_method: str = "ps", stream=None, max_refine: int = 12,
-                 refine_tol: float = 1e-14, factor: str = "recursive_tc", lu_leaf_width: int = 0,
+                 refine_tol: float = 1e-12, factor: str = "recursive_tc", lu_leaf_width: int = 0,
                  lu_tensor_min: int = 0, disk_precision: str | None = None, path_precision: str | None = None,
                  moment_sums: str = "auto"):
         lib = load()
@@ -452,6 +453,15 @@ def spmv_csr(rowptr, col, val, x, transpose=False, stream=None):
     _check(load().pdd_spmv_csr(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y), 1 if transpose else 0,
                                _stream(stream)))
     return y
+
+
+def split_df(v, stream=None):
+    """The double-float split (hi, lo) of a float64 CUDA tensor, as the double-float moment sums
+    apply it: returns a float32 tensor of shape v.shape + (2,)."""
+    assert v.dtype == torch.float64 and v.is_cuda and v.is_contiguous()
+    out = torch.empty(v.shape + (2,), dtype=torch.float32, device=v.device)
+    _check(load().pdd_split_df(_ptr(v), _ptr(out), v.numel(), _stream(stream)))
+    return out
 
 
 def gemm_sub_tf32x3(C, A, B, stream=None):

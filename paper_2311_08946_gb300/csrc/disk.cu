@@ -569,6 +569,28 @@ __global__ void __launch_bounds__(128) k_diag_inv(const float *LUall, int n, lon
     for (int r = 0; r < kRlTB; ++r) out[r * kRlTB + j] = Xs[w][r][j];
 }
 
+// packed FP32 pairs: fma.rn.f32x2 is two correctly rounded FMAs (the same results as fmaf)
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// shared-memory floats of the right-looking solve: the panel's solved rows padded to 4-float
+// rows, the diagonal-block inverse, the n x CG right-hand sides
+__host__ __device__ constexpr int rl_cgp(int CG) { return (CG + 3) & ~3; }
+static size_t rl_smem_bytes(int n, int CG) {
+    return ((size_t)kRlTB * rl_cgp(CG) + (size_t)kRlTB * (kRlTB + 1) + (size_t)n * CG) * sizeof(float);
+}
+
 // X += inv(LU) P R for the columns [blockIdx.y CG, ...) of every disk not yet
 // converged; the largest |correction| and |X| of each disk go to dmaxb/xmaxb
 // (bit patterns of non-negative doubles, ordered like the values)
@@ -582,9 +604,12 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
     constexpr int NT = kRlThreads, TB = kRlTB;
     constexpr bool VEC = (CG % 4) == 0;                // 16-byte shared-memory access to the columns
     constexpr int PD = (CG <= 20) ? 16 : (CG <= 36 ? 8 : 2);   // factor entries per row in flight
+    constexpr int CGP = rl_cgp(CG);
+    constexpr int NP = CG / 2;                         // column pairs (a last odd column is scalar)
     extern __shared__ __align__(16) float rsm[];
-    float *Bs = rsm;                                   // n x CG: right-hand sides, then solutions
-    float *Ds = rsm + (size_t)n * CG;                  // TB x (TB + 1) diagonal-block inverse (padded rows)
+    float *Xp = rsm;                                   // TB x CGP: the panel's solved rows, 16-byte rows
+    float *Ds = Xp + TB * CGP;                         // TB x (TB + 1) diagonal-block inverse (padded rows)
+    float *Bs = Ds + TB * (TB + 1);                    // n x CG: right-hand sides, then solutions
     const int disk = blockIdx.x, tid = threadIdx.x;
     if (conv[disk]) return;
     const int c0 = blockIdx.y * CG, cg = min(CG, nrhs - c0);
@@ -598,6 +623,7 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
         const int p = e / CG, c = e - p * CG;
         Bs[e] = (c < cg) ? (float)R[(long)perm[p] * nrhs + c0 + c] : 0.f;
     }
+    for (int e = tid; e < TB * CGP; e += NT) Xp[e] = 0.f;
     for (int pass = 0; pass < 2; ++pass) {             // 0: L (unit lower), 1: U (upper)
         for (int bi = 0; bi < nblk; ++bi) {
             const int blk = pass == 0 ? bi : nblk - 1 - bi;
@@ -641,31 +667,41 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
             for (int qp = 0; qp < QP; ++qp) {
                 const int q = warp + qp * NW;
                 if (q < NQ && lane < tb) {
-                    if constexpr (VEC) *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * q) = xo[qp];
-                    else Bs[(size_t)(i0 + lane) * CG + q] = xo[qp].x;
+                    if constexpr (VEC) {
+                        *reinterpret_cast<float4 *>(Bs + (size_t)(i0 + lane) * CG + 4 * q) = xo[qp];
+                        *reinterpret_cast<float4 *>(Xp + lane * CGP + 4 * q) = xo[qp];
+                    } else {
+                        Bs[(size_t)(i0 + lane) * CG + q] = xo[qp].x;
+                        Xp[lane * CGP + q] = xo[qp].x;
+                    }
                 }
             }
             __syncthreads();
             // rows still to solve: B_r -= T_rb X_b, two rows per thread so that each broadcast read of
             // a solved row feeds both
-            const float *xs = Bs + (size_t)i0 * CG;
             for (int base = ra; base < rb; base += 2 * NT) {
                 // the rows of this pass paired as (t, t + half): no thread carries an empty second row
                 const int m = min(2 * NT, rb - base), half = (m + 1) >> 1;
                 if (tid >= half) continue;
                 const int r = base + tid, r2 = r + half;
                 const bool two = r2 < base + m;
-                float acc0[CG], acc1[CG];
                 float *b0 = Bs + (size_t)r * CG, *b1 = Bs + (size_t)(two ? r2 : r) * CG;
-#pragma unroll
-                for (int c = 0; c < CG; ++c) {
-                    acc0[c] = b0[c];
-                    acc1[c] = b1[c];
-                }
                 // factor entries T[r][i0 + k] = LUT[(i0 + k) n + r]: consecutive rows, consecutive addresses
                 const float *l0 = LUT + (long)i0 * n + r, *l1 = LUT + (long)i0 * n + (two ? r2 : r);
                 if (full) {
-                    // PD entries per row in flight before their FMAs (the loads of a warp are coalesced)
+                    // the rows as packed column pairs; the panel's solved rows as 16-byte loads, each
+                    // feeding both rows; PD factor entries per row in flight before their FMAs
+                    unsigned long long p0[NP > 0 ? NP : 1], p1[NP > 0 ? NP : 1];
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) {
+                        p0[c] = pk2(b0[2 * c], b0[2 * c + 1]);
+                        p1[c] = pk2(b1[2 * c], b1[2 * c + 1]);
+                    }
+                    if (CG & 1) {
+                        s0 = b0[CG - 1];
+                        s1 = b1[CG - 1];
+                    }
 #pragma unroll 1
                     for (int k0 = 0; k0 < TB; k0 += PD) {
                         float m0[PD], m1[PD];
@@ -676,34 +712,48 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                         }
 #pragma unroll
                         for (int kk = 0; kk < PD; ++kk) {
-                            const float *xr = xs + (size_t)(k0 + kk) * CG;
-                            if constexpr (VEC) {
+                            const float4 *xr = reinterpret_cast<const float4 *>(Xp + (k0 + kk) * CGP);
+                            const unsigned long long n0 = pk2(-m0[kk], -m0[kk]), n1 = pk2(-m1[kk], -m1[kk]);
 #pragma unroll
-                                for (int c = 0; c < CG; c += 4) {
-                                    const float4 x = *reinterpret_cast<const float4 *>(xr + c);
-                                    acc0[c] = fmaf(-m0[kk], x.x, acc0[c]);
-                                    acc0[c + 1] = fmaf(-m0[kk], x.y, acc0[c + 1]);
-                                    acc0[c + 2] = fmaf(-m0[kk], x.z, acc0[c + 2]);
-                                    acc0[c + 3] = fmaf(-m0[kk], x.w, acc0[c + 3]);
-                                    acc1[c] = fmaf(-m1[kk], x.x, acc1[c]);
-                                    acc1[c + 1] = fmaf(-m1[kk], x.y, acc1[c + 1]);
-                                    acc1[c + 2] = fmaf(-m1[kk], x.z, acc1[c + 2]);
-                                    acc1[c + 3] = fmaf(-m1[kk], x.w, acc1[c + 3]);
+                            for (int c4 = 0; c4 < CGP / 4; ++c4) {
+                                const float4 x = xr[c4];
+                                if (2 * c4 < NP) {
+                                    const unsigned long long xa = pk2(x.x, x.y);
+                                    p0[2 * c4] = fma2(n0, xa, p0[2 * c4]);
+                                    p1[2 * c4] = fma2(n1, xa, p1[2 * c4]);
+                                } else if ((CG & 1) && 4 * c4 == CG - 1) {
+                                    s0 = fmaf(-m0[kk], x.x, s0);
+                                    s1 = fmaf(-m1[kk], x.x, s1);
                                 }
-                            } else {
-#pragma unroll
-                                for (int c = 0; c < CG; ++c) {
-                                    const float x = xr[c];
-                                    acc0[c] = fmaf(-m0[kk], x, acc0[c]);
-                                    acc1[c] = fmaf(-m1[kk], x, acc1[c]);
+                                if (2 * c4 + 1 < NP) {
+                                    const unsigned long long xb = pk2(x.z, x.w);
+                                    p0[2 * c4 + 1] = fma2(n0, xb, p0[2 * c4 + 1]);
+                                    p1[2 * c4 + 1] = fma2(n1, xb, p1[2 * c4 + 1]);
+                                } else if ((CG & 1) && 4 * c4 + 2 == CG - 1) {
+                                    s0 = fmaf(-m0[kk], x.z, s0);
+                                    s1 = fmaf(-m1[kk], x.z, s1);
                                 }
                             }
                         }
                     }
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) upk2(p0[c], b0[2 * c], b0[2 * c + 1]);
+                    if (CG & 1) b0[CG - 1] = s0;
+                    if (two) {
+#pragma unroll
+                        for (int c = 0; c < NP; ++c) upk2(p1[c], b1[2 * c], b1[2 * c + 1]);
+                        if (CG & 1) b1[CG - 1] = s1;
+                    }
                 } else {
+                    float acc0[CG], acc1[CG];
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        acc0[c] = b0[c];
+                        acc1[c] = b1[c];
+                    }
                     for (int k = 0; k < tb; ++k) {
                         const float m0 = __ldg(l0 + (long)k * n), m1 = __ldg(l1 + (long)k * n);
-                        const float *xr = xs + (size_t)k * CG;
+                        const float *xr = Xp + k * CGP;
 #pragma unroll
                         for (int c = 0; c < CG; ++c) {
                             const float x = xr[c];
@@ -711,12 +761,12 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                             acc1[c] = fmaf(-m1, x, acc1[c]);
                         }
                     }
-                }
 #pragma unroll
-                for (int c = 0; c < CG; ++c) b0[c] = acc0[c];
-                if (two) {
+                    for (int c = 0; c < CG; ++c) b0[c] = acc0[c];
+                    if (two) {
 #pragma unroll
-                    for (int c = 0; c < CG; ++c) b1[c] = acc1[c];
+                        for (int c = 0; c < CG; ++c) b1[c] = acc1[c];
+                    }
                 }
             }
             __syncthreads();
@@ -847,7 +897,7 @@ static int rl_width(int n, int nrhs, int &groups) {
                 break;
             }
         if (!W) continue;
-        const size_t sm = ((size_t)n * W + (size_t)kRlTB * (kRlTB + 1)) * sizeof(float);
+        const size_t sm = rl_smem_bytes(n, W);
         if (sm <= kRlSmemMax) {
             groups = (nrhs + W - 1) / W;
             return W;
@@ -876,7 +926,7 @@ struct RlArgs {
 
 template <int CG>
 static void launch_rl_cg(const RlArgs &a, cudaStream_t st) {
-    const size_t sm = ((size_t)a.n * CG + (size_t)kRlTB * (kRlTB + 1)) * sizeof(float);
+    const size_t sm = rl_smem_bytes(a.n, CG);
     PDD_CUDA(cudaFuncSetAttribute(k_lu_solve_rl<CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     PDD_LAUNCH(k_lu_solve_rl<CG>, dim3(a.nd, a.groups), kRlThreads, sm, st, a.LU, a.n, a.sA, a.perm, a.Dinv, a.R,
                a.nrhs, a.sR, a.X, a.conv, a.dmb, a.xmb, a.D, a.dmode);
@@ -992,7 +1042,7 @@ __global__ void __launch_bounds__(256) k_residual_df(Shape S, const NodeCoef *co
     extern __shared__ float2 wdf[];                 // per node: weights, then (c, s)
     const int nw = (S.nc - 1) + S.nt, np = S.nc + 1, half = S.nt >> 1;
     const int p0 = blockIdx.x * kResNP, npb = min(kResNP, S.n - p0);
-    float2 *cab = wdf + (size_t)kResNP * nw;        // per node: alpha, beta, gamma, delta, c, s
+    float2 *cab = wdf + (size_t)kResNP * nw;      // per node: alpha, beta, gamma, delta, c, s
     for (int pl = threadIdx.x; pl < npb; pl += blockDim.x) {
         const NodeCoef cf = coefAll[disk * strideC + p0 + pl];
         cab[6 * pl + 0] = df_split(cf.alpha);
@@ -1507,7 +1557,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             PDD_CUDA(cudaMemsetAsync(sweeps.p, 0, nd * sizeof(int), st));
             PDD_CUDA(cudaMemsetAsync(X.p, 0, (size_t)nd * sR * sizeof(double), st));
             const int maxs = std::max(1, o.max_refine);
-            const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-14;
+            const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-12;
             const int nw = (S.nc - 1) + S.nt;
             const size_t rsm = (size_t)kResNP * nw * sizeof(double);
             const size_t rsm_df = ((size_t)kResNP * nw + 6 * kResNP) * sizeof(float2);

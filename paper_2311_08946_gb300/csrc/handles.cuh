@@ -161,6 +161,16 @@ void grad_impl(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &
 void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int nd, cudaStream_t st, int W,
                       int tensor_min, float *ms_gemm = nullptr, double *gemm_flop = nullptr);
 
+// batched split-TF32 tensor-core GEMM C_b (-)= A_b B_b (tc_gemm.cu); `alias` states how C meets
+// the operands, scratch holds pre-split tiles for the cases the fused kernel does not take
+enum { TC_ALIAS_NONE = 0, TC_ALIAS_A = 1, TC_ALIAS_B = 2, TC_ALIAS_UNKNOWN = 3 };
+void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
+             int ldb, bool transB, float *C, long sC, int ldc, bool sub, int alias, float *scratch,
+             size_t scratch_floats, int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev);
+bool tc_gemm_fused_ok(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B,
+                      long sB, int ldb, bool transB, const float *C, long sC, int ldc, int alias);
+size_t tc_tile_floats(int rows, int K);
+
 // device-wide exclusive scan of int32 counts by warp scans (out[n] = the total): the _async form
 // queues the work on st and returns at once (the total optionally to *total_dev); exclusive_scan
 // also returns the total to the host (one synchronisation)

@@ -16,19 +16,16 @@
 //                (GEMM, K = w1); lu(k0 + w1, w - w1)
 //   trsm(r0, w): w <= 64: X = L_D^-1 X (GEMM); else trsm(r0, w1);
 //                X2 -= L21 X1 (GEMM); trsm(r0 + w1, w - w1)
-// The GEMMs are tc_gemm (tc_gemm.cu): operands split once into hi/lo TF32
-// tiles, persistent warp-specialised tcgen05 kernel, FP32 accumulation.
+// The GEMMs are tc_gemm (tc_gemm.cu), split-TF32 on tcgen05 with FP32
+// accumulation in tensor memory: the K = 64 updates through the kernel that
+// splits its FP32 operands as it stages them, the longer ones through operands
+// split once into tiles and streamed by bulk copies.
 #include <algorithm>
 #include <vector>
 
 #include "handles.cuh"
 
 namespace pdd {
-
-void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
-             int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
-             int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev);
-size_t tc_tile_floats(int rows, int K);
 
 static constexpr int kLeafW = 64;
 static constexpr float kTinyPivot = 1e-5f;       // rows are equilibrated to max |a_ij| = 1
@@ -108,10 +105,10 @@ struct NpLU {
     const float *invU(int k0) const { return invL(k0) + kLeafW * kLeafW; }
 
     void gemm(int M, int N, int K, const float *a, long sa, int lda, const float *b, long sb, int ldb, float *c,
-              bool sub) {
+              bool sub, int alias) {
         if (M <= 0 || N <= 0 || K <= 0) return;
-        tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, scratch, scratch_floats, err, st,
-                gev);
+        tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, alias, scratch, scratch_floats,
+                err, st, gev);
         flop += 2.0 * M * N * K * nd;
     }
 
@@ -120,12 +117,12 @@ struct NpLU {
     // X = L[r0:r0+w, r0:r0+w]^-1 X with X = A[r0:r0+w, c0:c0+nc] (unit lower L)
     void trsm(int r0, int w, int c0, int nc) {
         if (w <= kLeafW) {
-            gemm(w, nc, w, invL(r0), sInv, kLeafW, at(r0, c0), sA, n, at(r0, c0), false);
+            gemm(w, nc, w, invL(r0), sInv, kLeafW, at(r0, c0), sA, n, at(r0, c0), false, TC_ALIAS_B);
             return;
         }
         const int w1 = split(w);
         trsm(r0, w1, c0, nc);
-        gemm(w - w1, nc, w1, at(r0 + w1, r0), sA, n, at(r0, c0), sA, n, at(r0 + w1, c0), true);
+        gemm(w - w1, nc, w1, at(r0 + w1, r0), sA, n, at(r0, c0), sA, n, at(r0 + w1, c0), true, TC_ALIAS_NONE);
         trsm(r0 + w1, w - w1, c0, nc);
     }
 
@@ -133,13 +130,15 @@ struct NpLU {
         if (w <= kLeafW) {
             PDD_LAUNCH(k_leaf_diag, nd, 256, 0, st, A, n, sA, k0, w, inv, sInv, info);
             const int below = n - k0 - w;
-            if (below > 0) gemm(below, w, w, at(k0 + w, k0), sA, n, invU(k0), sInv, kLeafW, at(k0 + w, k0), false);
+            if (below > 0)
+                gemm(below, w, w, at(k0 + w, k0), sA, n, invU(k0), sInv, kLeafW, at(k0 + w, k0), false, TC_ALIAS_A);
             return;
         }
         const int w1 = split(w);
         lu(k0, w1);
         trsm(k0, w1, k0 + w1, w - w1);
-        gemm(n - (k0 + w1), w - w1, w1, at(k0 + w1, k0), sA, n, at(k0, k0 + w1), sA, n, at(k0 + w1, k0 + w1), true);
+        gemm(n - (k0 + w1), w - w1, w1, at(k0 + w1, k0), sA, n, at(k0, k0 + w1), sA, n, at(k0 + w1, k0 + w1), true,
+             TC_ALIAS_NONE);
         lu(k0 + w1, w - w1);
     }
 };
@@ -150,11 +149,9 @@ long lu_np_inv_floats(int n) { return (long)cdiv(n, kLeafW) * 2 * kLeafW * kLeaf
 size_t lu_np_scratch_floats_per_disk(int n) {
     if (n <= kLeafW) return 0;
     const int w1 = std::max(kLeafW, ((n / 2) / kLeafW) * kLeafW);
-    // the top-level Schur update (M = n - w1, N = n - w1, K = w1) and the first leaf panel
-    // (M = n - 64, N = 64, K = 64) bound every other GEMM of the recursion
-    const size_t top = tc_tile_floats(n - w1, w1) * 2;
-    const size_t leaf = tc_tile_floats(n - kLeafW, kLeafW) + tc_tile_floats(kLeafW, kLeafW);
-    return std::max(top, leaf);
+    // the GEMMs with K > 64 go through pre-split tiles; the top-level Schur update (M = n - w1,
+    // N = n - w1, K = w1) bounds them all (the K = 64 updates take the fused kernel)
+    return tc_tile_floats(n - w1, w1) * 2;
 }
 
 __global__ void k_iota_perm_np(int n, int nd, int *perm) {

@@ -634,9 +634,13 @@ __global__ void __launch_bounds__(512) k_mc_finalize(Problem P, FinalArgs F) {
         ukl[q] = (float)(uk[q] - (double)ukf[q]);
     }
     const float c2f = (float)F.c2, c2l = (float)(F.c2 - (double)c2f);
-    const int mode = (F.mixed && imq) ? (F.sums != PDD_SUMS_AUTO ? F.sums - 1
-                                                                 : (F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2)))
-                                      : 2;
+    // a forced mode applies to either path form (FP64 records carry no FP32 increments); the
+    // automatic choice keeps FP64 sums for FP64 paths
+    int mode = 2;
+    if (imq) {
+        if (F.sums != PDD_SUMS_AUTO) mode = F.sums - 1;
+        else if (F.mixed) mode = F.kcond[m] <= kFastKappa ? 0 : (F.kcond[m] <= kDfKappa ? 1 : 2);
+    }
     const int nq = (ns + 31) >> 5;                     // slices holding stencil knots (block-uniform)
     for (int bt = warp; bt < kBatches; bt += 16) {         // 16 warps, two batches each (p mod 32)
         double acc[NQ];
@@ -1603,3 +1607,27 @@ void grad_mc(const pdd_cover &cov, const Problem &P, const pdd_assembly_opts &o,
 }
 
 }  // namespace pdd
+
+namespace pdd {
+__global__ void k_split_df(const double *v, float2 *out, long n) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = split_df_bits(v[t]);
+}
+}  // namespace pdd
+
+// C ABI: the double-float split of the finalize's sum mode 1 (see include/pdd.h)
+extern "C" pdd_status pdd_split_df(const double *v_dev, float *hilo_dev, long long n, void *stream) {
+    using namespace pdd;
+    try {
+        if (n < 0 || (n > 0 && (!v_dev || !hilo_dev))) fail(PDD_EINVAL, "negative count or null buffer");
+        if (((uintptr_t)hilo_dev & 7) != 0) fail(PDD_EINVAL, "output not 8-byte aligned");
+        if (n == 0) return PDD_OK;
+        cudaStream_t st = (cudaStream_t)stream;
+        PDD_LAUNCH(k_split_df, (unsigned)cdiv((long)n, 256), 256, 0, st, v_dev, reinterpret_cast<float2 *>(hilo_dev),
+                   (long)n);
+        PDD_CUDA(cudaStreamSynchronize(st));
+    } catch (const Fail &f) {
+        return f.st;
+    }
+    return PDD_OK;
+}

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "handles.cuh"
+#include "mbarrier.cuh"
 
 namespace pdd {
 
@@ -36,11 +37,6 @@ static constexpr int kOpBytes = kTM * kTK * 4;          // one operand copy: 8 K
 static constexpr int kStageBytes = 4 * kOpBytes;        // A_hi, A_lo, B_hi, B_lo
 static constexpr int kTcSmem = 2 * kStageBytes;        // two stages (64 KB: two CTAs per SM)
 static constexpr int kTmemCols = 128;                   // one 128 x 128 FP32 accumulator
-static constexpr long long kWaitLimit = 1LL << 22;   // polls before a wait is declared failed
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
@@ -79,24 +75,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                  : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try(mbar, parity)) return true;
-    return false;
 }
 
 // element (r, k) of a rows x 32 operand tile in the canonical layout
@@ -452,24 +430,6 @@ struct TcPipeArgs {
     int *err;
 };
 
-__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
-}
-
 __device__ __forceinline__ void pipe_tile(long t, const TcPipeArgs &g, int &b, int &mt, int &nt) {
     const long per = (long)g.mtiles * g.ntiles;
     b = (int)(t / per);
@@ -655,6 +615,353 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
     if (threadIdx.x == 0 && failed) atomicAdd(g.err, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Fused form (the recursive disk LU's GEMMs): the operands are read as FP32
+// from their matrices and split into hi/lo TF32 inside the GEMM kernel, so no
+// split copy of either operand passes through device memory.  Persistent
+// (one CTA per SM), warp-specialised, tiles of 128 rows x TN columns
+// (TN = 64, 128 or 256 by N), K in chunks of 16 through a 4-stage ring:
+//   warps 0-7   converters: each K chunk of the A tile (128 x 16, row-major
+//               source: 16-byte loads of 4 k) and of the B tile (16 x TN,
+//               row-major source: each thread loads a 4 k x TN/64 block, one
+//               float per row of 32 consecutive columns, and writes it
+//               transposed as 16-byte rows) is loaded a few chunks ahead
+//               into registers, split, and stored in the canonical no-swizzle
+//               K-major layout (LBO = rows x 16 B, SBO = 128 B; the 16-byte
+//               unit of operand row r is r, so both stores are free of bank
+//               conflicts); each warp makes its stores visible to the tensor
+//               cores (fence.proxy.async) and arrives on the stage's mbarrier;
+//               warp 0 also allocates 2 TN TMEM columns (two accumulators),
+//               and its lane 0, once all converters have stored a chunk,
+//               issues 2 k-steps x 3 tcgen05.mma.kind::tf32 (M = 128, N = TN)
+//               for it and releases the stage with tcgen05.commit (12 warps:
+//               three per scheduler, so up to 168 registers per thread);
+//   warps 8-11  epilogue: C -= acc (or C = acc) from TMEM (warp w reads lanes
+//               32 (w mod 4) ..), each 32-column group of C loaded one group
+//               ahead (the first before the accumulator is ready), overlapping
+//               the next tile's MMAs.
+// C may be one of the operands only when every tile that reads the aliased part
+// also writes it: A with N <= TN, or B with M <= 128.
+// Every mbarrier wait is bounded, as in the pipelined form.
+// ---------------------------------------------------------------------------
+static constexpr int kFzK = 16;
+static constexpr int kFzStages = 4;
+static constexpr int kFzConvWarps = 8;
+static constexpr int kFzThreads = (kFzConvWarps + 4) * 32;
+
+__host__ __device__ constexpr int fz_smem(int TN) { return kFzStages * 2 * (128 + TN) * kFzK * 4; }
+// chunks in flight ahead of the one being stored (the register ring holds FZ_DEPTH + 1 chunks)
+__host__ __device__ constexpr int fz_depth(int TN) { return TN >= 256 ? 2 : (TN >= 128 ? 4 : 6); }
+
+struct FzArgs {
+    int M, N, K, mtiles, ntiles, nkc, batch;
+    const float *A;
+    long sA;
+    int lda;
+    const float *B;
+    long sB;
+    int ldb;
+    float *C;
+    long sC;
+    int ldc;
+    int *err;
+};
+
+// where the converters' loads are: tile t (b, mt, nt) and chunk kc
+struct FzCursor {
+    long t;
+    int kc;
+    const float *a, *b;   // this tile's A rows (row mt 128) and B columns (column nt TN)
+    int rows, cols;       // valid rows of the A tile, valid columns of the B tile
+};
+
+template <int TN>
+__device__ __forceinline__ void fz_seek(FzCursor &c, const FzArgs &g) {
+    const long per = (long)g.mtiles * g.ntiles;
+    const int b = (int)(c.t / per);
+    const int rem = (int)(c.t - (long)b * per);
+    const int mt = rem / g.ntiles, nt = rem - mt * g.ntiles;
+    c.a = g.A + b * g.sA + (long)mt * 128 * g.lda;
+    c.b = g.B + b * g.sB + (long)nt * TN;
+    c.rows = g.M - mt * 128;
+    c.cols = g.N - nt * TN;
+}
+
+template <int TN>
+__device__ __forceinline__ void fz_advance(FzCursor &c, const FzArgs &g) {
+    if (++c.kc == g.nkc) {
+        c.kc = 0;
+        c.t += gridDim.x;
+        if (c.t < (long)g.batch * g.mtiles * g.ntiles) fz_seek<TN>(c, g);
+    }
+}
+
+// one K chunk: A 2 x float4 (rows 8 (8 i + w) + (l & 7), k = 4 (l >> 3) ..), B V x 4 floats
+// (k = 4 (w >> 1) + kk, column l + 32 ((w & 1) + 2 e))
+template <int TN, bool VEC>
+__device__ __forceinline__ void fz_load(float4 (&a)[2], float (&bv)[TN / 64][4], const FzCursor &c,
+                                        const FzArgs &g, int w, int l) {
+    constexpr int V = TN / 64;
+    const int k0 = c.kc * kFzK;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int row = 8 * (8 * i + w) + (l & 7), k = k0 + 4 * (l >> 3);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < c.rows) {
+            const float *p = c.a + (long)row * g.lda + k;
+            if (VEC && k + 3 < g.K) {
+                v = *reinterpret_cast<const float4 *>(p);
+            } else {
+                if (k < g.K) v.x = p[0];
+                if (k + 1 < g.K) v.y = p[1];
+                if (k + 2 < g.K) v.z = p[2];
+                if (k + 3 < g.K) v.w = p[3];
+            }
+        }
+        a[i] = v;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = k0 + 4 * (w >> 1) + kk;
+        const float *p = c.b + (long)k * g.ldb;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int col = l + 32 * ((w & 1) + 2 * e);
+            bv[e][kk] = (k < g.K && col < c.cols) ? p[col] : 0.f;
+        }
+    }
+}
+
+template <int TN>
+__device__ __forceinline__ void fz_store(const float4 (&a)[2], const float (&bv)[TN / 64][4], float *st, int w,
+                                         int l) {
+    constexpr int V = TN / 64, AF = 128 * kFzK, BF = TN * kFzK;
+    float *ahi = st, *alo = st + AF, *bhi = st + 2 * AF, *blo = st + 2 * AF + BF;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int row = 8 * (8 * i + w) + (l & 7);
+        const int off = (l >> 3) * (128 * 4) + row * 4;
+        const float4 h = split_hi(a[i]);
+        *reinterpret_cast<float4 *>(ahi + off) = h;
+        *reinterpret_cast<float4 *>(alo + off) = split_lo(a[i], h);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int col = l + 32 * ((w & 1) + 2 * e);
+        const int off = (w >> 1) * (TN * 4) + col * 4;
+        const float4 v = make_float4(bv[e][0], bv[e][1], bv[e][2], bv[e][3]);
+        const float4 h = split_hi(v);
+        *reinterpret_cast<float4 *>(bhi + off) = h;
+        *reinterpret_cast<float4 *>(blo + off) = split_lo(v, h);
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// C[row, col .. col + 31] (vector form: whole group in range) into registers
+__device__ __forceinline__ void fz_cload(float4 (&cv)[8], const float *cp, bool ok) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) cv[e] = ok ? *reinterpret_cast<const float4 *>(cp + 4 * e) : make_float4(0, 0, 0, 0);
+}
+
+template <bool SUB, int TN, bool VEC>
+__global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
+    constexpr int V = TN / 64, D = fz_depth(TN), R = D + 1;
+    constexpr int AF = 128 * kFzK, BF = TN * kFzK, SF = 2 * (AF + BF);
+    extern __shared__ __align__(1024) unsigned char zsm[];
+    __shared__ __align__(8) uint64_t full[kFzStages], empty[kFzStages], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long total = (long)g.batch * g.mtiles * g.ntiles;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < kFzStages; ++s) {
+            mbar_init(smem_u32(&full[s]), kFzConvWarps);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&accf[a]), 1);
+            mbar_init(smem_u32(&acce[a]), 128);
+        }
+        mbar_init(smem_u32(&fin), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    float *ring = reinterpret_cast<float *>(zsm);
+    const uint32_t base = smem_u32(zsm);
+    if (warp < kFzConvWarps) {                             // converters (+ the MMA lane)
+        const bool mma_lane = warp == 0 && lane == 0;
+        const uint32_t idesc = idesc_tf32(128, TN);
+        const uint32_t lbo_a = 128 * 16, lbo_b = TN * 16, sbo = 128;
+        int m_kc = 0, m_tc = 0;                            // the MMA lane's chunk and tile count
+        bool issued = false;
+        const long mine = total > blockIdx.x ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const long n_items = mine * g.nkc;
+        FzCursor cur{(long)blockIdx.x, 0, nullptr, nullptr, 0, 0};
+        if (n_items > 0) fz_seek<TN>(cur, g);
+        float4 ra[R][2];
+        float rb[R][V][4];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            if (j < n_items) {
+                fz_load<TN, VEC>(ra[j], rb[j], cur, g, warp, lane);
+                fz_advance<TN>(cur, g);
+            }
+        }
+        bool stop = false;
+        for (long it0 = 0; it0 < n_items && !stop; it0 += R) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const long it = it0 + j;
+                if (it >= n_items) break;
+                if (it + D < n_items) {
+                    fz_load<TN, VEC>(ra[(j + D) % R], rb[(j + D) % R], cur, g, warp, lane);
+                    fz_advance<TN>(cur, g);
+                }
+                const int s = (int)(it % kFzStages);
+                const long r = it / kFzStages;
+                // lane 0 waits for the stage to be free; the warp leaves together on a failure
+                int go = 1;
+                if (lane == 0) {
+                    if (failed) go = 0;
+                    else if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
+                        failed = 1;
+                        go = 0;
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    stop = true;
+                    break;
+                }
+                fz_store<TN>(ra[j], rb[j], ring + (size_t)s * SF, warp, lane);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+                if (mma_lane) {
+                    // chunk m_kc of this CTA's tile m_tc, once every converter has stored it
+                    const int acc = m_tc & 1, use = m_tc >> 1;
+                    bool ok = true;
+                    if (m_kc == 0 && use > 0) ok = mbar_wait(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1));
+                    if (ok) ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(r & 1));
+                    if (!ok) {
+                        failed = 1;
+                    } else {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t d = tmem + (uint32_t)(acc * TN);
+                        const uint32_t a_hi = base + (uint32_t)(s * SF * 4), a_lo = a_hi + AF * 4;
+                        const uint32_t b_hi = a_hi + 2 * AF * 4, b_lo = b_hi + BF * 4;
+#pragma unroll
+                        for (int k8 = 0; k8 < kFzK / 8; ++k8) {
+                            const uint32_t koa = k8 * 2 * lbo_a, kob = k8 * 2 * lbo_b;
+                            mma_tf32(d, smem_desc(a_hi + koa, lbo_a, sbo), smem_desc(b_hi + kob, lbo_b, sbo), idesc,
+                                     (m_kc | k8) ? 1 : 0);
+                            mma_tf32(d, smem_desc(a_hi + koa, lbo_a, sbo), smem_desc(b_lo + kob, lbo_b, sbo), idesc,
+                                     1);
+                            mma_tf32(d, smem_desc(a_lo + koa, lbo_a, sbo), smem_desc(b_hi + kob, lbo_b, sbo), idesc,
+                                     1);
+                        }
+                        issued = true;
+                        mma_commit(smem_u32(&empty[s]));
+                        if (++m_kc == g.nkc) {
+                            mma_commit(smem_u32(&accf[acc]));
+                            m_kc = 0;
+                            ++m_tc;
+                        }
+                    }
+                }
+            }
+        }
+        // every MMA this lane issued is complete before TMEM is freed
+        if (mma_lane && issued) {
+            mma_commit(smem_u32(&fin));
+            if (!mbar_wait(smem_u32(&fin), 0)) failed = 1;
+        }
+    } else {                                               // epilogue: warps 8..11
+        const int q = warp & 3;
+        int tc = 0;
+        const bool vec = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 && (g.sC & 3) == 0;
+        for (long t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
+            const int acc = tc & 1, use = tc >> 1;
+            const long per = (long)g.mtiles * g.ntiles;
+            const int b = (int)(t / per);
+            const int rem = (int)(t - (long)b * per);
+            const int mt = rem / g.ntiles, nt = rem - mt * g.ntiles;
+            const int row = mt * 128 + q * 32 + lane;
+            float *crow = g.C + b * g.sC + (long)row * g.ldc + nt * TN;
+            const bool rok = row < g.M;
+            // C's first 32-column group is read while the accumulator is still being formed
+            float4 cv[2][8];
+            if (SUB && vec) fz_cload(cv[0], crow, rok && nt * TN + 32 <= g.N);
+            if (failed || !mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) {
+                failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int gi = 0; gi < TN / 32; ++gi) {
+                const int c0 = gi * 32, col = nt * TN + c0;
+                if (SUB && vec && gi + 1 < TN / 32)
+                    fz_cload(cv[(gi + 1) & 1], crow + c0 + 32, rok && col + 64 <= g.N);
+                uint32_t v[32];
+                tmem_ld32(tmem + (uint32_t)(acc * TN + c0) + ((uint32_t)(q * 32) << 16), v);
+                if (rok && col < g.N) {
+                    float *cp = crow + c0;
+                    if (vec && col + 32 <= g.N) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            float4 o;
+                            if (SUB) {
+                                o = cv[gi & 1][e];
+                                o.x -= __uint_as_float(v[4 * e]);
+                                o.y -= __uint_as_float(v[4 * e + 1]);
+                                o.z -= __uint_as_float(v[4 * e + 2]);
+                                o.w -= __uint_as_float(v[4 * e + 3]);
+                            } else {
+                                o = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                                __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                            }
+                            *reinterpret_cast<float4 *>(cp + 4 * e) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (col + e < g.N) cp[e] = SUB ? cp[e] - __uint_as_float(v[e]) : __uint_as_float(v[e]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acce[acc]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+    if (threadIdx.x == 0 && failed) atomicAdd(g.err, 1);
+}
+
 static int g_sms[64] = {0};
 
 static int sm_count() {
@@ -667,19 +974,26 @@ static int sm_count() {
 
 size_t tc_tile_floats(int rows, int K) { return (size_t)cdiv(rows, kPipeRows) * cdiv(K, kPipeK) * kPairFloats; }
 
-// C_b (-)= A_b B_b for b < batch through pre-split tiles.  A: M x K (row stride lda), or with
-// transA its transpose stored K x M; B: K x N (ldb), or with transB its transpose stored N x K.
-// scratch: at least chunk * (tc_tile_floats(M, K) + tc_tile_floats(N, K)) floats; the batch is
-// processed in chunks that fit.
-void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
-             int ldb, bool transB, float *C, long sC, int ldc, bool sub, float *scratch, size_t scratch_floats,
-             int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev) {
-    if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
-    static bool attr = false;
-    if (!attr) {
+static int cur_device() {
+    int dev = 0;
+    PDD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(PDD_EINVAL, "device ordinal out of range");
+    return dev;
+}
+
+// C_b (-)= A_b B_b through pre-split tiles (any transposition, any aliasing of C in the C = A B
+// form).  scratch: at least chunk * (tc_tile_floats(M, K) + tc_tile_floats(N, K)) floats; the
+// batch is processed in chunks that fit.
+static void tc_gemm_presplit(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA,
+                             const float *B, long sB, int ldb, bool transB, float *C, long sC, int ldc, bool sub,
+                             float *scratch, size_t scratch_floats, int *err, cudaStream_t st,
+                             std::vector<cudaEvent_t> *kev) {
+    static bool attr[64] = {false};
+    const int dev = cur_device();
+    if (!attr[dev]) {
         PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
         PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
-        attr = true;
+        attr[dev] = true;
     }
     const int mt = cdiv(M, kPipeRows), ntl = cdiv(N, kPipeRows), nkc = cdiv(K, kPipeK);
     const size_t fa = tc_tile_floats(M, K), fb = tc_tile_floats(N, K);
@@ -714,6 +1028,112 @@ void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, b
         else PDD_LAUNCH(k_tc_gemm_pipe<false>, grid, kPipeThreads, kPipeSmem, st, g);
         if (kev) PDD_CUDA(cudaEventRecord(e1, st));
     }
+}
+
+// [lo, hi) float addresses touched by a batch of row-major matrices
+static void span(const float *p, long s, int batch, int rows, int ld, int cols, uintptr_t &lo, uintptr_t &hi) {
+    lo = (uintptr_t)p;
+    hi = (uintptr_t)(p + (long)(batch - 1) * s + (long)(rows - 1) * ld + cols);
+}
+
+static bool spans_disjoint(const float *a, long sa, int rowsa, int lda, int colsa, const float *c, long sc,
+                           int rowsc, int ldc, int colsc, int batch) {
+    uintptr_t a0, a1, c0, c1;
+    span(a, sa, batch, rowsa, lda, colsa, a0, a1);
+    span(c, sc, batch, rowsc, ldc, colsc, c0, c1);
+    return a1 <= c0 || c1 <= a0;
+}
+
+static int fused_tile_n(int N) { return N > 128 ? 256 : (N > 64 ? 128 : 64); }
+
+// Longest K sent to the fused kernel.  Its converters hold the next chunks in registers, which
+// covers the load latency of short updates (K = 64: the leaf panels, the leaf triangular solves
+// and the thinnest Schur and TRSM updates, where it beats splitting first: 0.84-0.93x the time
+// of split + pipelined GEMM on the 16-disk n = 3072 case) but not the operand rate of long ones
+// (K >= 192: 1.2-2x), which the pipelined kernel streams from pre-split tiles with bulk copies.
+static constexpr int kFusedMaxK = 64;
+
+// whether tc_gemm takes the fused kernel (needs no scratch) for these operands
+bool tc_gemm_fused_ok(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B,
+                      long sB, int ldb, bool transB, const float *C, long sC, int ldc, int alias) {
+    if (K > kFusedMaxK) return false;
+    const int mt = cdiv(M, 128), ntl = cdiv(N, fused_tile_n(N));
+    const bool same_a = C == A && sC == sA && ldc == lda;
+    const bool same_b = C == B && sC == sB && ldc == ldb;
+    if (transA || transB) return false;
+    if (alias == TC_ALIAS_A) return same_a && ntl == 1;
+    if (alias == TC_ALIAS_B) return same_b && mt == 1;
+    if (alias == TC_ALIAS_UNKNOWN)
+        return (spans_disjoint(A, sA, M, lda, K, C, sC, M, ldc, N, batch) || (same_a && ntl == 1)) &&
+               (spans_disjoint(B, sB, K, ldb, N, C, sC, M, ldc, N, batch) || (same_b && mt == 1));
+    return true;
+}
+
+template <bool SUB, int TN, bool VEC>
+static void launch_fused_t(int grid, cudaStream_t st, const FzArgs &g) {
+    static bool attr[64] = {false};
+    const int dev = cur_device();
+    if (!attr[dev]) {
+        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_fused<SUB, TN, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fz_smem(TN)));
+        attr[dev] = true;
+    }
+    auto kern = k_tc_gemm_fused<SUB, TN, VEC>;
+    PDD_LAUNCH(kern, grid, kFzThreads, fz_smem(TN), st, g);
+}
+
+// code bits: 1 subtract, 2 16-byte A loads, 4 TN = 128, 8 TN = 256 (neither: TN = 64)
+static void launch_fused(int code, int grid, cudaStream_t st, const FzArgs &g) {
+    switch (code) {
+        case 0: launch_fused_t<false, 64, false>(grid, st, g); break;
+        case 1: launch_fused_t<true, 64, false>(grid, st, g); break;
+        case 2: launch_fused_t<false, 64, true>(grid, st, g); break;
+        case 3: launch_fused_t<true, 64, true>(grid, st, g); break;
+        case 4: launch_fused_t<false, 128, false>(grid, st, g); break;
+        case 5: launch_fused_t<true, 128, false>(grid, st, g); break;
+        case 6: launch_fused_t<false, 128, true>(grid, st, g); break;
+        case 7: launch_fused_t<true, 128, true>(grid, st, g); break;
+        case 8: launch_fused_t<false, 256, false>(grid, st, g); break;
+        case 9: launch_fused_t<true, 256, false>(grid, st, g); break;
+        case 10: launch_fused_t<false, 256, true>(grid, st, g); break;
+        default: launch_fused_t<true, 256, true>(grid, st, g); break;
+    }
+}
+
+// C_b (-)= A_b B_b for b < batch.  A: M x K (row stride lda), or with transA its transpose stored
+// K x M; B: K x N (ldb), or with transB its transpose stored N x K.  `alias` states how C meets
+// the operands: TC_ALIAS_NONE (disjoint: the caller knows, e.g. separate blocks of one matrix),
+// TC_ALIAS_A / TC_ALIAS_B (C is that operand, same pointer, stride and row stride), or
+// TC_ALIAS_UNKNOWN (checked here by address ranges).  Untransposed operands with K <= 64 go
+// through the fused kernel (no scratch) when every aliased part is read and written by the same
+// tile (C = A with N <= TN, C = B with M <= 128); the rest through pre-split tiles in `scratch`.
+void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
+             int ldb, bool transB, float *C, long sC, int ldc, bool sub, int alias, float *scratch,
+             size_t scratch_floats, int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev) {
+    if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
+    const int TN = fused_tile_n(N);
+    const int mt = cdiv(M, 128), ntl = cdiv(N, TN);
+    if (!tc_gemm_fused_ok(batch, M, N, K, A, sA, lda, transA, B, sB, ldb, transB, C, sC, ldc, alias)) {
+        tc_gemm_presplit(batch, M, N, K, A, sA, lda, transA, B, sB, ldb, transB, C, sC, ldc, sub, scratch,
+                         scratch_floats, err, st, kev);
+        return;
+    }
+    // 16-byte loads of A: its matrices and rows start on 4-float boundaries
+    const bool vec = ((uintptr_t)A & 15) == 0 && lda % 4 == 0 && sA % 4 == 0;
+    const FzArgs g{M, N, K, mt, ntl, cdiv(K, kFzK), batch, A, sA, lda, B, sB, ldb, C, sC, ldc, err};
+    const long tiles = (long)batch * mt * ntl;
+    const int grid = (int)std::min<long>(tiles, sm_count());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (kev) {
+        PDD_CUDA(cudaEventCreate(&e0));
+        PDD_CUDA(cudaEventCreate(&e1));
+        kev->push_back(e0);
+        kev->push_back(e1);
+        PDD_CUDA(cudaEventRecord(e0, st));
+    }
+    const int code = (sub ? 1 : 0) | (vec ? 2 : 0) | (TN == 256 ? 8 : (TN == 128 ? 4 : 0));
+    launch_fused(code, grid, st, g);
+    if (kev) PDD_CUDA(cudaEventRecord(e1, st));
 }
 
 void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, int lda, const float *B, long sB,
@@ -780,10 +1200,15 @@ extern "C" pdd_status pdd_batched_gemm_tf32x3(int batch, int M, int N, int K, co
         err.alloc(1);
         PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
         const size_t per = tc_tile_floats(M, K) + tc_tile_floats(N, K);
-        const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, ((size_t)1 << 28) / per));
+        int chunk = 0;
         DevBuf<float> scr;
-        scr.alloc(per * chunk);
+        if (!tc_gemm_fused_ok(batch, M, N, K, A, (long)sA, lda, false, B, (long)sB, ldb, false, C, (long)sC, ldc,
+                              TC_ALIAS_UNKNOWN)) {
+            chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, ((size_t)1 << 28) / per));
+            scr.alloc(per * chunk);
+        }
         tc_gemm(batch, M, N, K, A, (long)sA, lda, false, B, (long)sB, ldb, false, C, (long)sC, ldc, subtract != 0,
+                TC_ALIAS_UNKNOWN,
                 scr.p, per * chunk, err.p, st, nullptr);
         int h = 0;
         PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -662,6 +662,55 @@ def test_mc_moment_sums_forced_modes(pdd, name, ill):
         assert err["auto"] <= 1e-9, err              # the automatic choice takes the accurate sums
 
 
+@pytest.mark.parametrize("name", ["varcoef", "poisson46"])
+def test_mc_double_float_sums_on_identical_records(pdd, name):
+    """Double-float basis sums (a12) against FP64 sums on the SAME path records: FP64 paths are
+    bit-reproducible, so two assemblies that differ only in the forced summation see identical
+    (Y, Z, exit angle, side).  The double-float phi and sums must then agree with the FP64 ones to
+    1e-12 relative (the split is within 2^-47, the double-float rsqrt within 1e-13)."""
+    paths = {"varcoef": 1000, "poisson46": 500}[name]
+    cfg = getattr(workloads, name)(paths=paths)
+    cov = pdd.Cover(cfg)
+    out = {}
+    for mode in ("fp64", "double_float"):
+        S = pdd.System(cov, cfg, "mixed", path_precision="fp64", moment_sums=mode)
+        mc = _np(S.mc())
+        out[mode] = (mc["moments"], mc["bmean"])
+    m64, b64 = out["fp64"]
+    mdf, bdf = out["double_float"]
+    assert np.array_equal(bdf, b64)                   # r_i does not go through the basis sums
+    assert np.abs(mdf - m64).max() <= 1e-12 * np.abs(m64).max(), np.abs(mdf - m64).max() / np.abs(m64).max()
+
+
+def test_split_df_bits(pdd):
+    """The integer-built double-float split of the double-float sums: hi + lo within 2^-47 of v for
+    2^-74 <= |v| < 2^128, lo = 0 and an error below 2^-23 for 2^-126 <= |v| < 2^-74, signed zeros
+    below 2^-126; hi is v truncated to FP32's 24 bits (|hi| <= |v|, same sign)."""
+    rng = np.random.default_rng(11)
+    ex = rng.uniform(-140.0, 127.0, 20000)
+    v = rng.uniform(1.0, 2.0, ex.size) * np.exp2(np.floor(ex)) * rng.choice([-1.0, 1.0], ex.size)
+    edge = []
+    for e in (-127, -126, -125, -75, -74, -73, -1, 0, 1, 126):
+        for m in (1.0, 1.0 + 2.0 ** -52, 1.5, 2.0 - 2.0 ** -52):
+            edge += [m * 2.0 ** e, -m * 2.0 ** e]
+    v = np.concatenate([v, np.array(edge), [0.0, -0.0, 1.0 / 3.0, np.pi, 1e-30, 1e30]])
+    hl = pdd.split_df(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    hi, lo = hl[:, 0], hl[:, 1]
+    av = np.abs(v)
+    big = av >= 2.0 ** -74
+    mid = (av >= 2.0 ** -126) & ~big
+    small = av < 2.0 ** -126
+    assert np.all(np.abs(hi + lo - v)[big] <= 2.0 ** -47 * av[big])
+    assert np.all(lo[mid] == 0.0) and np.all(np.abs(hi - v)[mid] < 2.0 ** -23 * av[mid])
+    assert np.all(hi[small] == 0.0) and np.all(lo[small] == 0.0)
+    assert np.all(np.signbit(hi) == np.signbit(v))
+    assert np.all(np.abs(hi) <= av)
+    # hi is the truncation: its 24 bits are v's leading bits
+    nz = ~small
+    ulp = np.exp2(np.frexp(av[nz])[1] - 24.0)         # weight of the 24th significant bit
+    assert np.all(hi[nz] == np.trunc(v[nz] / ulp) * ulp)
+
+
 def test_gmres_random_csr_against_direct(pdd):
     import scipy.sparse as sp
     rng = np.random.default_rng(7)

@@ -37,8 +37,9 @@ def test_gemm_sub_matches_fp64(pdd, b, M, N, K):
     assert bool((err <= bound).all()), float((err / bound).max())
 
 
-# the pipelined kernel of the pivot-free LU: several tiles per CTA (the 152-CTA persistent grid
-# wraps), ragged M/N/K, both C -= A B and C = A B
+# the kernel of the pivot-free LU (operands split inside the kernel; tiles of 128 x 64/128/256 by
+# N): several tiles per CTA (the persistent grid wraps), ragged M/N/K, the scalar operand path
+# (odd leading dimensions), both C -= A B and C = A B
 @pytest.mark.parametrize("b,M,N,K", [(1, 128, 128, 32), (3, 256, 128, 64), (2, 300, 200, 96),
                                      (4, 512, 384, 512), (3, 260, 132, 68), (2, 96, 200, 36),
                                      (2, 129, 65, 33), (1, 1, 1, 1), (40, 640, 640, 320), (7, 1536, 64, 64)])
@@ -62,6 +63,35 @@ def test_pipelined_gemm_in_place_product(pdd):
     g = torch.Generator(device="cuda").manual_seed(3)
     A = torch.randn(5, 700, 64, device="cuda", generator=g, dtype=torch.float32)
     B = torch.randn(5, 64, 64, device="cuda", generator=g, dtype=torch.float32)
+    want = torch.bmm(A.double(), B.double())
+    bound = 2.0 ** -19 * torch.bmm(A.double().abs(), B.double().abs())
+    pdd.gemm_tf32x3(A, A, B, subtract=False)
+    err = (A.double() - want).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+
+
+@pytest.mark.parametrize("M,N", [(64, 700), (200, 300)])
+def test_pipelined_gemm_in_place_rhs(pdd, M, N):
+    """C = A B with C aliasing B (the leaf triangular solve X = L^-1 X of the pivot-free LU): one row
+    tile with K = 64 goes through the fused kernel, two row tiles (M = K = 200) through the pre-split
+    tiles."""
+    g = torch.Generator(device="cuda").manual_seed(M + N)
+    A = torch.randn(3, M, M, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(3, M, N, device="cuda", generator=g, dtype=torch.float32)
+    want = torch.bmm(A.double(), B.double())
+    bound = 2.0 ** -19 * torch.bmm(A.double().abs(), B.double().abs())
+    pdd.gemm_tf32x3(B, A, B, subtract=False)
+    err = (B.double() - want).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+
+
+@pytest.mark.parametrize("K", [200, 300])
+def test_pipelined_gemm_in_place_lhs_wide(pdd, K):
+    """C = A B with C aliasing A and N = K > 64: through the pre-split tiles, which are read in full
+    before C is written (in the fused kernel a tile would overwrite columns another tile reads)."""
+    g = torch.Generator(device="cuda").manual_seed(K)
+    A = torch.randn(2, 333, K, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(2, K, K, device="cuda", generator=g, dtype=torch.float32)
     want = torch.bmm(A.double(), B.double())
     bound = 2.0 ** -19 * torch.bmm(A.double().abs(), B.double().abs())
     pdd.gemm_tf32x3(A, A, B, subtract=False)
