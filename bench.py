@@ -242,7 +242,7 @@ def run_ours(args, rank, world):
             solve.append(S.last_solve)
             N = cov.N
             del cov, S, u
-    launches = (pdd.launch_count() - launches0) // max(1, args.steps)
+    launches = pdd.launch_count() - launches0            # this library's kernels in the K timed steps
     timed_solve_ms = statistics.mean(SOLVE_MS[-args.steps:])
     ms = statistics.mean(times)
     ms_max = max_over_ranks(ms, world)
@@ -279,14 +279,16 @@ def run_ours(args, rank, world):
            "mc_path_steps_per_s": world * mc_rate, "path_steps_per_step": path_steps,
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
                                             "ms_refine", "ms_eval", "ms_paths", "ms_finalize", "ms_trisolve",
-                                            "ms_tc_gemm")},
+                                            "ms_tc_gemm", "ms_gemm_fused")},
+           "refine_tol": 1e-12,
            "gmres": dict(solve[-1], precond=args.precond, ms=timed_solve_ms),
            "refine_sweeps_max": st["max_refine_sweeps"],
            "lu": ("pivot-free recursive, 64 x 64 diagonal blocks" if st["lu_leaf_width"] == 64 and not st["lu_blocked"]
                   else ("blocked" if st["lu_blocked"] else
                         f"pivoted recursive leaf={st['lu_leaf_width']} tensor_min={st['lu_tensor_min']}")) +
                  (" (pivoted fallback used)" if st["lu_pivoted_fallback"] else ""),
-           "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary()}
+           "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) // max(1, args.steps), "e2e": e2e,
+           "clocks": clk.summary()}
 
     # rooflines: the dominant kernel (device time from CUDA events inside the library) and the disk path
     out["roofline"] = roofline(stats, cfg, N, timed_solve_ms)
@@ -312,16 +314,18 @@ def run_ours(args, rank, world):
     return out
 
 
-# Thread-instructions per Euler-Maruyama step of k_paths<float,1,1> on the variable-coefficient workload,
-# from ncu (smsp__thread_inst_executed.sum / path-steps at 4096 paths per knot,
-# profiles/k_paths_varcoef_mixed.md).  Refresh when the kernel changes.
-PATHS_THREAD_INST_PER_STEP = 236.0
+# Thread-instructions per Euler-Maruyama step of k_paths<float,0,0,0>, the variant the scaled workload
+# runs (f = c = 0, no control variate), from ncu: smsp__thread_inst_executed.sum / path-steps on the
+# 6 x 6 lattice of the scaled workload's circles (profiles/k_paths_poisson46_mixed.md).  Refresh when
+# the kernel changes.
+PATHS_THREAD_INST_PER_STEP = 149.3
 # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per useful flop of k_tc_gemm_fused from ncu on the top-level Schur update
-# of the scaled workload's disks (profiles/k_tc_gemm_fused_scaled_mixed.md); None until captured for
-# the current kernel
-GEMM_DRAM_BYTES_PER_FLOP = None
+# DRAM bytes (read + write) per useful flop of k_tc_gemm_pipe<1> from one ncu capture: the top-level
+# Schur update (M = N = K = 1536) of 16 disks of the scaled workload, 773.6 MB read + 134.8 MB written
+# for 1.1596e11 flop (profiles/k_tc_gemm_pipe_scaled_mixed.md).  Its operands and C grow with the
+# flops of the same shape, so a full launch's traffic is taken in proportion.
+GEMM_DRAM_BYTES_PER_FLOP = (773.603072e6 + 134.844672e6) / (16 * 2.0 * 1536 ** 3)
 
 
 def tf32_peak(pk):
@@ -344,17 +348,28 @@ def roofline(stats, cfg, N, ms_solve):
     out = {"stage_ms": {"paths": mean("ms_paths"), "factor": mean("ms_factor"), "refine": mean("ms_refine"),
                         "finalize": mean("ms_finalize"), "operator": mean("ms_operator"), "eval": mean("ms_eval"),
                         "solve": ms_solve}}
-    # a7: split-TF32 GEMMs of the pivot-free LU on tcgen05 (useful 2MNK flop; three TF32 products each)
-    gflop = st["tc_gemm_flop"]
-    gem = {"kernel": "k_tc_gemm_fused (a7 Schur updates, panels, TRSM leaves; operands split in the kernel)",
-           "bound": "tensor",
-           "ms": mean("ms_tc_gemm"), "unit": "TFLOP/s",
-           "achieved": gflop / (mean("ms_tc_gemm") / 1e3) / 1e12 if mean("ms_tc_gemm") else None,
+    # a7: split-TF32 GEMMs of the pivot-free LU on tcgen05 (useful 2MNK flop; three TF32 products each).
+    # The long-K updates stream pre-split tiles (k_tc_gemm_pipe, tensor-bound); the K = 64 updates split
+    # their operands in the kernel (k_tc_gemm_fused, bound by HBM: A, B and C move once per launch).
+    ms_fz = mean("ms_gemm_fused")
+    ms_pp = mean("ms_tc_gemm") - ms_fz
+    flop_pp = st["tc_gemm_flop"] - st["gemm_fused_flop"]
+    n_pp = max(1, st.get("gemm_pipe_launches", 1))
+    gem = {"kernel": "k_tc_gemm_pipe (a7 Schur and TRSM updates with K > 64, pre-split tiles)", "bound": "tensor",
+           "ms": ms_pp, "unit": "TFLOP/s", "launches": n_pp,
+           "achieved": flop_pp / (ms_pp / 1e3) / 1e12 if ms_pp > 0 else None,
            "peak": tf32 / 3.0,
            "peak_source": f"TF32 dense = {src} bf16_tflops x 1.1/2.25 (nominal ratio) = {tf32:.1f}, / 3 products "
                           "per useful flop (split TF32)",
-           "traffic": (GEMM_DRAM_BYTES_PER_FLOP * gflop / max(1, st.get("tc_gemm_launches", 1))
-                       if GEMM_DRAM_BYTES_PER_FLOP else None)}
+           "traffic": GEMM_DRAM_BYTES_PER_FLOP * flop_pp / n_pp,
+           "traffic_note": "bytes per launch: the measured bytes per flop of one captured launch x this step's "
+                           "mean flops per launch"}
+    fz = {"kernel": "k_tc_gemm_fused (a7 K = 64 updates: leaf panels, leaf TRSMs, thinnest Schur/TRSM)",
+          "bound": "hbm", "ms": ms_fz, "unit": "GB/s",
+          "achieved": st["gemm_fused_bytes"] / (ms_fz / 1e3) / 1e9 if ms_fz > 0 else None,
+          "peak": pk["hbm_gbs"], "peak_source": f"{src} hbm_gbs (copy)", "traffic": None,
+          "tflops": st["gemm_fused_flop"] / (ms_fz / 1e3) / 1e12 if ms_fz > 0 else None,
+          "note": "algorithmic bytes = A and B read once, C written (read and written when subtracting)"}
     # a8: right-looking triangular solves, FP32 FMA (2 n^2 (n_k+1) flop per disk and sweep)
     tri_flop = st["disk_solves"] * 2.0 * n * n * nrhs
     tri = {"kernel": "k_lu_solve_rl (a8)", "bound": "hbm", "ms": mean("ms_trisolve"), "unit": "GB/s",
@@ -371,7 +386,7 @@ def roofline(stats, cfg, N, ms_solve):
            "peak_source": (f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz / "
                            f"{PATHS_THREAD_INST_PER_STEP:.0f} thread-instructions per step (ncu, variable-"
                            "coefficient workload)")}
-    ks = [gem, tri, pth]
+    ks = [gem, fz, tri, pth]
     for k in ks:
         k["frac"] = (k["achieved"] / k["peak"]) if (k.get("achieved") and k.get("peak")) else None
     ks.sort(key=lambda k: -(k["ms"] or 0.0))

@@ -279,6 +279,12 @@ typedef struct {
     int lu_pivoted_fallback;  /* 1: a wave of the pivot-free LU was redone with partial
                                  pivoting (a tiny pivot or a refinement that missed its
                                  tolerance)                                           */
+    double ms_gemm_fused;     /* the part of ms_tc_gemm spent in the kernel that splits
+                                 its operands as it stages them (the K = 64 updates) */
+    double gemm_fused_flop;   /* their useful flops                                   */
+    double gemm_fused_bytes;  /* their algorithmic bytes: A and B read once, C written
+                                 (read and written when subtracting)                 */
+    int64_t gemm_pipe_launches; /* launches of the kernel that streams pre-split tiles */
 } pdd_assembly_stats;
 
 /*

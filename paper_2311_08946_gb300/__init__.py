@@ -100,7 +100,9 @@ class _AssemblyStats(ctypes.Structure):
                 ("ms_eval", ctypes.c_double), ("lu_blocked", ctypes.c_int), ("lu_leaf_width", ctypes.c_int),
                 ("lu_tensor_min", ctypes.c_int), ("ms_trisolve", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double),
                 ("disk_solves", ctypes.c_int64), ("tc_gemm_flop", ctypes.c_double),
-                ("lu_pivoted_fallback", ctypes.c_int)]
+                ("lu_pivoted_fallback", ctypes.c_int), ("ms_gemm_fused", ctypes.c_double),
+                ("gemm_fused_flop", ctypes.c_double), ("gemm_fused_bytes", ctypes.c_double),
+                ("gemm_pipe_launches", ctypes.c_int64)]
 
 
 class _SolveOpts(ctypes.Structure):

@@ -354,6 +354,10 @@ pdd_status pdd_assemble_G(const pdd_cover *cov, const pdd_operator *op, const pd
         S.disk_solves = ds.disk_solves;
         S.tc_gemm_flop = ds.tc_gemm_flop;
         S.lu_pivoted_fallback = ds.lu_fallback;
+        S.ms_gemm_fused = ds.ms_gemm_fused;
+        S.gemm_fused_flop = ds.gemm_fused_flop;
+        S.gemm_fused_bytes = ds.gemm_fused_bytes;
+        S.gemm_pipe_launches = ds.gemm_pipe_launches;
         if (ms.capped) fail(PDD_EPATH_CAP, std::to_string(ms.capped) + " paths reached the step cap");
         if (ds.unconverged)
             fail(PDD_ENOCONV, std::to_string(ds.unconverged) + " disks missed the refinement tolerance");

@@ -1364,7 +1364,7 @@ static void launch_lu(T *A, int n, long strideA, int *perm, int *info, int nd, c
 // of up to 64 of the wave's matrices; the fastest is kept for the process.
 // ---------------------------------------------------------------------------
 void lu_nopivot_f32(float *A, int n, long strideA, int *perm, int *info, int nd, float *inv, long sInv,
-                    float *scratch, size_t scratch_floats, cudaStream_t st, float *ms_gemm, double *gemm_flop);
+                    float *scratch, size_t scratch_floats, cudaStream_t st, DiskStats *ds);
 long lu_np_inv_floats(int n);
 size_t lu_np_scratch_floats_per_disk(int n);
 
@@ -1502,7 +1502,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                 // pivot-free tensor-core LU; a pivot below the threshold sends the wave to the
                 // pivoted factorisation (the operator is rebuilt: the factor overwrote it)
                 lu_nopivot_f32(A.p, S.n, sA, perm.p, info.p, nd, npinv.p, np_inv_per, npscr.p, np_scr_floats, st,
-                               &wv.ms_tc_gemm, &wv.tc_gemm_flop);
+                               &wv);
                 std::vector<int> hi(nd);
                 PDD_CUDA(cudaMemcpyAsync(hi.data(), info.p, nd * sizeof(int), cudaMemcpyDeviceToHost, st));
                 PDD_CUDA(cudaStreamSynchronize(st));
@@ -1510,6 +1510,9 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                 if (!np_used) {
                     wv.ms_tc_gemm = 0.f;
                     wv.tc_gemm_flop = 0.0;
+                    wv.ms_gemm_fused = 0.f;
+                    wv.gemm_fused_flop = wv.gemm_fused_bytes = 0.0;
+                    wv.gemm_pipe_launches = 0;
                     build_operator<T>(P, S, dd.p, nd, A.p, sA, RHS.p, sR, coef.p, sC, st);
                 }
             }
@@ -1659,6 +1662,10 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
         ds.ms_eval += tm.ms(3, 4);
         ds.ms_tc_gemm += wv.ms_tc_gemm;
         ds.tc_gemm_flop += wv.tc_gemm_flop;
+        ds.ms_gemm_fused += wv.ms_gemm_fused;
+        ds.gemm_fused_flop += wv.gemm_fused_flop;
+        ds.gemm_fused_bytes += wv.gemm_fused_bytes;
+        ds.gemm_pipe_launches += wv.gemm_pipe_launches;
         ds.ms_trisolve += wv.ms_trisolve;
         ds.max_sweeps = std::max(ds.max_sweeps, wv.max_sweeps);
         ds.unconverged += wv.unconverged;
@@ -1710,6 +1717,10 @@ DiskStats assemble_disks(const pdd_cover &cov, const Problem &P, const pdd_assem
         all.ms_eval += d.ms_eval;
         all.ms_trisolve += d.ms_trisolve;
         all.ms_tc_gemm += d.ms_tc_gemm;
+        all.ms_gemm_fused += d.ms_gemm_fused;
+        all.gemm_fused_flop += d.gemm_fused_flop;
+        all.gemm_fused_bytes += d.gemm_fused_bytes;
+        all.gemm_pipe_launches += d.gemm_pipe_launches;
         all.disk_solves += d.disk_solves;
         all.tc_gemm_flop += d.tc_gemm_flop;
         if (d.lu_leaf || d.lu_blocked) {

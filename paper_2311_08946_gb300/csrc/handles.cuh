@@ -87,6 +87,9 @@ struct DiskStats {
     float ms_trisolve = 0, ms_tc_gemm = 0;                 // kernel-only device times (mixed form)
     int64_t disk_solves = 0;                               // (disk, sweep) triangular solves
     double tc_gemm_flop = 0;                               // useful flops of the tensor-core launches
+    float ms_gemm_fused = 0;                               // the fused-split part of ms_tc_gemm
+    double gemm_fused_flop = 0, gemm_fused_bytes = 0;      // its flops and algorithmic bytes
+    int64_t gemm_pipe_launches = 0;                        // launches of the pre-split (pipelined) kernel
 };
 
 // CUDA events bracketing consecutive stages on one stream
@@ -164,9 +167,16 @@ void lu_recursive_f32(float *A, int n, long strideA, int *perm, int *info, int n
 // batched split-TF32 tensor-core GEMM C_b (-)= A_b B_b (tc_gemm.cu); `alias` states how C meets
 // the operands, scratch holds pre-split tiles for the cases the fused kernel does not take
 enum { TC_ALIAS_NONE = 0, TC_ALIAS_A = 1, TC_ALIAS_B = 2, TC_ALIAS_UNKNOWN = 3 };
+// CUDA event pairs around the GEMM kernels (not the operand splits), by kernel form, with the useful
+// flops (2MNK per matrix) and, for the fused form, the algorithmic bytes (A and B read once, C
+// written, or read and written when subtracting)
+struct TcTiming {
+    std::vector<cudaEvent_t> pipe, fused;
+    double flop_pipe = 0, flop_fused = 0, bytes_fused = 0;
+};
 void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
              int ldb, bool transB, float *C, long sC, int ldc, bool sub, int alias, float *scratch,
-             size_t scratch_floats, int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev);
+             size_t scratch_floats, int *err, cudaStream_t st, TcTiming *tt);
 bool tc_gemm_fused_ok(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B,
                       long sB, int ldb, bool transB, const float *C, long sC, int ldc, int alias);
 size_t tc_tile_floats(int rows, int K);

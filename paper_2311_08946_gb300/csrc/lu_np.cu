@@ -97,8 +97,7 @@ struct NpLU {
     float *scratch;
     size_t scratch_floats;
     cudaStream_t st;
-    std::vector<cudaEvent_t> *gev;   // event pairs around the tensor-core GEMM kernels, or null
-    double flop;                     // useful flops of the GEMMs
+    TcTiming *tt;                    // event pairs around the tensor-core GEMM kernels, or null
 
     float *at(int r, int c) const { return A + (long)r * n + c; }
     const float *invL(int k0) const { return inv + (long)(k0 / kLeafW) * 2 * kLeafW * kLeafW; }
@@ -108,8 +107,7 @@ struct NpLU {
               bool sub, int alias) {
         if (M <= 0 || N <= 0 || K <= 0) return;
         tc_gemm(nd, M, N, K, a, sa, lda, false, b, sb, ldb, false, c, sA, n, sub, alias, scratch, scratch_floats,
-                err, st, gev);
-        flop += 2.0 * M * N * K * nd;
+                err, st, tt);
     }
 
     int split(int w) const { return std::max(kLeafW, ((w / 2) / kLeafW) * kLeafW); }
@@ -161,34 +159,46 @@ __global__ void k_iota_perm_np(int n, int nd, int *perm) {
 
 // info[d] = 1-based index of the first pivot below kTinyPivot of disk d, 0 when none
 void lu_nopivot_f32(float *A, int n, long strideA, int *perm, int *info, int nd, float *inv, long sInv,
-                    float *scratch, size_t scratch_floats, cudaStream_t st, float *ms_gemm, double *gemm_flop) {
+                    float *scratch, size_t scratch_floats, cudaStream_t st, DiskStats *ds) {
     DevBuf<int> err;
     err.alloc(1);
     PDD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     PDD_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * nd, st));
     PDD_LAUNCH(k_iota_perm_np, cdiv((long)n * nd, 256), 256, 0, st, n, nd, perm);
-    std::vector<cudaEvent_t> gev;
-    NpLU r{A, n, strideA, nd, inv, sInv, info, err.p, scratch, scratch_floats, st, ms_gemm ? &gev : nullptr, 0.0};
+    TcTiming tt;
+    auto destroy = [&tt]() {
+        for (cudaEvent_t e : tt.pipe) cudaEventDestroy(e);
+        for (cudaEvent_t e : tt.fused) cudaEventDestroy(e);
+    };
+    NpLU r{A, n, strideA, nd, inv, sInv, info, err.p, scratch, scratch_floats, st, ds ? &tt : nullptr};
     try {
         r.lu(0, n);
     } catch (...) {
-        for (cudaEvent_t e : gev) cudaEventDestroy(e);
+        destroy();
         throw;
     }
     int h = 0;
     PDD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PDD_CUDA(cudaStreamSynchronize(st));
-    if (ms_gemm) {
-        float tot = 0.f;
-        for (size_t k = 0; k + 1 < gev.size(); k += 2) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, gev[k], gev[k + 1]);
-            tot += t;
-        }
-        *ms_gemm += tot;
+    if (ds) {
+        auto sum = [](const std::vector<cudaEvent_t> &ev) {
+            float tot = 0.f;
+            for (size_t k = 0; k + 1 < ev.size(); k += 2) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                tot += t;
+            }
+            return tot;
+        };
+        const float mf = sum(tt.fused);
+        ds->ms_tc_gemm += sum(tt.pipe) + mf;
+        ds->ms_gemm_fused += mf;
+        ds->tc_gemm_flop += tt.flop_pipe + tt.flop_fused;
+        ds->gemm_fused_flop += tt.flop_fused;
+        ds->gemm_fused_bytes += tt.bytes_fused;
+        ds->gemm_pipe_launches += (int64_t)(tt.pipe.size() / 2);
     }
-    if (gemm_flop) *gemm_flop += r.flop;
-    for (cudaEvent_t e : gev) cudaEventDestroy(e);
+    destroy();
     if (h) fail(PDD_ECUDA, "tensor-core GEMM timed out waiting for its pipeline");
 }
 

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&accf[a]), 1);
-            mbar_init(smem_u32(&acce[a]), 128);
+            mbar_init(smem_u32(&acce[a]), 4);         // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&fin), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -552,7 +552,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
         const bool vec = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 && (g.sC & 3) == 0;
         for (long t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
             const int acc = tc & 1, use = tc >> 1;
-            if (!mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) {
+            // lane 0 waits for the accumulator; the warp goes on (or leaves) together
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1)) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 failed = 1;
                 break;
             }
@@ -602,8 +605,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
                     }
                 }
             }
+            // the warp's TMEM reads are done: one arrival per warp (128 single-thread arrivals on one
+            // mbarrier serialise, and the MMA lane waits on this before reusing the accumulator)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(smem_u32(&acce[acc]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce[acc]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -645,11 +651,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
 // Every mbarrier wait is bounded, as in the pipelined form.
 // ---------------------------------------------------------------------------
 static constexpr int kFzK = 16;
-static constexpr int kFzStages = 4;
+static constexpr int kFzStgLd = 68;         // epilogue staging row stride (64 columns + 4: rows shift banks)
 static constexpr int kFzConvWarps = 8;
 static constexpr int kFzThreads = (kFzConvWarps + 4) * 32;
 
-__host__ __device__ constexpr int fz_smem(int TN) { return kFzStages * 2 * (128 + TN) * kFzK * 4; }
+// ring stages (4; 3 at TN = 256 so that the epilogue's staging fits beside them) and shared bytes
+__host__ __device__ constexpr int fz_stages(int TN) { return TN >= 256 ? 3 : 4; }
+__host__ __device__ constexpr int fz_smem(int TN) {
+    return fz_stages(TN) * 2 * (128 + TN) * kFzK * 4 + 128 * kFzStgLd * 4;
+}
 // chunks in flight ahead of the one being stored (the register ring holds FZ_DEPTH + 1 chunks)
 __host__ __device__ constexpr int fz_depth(int TN) { return TN >= 256 ? 2 : (TN >= 128 ? 4 : 6); }
 
@@ -769,31 +779,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// C[row, col .. col + 31] (vector form: whole group in range) into registers
-__device__ __forceinline__ void fz_cload(float4 (&cv)[8], const float *cp, bool ok) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) cv[e] = ok ? *reinterpret_cast<const float4 *>(cp + 4 * e) : make_float4(0, 0, 0, 0);
-}
-
 template <bool SUB, int TN, bool VEC>
 __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
-    constexpr int V = TN / 64, D = fz_depth(TN), R = D + 1;
+    constexpr int V = TN / 64, D = fz_depth(TN), R = D + 1, NS = fz_stages(TN);
     constexpr int AF = 128 * kFzK, BF = TN * kFzK, SF = 2 * (AF + BF);
     extern __shared__ __align__(1024) unsigned char zsm[];
-    __shared__ __align__(8) uint64_t full[kFzStages], empty[kFzStages], accf[2], acce[2], fin;
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int failed;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long total = (long)g.batch * g.mtiles * g.ntiles;
     if (threadIdx.x == 0) {
         failed = 0;
-        for (int s = 0; s < kFzStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&full[s]), kFzConvWarps);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&accf[a]), 1);
-            mbar_init(smem_u32(&acce[a]), 128);
+            mbar_init(smem_u32(&acce[a]), 4);         // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&fin), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -839,8 +843,8 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
                     fz_load<TN, VEC>(ra[(j + D) % R], rb[(j + D) % R], cur, g, warp, lane);
                     fz_advance<TN>(cur, g);
                 }
-                const int s = (int)(it % kFzStages);
-                const long r = it / kFzStages;
+                const int s = (int)(it % NS);
+                const long r = it / NS;
                 // lane 0 waits for the stage to be free; the warp leaves together on a failure
                 int go = 1;
                 if (lane == 0) {
@@ -898,60 +902,109 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
             if (!mbar_wait(smem_u32(&fin), 0)) failed = 1;
         }
     } else {                                               // epilogue: warps 8..11
+        // warp q owns TMEM lanes 32 q .. = tile rows 32 q ..; C moves through a shared staging block
+        // of those 32 rows x 64 columns as whole-row coalesced accesses (a thread-per-row access of C
+        // would touch 32 rows, 32 cache lines, per instruction).  When subtracting, a slab's 16 loads
+        // per thread are in flight together: the first slab's before the accumulator is ready, the
+        // next slab's while this one is combined and stored.
         const int q = warp & 3;
+        float *stg = ring + (size_t)NS * SF + (size_t)(q * 32) * kFzStgLd;
         int tc = 0;
         const bool vec = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 && (g.sC & 3) == 0;
+        const int hr = lane >> 4, hc = 4 * (lane & 15);      // coalesced form: 2 rows x 16 float4 per pass
+        float4 cl[16];
         for (long t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
             const int acc = tc & 1, use = tc >> 1;
             const long per = (long)g.mtiles * g.ntiles;
             const int b = (int)(t / per);
             const int rem = (int)(t - (long)b * per);
             const int mt = rem / g.ntiles, nt = rem - mt * g.ntiles;
-            const int row = mt * 128 + q * 32 + lane;
-            float *crow = g.C + b * g.sC + (long)row * g.ldc + nt * TN;
-            const bool rok = row < g.M;
-            // C's first 32-column group is read while the accumulator is still being formed
-            float4 cv[2][8];
-            if (SUB && vec) fz_cload(cv[0], crow, rok && nt * TN + 32 <= g.N);
-            if (failed || !mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) {
+            const int rbase = mt * 128 + q * 32;
+            float *cbase = g.C + b * g.sC;
+            // the warp's 32 rows x 64 columns of C from column colg, two rows per pass
+            auto cload = [&](int colg) {
+                const int ncol = g.N - colg;
+#pragma unroll
+                for (int it = 0; it < 16; ++it) {
+                    const int grow = rbase + 2 * it + hr;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (grow < g.M && hc < ncol) {
+                        const float *cp = cbase + (long)grow * g.ldc + colg + hc;
+                        if (vec && hc + 4 <= ncol) {
+                            v = *reinterpret_cast<const float4 *>(cp);
+                        } else {
+                            v.x = cp[0];
+                            if (hc + 1 < ncol) v.y = cp[1];
+                            if (hc + 2 < ncol) v.z = cp[2];
+                            if (hc + 3 < ncol) v.w = cp[3];
+                        }
+                    }
+                    cl[it] = v;
+                }
+            };
+            if (SUB) cload(nt * TN);
+            // lane 0 waits for the accumulator; the warp goes on (or leaves) together
+            int ok = 1;
+            if (lane == 0) ok = (!failed && mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 failed = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int sl = 0; sl < TN / 64; ++sl) {
+                const int colg = nt * TN + sl * 64;          // first column of this slab in C
+                const int ncol = g.N - colg;                 // valid columns from colg (may exceed 64)
+                if (SUB) {                                   // C's slab into the staging rows
 #pragma unroll
-            for (int gi = 0; gi < TN / 32; ++gi) {
-                const int c0 = gi * 32, col = nt * TN + c0;
-                if (SUB && vec && gi + 1 < TN / 32)
-                    fz_cload(cv[(gi + 1) & 1], crow + c0 + 32, rok && col + 64 <= g.N);
-                uint32_t v[32];
-                tmem_ld32(tmem + (uint32_t)(acc * TN + c0) + ((uint32_t)(q * 32) << 16), v);
-                if (rok && col < g.N) {
-                    float *cp = crow + c0;
-                    if (vec && col + 32 <= g.N) {
+                    for (int it = 0; it < 16; ++it)
+                        *reinterpret_cast<float4 *>(stg + (2 * it + hr) * kFzStgLd + hc) = cl[it];
+                    __syncwarp();
+                    if (sl + 1 < TN / 64) cload(colg + 64);
+                }
+                // this thread's row: the accumulator's 64 columns into the staging row
+                uint32_t v0[32], v1[32];
+                const uint32_t taddr = tmem + (uint32_t)(acc * TN + sl * 64) + ((uint32_t)(q * 32) << 16);
+                tmem_ld32(taddr, v0);
+                tmem_ld32(taddr + 32, v1);
+                float *sr = stg + lane * kFzStgLd;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            float4 o;
-                            if (SUB) {
-                                o = cv[gi & 1][e];
-                                o.x -= __uint_as_float(v[4 * e]);
-                                o.y -= __uint_as_float(v[4 * e + 1]);
-                                o.z -= __uint_as_float(v[4 * e + 2]);
-                                o.w -= __uint_as_float(v[4 * e + 3]);
-                            } else {
-                                o = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
-                                                __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
-                            }
-                            *reinterpret_cast<float4 *>(cp + 4 * e) = o;
+                for (int e = 0; e < 16; ++e) {
+                    const uint32_t *vv = e < 8 ? v0 : v1;
+                    const int k = 4 * (e & 7);
+                    float4 o = make_float4(__uint_as_float(vv[k]), __uint_as_float(vv[k + 1]),
+                                           __uint_as_float(vv[k + 2]), __uint_as_float(vv[k + 3]));
+                    if (SUB) {
+                        const float4 c = *reinterpret_cast<const float4 *>(sr + 4 * e);
+                        o = make_float4(c.x - o.x, c.y - o.y, c.z - o.z, c.w - o.w);
+                    }
+                    *reinterpret_cast<float4 *>(sr + 4 * e) = o;
+                }
+                __syncwarp();
+                // the staging rows back to C, coalesced
+#pragma unroll 4
+                for (int it = 0; it < 16; ++it) {
+                    const int rr = 2 * it + hr, grow = rbase + rr;
+                    if (grow < g.M && hc < ncol) {
+                        const float4 v = *reinterpret_cast<const float4 *>(stg + rr * kFzStgLd + hc);
+                        float *cp = cbase + (long)grow * g.ldc + colg + hc;
+                        if (vec && hc + 4 <= ncol) {
+                            *reinterpret_cast<float4 *>(cp) = v;
+                        } else {
+                            cp[0] = v.x;
+                            if (hc + 1 < ncol) cp[1] = v.y;
+                            if (hc + 2 < ncol) cp[2] = v.z;
+                            if (hc + 3 < ncol) cp[3] = v.w;
                         }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            if (col + e < g.N) cp[e] = SUB ? cp[e] - __uint_as_float(v[e]) : __uint_as_float(v[e]);
                     }
                 }
+                __syncwarp();
             }
+            // the warp's TMEM reads are done: one arrival per warp (128 single-thread arrivals on one
+            // mbarrier serialise, and the MMA lane waits on this before reusing the accumulator)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(smem_u32(&acce[acc]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce[acc]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -987,7 +1040,7 @@ static int cur_device() {
 static void tc_gemm_presplit(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA,
                              const float *B, long sB, int ldb, bool transB, float *C, long sC, int ldc, bool sub,
                              float *scratch, size_t scratch_floats, int *err, cudaStream_t st,
-                             std::vector<cudaEvent_t> *kev) {
+                             std::vector<cudaEvent_t> *kev) {       // event pairs around the GEMM kernels
     static bool attr[64] = {false};
     const int dev = cur_device();
     if (!attr[dev]) {
@@ -1109,13 +1162,14 @@ static void launch_fused(int code, int grid, cudaStream_t st, const FzArgs &g) {
 // tile (C = A with N <= TN, C = B with M <= 128); the rest through pre-split tiles in `scratch`.
 void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, bool transA, const float *B, long sB,
              int ldb, bool transB, float *C, long sC, int ldc, bool sub, int alias, float *scratch,
-             size_t scratch_floats, int *err, cudaStream_t st, std::vector<cudaEvent_t> *kev) {
+             size_t scratch_floats, int *err, cudaStream_t st, TcTiming *tt) {
     if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return;
     const int TN = fused_tile_n(N);
     const int mt = cdiv(M, 128), ntl = cdiv(N, TN);
     if (!tc_gemm_fused_ok(batch, M, N, K, A, sA, lda, transA, B, sB, ldb, transB, C, sC, ldc, alias)) {
         tc_gemm_presplit(batch, M, N, K, A, sA, lda, transA, B, sB, ldb, transB, C, sC, ldc, sub, scratch,
-                         scratch_floats, err, st, kev);
+                         scratch_floats, err, st, tt ? &tt->pipe : nullptr);
+        if (tt) tt->flop_pipe += 2.0 * M * N * K * batch;
         return;
     }
     // 16-byte loads of A: its matrices and rows start on 4-float boundaries
@@ -1124,16 +1178,18 @@ void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, b
     const long tiles = (long)batch * mt * ntl;
     const int grid = (int)std::min<long>(tiles, sm_count());
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (kev) {
+    if (tt) {
         PDD_CUDA(cudaEventCreate(&e0));
         PDD_CUDA(cudaEventCreate(&e1));
-        kev->push_back(e0);
-        kev->push_back(e1);
+        tt->fused.push_back(e0);
+        tt->fused.push_back(e1);
         PDD_CUDA(cudaEventRecord(e0, st));
+        tt->flop_fused += 2.0 * M * N * K * batch;
+        tt->bytes_fused += 4.0 * batch * ((double)M * K + (double)K * N + (sub ? 2.0 : 1.0) * M * N);
     }
     const int code = (sub ? 1 : 0) | (vec ? 2 : 0) | (TN == 256 ? 8 : (TN == 128 ? 4 : 0));
     launch_fused(code, grid, st, g);
-    if (kev) PDD_CUDA(cudaEventRecord(e1, st));
+    if (tt) PDD_CUDA(cudaEventRecord(e1, st));
 }
 
 void gemm_sub_tf32x3(int batch, int M, int N, int K, const float *A, long sA, int lda, const float *B, long sB,
