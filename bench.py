@@ -322,10 +322,10 @@ PATHS_THREAD_INST_PER_STEP = 149.3
 # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per useful flop of k_tc_gemm_pipe<1> from one ncu capture: the top-level
-# Schur update (M = N = K = 1536) of 16 disks of the scaled workload, 773.6 MB read + 134.8 MB written
+# Schur update (M = N = K = 1536) of 16 disks of the scaled workload, 784.1 MB read + 137.0 MB written
 # for 1.1596e11 flop (profiles/k_tc_gemm_pipe_scaled_mixed.md).  Its operands and C grow with the
 # flops of the same shape, so a full launch's traffic is taken in proportion.
-GEMM_DRAM_BYTES_PER_FLOP = (773.603072e6 + 134.844672e6) / (16 * 2.0 * 1536 ** 3)
+GEMM_DRAM_BYTES_PER_FLOP = (784.086784e6 + 137.004544e6) / (16 * 2.0 * 1536 ** 3)
 
 
 def tf32_peak(pk):
@@ -384,8 +384,8 @@ def roofline(stats, cfg, N, ms_solve):
            "achieved": st["path_steps"] / (mean("ms_paths") / 1e3) / 1e9, "unit": "Gpath-steps/s",
            "traffic": None, "peak": issue / PATHS_THREAD_INST_PER_STEP / 1e9,
            "peak_source": (f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz / "
-                           f"{PATHS_THREAD_INST_PER_STEP:.0f} thread-instructions per step (ncu, variable-"
-                           "coefficient workload)")}
+                           f"{PATHS_THREAD_INST_PER_STEP:.0f} thread-instructions per step (ncu, this "
+                           "kernel variant on a 6 x 6 lattice of the workload's circles)")}
     ks = [gem, fz, tri, pth]
     for k in ks:
         k["frac"] = (k["achieved"] / k["peak"]) if (k.get("achieved") and k.get("peak")) else None
