@@ -30,6 +30,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// the same wait for a role that has nothing else to do meanwhile: each poll suspends the thread up
+// to `ns` nanoseconds (it resumes as soon as the phase completes), so a waiting warp stops taking
+// issue slots from the warps doing the work; bounded by kSleepWaitLimit polls
+static constexpr long long kSleepWaitLimit = 1LL << 20;
+
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t mbar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, uint32_t ns = 2000) {
+    for (long long i = 0; i < kSleepWaitLimit; ++i)
+        if (mbar_try_sleep(mbar, parity, ns)) return true;
+    return false;
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }

@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
                 for (int kc = 0; kc < g.nkc; ++kc, ++it) {
                     const int s = (int)(it % kPipeStages);
                     const long r = it / kPipeStages;
-                    if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
+                    if (r > 0 && !mbar_wait_sleep(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
                         failed = 1;
                         break;
                     }
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
             // each stage that was filled
             const long n_it = it;
             for (long q = n_it - kPipeStages < 0 ? 0 : n_it - kPipeStages; q < n_it; ++q)
-                mbar_wait(smem_u32(&full[q % kPipeStages]), (uint32_t)((q / kPipeStages) & 1));
+                mbar_wait_sleep(smem_u32(&full[q % kPipeStages]), (uint32_t)((q / kPipeStages) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {                                   // MMA issuer
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
             bool issued = false;
             for (long t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
                 const int acc = tc & 1, use = tc >> 1;
-                if (use > 0 && !mbar_wait(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1))) {
+                if (use > 0 && !mbar_wait_sleep(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1))) {
                     failed = 1;
                     break;
                 }
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
                 bool ok = true;
                 for (int kc = 0; kc < g.nkc; ++kc, ++it) {
                     const int s = (int)(it % kPipeStages);
-                    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / kPipeStages) & 1))) {
+                    if (!mbar_wait_sleep(smem_u32(&full[s]), (uint32_t)((it / kPipeStages) & 1))) {
                         ok = false;
                         break;
                     }
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
             // every MMA this lane issued is complete before TMEM is freed
             if (issued) {
                 mma_commit(smem_u32(&fin));
-                if (!mbar_wait(smem_u32(&fin), 0)) failed = 1;
+                if (!mbar_wait_sleep(smem_u32(&fin), 0)) failed = 1;
             }
         }
     } else {                                               // epilogue: warps 2..5
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
             const int acc = tc & 1, use = tc >> 1;
             // lane 0 waits for the accumulator; the warp goes on (or leaves) together
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1)) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait_sleep(smem_u32(&accf[acc]), (uint32_t)(use & 1)) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 failed = 1;
                 break;
@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
                 int go = 1;
                 if (lane == 0) {
                     if (failed) go = 0;
-                    else if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
+                    else if (r > 0 && !mbar_wait_sleep(smem_u32(&empty[s]), (uint32_t)((r - 1) & 1))) {
                         failed = 1;
                         go = 0;
                     }
@@ -866,8 +866,8 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
                     // chunk m_kc of this CTA's tile m_tc, once every converter has stored it
                     const int acc = m_tc & 1, use = m_tc >> 1;
                     bool ok = true;
-                    if (m_kc == 0 && use > 0) ok = mbar_wait(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1));
-                    if (ok) ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(r & 1));
+                    if (m_kc == 0 && use > 0) ok = mbar_wait_sleep(smem_u32(&acce[acc]), (uint32_t)((use - 1) & 1));
+                    if (ok) ok = mbar_wait_sleep(smem_u32(&full[s]), (uint32_t)(r & 1));
                     if (!ok) {
                         failed = 1;
                     } else {
@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
         // every MMA this lane issued is complete before TMEM is freed
         if (mma_lane && issued) {
             mma_commit(smem_u32(&fin));
-            if (!mbar_wait(smem_u32(&fin), 0)) failed = 1;
+            if (!mbar_wait_sleep(smem_u32(&fin), 0)) failed = 1;
         }
     } else {                                               // epilogue: warps 8..11
         // warp q owns TMEM lanes 32 q .. = tile rows 32 q ..; C moves through a shared staging block
@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
             if (SUB) cload(nt * TN);
             // lane 0 waits for the accumulator; the warp goes on (or leaves) together
             int ok = 1;
-            if (lane == 0) ok = (!failed && mbar_wait(smem_u32(&accf[acc]), (uint32_t)(use & 1))) ? 1 : 0;
+            if (lane == 0) ok = (!failed && mbar_wait_sleep(smem_u32(&accf[acc]), (uint32_t)(use & 1))) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 failed = 1;
                 break;
