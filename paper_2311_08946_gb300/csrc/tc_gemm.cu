@@ -655,13 +655,17 @@ static constexpr int kFzStgLd = 68;         // epilogue staging row stride (64 c
 static constexpr int kFzConvWarps = 8;
 static constexpr int kFzThreads = (kFzConvWarps + 4) * 32;
 
-// ring stages (4; 3 at TN = 256 so that the epilogue's staging fits beside them) and shared bytes
-__host__ __device__ constexpr int fz_stages(int TN) { return TN >= 256 ? 3 : 4; }
+// ring stages (4; 3 at TN = 256 so that the epilogue's staging fits beside them; 2 at TN = 64,
+// where two CTAs share an SM) and shared bytes
+__host__ __device__ constexpr int fz_stages(int TN) { return TN >= 256 ? 3 : 2; }
+// CTAs per SM: the 64- and 128-wide tiles are bound by the converters' issue, so two CTAs (24 warps,
+// at most 85 registers each; TMEM 2 x 2 TN columns) hide each other's stalls
+__host__ __device__ constexpr int fz_ctas(int TN) { return TN >= 256 ? 1 : 2; }
 __host__ __device__ constexpr int fz_smem(int TN) {
     return fz_stages(TN) * 2 * (128 + TN) * kFzK * 4 + 128 * kFzStgLd * 4;
 }
 // chunks in flight ahead of the one being stored (the register ring holds FZ_DEPTH + 1 chunks)
-__host__ __device__ constexpr int fz_depth(int TN) { return TN >= 256 ? 2 : (TN >= 128 ? 4 : 6); }
+__host__ __device__ constexpr int fz_depth(int TN) { return TN >= 256 ? 2 : (TN >= 128 ? 2 : 3); }
 
 struct FzArgs {
     int M, N, K, mtiles, ntiles, nkc, batch;
@@ -779,8 +783,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 template <bool SUB, int TN, bool VEC>
-__global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
+__global__ void __launch_bounds__(kFzThreads, fz_ctas(TN)) k_tc_gemm_fused(FzArgs g) {
     constexpr int V = TN / 64, D = fz_depth(TN), R = D + 1, NS = fz_stages(TN);
     constexpr int AF = 128 * kFzK, BF = TN * kFzK, SF = 2 * (AF + BF);
     extern __shared__ __align__(1024) unsigned char zsm[];
@@ -942,12 +956,42 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
                     cl[it] = v;
                 }
             };
-            if (SUB) cload(nt * TN);
+            // C's slab at column colg straight into the staging rows by asynchronous 16-byte copies (no
+            // registers held; partial edges filled directly), for the tiles that run two CTAs per SM
+            auto cload_async = [&](int colg) {
+                const int ncol = g.N - colg;
+#pragma unroll
+                for (int it = 0; it < 16; ++it) {
+                    const int rr = 2 * it + hr, grow = rbase + rr;
+                    float *dst = stg + rr * kFzStgLd + hc;
+                    const float *cp = cbase + (long)grow * g.ldc + colg + hc;
+                    if (grow < g.M && vec && hc + 4 <= ncol) {
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(cp)
+                                     : "memory");
+                    } else {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (grow < g.M && hc < ncol) {
+                            v.x = cp[0];
+                            if (hc + 1 < ncol) v.y = cp[1];
+                            if (hc + 2 < ncol) v.z = cp[2];
+                            if (hc + 3 < ncol) v.w = cp[3];
+                        }
+                        *reinterpret_cast<float4 *>(dst) = v;
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            constexpr bool kAsyncC = TN <= 128;
+            if (SUB) {
+                if constexpr (kAsyncC) cload_async(nt * TN);
+                else cload(nt * TN);
+            }
             // lane 0 waits for the accumulator; the warp goes on (or leaves) together
             int ok = 1;
             if (lane == 0) ok = (!failed && mbar_wait_sleep(smem_u32(&accf[acc]), (uint32_t)(use & 1))) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 failed = 1;
+                if (SUB && kAsyncC) asm volatile("cp.async.wait_group 0;" ::: "memory");
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -956,29 +1000,35 @@ __global__ void __launch_bounds__(kFzThreads, 1) k_tc_gemm_fused(FzArgs g) {
                 const int colg = nt * TN + sl * 64;          // first column of this slab in C
                 const int ncol = g.N - colg;                 // valid columns from colg (may exceed 64)
                 if (SUB) {                                   // C's slab into the staging rows
+                    if constexpr (kAsyncC) {
+                        if (sl > 0) cload_async(colg);       // the staging rows are free again
+                        asm volatile("cp.async.wait_group 0;" ::: "memory");
+                    } else {
 #pragma unroll
-                    for (int it = 0; it < 16; ++it)
-                        *reinterpret_cast<float4 *>(stg + (2 * it + hr) * kFzStgLd + hc) = cl[it];
+                        for (int it = 0; it < 16; ++it)
+                            *reinterpret_cast<float4 *>(stg + (2 * it + hr) * kFzStgLd + hc) = cl[it];
+                    }
                     __syncwarp();
-                    if (sl + 1 < TN / 64) cload(colg + 64);
+                    if (!kAsyncC && sl + 1 < TN / 64) cload(colg + 64);
                 }
-                // this thread's row: the accumulator's 64 columns into the staging row
-                uint32_t v0[32], v1[32];
+                // this thread's row: the accumulator's 64 columns into the staging row, 16 at a time
                 const uint32_t taddr = tmem + (uint32_t)(acc * TN + sl * 64) + ((uint32_t)(q * 32) << 16);
-                tmem_ld32(taddr, v0);
-                tmem_ld32(taddr + 32, v1);
                 float *sr = stg + lane * kFzStgLd;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const uint32_t *vv = e < 8 ? v0 : v1;
-                    const int k = 4 * (e & 7);
-                    float4 o = make_float4(__uint_as_float(vv[k]), __uint_as_float(vv[k + 1]),
-                                           __uint_as_float(vv[k + 2]), __uint_as_float(vv[k + 3]));
-                    if (SUB) {
-                        const float4 c = *reinterpret_cast<const float4 *>(sr + 4 * e);
-                        o = make_float4(c.x - o.x, c.y - o.y, c.z - o.z, c.w - o.w);
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr + 16 * p4, v);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float4 o = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                               __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                        float *d = sr + 16 * p4 + 4 * e;
+                        if (SUB) {
+                            const float4 c = *reinterpret_cast<const float4 *>(d);
+                            o = make_float4(c.x - o.x, c.y - o.y, c.z - o.z, c.w - o.w);
+                        }
+                        *reinterpret_cast<float4 *>(d) = o;
                     }
-                    *reinterpret_cast<float4 *>(sr + 4 * e) = o;
                 }
                 __syncwarp();
                 // the staging rows back to C, coalesced
@@ -1176,7 +1226,7 @@ void tc_gemm(int batch, int M, int N, int K, const float *A, long sA, int lda, b
     const bool vec = ((uintptr_t)A & 15) == 0 && lda % 4 == 0 && sA % 4 == 0;
     const FzArgs g{M, N, K, mt, ntl, cdiv(K, kFzK), batch, A, sA, lda, B, sB, ldb, C, sC, ldc, err};
     const long tiles = (long)batch * mt * ntl;
-    const int grid = (int)std::min<long>(tiles, sm_count());
+    const int grid = (int)std::min<long>(tiles, (long)fz_ctas(TN) * sm_count());
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tt) {
         PDD_CUDA(cudaEventCreate(&e0));
