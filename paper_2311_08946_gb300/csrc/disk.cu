@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
                                                                float2 *Dall, int dmode) {
     constexpr int NT = kRlThreads, TB = kRlTB;
     constexpr bool VEC = (CG % 4) == 0;                // 16-byte shared-memory access to the columns
-    constexpr int PD = (CG <= 20) ? 16 : (CG <= 36 ? 8 : 2);   // factor entries per row in flight
+    constexpr int PD = (CG <= 20) ? 32 : (CG <= 36 ? 8 : 2);   // factor entries per row in flight
     constexpr int CGP = rl_cgp(CG);
     constexpr int NP = CG / 2;                         // column pairs (a last odd column is scalar)
     extern __shared__ __align__(16) float rsm[];
