@@ -624,6 +624,14 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
         Bs[e] = (c < cg) ? (float)R[(long)perm[p] * nrhs + c0 + c] : 0.f;
     }
     for (int e = tid; e < TB * CGP; e += NT) Xp[e] = 0.f;
+    // each panel's diagonal-block inverse is loaded into registers one panel ahead (NT >= TB TB / 2)
+    static_assert(2 * NT >= TB * TB, "two inverse entries per thread");
+    float dnext[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * NT;
+        dnext[h] = e < TB * TB ? Dv[e] : 0.f;                       // pass 0, block 0
+    }
     for (int pass = 0; pass < 2; ++pass) {             // 0: L (unit lower), 1: U (upper)
         for (int bi = 0; bi < nblk; ++bi) {
             const int blk = pass == 0 ? bi : nblk - 1 - bi;
@@ -634,8 +642,26 @@ __global__ void __launch_bounds__(kRlThreads, 1) k_lu_solve_rl(const float *LUTa
             // is not a multiple of 4), lane i the panel row i; the row of the inverse comes from shared
             // memory and the panel's right-hand sides are read as broadcasts
             const int warp = tid >> 5, lane = tid & 31;
-            const float *Dt = Dv + ((long)blk * 2 + pass) * (TB * TB);
-            for (int e = tid; e < TB * TB; e += NT) Ds[(e >> 5) * (TB + 1) + (e & 31)] = Dt[e];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = tid + h * NT;
+                if (e < TB * TB) Ds[(e >> 5) * (TB + 1) + (e & 31)] = dnext[h];
+            }
+            {   // the next panel's inverse (L pass in block order, then U pass in reverse)
+                const bool last_l = pass == 0 && bi == nblk - 1;
+                const int npass = last_l ? 1 : pass;
+                const int nblk_i = last_l ? nblk - 1 : (pass == 0 ? blk + 1 : blk - 1);
+                if (npass == 1 && nblk_i < 0) {
+                    dnext[0] = dnext[1] = 0.f;
+                } else {
+                    const float *Dn = Dv + ((long)nblk_i * 2 + npass) * (TB * TB);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = tid + h * NT;
+                        if (e < TB * TB) dnext[h] = Dn[e];
+                    }
+                }
+            }
             __syncthreads();
             constexpr int NQ = VEC ? CG / 4 : CG, NW = NT / 32, QP = (NQ + NW - 1) / NW;
             float4 xo[QP];
