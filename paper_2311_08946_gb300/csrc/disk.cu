@@ -112,20 +112,6 @@ struct NodeCoef {
     double alpha, beta, gamma, delta, c, s;
 };
 
-__device__ __forceinline__ double a_entry(const Shape &S, int k, int j, int q, double al, double be,
-                                          double ga, double de, double cv, int p) {
-    const int l = q / S.nt + 1, jp = q - (l - 1) * S.nt, half = S.nt >> 1, np = S.nc + 1;
-    double v = 0.0;
-    if (jp == j) v += al * S.D2[k * np + l] + be * S.D[k * np + l];
-    if (jp == (j + half) % S.nt) v += al * S.D2[k * np + S.nc - l] + be * S.D[k * np + S.nc - l];
-    if (l == k) {
-        int d = (j - jp + S.nt) % S.nt;
-        v += ga * S.F2[d] + de * S.F1[d];
-    }
-    if (q == p) v += cv;
-    return v;
-}
-
 // per node: coefficients of the polar operator, the row scale 1/max|A_pq| (the
 // nonzeros of a row are the radial line through the node, its mirror through
 // the centre, the node's ring and the diagonal) and the right-hand sides
@@ -189,17 +175,46 @@ __global__ void __launch_bounds__(256) k_fill_operator(Shape S, T *A, long strid
     const int p = blockIdx.x * rows_per_block + warp;
     if (p >= S.n) return;
     T *row = reinterpret_cast<T *>(fsm_raw) + (size_t)warp * S.n;
-    for (int q = lane; q < S.n; q += 32) row[q] = (T)0;
+    if ((S.n * sizeof(T)) % 16 == 0) {
+        float4 *r4 = reinterpret_cast<float4 *>(row);
+        for (int q = lane; q < (int)(S.n * sizeof(T) / 16); q += 32) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int q = lane; q < S.n; q += 32) row[q] = (T)0;
+    }
     __syncwarp();
     const NodeCoef cf = coef[disk * strideC + p];
-    const int k = p / S.nt + 1, j = p % S.nt, jm = (j + (S.nt >> 1)) % S.nt;
+    const int k = p / S.nt + 1, j = p % S.nt, half = S.nt >> 1, jm = (j + half) % S.nt, np = S.nc + 1;
     const int ncand = 2 * S.nr + S.nt;
+    // the candidates are the radial line through node p, its mirror through the centre and the ring
+    // of p; each entry sums the operator's terms that reach it (radial, mirror, ring, diagonal, in
+    // that order), the candidate's line and angle known without index division
     for (int c = lane; c < ncand; c += 32) {
         int q;
-        if (c < S.nr) q = c * S.nt + j;
-        else if (c < 2 * S.nr) q = (c - S.nr) * S.nt + jm;
-        else q = (k - 1) * S.nt + (c - 2 * S.nr);
-        row[q] = (T)(cf.s * a_entry(S, k, j, q, cf.alpha, cf.beta, cf.gamma, cf.delta, cf.c, p));
+        double v = 0.0;
+        if (c < S.nr) {                                      // radial line: l = c + 1, angle j
+            const int l = c + 1;
+            q = c * S.nt + j;
+            v += cf.alpha * S.D2[k * np + l] + cf.beta * S.D[k * np + l];
+            if (l == k) {
+                v += cf.gamma * S.F2[0] + cf.delta * S.F1[0];
+                v += cf.c;                                   // q == p
+            }
+        } else if (c < 2 * S.nr) {                           // mirror line: angle jm
+            const int l = c - S.nr + 1;
+            q = (l - 1) * S.nt + jm;
+            v += cf.alpha * S.D2[k * np + S.nc - l] + cf.beta * S.D[k * np + S.nc - l];
+            if (l == k) v += cf.gamma * S.F2[half] + cf.delta * S.F1[half];
+        } else {                                             // ring of p: l = k, angle jp
+            const int jp = c - 2 * S.nr;
+            q = (k - 1) * S.nt + jp;
+            if (jp == j) v += cf.alpha * S.D2[k * np + k] + cf.beta * S.D[k * np + k];
+            if (jp == jm) v += cf.alpha * S.D2[k * np + S.nc - k] + cf.beta * S.D[k * np + S.nc - k];
+            int d = j - jp;
+            d += d < 0 ? S.nt : 0;
+            v += cf.gamma * S.F2[d] + cf.delta * S.F1[d];
+            if (jp == j) v += cf.c;                          // q == p
+        }
+        row[q] = (T)(cf.s * v);
     }
     __syncwarp();
     T *Arow = A + disk * strideA + (long)p * S.n;
@@ -979,6 +994,9 @@ __global__ void k_split_df(const double *v, float2 *out, int n) {
 // and the (node, column) outputs are spread over all threads of the block.
 // With R1 non-null the residual is also stored as (hi, lo) FP32 pairs.
 static constexpr int kResNP = 64;
+// the double-float kernel's block: 32 nodes (41 KB of weights, five blocks per SM: its double-float
+// sums are long dependent chains, so more resident warps hide their latency)
+static constexpr int kResNPdf = 32;
 
 __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefAll, long strideC,
                                                   const double *RHSall, const double *Xall,
@@ -1067,8 +1085,8 @@ __global__ void __launch_bounds__(256) k_residual_df(Shape S, const NodeCoef *co
     if (conv[disk]) return;
     extern __shared__ float2 wdf[];                 // per node: weights, then (c, s)
     const int nw = (S.nc - 1) + S.nt, np = S.nc + 1, half = S.nt >> 1;
-    const int p0 = blockIdx.x * kResNP, npb = min(kResNP, S.n - p0);
-    float2 *cab = wdf + (size_t)kResNP * nw;      // per node: alpha, beta, gamma, delta, c, s
+    const int p0 = blockIdx.x * kResNPdf, npb = min(kResNPdf, S.n - p0);
+    float2 *cab = wdf + (size_t)kResNPdf * nw;      // per node: alpha, beta, gamma, delta, c, s
     for (int pl = threadIdx.x; pl < npb; pl += blockDim.x) {
         const NodeCoef cf = coefAll[disk * strideC + p0 + pl];
         cab[6 * pl + 0] = df_split(cf.alpha);
@@ -1589,10 +1607,10 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
             const double tol = o.refine_tol > 0 ? o.refine_tol : 1e-12;
             const int nw = (S.nc - 1) + S.nt;
             const size_t rsm = (size_t)kResNP * nw * sizeof(double);
-            const size_t rsm_df = ((size_t)kResNP * nw + 6 * kResNP) * sizeof(float2);
+            const size_t rsm_df = ((size_t)kResNPdf * nw + 6 * kResNPdf) * sizeof(float2);
             PDD_CUDA(cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
             PDD_CUDA(cudaFuncSetAttribute(k_residual_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm_df));
-            dim3 g_res(cdiv(S.n, kResNP), nd);
+            dim3 g_res(cdiv(S.n, kResNP), nd), g_res_df(cdiv(S.n, kResNPdf), nd);
             std::vector<cudaEvent_t> sev(rlW ? 2 * maxs : 0);
             for (cudaEvent_t &e : sev) PDD_CUDA(cudaEventCreate(&e));
             struct EvFree {
@@ -1621,7 +1639,7 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
                             PDD_LAUNCH(k_residual, g_res, 256, rsm, st, S, coef.p, sC, RHS.p, X.p, Rr.p, sR, conv.p,
                                        R1hl.p);
                         else
-                            PDD_LAUNCH(k_residual_df, g_res, 256, rsm_df, st, S, coef.p, sC, R1hl.p, Dhl.p, Rr.p, sR,
+                            PDD_LAUNCH(k_residual_df, g_res_df, 256, rsm_df, st, S, coef.p, sC, R1hl.p, Dhl.p, Rr.p, sR,
                                        conv.p);
                     }
                 } else {
