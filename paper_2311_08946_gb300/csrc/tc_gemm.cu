@@ -336,6 +336,7 @@ static constexpr int kPairFloats = 2 * kBlkFloats;             // hi + lo: 32 KB
 static constexpr int kPipeStages = 3;
 static constexpr int kPipeStageBytes = 2 * kPairFloats * 4;    // A pair + B pair: 64 KB
 static constexpr int kPipeSmem = kPipeStages * kPipeStageBytes;
+static constexpr int kPipeSmemAll = kPipeSmem + kPipeRows * 68 * 4;      // + the epilogue's staging block
 static constexpr int kPipeThreads = 192;
 static constexpr int kPipeTmemCols = 256;
 
@@ -417,6 +418,32 @@ __global__ void __launch_bounds__(256) k_split_tiles(const float *X, long sX, in
         *reinterpret_cast<float4 *>(lo + off) = split_lo(w, h);
     }
 }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// epilogue staging row stride of both GEMM forms (64 columns + 4: consecutive rows shift banks)
+static constexpr int kStgLd = 68;
 
 struct TcPipeArgs {
     int M, N, mtiles, ntiles, nkc, batch;
@@ -547,11 +574,42 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
             }
         }
     } else {                                               // epilogue: warps 2..5
+        // warp q owns TMEM lanes 32 q .. = tile rows 32 q ..; C moves through a shared staging block
+        // of those 32 rows x 64 columns as whole-row coalesced accesses, a slab's C loads in flight
+        // together (the first slab's before the accumulator is ready), as in the fused form
         const int q = warp & 3;
+        float *stg = reinterpret_cast<float *>(psm + kPipeSmem) + (size_t)(q * 32) * kStgLd;
         int tc = 0;
         const bool vec = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 && (g.sC & 3) == 0;
+        const int hr = lane >> 4, hc = 4 * (lane & 15);
+        float4 cl[16];
         for (long t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
             const int acc = tc & 1, use = tc >> 1;
+            int b, mt, nt;
+            pipe_tile(t, g, b, mt, nt);
+            const int rbase = mt * kPipeRows + q * 32;
+            float *cbase = g.C + b * g.sC;
+            auto cload = [&](int colg) {
+                const int ncol = g.N - colg;
+#pragma unroll
+                for (int it = 0; it < 16; ++it) {
+                    const int grow = rbase + 2 * it + hr;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (grow < g.M && hc < ncol) {
+                        const float *cp = cbase + (long)grow * g.ldc + colg + hc;
+                        if (vec && hc + 4 <= ncol) {
+                            v = *reinterpret_cast<const float4 *>(cp);
+                        } else {
+                            v.x = cp[0];
+                            if (hc + 1 < ncol) v.y = cp[1];
+                            if (hc + 2 < ncol) v.z = cp[2];
+                            if (hc + 3 < ncol) v.w = cp[3];
+                        }
+                    }
+                    cl[it] = v;
+                }
+            };
+            if (SUB) cload(nt * kPipeRows);
             // lane 0 waits for the accumulator; the warp goes on (or leaves) together
             int ok = 1;
             if (lane == 0) ok = mbar_wait_sleep(smem_u32(&accf[acc]), (uint32_t)(use & 1)) ? 1 : 0;
@@ -560,50 +618,51 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            int b, mt, nt;
-            pipe_tile(t, g, b, mt, nt);
-            const int row = mt * kPipeRows + q * 32 + lane;
-            float *crow = g.C + b * g.sC + (long)row * g.ldc + nt * kPipeRows;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kPipeRows; c0 += 32) {
-                uint32_t v[32];
-                const uint32_t taddr = tmem + (uint32_t)(acc * kPipeRows + c0) + ((uint32_t)(q * 32) << 16);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int col = nt * kPipeRows + c0;
-                if (row < g.M && col < g.N) {
-                    float *cp = crow + c0;
-                    if (vec && col + 32 <= g.N) {
+            for (int sl = 0; sl < kPipeRows / 64; ++sl) {
+                const int colg = nt * kPipeRows + sl * 64, ncol = g.N - colg;
+                if (SUB) {
 #pragma unroll
-                        for (int e = 0; e < 32; e += 4) {
-                            float4 cv;
-                            if (SUB) {
-                                cv = *reinterpret_cast<float4 *>(cp + e);
-                                cv.x -= __uint_as_float(v[e]);
-                                cv.y -= __uint_as_float(v[e + 1]);
-                                cv.z -= __uint_as_float(v[e + 2]);
-                                cv.w -= __uint_as_float(v[e + 3]);
-                            } else {
-                                cv = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
-                                                 __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
-                            }
-                            *reinterpret_cast<float4 *>(cp + e) = cv;
+                    for (int it = 0; it < 16; ++it)
+                        *reinterpret_cast<float4 *>(stg + (2 * it + hr) * kStgLd + hc) = cl[it];
+                    __syncwarp();
+                    if (sl + 1 < kPipeRows / 64) cload(colg + 64);
+                }
+                uint32_t v0[32], v1[32];
+                const uint32_t taddr = tmem + (uint32_t)(acc * kPipeRows + sl * 64) + ((uint32_t)(q * 32) << 16);
+                tmem_ld32(taddr, v0);
+                tmem_ld32(taddr + 32, v1);
+                float *sr = stg + lane * kStgLd;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const uint32_t *vv = e < 8 ? v0 : v1;
+                    const int k = 4 * (e & 7);
+                    float4 o = make_float4(__uint_as_float(vv[k]), __uint_as_float(vv[k + 1]),
+                                           __uint_as_float(vv[k + 2]), __uint_as_float(vv[k + 3]));
+                    if (SUB) {
+                        const float4 c = *reinterpret_cast<const float4 *>(sr + 4 * e);
+                        o = make_float4(c.x - o.x, c.y - o.y, c.z - o.z, c.w - o.w);
+                    }
+                    *reinterpret_cast<float4 *>(sr + 4 * e) = o;
+                }
+                __syncwarp();
+#pragma unroll 4
+                for (int it = 0; it < 16; ++it) {
+                    const int rr = 2 * it + hr, grow = rbase + rr;
+                    if (grow < g.M && hc < ncol) {
+                        const float4 v = *reinterpret_cast<const float4 *>(stg + rr * kStgLd + hc);
+                        float *cp = cbase + (long)grow * g.ldc + colg + hc;
+                        if (vec && hc + 4 <= ncol) {
+                            *reinterpret_cast<float4 *>(cp) = v;
+                        } else {
+                            cp[0] = v.x;
+                            if (hc + 1 < ncol) cp[1] = v.y;
+                            if (hc + 2 < ncol) cp[2] = v.z;
+                            if (hc + 3 < ncol) cp[3] = v.w;
                         }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            if (col + e < g.N) cp[e] = SUB ? cp[e] - __uint_as_float(v[e]) : __uint_as_float(v[e]);
                     }
                 }
+                __syncwarp();
             }
             // the warp's TMEM reads are done: one arrival per warp (128 single-thread arrivals on one
             // mbarrier serialise, and the MMA lane waits on this before reusing the accumulator)
@@ -651,7 +710,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_tc_gemm_pipe(TcPipeArgs g) 
 // Every mbarrier wait is bounded, as in the pipelined form.
 // ---------------------------------------------------------------------------
 static constexpr int kFzK = 16;
-static constexpr int kFzStgLd = 68;         // epilogue staging row stride (64 columns + 4: rows shift banks)
+static constexpr int kFzStgLd = kStgLd;
 static constexpr int kFzConvWarps = 8;
 static constexpr int kFzThreads = (kFzConvWarps + 4) * 32;
 
@@ -770,28 +829,6 @@ __device__ __forceinline__ void fz_store(const float4 (&a)[2], const float (&bv)
     }
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 template <bool SUB, int TN, bool VEC>
 __global__ void __launch_bounds__(kFzThreads, fz_ctas(TN)) k_tc_gemm_fused(FzArgs g) {
@@ -1094,8 +1131,8 @@ static void tc_gemm_presplit(int batch, int M, int N, int K, const float *A, lon
     static bool attr[64] = {false};
     const int dev = cur_device();
     if (!attr[dev]) {
-        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
-        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
+        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemAll));
+        PDD_CUDA(cudaFuncSetAttribute(k_tc_gemm_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemAll));
         attr[dev] = true;
     }
     const int mt = cdiv(M, kPipeRows), ntl = cdiv(N, kPipeRows), nkc = cdiv(K, kPipeK);
@@ -1127,8 +1164,8 @@ static void tc_gemm_presplit(int batch, int M, int N, int K, const float *A, lon
             kev->push_back(e1);
             PDD_CUDA(cudaEventRecord(e0, st));
         }
-        if (sub) PDD_LAUNCH(k_tc_gemm_pipe<true>, grid, kPipeThreads, kPipeSmem, st, g);
-        else PDD_LAUNCH(k_tc_gemm_pipe<false>, grid, kPipeThreads, kPipeSmem, st, g);
+        if (sub) PDD_LAUNCH(k_tc_gemm_pipe<true>, grid, kPipeThreads, kPipeSmemAll, st, g);
+        else PDD_LAUNCH(k_tc_gemm_pipe<false>, grid, kPipeThreads, kPipeSmemAll, st, g);
         if (kev) PDD_CUDA(cudaEventRecord(e1, st));
     }
 }
