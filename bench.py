@@ -322,10 +322,10 @@ PATHS_THREAD_INST_PER_STEP = 149.3
 # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per useful flop of k_tc_gemm_pipe<1> from one ncu capture: the top-level
-# Schur update (M = N = K = 1536) of 16 disks of the scaled workload, 784.1 MB read + 137.0 MB written
+# Schur update (M = N = K = 1536) of 16 disks of the scaled workload, 795.7 MB read + 138.1 MB written
 # for 1.1596e11 flop (profiles/k_tc_gemm_pipe_scaled_mixed.md).  Its operands and C grow with the
 # flops of the same shape, so a full launch's traffic is taken in proportion.
-GEMM_DRAM_BYTES_PER_FLOP = (784.086784e6 + 137.004544e6) / (16 * 2.0 * 1536 ** 3)
+GEMM_DRAM_BYTES_PER_FLOP = (795.685888e6 + 138.077440e6) / (16 * 2.0 * 1536 ** 3)
 
 
 def tf32_peak(pk):
