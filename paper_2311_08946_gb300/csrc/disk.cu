@@ -992,10 +992,10 @@ __global__ void k_split_df(const double *v, float2 *out, int n) {
 // R = RHS - A X in FP64 without forming A (equilibrated rows).  A block takes
 // kResNP nodes; their combined radial and angular weights go to shared memory
 // and the (node, column) outputs are spread over all threads of the block.
-// With R1 non-null the residual is also stored as (hi, lo) FP32 pairs.
-static constexpr int kResNP = 64;
-// the double-float kernel's block: 32 nodes (41 KB of weights, five blocks per SM: its double-float
-// sums are long dependent chains, so more resident warps hide their latency)
+// With R1 non-null the residual is also stored as (hi, lo) FP32 pairs.  Both forms take 32 nodes
+// per block (41 KB of weights for the double-float one, five blocks per SM): their FP64 and
+// double-float sums are long dependent chains, so more resident warps hide their latency.
+static constexpr int kResNP = 32;
 static constexpr int kResNPdf = 32;
 
 __global__ void __launch_bounds__(256) k_residual(Shape S, const NodeCoef *coefAll, long strideC,

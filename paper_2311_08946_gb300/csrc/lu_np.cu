@@ -10,8 +10,8 @@
 // and the caller then refactors that wave with partial pivoting; the FP64
 // refinement of a8 recovers the accuracy either way.
 //
-//   lu(k0, w):   w <= 64: factor the diagonal block D (one CTA per disk, shared
-//                memory) and store L_D^-1 and U_D^-1; L21 = A21 U_D^-1 (GEMM);
+//   lu(k0, w):   w <= 64: factor the diagonal block D (one CTA per disk, the
+//                block in registers) and store L_D^-1 and U_D^-1; L21 = A21 U_D^-1 (GEMM);
 //                else lu(k0, w1); U12 = L11^-1 A12 (trsm); A22 -= L21 U12
 //                (GEMM, K = w1); lu(k0 + w1, w - w1)
 //   trsm(r0, w): w <= 64: X = L_D^-1 X (GEMM); else trsm(r0, w1);
@@ -21,6 +21,7 @@
 // splits its FP32 operands as it stages them, the longer ones through operands
 // split once into tiles and streamed by bulk copies.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "handles.cuh"
@@ -33,57 +34,106 @@ static constexpr float kTinyPivot = 1e-5f;       // rows are equilibrated to max
 // Factor the w x w diagonal block at (k0, k0) without interchanges (in place) and store the
 // inverses of its unit-lower and upper factors: inv[disk][k0 / 64][0] = L_D^-1,
 // inv[disk][k0 / 64][1] = U_D^-1 (64 x 64 row-major, zero outside the w x w block).
+//
+// One sweep over the pivots k with one barrier per step; thread (ty, tx) keeps the 16
+// elements (ty + 8a, tx + 32c) in registers for the whole sweep.  An element (i, j) holds its
+// Schur-complement value until step min(i, j), then the accumulator of L^-1 (i > j: the
+// elimination applied to the identity) or of U^-1 (i < j: X U = I column by column, unscaled
+// by 1 / u_jj until the end).  Step k applies one rank-1 form  acc_ij -= m_i r_j  to
+//   rows > k (Schur complement for columns > k, L^-1 for columns <= k) and
+//   rows <= k, columns > k (U^-1),
+// with m_i = (column k of row i) / u_kk (1 / u_kk on row k) and r_j = row k (1 at column k).
+// Column k reaches the warp's rows by shuffles from the lane that holds it; row k + 1 is
+// published to a double-buffered shared row after step k.  The final factor entries go to a
+// shared tile as they become final (row k+1 of U after step k, multipliers of column k in
+// step k) and are written out with the inverses at the end.
 __global__ void __launch_bounds__(256) k_leaf_diag(float *Aall, int n, long sA, int k0, int w, float *invAll,
                                                    long sInv, int *info) {
-    __shared__ float D[kLeafW][kLeafW + 1];
-    __shared__ float Li[kLeafW][kLeafW + 1];
-    __shared__ float Ui[kLeafW][kLeafW + 1];
-    const int disk = blockIdx.x, tid = threadIdx.x;
+    __shared__ float Dout[kLeafW][kLeafW + 1];
+    __shared__ float R[2][kLeafW];
+    __shared__ float RD[kLeafW];
+    const int disk = blockIdx.x, tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     float *A = Aall + disk * sA;
-    for (int e = tid; e < kLeafW * kLeafW; e += 256) {
-        const int i = e / kLeafW, j = e - i * kLeafW;
-        D[i][j] = (i < w && j < w) ? A[(long)(k0 + i) * n + k0 + j] : (i == j ? 1.f : 0.f);
-        Li[i][j] = 0.f;
-        Ui[i][j] = 0.f;
+    float acc[8][2];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = ty + 8 * a, j = tx + 32 * c;
+            acc[a][c] = (i < w && j < w) ? A[(long)(k0 + i) * n + k0 + j] : (i == j ? 1.f : 0.f);
+        }
+    if (ty == 0) {
+        R[0][tx] = Dout[0][tx] = acc[0][0];
+        R[0][tx + 32] = Dout[0][tx + 32] = acc[0][1];
     }
     __syncthreads();
-    for (int k = 0; k < w; ++k) {
-        const float d = D[k][k];
-        if (tid == 0 && !(fabsf(d) >= kTinyPivot)) atomicCAS(info + disk, 0, k0 + k + 1);
-        const int m = w - k - 1;
-        if (tid < m) D[k + 1 + tid][k] = (d != 0.f) ? D[k + 1 + tid][k] / d : 0.f;
-        __syncthreads();
-        for (int e = tid; e < m * m; e += 256) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            D[i][j] = fmaf(-D[i][k], D[k][j], D[i][j]);
+    // step k; HI = (k >= 32) names the register that holds column k at compile time
+    auto step = [&](int k, auto hi_c) {
+        constexpr int HI = decltype(hi_c)::value;
+        const int b = k & 1, src = k & 31;
+        const float d = R[b][k];
+        const float rd = (d != 0.f) ? 1.f / d : 0.f;
+        if (tid == 0) {
+            RD[k] = rd;
+            if (!(fabsf(d) >= kTinyPivot)) atomicCAS(info + disk, 0, k0 + k + 1);
+        }
+        const float r0 = (tx == k) ? 1.f : R[b][tx];
+        const float r1 = (tx + 32 == k) ? 1.f : R[b][tx + 32];
+        const bool up0 = tx > k, up1 = tx + 32 > k;
+        float m[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) m[a] = __shfl_sync(0xffffffffu, acc[a][HI], src) * rd;
+        if (tx == src) {     // column k: multipliers out, then L^-1's column k restarts (1 on the diagonal)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int i = ty + 8 * a;
+                if (i > k) Dout[i][k] = m[a];
+                if (i >= k) acc[a][HI] = (i == k) ? 1.f : 0.f;
+            }
+        }
+        if (ty == (k & 7)) { // row k: U^-1's row k starts from 0 with multiplier 1 / u_kk
+            const int ak = k >> 3;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (a == ak) {
+                    m[a] = rd;
+                    if (up0) acc[a][0] = 0.f;
+                    if (up1) acc[a][1] = 0.f;
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const bool below = ty + 8 * a > k;
+            if (below || up0) acc[a][0] = fmaf(-m[a], r0, acc[a][0]);
+            if (below || up1) acc[a][1] = fmaf(-m[a], r1, acc[a][1]);
+        }
+        if (k + 1 < w && ty == ((k + 1) & 7)) {
+            const int ap = (k + 1) >> 3;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (a == ap) {
+                    R[b ^ 1][tx] = acc[a][0];
+                    R[b ^ 1][tx + 32] = acc[a][1];
+                    if (up0) Dout[k + 1][tx] = acc[a][0];
+                    if (up1) Dout[k + 1][tx + 32] = acc[a][1];
+                }
         }
         __syncthreads();
-    }
-    // column j of L^-1 (threads 0..63, rows top-down) and of U^-1 (threads 64..127, bottom-up); the
-    // loops run over the same rows in every thread so the factor reads are broadcasts
-    if (tid < kLeafW) {
-        const int j = tid;
-        for (int i = 0; i < w; ++i) {
-            float s = (i == j) ? 1.f : 0.f;
-            for (int l = 0; l < i; ++l) s = fmaf(-D[i][l], Li[l][j], s);
-            Li[i][j] = (j <= i) ? s : 0.f;
-        }
-    } else if (tid < 2 * kLeafW) {
-        const int j = tid - kLeafW;
-        for (int i = w - 1; i >= 0; --i) {
-            float s = (i == j) ? 1.f : 0.f;
-            for (int l = i + 1; l < w; ++l) s = fmaf(-D[i][l], Ui[l][j], s);
-            Ui[i][j] = (j >= i && D[i][i] != 0.f) ? s / D[i][i] : 0.f;
-        }
-    }
-    __syncthreads();
+    };
+    const int kh = w < 32 ? w : 32;
+    for (int k = 0; k < kh; ++k) step(k, std::integral_constant<int, 0>());
+    for (int k = 32; k < w; ++k) step(k, std::integral_constant<int, 1>());
     float *inv = invAll + disk * sInv + (long)(k0 / kLeafW) * 2 * kLeafW * kLeafW;
-    for (int e = tid; e < kLeafW * kLeafW; e += 256) {
-        const int i = e / kLeafW, j = e - i * kLeafW;
-        if (i < w && j < w) A[(long)(k0 + i) * n + k0 + j] = D[i][j];
-        inv[e] = Li[i][j];
-        inv[kLeafW * kLeafW + e] = Ui[i][j];
-    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = ty + 8 * a, j = tx + 32 * c;
+            const bool in = i < w && j < w;
+            if (in) A[(long)(k0 + i) * n + k0 + j] = Dout[i][j];
+            inv[i * kLeafW + j] = in ? (i > j ? acc[a][c] : (i == j ? 1.f : 0.f)) : 0.f;
+            inv[kLeafW * kLeafW + i * kLeafW + j] = (in && i <= j) ? acc[a][c] * RD[j] : 0.f;
+        }
 }
 
 struct NpLU {
