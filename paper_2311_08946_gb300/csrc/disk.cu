@@ -28,6 +28,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "handles.cuh"
@@ -135,37 +136,44 @@ __global__ void __launch_bounds__(256) k_node_coef(Problem P, Shape S, const Dis
     const double be = 0.5 / (R2 * rho) + (bx * ct + by * st) / dd.R;
     const double ga = 0.5 / (R2 * rho * rho);
     const double de = (-bx * st + by * ct) / (dd.R * rho);
-    double amax = 0.0;
+    // the row scale only equilibrates (any nearby value serves), so the candidates are evaluated
+    // on the FP32 pipes (FP64 runs at a small fraction of their rate here): same terms, same order
+    const float alf = (float)al, bef = (float)be, gaf = (float)ga, def = (float)de, cvf = (float)cv;
+    const float2 *Dk = S.Dhl + k * np, *D2k = S.D2hl + k * np;
+    float amax = 0.f;
     for (int l = 1; l <= S.nr; ++l) {
-        double v = al * S.D2[k * np + l] + be * S.D[k * np + l];
-        double vm = al * S.D2[k * np + S.nc - l] + be * S.D[k * np + S.nc - l];
+        float v = alf * D2k[l].x + bef * Dk[l].x;
+        float vm = alf * D2k[S.nc - l].x + bef * Dk[S.nc - l].x;
         if (l == k) {                              // the node's own ring crosses both lines
-            v += ga * S.F2[0] + de * S.F1[0] + cv;
-            vm += ga * S.F2[half] + de * S.F1[half];
+            v += gaf * S.F2hl[0].x + def * S.F1hl[0].x + cvf;
+            vm += gaf * S.F2hl[half].x + def * S.F1hl[half].x;
         }
-        amax = fmax(amax, fabs(v));
-        amax = fmax(amax, fabs(vm));
+        amax = fmaxf(amax, fabsf(v));
+        amax = fmaxf(amax, fabsf(vm));
     }
+    const int jm = j + half < S.nt ? j + half : j + half - S.nt;
     for (int jp = 0; jp < S.nt; ++jp) {
-        if (jp == j || jp == (j + half) % S.nt) continue;          // counted with the radial line
-        const int d = (j - jp + S.nt) % S.nt;
-        amax = fmax(amax, fabs(ga * S.F2[d] + de * S.F1[d]));
+        if (jp == j || jp == jm) continue;                          // counted with the radial line
+        const int d = jp <= j ? j - jp : j - jp + S.nt;
+        amax = fmaxf(amax, fabsf(gaf * S.F2hl[d].x + def * S.F1hl[d].x));
     }
-    const double sc = amax > 0.0 ? 1.0 / amax : 1.0;
+    const double sc = amax > 0.f ? 1.0 / (double)amax : 1.0;
     coef[disk * strideC + p] = NodeCoef{al, be, ga, de, cv, sc};
     const double w0 = al * S.D2[k * np + 0] + be * S.D[k * np + 0];
     const double wN = al * S.D2[k * np + S.nc] + be * S.D[k * np + S.nc];
     double *Rrow = RHS + disk * strideR + (long)p * S.nrhs;
     for (int col = 0; col < S.nk; ++col)
-        Rrow[col] = sc * (w0 * S.Hg[j * S.nk + col] + wN * S.Hg[((j + half) % S.nt) * S.nk + col]);
+        Rrow[col] = sc * (w0 * S.Hg[j * S.nk + col] + wN * S.Hg[jm * S.nk + col]);
     Rrow[S.nk] = -sc * fv;
 }
 
 // rows of the equilibrated collocation matrix, one warp per row: the row is
 // zeroed in shared memory, its nonzeros (the node's radial line, the mirrored
 // line and the node's ring: 2 nr + nt candidates, the crossings computed twice
-// with the same value) are evaluated in FP64, and the row is stored with
-// 16-byte writes
+// with the same value) are evaluated in the matrix's precision (the FP32 rows
+// of the mixed form feed only the LU that preconditions the refinement, whose
+// residuals use the FP64 coefficients), and the row is stored with 16-byte
+// writes
 template <typename T>
 __global__ void __launch_bounds__(256) k_fill_operator(Shape S, T *A, long strideA, const NodeCoef *coef,
                                                        long strideC, int rows_per_block) {
@@ -188,33 +196,67 @@ __global__ void __launch_bounds__(256) k_fill_operator(Shape S, T *A, long strid
     // the candidates are the radial line through node p, its mirror through the centre and the ring
     // of p; each entry sums the operator's terms that reach it (radial, mirror, ring, diagonal, in
     // that order), the candidate's line and angle known without index division
-    for (int c = lane; c < ncand; c += 32) {
-        int q;
-        double v = 0.0;
-        if (c < S.nr) {                                      // radial line: l = c + 1, angle j
-            const int l = c + 1;
-            q = c * S.nt + j;
-            v += cf.alpha * S.D2[k * np + l] + cf.beta * S.D[k * np + l];
-            if (l == k) {
-                v += cf.gamma * S.F2[0] + cf.delta * S.F1[0];
-                v += cf.c;                                   // q == p
+    if constexpr (std::is_same<T, float>::value) {
+        const float al = (float)cf.alpha, be = (float)cf.beta, ga = (float)cf.gamma, de = (float)cf.delta;
+        const float cv = (float)cf.c, sc = (float)cf.s;
+        const float2 *Dk = S.Dhl + k * np, *D2k = S.D2hl + k * np;
+        for (int c = lane; c < ncand; c += 32) {
+            int q;
+            float v = 0.f;
+            if (c < S.nr) {
+                const int l = c + 1;
+                q = c * S.nt + j;
+                v += al * D2k[l].x + be * Dk[l].x;
+                if (l == k) {
+                    v += ga * S.F2hl[0].x + de * S.F1hl[0].x;
+                    v += cv;
+                }
+            } else if (c < 2 * S.nr) {
+                const int l = c - S.nr + 1;
+                q = (l - 1) * S.nt + jm;
+                v += al * D2k[S.nc - l].x + be * Dk[S.nc - l].x;
+                if (l == k) v += ga * S.F2hl[half].x + de * S.F1hl[half].x;
+            } else {
+                const int jp = c - 2 * S.nr;
+                q = (k - 1) * S.nt + jp;
+                if (jp == j) v += al * D2k[k].x + be * Dk[k].x;
+                if (jp == jm) v += al * D2k[S.nc - k].x + be * Dk[S.nc - k].x;
+                int d = j - jp;
+                d += d < 0 ? S.nt : 0;
+                v += ga * S.F2hl[d].x + de * S.F1hl[d].x;
+                if (jp == j) v += cv;
             }
-        } else if (c < 2 * S.nr) {                           // mirror line: angle jm
-            const int l = c - S.nr + 1;
-            q = (l - 1) * S.nt + jm;
-            v += cf.alpha * S.D2[k * np + S.nc - l] + cf.beta * S.D[k * np + S.nc - l];
-            if (l == k) v += cf.gamma * S.F2[half] + cf.delta * S.F1[half];
-        } else {                                             // ring of p: l = k, angle jp
-            const int jp = c - 2 * S.nr;
-            q = (k - 1) * S.nt + jp;
-            if (jp == j) v += cf.alpha * S.D2[k * np + k] + cf.beta * S.D[k * np + k];
-            if (jp == jm) v += cf.alpha * S.D2[k * np + S.nc - k] + cf.beta * S.D[k * np + S.nc - k];
-            int d = j - jp;
-            d += d < 0 ? S.nt : 0;
-            v += cf.gamma * S.F2[d] + cf.delta * S.F1[d];
-            if (jp == j) v += cf.c;                          // q == p
+            row[q] = sc * v;
         }
-        row[q] = (T)(cf.s * v);
+    } else {
+        for (int c = lane; c < ncand; c += 32) {
+            int q;
+            double v = 0.0;
+            if (c < S.nr) {                                      // radial line: l = c + 1, angle j
+                const int l = c + 1;
+                q = c * S.nt + j;
+                v += cf.alpha * S.D2[k * np + l] + cf.beta * S.D[k * np + l];
+                if (l == k) {
+                    v += cf.gamma * S.F2[0] + cf.delta * S.F1[0];
+                    v += cf.c;                                   // q == p
+                }
+            } else if (c < 2 * S.nr) {                           // mirror line: angle jm
+                const int l = c - S.nr + 1;
+                q = (l - 1) * S.nt + jm;
+                v += cf.alpha * S.D2[k * np + S.nc - l] + cf.beta * S.D[k * np + S.nc - l];
+                if (l == k) v += cf.gamma * S.F2[half] + cf.delta * S.F1[half];
+            } else {                                             // ring of p: l = k, angle jp
+                const int jp = c - 2 * S.nr;
+                q = (k - 1) * S.nt + jp;
+                if (jp == j) v += cf.alpha * S.D2[k * np + k] + cf.beta * S.D[k * np + k];
+                if (jp == jm) v += cf.alpha * S.D2[k * np + S.nc - k] + cf.beta * S.D[k * np + S.nc - k];
+                int d = j - jp;
+                d += d < 0 ? S.nt : 0;
+                v += cf.gamma * S.F2[d] + cf.delta * S.F1[d];
+                if (jp == j) v += cf.c;                          // q == p
+            }
+            row[q] = (T)(cf.s * v);
+        }
     }
     __syncwarp();
     T *Arow = A + disk * strideA + (long)p * S.n;
