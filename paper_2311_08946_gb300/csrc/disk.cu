@@ -1532,6 +1532,24 @@ static DiskStats run_group(const pdd_cover &cov, const Problem &P, const pdd_ass
     int wave = (int)std::max<size_t>(1, budget / perDisk);
     wave = std::min<int>(wave, (int)disks.size());
     if ((size_t)wave * perDisk > freeb) fail(PDD_ENOMEM, "not enough device memory for one disk");
+    {
+        // equal waves, as many as fill the SMs in the fewest rounds: the kernels that take one CTA
+        // per disk (the triangular solves, one per SM; the leaf blocks, four) otherwise leave the
+        // last round of every wave part empty.  From the fewest waves memory allows to two more.
+        int dev = 0, sms = 0;
+        PDD_CUDA(cudaGetDevice(&dev));
+        PDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long total = (long)disks.size(), nw0 = (total + wave - 1) / wave;
+        long best = wave, best_rounds = -1;
+        for (long nw = nw0; nw <= std::min(nw0 + 2, total); ++nw) {
+            const long w = (total + nw - 1) / nw, rounds = nw * ((w + sms - 1) / sms);
+            if (best_rounds < 0 || rounds < best_rounds) {
+                best_rounds = rounds;
+                best = w;
+            }
+        }
+        wave = (int)best;
+    }
     DevBuf<T> A, W;
     DevBuf<double> RHS, X, Rr;
     DevBuf<NodeCoef> coef;
