@@ -274,7 +274,7 @@ def run_ours(args, rank, world):
            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 pivot-free LU on tcgen05 with split-TF32 "
                       "products + FP64 refinement; FP32 path positions, FP64 weights and scores)",
                       "solve": f"FP64 GMRES(64), rtol 1e-13, precond {args.precond}", "knots": N,
-                      "l2": "flushed between steps (512 MB write); working set 100+ GB",
+                      "l2": "flushed between steps (512 MB write); wave buffers about 58 GB, 270+ GB touched per step",
                       "parallelism": f"replicas x{world}"},
            "mc_path_steps_per_s": world * mc_rate, "path_steps_per_step": path_steps,
            "stages_ms": {k: st[k] for k in ("ms_cover_rows", "ms_disks", "ms_operator", "ms_factor",
